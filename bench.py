@@ -1,0 +1,369 @@
+"""Benchmark of the angle-dependent CT operator path on GB300.
+
+One step = one pass of the whole operator path over one batch of the
+256 x 256 / 180-view / 363-bin workload (random-ellipse phantom, 1-degree
+angle errors):
+    Y  = H(theta) X      for a Krylov block of K = 8 images
+    X' = H(theta)^T Y'   for a block of K = 8 sinograms
+    dy = J_theta dtheta  for one image
+    g  = J_theta^T r     for one image and one residual
+The metric is sinogram samples produced or consumed per second (GSamples/s),
+counted as V*B*(K + K + 1 + 1) per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank runs its own
+replica of the workload (the operators shard by views without any exchange;
+this build runs replicas only) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "A/Aᵀ/Jθ GSamples/s + NL-RMM-GKS iter time vs FP64 GPU form at equal error"
+WORKLOAD = "C2"
+KBLOCK = 8
+L2_FLUSH_BYTES = 512 * 1024 * 1024
+LSU_BYTES_PER_CLK_SM = 128          # L1/shared data path per SM per clock
+NUM_SMS = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def interp_steps_per_image(w):
+    """Algorithmic work: number of (ray, sample) pairs with -1 < q < N (exact, FP64)."""
+    N, B = w.N, w.B
+    th = w.theta_true
+    c, s = np.cos(th), np.sin(th)
+    h = 0.5 * (N - 1)
+    sb = np.arange(B)[None, :] - 0.5 * (B - 1)
+    rows = np.abs(c) >= np.abs(s)
+    r = np.arange(N)[:, None, None]
+    total = 0
+    for sel, cc, ss in ((rows, c, s), (~rows, c, s)):
+        if not sel.any():
+            continue
+        cv, sv = cc[sel][None, :, None], ss[sel][None, :, None]
+        if sel is rows:
+            q = (sb[None] - (h - r) * sv) / cv + h
+        else:
+            q = h - (sb[None] - (r - h) * cv) / sv
+        total += int(np.count_nonzero((q > -1) & (q < N)))
+    return total
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clk_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on the host cores, bounded sample of the same step."""
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    from paper_2605_06336_gb300 import synth
+    w = synth.make_workload(WORKLOAD)
+    g = oracle.Geometry(w.N, w.B, w.V)
+    rng = np.random.default_rng(1)
+    X = np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(KBLOCK - 1, w.N * w.N))])
+    Ys = oracle.forward(g, w.theta_true, X[:1])
+    dth = rng.standard_normal(w.V)
+    # a bounded sample: the step restricted to one image / one sinogram per operator
+    def step():
+        oracle.forward(g, w.theta_true, X[0])
+        oracle.adjoint(g, w.theta_true, Ys[0])
+        oracle.jac(g, w.theta_true, X[0], dth)
+        oracle.jacT(g, w.theta_true, X[0], Ys[0])
+    for _ in range(min(args.warmup, 1)):
+        step()
+    t0 = time.perf_counter()
+    n = 0
+    while n < args.steps and (time.perf_counter() - t0) < args.cpu_seconds:
+        step()
+        n += 1
+    dt = time.perf_counter() - t0
+    samples = w.V * w.B * 4 * n
+    val = samples / dt / 1e9
+    line = {"metric": METRIC, "value": val, "unit": "GSamples/s", "n_gpus": args.gpus, "steps": n,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(n, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "C2: 256x256 random-ellipse phantom, 180 views, 363 bins",
+                       "sample": "one image per operator (H, H^T, J, J^T) per step", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": "GSamples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} steps of H, H^T, J, J^T on one 256^2 image, 180x363 sinogram"},
+            "e2e": {"value": val, "unit": "GSamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, seconds):
+    import oracle
+    g = oracle.Geometry(w.N, w.B, w.V)
+    x = w.images.reshape(-1)
+    y = oracle.forward(g, w.theta_true, x)
+    dth = np.ones(w.V)
+    t0 = time.perf_counter()
+    n = 0
+    while n == 0 or (time.perf_counter() - t0) < seconds:
+        oracle.forward(g, w.theta_true, x)
+        oracle.adjoint(g, w.theta_true, y)
+        oracle.jac(g, w.theta_true, x, dth)
+        oracle.jacT(g, w.theta_true, x, y)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": w.V * w.B * 4 * n / dt / 1e9, "unit": "GSamples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} passes of H, H^T, J, J^T on one 256^2 image (not the 8-image block), FP64, "
+                      f"single thread, {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2605_06336_gb300 import ct, synth
+    ct.load_library()  # fails loudly if the CUDA library is missing
+
+    w = synth.make_workload(WORKLOAD)
+    N, B, V, K = w.N, w.B, w.V, KBLOCK
+    rng = np.random.default_rng(100 + rank)
+    Xh = np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(K - 1, N * N))]).astype(np.float32)
+    Ysh = rng.standard_normal((K, V * B)).astype(np.float32)
+    dth_h = rng.standard_normal(V)
+    op = ct.CTOperator(N, B, V, max_batch=K, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    theta = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
+    X = torch.tensor(Xh, device=dev)
+    Ys = torch.tensor(Ysh, device=dev)
+    dth = torch.tensor(dth_h, dtype=torch.float64, device=dev)
+    Y = torch.empty(K, V * B, device=dev)
+    Xa = torch.empty(K, N * N, device=dev)
+    dy = torch.empty(V * B, device=dev)
+    gt = torch.empty(V, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        ct.ct_forward(op.h, theta, None, X, Y, K)
+        if ev: ev[1].record(stream)
+        ct.ct_adjoint(op.h, theta, None, Ys, Xa, K)
+        if ev: ev[2].record(stream)
+        ct.ct_jac(op.h, theta, None, X[0], dth, None, dy)
+        if ev: ev[3].record(stream)
+        ct.ct_jacT(op.h, theta, None, X[0], Y[0], gt, None)
+        if ev: ev[4].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if op.status() != ct.CT_OK:
+        raise RuntimeError("device status not OK after warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clk = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()              # evict L2 between timed steps (outside the events)
+        step(evs[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    per_op = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)])
+    step_ms = per_op.sum(axis=1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    samples_per_step = V * B * (K + K + 1 + 1)
+    value = world * samples_per_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Xp = torch.tensor(Xh).pin_memory()
+    Ysp = torch.tensor(Ysh).pin_memory()
+    thp = torch.tensor(w.theta_true, dtype=torch.float64).pin_memory()
+    dthp = torch.tensor(dth_h, dtype=torch.float64).pin_memory()
+    Yp = torch.empty(K, V * B).pin_memory()
+    Xap = torch.empty(K, N * N).pin_memory()
+    dyp = torch.empty(V * B).pin_memory()
+    gtp = torch.empty(V, dtype=torch.float64).pin_memory()
+    h2d = Xp.numel() * 4 + Ysp.numel() * 4 + thp.numel() * 8 + dthp.numel() * 8
+    d2h = Yp.numel() * 4 + Xap.numel() * 4 + dyp.numel() * 4 + gtp.numel() * 8
+
+    def e2e_step():
+        theta.copy_(thp, non_blocking=True)
+        X.copy_(Xp, non_blocking=True)
+        Ys.copy_(Ysp, non_blocking=True)
+        dth.copy_(dthp, non_blocking=True)
+        step()
+        Yp.copy_(Y, non_blocking=True)
+        Xap.copy_(Xa, non_blocking=True)
+        dyp.copy_(dy, non_blocking=True)
+        gtp.copy_(gt, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * samples_per_step * args.steps / (e2e_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant operator call
+    steps_img = interp_steps_per_image(w)
+    op_names = ["forward_K8", "adjoint_K8", "jac", "jacT"]
+    mean_ms = per_op.mean(axis=0)
+    dom = int(np.argmax(mean_ms))
+    units = {0: K * steps_img, 1: K * steps_img, 2: steps_img, 3: steps_img}
+    gather_bytes = 8.0 * units[dom]          # two FP32 pixels (or bins) per interpolation
+    achieved = gather_bytes / (mean_ms[dom] * 1e-3) / 1e9
+    sm_mhz = SM_MAX_MHZ_NOMINAL
+    peak = NUM_SMS * LSU_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+    peaks, src = measured_peaks()
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GSamples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "C2: 256x256 random-ellipse phantom, 180 views (1 deg angle errors), 363 bins; "
+                               "step = H on 8 images + H^T on 8 sinograms + J dtheta + J^T r",
+                   "krylov_block": K, "samples_per_step": samples_per_step,
+                   "l2": "flushed between timed steps (512 MB write, outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "per_op_ms": dict(zip(op_names, [float(x) for x in mean_ms])),
+        "roofline": {"bound": "alu", "kernel": op_names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "basis": "8 B of gathered FP32 operands per interpolation step x steps per launch; peak = "
+                              f"{NUM_SMS} SMs x {LSU_BYTES_PER_CLK_SM} B/clk L1 data path x {sm_mhz:.0f} MHz",
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": "derived (unit counts x nominal max clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 12 * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * ctgb -- angle-dependent parallel-beam CT operators (GB300 / sm_103a).
+ *
+ * C ABI of the hot path of NL-RMM-GKS (nonlinear recycled MM-GKS with
+ * uncertain forward operators).  The forward model is H(p)u + e = b
+ * (Eq. (1.1)); the joint problem is min_{u,p} 1/2 ||H(p)u - b||^2 +
+ * lambda ||Psi u||_1 (Eq. (1.2), Eq. (4.1)).  Here H(p) is the Radon
+ * transform at perturbed view angles (Sec. 6.2), discretised with the
+ * Joseph rule, and p holds one angle theta_v per view (plus, optionally,
+ * one detector offset delta_v per view).
+ *
+ * Geometry (unit pixels, unit bins):
+ *   image   N x N, row-major X[i*N + j], pixel centre x_j = j - (N-1)/2,
+ *           y_i = (N-1)/2 - i
+ *   bins    B, bin centre s_b = b - (B-1)/2 + delta_v
+ *   ray     x cos(theta_v) + y sin(theta_v) = s_b
+ *   Joseph  |cos| >= |sin|: one linear interpolation per image row at
+ *           x = (s_b - y_i sin)/cos, weight 1/|cos|; otherwise one per
+ *           column at y = (s_b - x_j cos)/sin, weight 1/|sin|; pixels outside
+ *           the image are zero.
+ *
+ * Frames (block-diagonal operator of the dynamic problem, Sec. 7): the flat
+ * view list is split into consecutive frames, views_per_frame[f] views for
+ * frame f; views of frame f see image f.  An "image" argument is therefore
+ * n_frames * N * N elements and a "sinogram" n_views * B elements.  A batch
+ * of K images / sinograms is K such blocks back to back (the Krylov block
+ * H V of Sec. 3.2, stored column by column).
+ *
+ * Conventions for every call below:
+ *   * All array arguments are DEVICE pointers owned by the caller, on the
+ *     device that was current at ct_init.  Element type of images and
+ *     sinograms is float (precision 0) or double (precision 1); angle,
+ *     offset and gradient arrays are always double.
+ *   * Calls are asynchronous on the stream given to ct_init; they never
+ *     synchronise.  A handle is bound to that stream and is not thread safe.
+ *   * Outputs are overwritten, never accumulated into.
+ *   * Return value: CT_OK (0) or a negative CT_ERR_* code; on error nothing
+ *     has been launched.  ct_status() synchronises and reports device-side
+ *     conditions (non-finite angles) found by earlier calls.
+ */
+#ifndef CTGB_H
+#define CTGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CT_OK = 0,
+    CT_ERR_ARG = -1,      /* null pointer, bad size or batch out of range */
+    CT_ERR_CUDA = -2,     /* a CUDA runtime call failed (see ct_last_cuda_error) */
+    CT_ERR_OOM = -3,      /* device allocation failed in ct_init / the solver */
+    CT_ERR_TIMEOUT = -4,  /* a bounded device-side wait ran out */
+    CT_ERR_NAN = -5,      /* non-finite angle / offset or solver breakdown */
+    CT_ERR_NOCONV = -6    /* solver hit its iteration limit; outputs are valid */
+};
+
+typedef struct {
+    int32_t N;                        /* image side, 2 <= N <= 8192 */
+    int32_t B;                        /* detector bins, 1 <= B */
+    int32_t n_views;                  /* total views over all frames */
+    int32_t n_frames;                 /* >= 1 */
+    const int32_t *views_per_frame;   /* HOST array of n_frames counts, or NULL for one frame */
+    int32_t max_batch;                /* largest batch any call will pass, >= 1 */
+    int32_t use_offsets;              /* reserved: offsets are accepted whenever delta != NULL */
+    int32_t precision;                /* 0 = float32 images/sinograms, 1 = float64 */
+} ct_geom;
+
+typedef struct ct_handle ct_handle;
+
+/*
+ * Create a handle: copies the geometry, allocates the workspaces it needs
+ * (per-view tables, a transposed-image buffer of max_batch images, reduction
+ * partials) on the current device and binds it to cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream).  *out receives the handle.
+ */
+int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out);
+
+/* Release every workspace of the handle (synchronises its stream first). */
+void ct_destroy(ct_handle *h);
+
+/*
+ * Y = H(theta, delta) X for a batch of `batch` images (forward projection
+ * "H u" of every MM-GKS step, Eq. (3.3), Alg. "Enlarge").
+ *   theta  [n_views] radians; delta [n_views] bins or NULL (zero offsets)
+ *   X      [batch][n_frames][N][N]      Y [batch][n_views][B]
+ */
+int ct_forward(ct_handle *h, const double *theta, const double *delta,
+               const void *X, void *Y, int batch);
+
+/*
+ * X = H(theta, delta)^T Y, the exact transpose of ct_forward in gather form
+ * (one thread per pixel, no atomics); used in the residual
+ * H^T (H u - b) + lambda Psi^T P^2 Psi u of every MM-GKS step (Eq. (3.5)).
+ *   Y [batch][n_views][B]  ->  X [batch][n_frames][N][N]
+ */
+int ct_adjoint(ct_handle *h, const double *theta, const double *delta,
+               const void *Y, void *X, int batch);
+
+/*
+ * Angle (and offset) Jacobian-vector product of the forward projection at a
+ * fixed image x: dy[v,b] = dtheta_v d(Hx)[v,b]/dtheta_v
+ *                        + ddelta_v d(Hx)[v,b]/ddelta_v
+ * (the columns H_{p_i} u of Alg. "UPDATE-PARAM").  The derivative of the
+ * linear interpolation uses the slope of the cell floor(u) (right derivative
+ * at integer u).
+ *   x [n_frames][N][N], dtheta [n_views] (device, double),
+ *   ddelta [n_views] or NULL, dy [n_views][B]
+ */
+int ct_jac(ct_handle *h, const double *theta, const double *delta,
+           const void *x, const double *dtheta, const double *ddelta,
+           void *dy);
+
+/*
+ * Transposed Jacobian: gtheta[v] = sum_b r[v,b] d(Hx)[v,b]/dtheta_v and
+ * gdelta[v] = sum_b r[v,b] d(Hx)[v,b]/ddelta_v (gradient of the data term
+ * with respect to p, (H_{p_i} u)^T (H u - b), appendix lemma on the
+ * Lipschitz gradient).  Per-view sums are reduced in a fixed order (no
+ * atomics): results are bitwise reproducible.
+ *   x [n_frames][N][N], r [n_views][B], gtheta [n_views] (device double),
+ *   gdelta [n_views] or NULL
+ */
+int ct_jacT(ct_handle *h, const double *theta, const double *delta,
+            const void *x, const void *r, double *gtheta, double *gdelta);
+
+/*
+ * Fused per-view Gauss-Newton terms at image x and data b, one ray march:
+ *   res[v,b]  = (H x)[v,b] - bdata[v,b]          (may be NULL: not stored)
+ *   grad[v]   = sum_b res[v,b] d(Hx)[v,b]/dtheta_v
+ *   jnorm2[v] = sum_b (d(Hx)[v,b]/dtheta_v)^2
+ *   fval[v]   = 1/2 sum_b res[v,b]^2
+ * With per-view angles the Gauss-Newton matrix J^T J of Alg. "UPDATE-PARAM"
+ * is diagonal, so these four arrays are all the parameter update needs.
+ * grad, jnorm2, fval: [n_views] device double (fval may be NULL).
+ */
+int ct_gn_terms(ct_handle *h, const double *theta, const double *delta,
+                const void *x, const void *bdata, void *res, double *grad,
+                double *jnorm2, double *fval);
+
+/*
+ * Synchronise the handle's stream and report device-side conditions found
+ * since the last ct_status: CT_ERR_NAN if a non-finite angle or offset was
+ * passed, CT_ERR_CUDA on an asynchronous CUDA error, else CT_OK.
+ */
+int ct_status(ct_handle *h);
+
+/* Static description of an error code. */
+const char *ct_strerror(int code);
+
+/* Text of the last CUDA runtime error seen by this library (thread-local). */
+const char *ct_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTGB_H */

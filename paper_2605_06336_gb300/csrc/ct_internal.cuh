@@ -1,0 +1,95 @@
+// Internal declarations shared by the CUDA translation units of libctgb.
+//
+// Coordinates.  Every ray is marched in "march coordinates": for a view
+// that samples once per image row (|cos| >= |sin|) the march index r is the
+// row i and the in-row coordinate q is the column position u = x + (N-1)/2;
+// for a view that samples once per column r is the column j and q is the row
+// position t = (N-1)/2 - y, read from the transposed image.  In both cases
+//     q(b, r) = h + s_b * qb + (r - h) * qr,   h = (N-1)/2,
+// with s_b = b + n0 + phi (n0 integer, 0 <= phi < 1) the bin centre.  The
+// kernels carry q in 64-bit fixed point with 48 fractional bits (kFracBits):
+//     Q = Qc + (b + n0) * Qb + (2r - (N-1)) * Qh,
+// Qc = h + phi*qb, Qb = qb, Qh = qr/2, each rounded once.  The cell floor(q)
+// and the interpolation fraction come from integer shifts, so the cell
+// choice agrees with an FP64 evaluation except within ~1e-11 pixels of a cell
+// boundary, and exact coincidences at the image centre (the central ray of an
+// odd-sized image meets the centre pixel exactly) stay exact.  That matters
+// for the angle derivative, whose interpolation slope jumps at every cell
+// boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace ctgb {
+
+constexpr int kFracBits = 48;
+constexpr double kFixScale = 281474976710656.0;        // 2^48
+constexpr double kFixInv = 1.0 / 281474976710656.0;    // 2^-48
+constexpr int kMaxN = 4096;                            // keeps |q| * 2^48 inside int64
+constexpr int kChunk = 32;                             // bins per warp work item
+constexpr int kTile = 16;                              // adjoint pixel tile side
+
+enum ViewFlags : int { kAllRows = 1 };
+
+// Per-view constants, rebuilt on the device from (theta, delta) by every
+// call (angles change between Gauss-Newton steps).
+struct __align__(16) ViewGeo {
+    long long Qc, Qb, Qh;   // h + phi*qb, qb, qr/2 in fixed point
+    double alo, ahi, gam;   // rows with -1 < q < N lie between alo + b*gam and ahi + b*gam
+    double beta0, c, s;     // pixel-driven transpose: bin coordinate of pixel (i,j) = beta0 + j*c - i*s
+    double sb0d;            // s_b = sb0d + b (FP64 form)
+    float w;                // 1/|cos| or 1/|sin|
+    float dw;               // d w / d theta
+    float gs, gh, gr;       // dq/dtheta (b, r) = (s_b*gs + gh) + r*gr
+    float qbf;              // dq/ddelta = qb
+    float sb0;              // s_b = sb0 + b
+    int mode;               // 0: rows of X, 1: rows of X^T
+    int frame;
+    int flags;
+    int n0;                 // integer part of the bin-centre offset -(B-1)/2 + delta
+};
+
+struct Handle {
+    int N = 0, B = 0, V = 0, F = 1, max_batch = 1, precision = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int> views_per_frame;
+    ViewGeo *d_views = nullptr;
+    int *d_fov = nullptr;       // frame of each view
+    int *d_fstart = nullptr;    // first view of each frame
+    int *d_fcount = nullptr;    // views of each frame
+    int *d_flag = nullptr;      // device-side status bits
+    void *d_xt = nullptr;       // transposed images, max_batch * F * N * N elements
+    double *d_partial = nullptr;  // per (view, chunk) reduction partials, 4 per item
+    int nchunks = 0;              // ceil(B / kChunk)
+    int num_sms = 0;
+};
+
+// Kernel launchers (implemented in ct_kernels.cu).  All launch on h.stream.
+cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta);
+
+template <typename T>
+cudaError_t launch_transpose(const Handle &h, const T *X, T *XT, int nimg);
+
+template <typename T>
+cudaError_t launch_forward(const Handle &h, const T *X, const T *XT, T *Y, int batch);
+
+template <typename T>
+cudaError_t launch_adjoint(const Handle &h, const T *Y, T *X, int batch);
+
+template <typename T>
+cudaError_t launch_jvp(const Handle &h, const T *X, const T *XT, const double *dtheta,
+                       const double *ddelta, T *dY);
+
+// mode 0: J^T r (theta and, if gdelta != null, delta); mode 1: Gauss-Newton terms.
+template <typename T>
+cudaError_t launch_vjp(const Handle &h, const T *X, const T *XT, const T *R, double *gtheta,
+                       double *gdelta);
+
+template <typename T>
+cudaError_t launch_gn(const Handle &h, const T *X, const T *XT, const T *bdata, T *res,
+                      double *grad, double *jnorm2, double *fval);
+
+}  // namespace ctgb

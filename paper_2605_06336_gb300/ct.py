@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libctgb.so (the C ABI in include/ctgb.h).
+
+Functions carry the C names (``ct_init``, ``ct_forward``, ``ct_adjoint``,
+``ct_jac``, ``ct_jacT``, ``ct_gn_terms``, ``ct_status``, ``ct_destroy``) and
+only marshal arguments: tensors become device pointers, the current torch
+stream becomes the handle's stream.  Every operator runs in the library's
+CUDA kernels.  If the library is missing or no GPU is present the calls
+raise; there is no fallback path.
+
+:class:`CTOperator` bundles a handle with shape checks for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctgb.so")
+
+CT_OK = 0
+CT_ERR_ARG = -1
+CT_ERR_CUDA = -2
+CT_ERR_OOM = -3
+CT_ERR_TIMEOUT = -4
+CT_ERR_NAN = -5
+CT_ERR_NOCONV = -6
+
+
+class CTError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        lib = _lib_or_none()
+        msg = lib.ct_strerror(code).decode() if lib else str(code)
+        if code == CT_ERR_CUDA and lib:
+            msg += " (" + lib.ct_last_cuda_error().decode() + ")"
+        super().__init__(f"{what}: {msg}")
+        self.code = code
+
+
+class ct_geom(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32),
+        ("B", ctypes.c_int32),
+        ("n_views", ctypes.c_int32),
+        ("n_frames", ctypes.c_int32),
+        ("views_per_frame", ctypes.POINTER(ctypes.c_int32)),
+        ("max_batch", ctypes.c_int32),
+        ("use_offsets", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def load_library(path: str | None = None):
+    """Open libctgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2605_06336_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.ct_init.argtypes = [ctypes.POINTER(ct_geom), P, ctypes.POINTER(P)]
+    lib.ct_destroy.argtypes = [P]
+    lib.ct_destroy.restype = None
+    lib.ct_forward.argtypes = [P, P, P, P, P, I]
+    lib.ct_adjoint.argtypes = [P, P, P, P, P, I]
+    lib.ct_jac.argtypes = [P, P, P, P, P, P, P]
+    lib.ct_jacT.argtypes = [P, P, P, P, P, P, P]
+    lib.ct_gn_terms.argtypes = [P, P, P, P, P, P, P, P, P]
+    lib.ct_status.argtypes = [P]
+    lib.ct_strerror.argtypes = [I]
+    lib.ct_strerror.restype = ctypes.c_char_p
+    lib.ct_last_cuda_error.argtypes = []
+    lib.ct_last_cuda_error.restype = ctypes.c_char_p
+    for f in ("ct_init", "ct_forward", "ct_adjoint", "ct_jac", "ct_jacT", "ct_gn_terms", "ct_status"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != CT_OK:
+        raise CTError(rc, what)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# --- C-named entry points (argument marshalling only) ----------------------
+
+def ct_init(N, B, n_views, views_per_frame=None, max_batch=1, precision=0, stream=None):
+    lib = load_library()
+    g = ct_geom()
+    g.N, g.B, g.n_views = int(N), int(B), int(n_views)
+    keep = None
+    if views_per_frame is not None:
+        keep = (ctypes.c_int32 * len(views_per_frame))(*[int(v) for v in views_per_frame])
+        g.n_frames = len(views_per_frame)
+        g.views_per_frame = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int32))
+    else:
+        g.n_frames = 1
+        g.views_per_frame = None
+    g.max_batch, g.use_offsets, g.precision = int(max_batch), 1, int(precision)
+    h = ctypes.c_void_p()
+    _check(lib.ct_init(ctypes.byref(g), _stream_ptr(stream), ctypes.byref(h)), "ct_init")
+    return h
+
+
+def ct_destroy(h):
+    load_library().ct_destroy(h)
+
+
+def ct_forward(h, theta, delta, X, Y, batch):
+    _check(load_library().ct_forward(h, _p(theta), _p(delta), _p(X), _p(Y), int(batch)), "ct_forward")
+
+
+def ct_adjoint(h, theta, delta, Y, X, batch):
+    _check(load_library().ct_adjoint(h, _p(theta), _p(delta), _p(Y), _p(X), int(batch)), "ct_adjoint")
+
+
+def ct_jac(h, theta, delta, x, dtheta, ddelta, dy):
+    _check(load_library().ct_jac(h, _p(theta), _p(delta), _p(x), _p(dtheta), _p(ddelta), _p(dy)), "ct_jac")
+
+
+def ct_jacT(h, theta, delta, x, r, gtheta, gdelta):
+    _check(load_library().ct_jacT(h, _p(theta), _p(delta), _p(x), _p(r), _p(gtheta), _p(gdelta)), "ct_jacT")
+
+
+def ct_gn_terms(h, theta, delta, x, bdata, res, grad, jnorm2, fval):
+    _check(load_library().ct_gn_terms(h, _p(theta), _p(delta), _p(x), _p(bdata), _p(res), _p(grad), _p(jnorm2),
+                                      _p(fval)), "ct_gn_terms")
+
+
+def ct_status(h):
+    return load_library().ct_status(h)
+
+
+# --- tensor-level wrapper ---------------------------------------------------
+
+class CTOperator:
+    """A ct handle plus shape/dtype checks for CUDA tensors.
+
+    Images are ``(K, F*N*N)`` (or ``(F*N*N,)``), sinograms ``(K, V*B)``;
+    angles/offsets are float64 CUDA tensors of length V.
+    """
+
+    def __init__(self, N, B, n_views, views_per_frame=None, max_batch=8, dtype=torch.float32, device="cuda"):
+        if dtype not in (torch.float32, torch.float64):
+            raise ValueError("dtype must be float32 or float64")
+        self.N, self.B, self.V = int(N), int(B), int(n_views)
+        self.views_per_frame = list(views_per_frame) if views_per_frame is not None else [self.V]
+        self.F = len(self.views_per_frame)
+        self.max_batch = int(max_batch)
+        self.dtype = dtype
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.h = ct_init(N, B, n_views, views_per_frame, max_batch, 1 if dtype == torch.float64 else 0)
+
+    @property
+    def n(self):
+        return self.F * self.N * self.N
+
+    @property
+    def m(self):
+        return self.V * self.B
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            ct_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, t, last, name):
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.shape[-1] == last):
+            raise ValueError(f"{name}: expected contiguous {self.dtype} CUDA tensor with last dim {last}, "
+                             f"got {tuple(t.shape)} {t.dtype} {t.device}")
+
+    def _ang(self, a, name):
+        if a is None:
+            return None
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == self.V):
+            raise ValueError(f"{name}: expected contiguous float64 CUDA tensor of {self.V} views")
+        return a
+
+    def forward(self, X, theta, delta=None, out=None):
+        self._chk(X, self.n, "X")
+        K = 1 if X.dim() == 1 else X.shape[0]
+        Y = out if out is not None else torch.empty(X.shape[:-1] + (self.m,), dtype=self.dtype, device=X.device)
+        ct_forward(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), X, Y, K)
+        return Y
+
+    def adjoint(self, Y, theta, delta=None, out=None):
+        self._chk(Y, self.m, "Y")
+        K = 1 if Y.dim() == 1 else Y.shape[0]
+        X = out if out is not None else torch.empty(Y.shape[:-1] + (self.n,), dtype=self.dtype, device=Y.device)
+        ct_adjoint(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), Y, X, K)
+        return X
+
+    def jac(self, x, theta, dtheta, delta=None, ddelta=None, out=None):
+        self._chk(x, self.n, "x")
+        dy = out if out is not None else torch.empty(self.m, dtype=self.dtype, device=x.device)
+        ct_jac(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, self._ang(dtheta, "dtheta"),
+               self._ang(ddelta, "ddelta"), dy)
+        return dy
+
+    def jacT(self, x, theta, r, delta=None, want_delta=False):
+        self._chk(x, self.n, "x")
+        self._chk(r, self.m, "r")
+        gt = torch.empty(self.V, dtype=torch.float64, device=x.device)
+        gd = torch.empty(self.V, dtype=torch.float64, device=x.device) if want_delta else None
+        ct_jacT(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, r, gt, gd)
+        return (gt, gd) if want_delta else gt
+
+    def gn_terms(self, x, theta, bdata, delta=None, want_residual=False):
+        self._chk(x, self.n, "x")
+        self._chk(bdata, self.m, "bdata")
+        res = torch.empty(self.m, dtype=self.dtype, device=x.device) if want_residual else None
+        g = torch.empty(self.V, dtype=torch.float64, device=x.device)
+        j2 = torch.empty(self.V, dtype=torch.float64, device=x.device)
+        f = torch.empty(self.V, dtype=torch.float64, device=x.device)
+        ct_gn_terms(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, bdata, res, g, j2, f)
+        return g, j2, f, res
+
+    def status(self):
+        return ct_status(self.h)

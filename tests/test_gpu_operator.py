@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA operators (through the C ABI) against the FP64 oracle.
+
+Tolerances (normwise relative, ||gpu - oracle|| / ||oracle||):
+  * float32 operators: 1e-5 for H, H^T, J and J^T;
+  * float64 operators: 1e-12.
+Angles are kept away from |cos| = |sin| (the Joseph axis switch), where the
+two sides could break the tie differently in the last bit.  For the angle
+derivative the view at "pi/2" is pi/2 + 1e-7: at pi/2 itself cos() is 6e-17,
+a ray slope below the 2^-49 resolution of the kernels' fixed-point line, and
+the one-sided slope chosen at the (then exact) interpolation kinks depends on
+the sign of that sub-resolution slope.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_06336_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float32: 1e-5, torch.float64: 1e-12}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def ct():
+    from paper_2605_06336_gb300 import ct as ctmod
+    ctmod.load_library()
+    return ctmod
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+CASES = [
+    # (N, B, views_per_frame, batch, offsets)
+    (2, 3, [5], 1, False),
+    (16, 23, [8], 3, True),
+    (37, 53, [11], 11, False),       # ragged tiles, ragged warps, batch 8+2+1
+    (24, 35, [4, 1, 0, 6], 2, True),  # uneven frames, one empty
+    (64, 91, [90], 8, False),         # small end-to-end workload shape
+]
+
+
+def _case_inputs(N, B, vpf, batch, offs, seed, near_axis=0.0):
+    rng = np.random.default_rng(seed)
+    V = sum(vpf)
+    theta = synth.random_angles(V, rng)
+    if V >= 3:
+        theta[0], theta[1] = 0.0, math.pi / 2 + near_axis  # axis-aligned views
+    delta = rng.normal(0, 0.5, V) if offs else None
+    F = len(vpf)
+    X = rng.uniform(size=(batch, F * N * N))
+    Y = rng.standard_normal((batch, V * B))
+    return theta, delta, X, Y
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("case", CASES)
+def test_forward_adjoint_parity(ct, case, dtype):
+    N, B, vpf, batch, offs = case
+    theta, delta, X, Y = _case_inputs(N, B, vpf, batch, offs, seed=N * 7 + batch)
+    g = oracle.Geometry(N, B, sum(vpf), vpf)
+    op = ct.CTOperator(N, B, sum(vpf), vpf, max_batch=batch, dtype=dtype)
+    th, dl = dev(theta), (dev(delta) if delta is not None else None)
+    Yg = op.forward(dev(X, dtype), th, dl)
+    Xg = op.adjoint(dev(Y, dtype), th, dl)
+    torch.cuda.synchronize()
+    assert op.status() == ct.CT_OK
+    Yo = oracle.forward(g, theta, X, delta)
+    Xo = oracle.adjoint(g, theta, Y, delta)
+    assert rel(host(Yg), Yo) <= TOL[dtype]
+    assert rel(host(Xg), Xo) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("case", CASES)
+def test_jacobian_parity(ct, case, dtype):
+    N, B, vpf, _, offs = case
+    theta, delta, X, Y = _case_inputs(N, B, vpf, 1, offs, seed=N * 11 + 1, near_axis=1e-7)
+    V = sum(vpf)
+    rng = np.random.default_rng(N)
+    dth = rng.standard_normal(V)
+    ddl = rng.standard_normal(V) if offs else None
+    g = oracle.Geometry(N, B, V, vpf)
+    op = ct.CTOperator(N, B, V, vpf, max_batch=1, dtype=dtype)
+    th, dl = dev(theta), (dev(delta) if delta is not None else None)
+    x, r = X[0], Y[0]
+    dy = op.jac(dev(x, dtype), th, dev(dth), dl, dev(ddl) if ddl is not None else None)
+    gt, gd = op.jacT(dev(x, dtype), th, dev(r, dtype), dl, want_delta=True)
+    torch.cuda.synchronize()
+    dyo = oracle.jac(g, theta, x, dth, delta, ddl)
+    gto, gdo = oracle.jacT(g, theta, x, r, delta)
+    assert rel(host(dy), dyo) <= TOL[dtype]
+    assert rel(host(gt), gto) <= TOL[dtype]
+    assert rel(host(gd), gdo) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_gauss_newton_terms(ct, dtype):
+    N, B, V = 48, 69, 21
+    rng = np.random.default_rng(3)
+    theta = synth.random_angles(V, rng)
+    x = rng.uniform(size=N * N)
+    bdata = rng.standard_normal(V * B) * 5
+    g = oracle.Geometry(N, B, V)
+    op = ct.CTOperator(N, B, V, dtype=dtype, max_batch=1)
+    gr, j2, f, res = op.gn_terms(dev(x, dtype), dev(theta), dev(bdata, dtype), want_residual=True)
+    torch.cuda.synchronize()
+    r_o = oracle.forward(g, theta, x) - bdata
+    dt, _ = oracle.dsample(g, theta, x)
+    dt = dt.reshape(V, B)
+    R = r_o.reshape(V, B)
+    assert rel(host(res), r_o) <= TOL[dtype]
+    assert rel(host(gr), (R * dt).sum(1)) <= TOL[dtype]
+    assert rel(host(j2), (dt * dt).sum(1)) <= TOL[dtype]
+    assert rel(host(f), 0.5 * (R * R).sum(1)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_adjoint_identity_on_gpu(ct, dtype):
+    N, B, V = 96, 137, 45
+    rng = np.random.default_rng(4)
+    theta = synth.random_angles(V, rng)
+    op = ct.CTOperator(N, B, V, dtype=dtype, max_batch=1)
+    th = dev(theta)
+    x = dev(rng.standard_normal(N * N), dtype)
+    y = dev(rng.standard_normal(V * B), dtype)
+    Ax = op.forward(x, th)
+    ATy = op.adjoint(y, th)
+    lhs = float((Ax.double() * y.double()).sum())
+    rhs = float((x.double() * ATy.double()).sum())
+    scale = float(Ax.double().norm() * y.double().norm())
+    assert abs(lhs - rhs) / scale <= (1e-6 if dtype == torch.float32 else 1e-14)
+    dth = dev(rng.standard_normal(V))
+    jd = op.jac(x, th, dth)
+    gt = op.jacT(x, th, y)
+    lhs = float((jd.double() * y.double()).sum())
+    rhs = float((dth * gt).sum())
+    assert abs(lhs - rhs) / (float(jd.double().norm() * y.double().norm()) + 1e-300) <= (
+        1e-5 if dtype == torch.float32 else 1e-12)
+
+
+@pytest.mark.parametrize("name", ["C2"])
+def test_full_size_workload_parity(ct, name):
+    """The 256^2 / 180-view / 363-bin workload, batch 8, as the benchmark runs it."""
+    w = synth.make_workload(name)
+    N, B, V = w.N, w.B, w.V
+    g = oracle.Geometry(N, B, V)
+    rng = np.random.default_rng(9)
+    X = np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(w.batch - 1, N * N))])
+    op = ct.CTOperator(N, B, V, dtype=torch.float32, max_batch=w.batch)
+    th = dev(w.theta_true)
+    Yg = host(op.forward(dev(X, torch.float32), th))
+    Yo = oracle.forward(g, w.theta_true, X)
+    assert rel(Yg, Yo) <= 1e-5
+    Xg = host(op.adjoint(dev(Yo, torch.float32), th))
+    Xo = oracle.adjoint(g, w.theta_true, Yo)
+    assert rel(Xg, Xo) <= 1e-5
+    dth = rng.standard_normal(V)
+    dy = host(op.jac(dev(X[0], torch.float32), th, dev(dth)))
+    assert rel(dy, oracle.jac(g, w.theta_true, X[0], dth)) <= 1e-5
+    r = Yo[0] - oracle.forward(g, w.theta_nominal, X[0])
+    gt = host(op.jacT(dev(X[0], torch.float32), th, dev(r, torch.float32)))
+    assert rel(gt, oracle.jacT(g, w.theta_true, X[0], r)[0]) <= 1e-5
+
+
+def test_large_image_sampled_views(ct):
+    """2048^2 image, 2897 bins: a few views checked against the oracle ray by ray."""
+    N = 2048
+    B = synth.n_bins(N)
+    rng = np.random.default_rng(12)
+    V = 4
+    theta = synth.random_angles(V, rng)
+    ells = synth.random_ellipses(N, 40, rng)
+    x = synth.rasterize(N, ells, supersample=2).ravel()
+    g = oracle.Geometry(N, B, V)
+    op = ct.CTOperator(N, B, V, dtype=torch.float32, max_batch=1)
+    th = dev(theta)
+    xg = dev(x, torch.float32)
+    assert rel(host(op.forward(xg, th)), oracle.forward(g, theta, x)) <= 1e-5
+    dth = rng.standard_normal(V)
+    assert rel(host(op.jac(xg, th, dev(dth))), oracle.jac(g, theta, x, dth)) <= 1e-5
+    y = rng.standard_normal(V * B)
+    assert rel(host(op.adjoint(dev(y, torch.float32), th)), oracle.adjoint(g, theta, y)) <= 1e-5
+
+
+def test_argument_errors(ct):
+    op = ct.CTOperator(16, 23, 4, max_batch=2)
+    th = dev(np.zeros(4))
+    X = torch.zeros(3, 256, device="cuda")
+    Y = torch.zeros(3, 4 * 23, device="cuda")
+    with pytest.raises(ct.CTError) as e:
+        ct.ct_forward(op.h, th, None, X, Y, 3)  # batch above max_batch
+    assert e.value.code == ct.CT_ERR_ARG
+    with pytest.raises(ct.CTError):
+        ct.ct_forward(op.h, None, None, X, Y, 1)
+    bad = dev(np.array([0.1, float("nan"), 0.2, 0.3]))
+    op.forward(X[0], bad)
+    assert op.status() == ct.CT_ERR_NAN
+    assert op.status() == ct.CT_OK  # the flag is cleared once reported
