@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 METRIC = "A/Aᵀ/Jθ GSamples/s + NL-RMM-GKS iter time vs FP64 GPU form at equal error"
 WORKLOAD = "C2"
 KBLOCK = 8
+# kernels per step: forward (view table, pair layouts, march), transpose
+# (view table, sinogram pairs, gather), JVP (table, pairs, march),
+# VJP (table, pairs, march, per-view sums)
+LAUNCHES_PER_STEP = 3 + 3 + 3 + 4
 L2_FLUSH_BYTES = 512 * 1024 * 1024
 LSU_BYTES_PER_CLK_SM = 128          # L1/shared data path per SM per clock
 NUM_SMS = 152
@@ -50,6 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch shapes 'fkb,fsplit,akb,asplit,jsplit' instead of autotuning")
     return ap.parse_args()
 
 
@@ -224,6 +230,11 @@ def main():
     Ysh = rng.standard_normal((K, V * B)).astype(np.float32)
     dth_h = rng.standard_normal(V)
     op = ct.CTOperator(N, B, V, max_batch=K, dtype=torch.float32)
+    if args.tuning:
+        op.tuning = [int(x) for x in args.tuning.split(",")]
+        tuning = op.tuning
+    else:
+        tuning = op.autotune()
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
     X = torch.tensor(Xh, device=dev)
@@ -356,7 +367,9 @@ def main():
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": "derived (unit counts x nominal max clock)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 12 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "tuning": dict(zip(["fwd_images_per_lane", "fwd_warps_per_ray", "adj_images_per_thread",
+                            "adj_view_groups", "jac_warps_per_ray"], tuning)),
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }

@@ -58,7 +58,7 @@ enum {
 };
 
 typedef struct {
-    int32_t N;                        /* image side, 2 <= N <= 8192 */
+    int32_t N;                        /* image side, 2 <= N <= 4096 */
     int32_t B;                        /* detector bins, 1 <= B */
     int32_t n_views;                  /* total views over all frames */
     int32_t n_frames;                 /* >= 1 */
@@ -72,9 +72,11 @@ typedef struct ct_handle ct_handle;
 
 /*
  * Create a handle: copies the geometry, allocates the workspaces it needs
- * (per-view tables, a transposed-image buffer of max_batch images, reduction
- * partials) on the current device and binds it to cuda_stream (a
- * cudaStream_t; NULL = legacy default stream).  *out receives the handle.
+ * on the current device (per-view tables; zero-padded "pair" copies of
+ * max_batch images, of their transposes and of max_batch sinograms, about
+ * 4 x 8 bytes per pixel and 8 bytes per sample and image in float32; the
+ * reduction partials) and binds it to cuda_stream (a cudaStream_t; NULL =
+ * legacy default stream).  *out receives the handle.
  */
 int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out);
 
@@ -138,6 +140,31 @@ int ct_jacT(ct_handle *h, const double *theta, const double *delta,
 int ct_gn_terms(ct_handle *h, const double *theta, const double *delta,
                 const void *x, const void *bdata, void *res, double *grad,
                 double *jnorm2, double *fval);
+
+/*
+ * Rebind the handle to another stream (for example a stream being captured
+ * into a CUDA graph).  Later calls launch on it.
+ */
+int ct_set_stream(ct_handle *h, void *cuda_stream);
+
+/*
+ * Pick launch shapes for this handle's geometry by timing the candidates on
+ * its stream: images per lane (1, 2, 4, 8) and warps per ray group (1, 2, 4,
+ * 8) for the forward projection at max_batch, images per thread and view
+ * groups per pixel tile (1, 2, 4) for the transpose, warps per ray group for
+ * the Jacobian kernels.  Synchronises; allocates and frees scratch buffers;
+ * must not run during stream capture.  Results of every operator are
+ * independent of the chosen shapes up to floating-point summation order.
+ */
+int ct_autotune(ct_handle *h);
+
+/*
+ * Read / set the launch shapes: {fwd images per lane, fwd warps per ray
+ * group, transpose images per thread, transpose view groups, Jacobian warps
+ * per ray group}; each a power of two, at most 8 (view groups at most 4).
+ */
+int ct_get_tuning(ct_handle *h, int32_t *out5);
+int ct_set_tuning(ct_handle *h, const int32_t *in5);
 
 /*
  * Synchronise the handle's stream and report device-side conditions found

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -39,64 +40,176 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_fstart);
     cudaFree(h.d_fcount);
     cudaFree(h.d_flag);
-    cudaFree(h.d_xt);
+    cudaFree(h.d_px);
+    cudaFree(h.d_pt);
+    cudaFree(h.d_yp);
     cudaFree(h.d_partial);
     h.d_views = nullptr;
     h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = nullptr;
-    h.d_xt = nullptr;
+    h.d_px = h.d_pt = h.d_yp = nullptr;
     h.d_partial = nullptr;
 }
 
 template <typename T>
-int do_forward(ct_handle *H, const double *theta, const double *delta, const void *X, void *Y, int batch)
+int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
-    ctgb::Handle &h = H->h;
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_transpose<T>(h, (const T *)X, (T *)h.d_xt, batch * h.F));
-    CT_CUDA(ctgb::launch_forward<T>(h, (const T *)X, (const T *)h.d_xt, (T *)Y, batch));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F));
+    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split));
     return CT_OK;
 }
 
 template <typename T>
-int do_adjoint(ct_handle *H, const double *theta, const double *delta, const void *Y, void *X, int batch)
+int do_adjoint(ctgb::Handle &h, const double *theta, const double *delta, const void *Y, void *X, int batch)
 {
-    ctgb::Handle &h = H->h;
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_adjoint<T>(h, (const T *)Y, (T *)X, batch));
+    CT_CUDA(ctgb::launch_pairs_sino<T>(h, (const T *)Y, batch));
+    CT_CUDA(ctgb::launch_adjoint<T>(h, (T *)X, batch, h.tune.adj_kb, h.tune.adj_split));
     return CT_OK;
 }
 
 template <typename T>
-int do_jac(ct_handle *H, const double *theta, const double *delta, const void *x, const double *dtheta,
+int do_jac(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const double *dtheta,
            const double *ddelta, void *dy)
 {
-    ctgb::Handle &h = H->h;
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_transpose<T>(h, (const T *)x, (T *)h.d_xt, h.F));
-    CT_CUDA(ctgb::launch_jvp<T>(h, (const T *)x, (const T *)h.d_xt, dtheta, ddelta, (T *)dy));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
+    CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split));
     return CT_OK;
 }
 
 template <typename T>
-int do_jacT(ct_handle *H, const double *theta, const double *delta, const void *x, const void *r, double *gtheta,
+int do_jacT(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *r, double *gtheta,
             double *gdelta)
 {
-    ctgb::Handle &h = H->h;
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_transpose<T>(h, (const T *)x, (T *)h.d_xt, h.F));
-    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)x, (const T *)h.d_xt, (const T *)r, gtheta, gdelta));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
+    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split));
     return CT_OK;
 }
 
 template <typename T>
-int do_gn(ct_handle *H, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
+int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
           double *grad, double *jnorm2, double *fval)
 {
-    ctgb::Handle &h = H->h;
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_transpose<T>(h, (const T *)x, (T *)h.d_xt, h.F));
-    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)x, (const T *)h.d_xt, (const T *)bdata, (T *)res, grad, jnorm2, fval));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
+    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split));
     return CT_OK;
+}
+
+// Default launch shapes before (or without) autotuning: enough warps per SM
+// for the small workloads, batch folding for the large ones.
+void default_tuning(ctgb::Handle &h)
+{
+    const int kb = h.max_batch >= 8 ? 8 : (h.max_batch >= 4 ? 4 : (h.max_batch >= 2 ? 2 : 1));
+    h.tune.fwd_kb = std::min(kb, 4);
+    h.tune.adj_kb = std::min(kb, 4);
+    const long long rays = (long long)h.V * h.nchunks;  // warps per image
+    h.tune.fwd_split = rays >= 16LL * h.num_sms ? 2 : 4;
+    h.tune.adj_split = 2;
+    h.tune.der_split = rays >= 32LL * h.num_sms ? 2 : 4;
+}
+
+// Time one configuration: median of `reps` launches after one warm-up.
+template <typename F> float time_config(cudaStream_t s, F &&launch, int reps = 5)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch();
+    std::vector<float> ms;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, s);
+        launch();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms.push_back(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
+template <typename T> int autotune_impl(ctgb::Handle &h)
+{
+    // Representative inputs: evenly spaced angles, pair buffers as they are
+    // (values do not change the timing), a scratch output.
+    std::vector<double> th(h.V);
+    for (int v = 0; v < h.V; ++v) th[v] = 3.14159265358979 * (v + 0.37) / h.V;
+    double *d_th = nullptr, *d_g = nullptr;
+    void *d_out = nullptr;
+    const size_t out_elems = std::max((size_t)h.max_batch * h.V * h.B, (size_t)h.max_batch * h.F * h.N * h.N);
+    if (cudaMalloc(&d_th, sizeof(double) * h.V) != cudaSuccess ||
+        cudaMalloc(&d_g, sizeof(double) * h.V) != cudaSuccess ||
+        cudaMalloc(&d_out, out_elems * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_th);
+        cudaFree(d_g);
+        cudaFree(d_out);
+        return CT_ERR_OOM;
+    }
+    int rc = CT_OK;
+    do {
+        cudaError_t e = cudaMemcpy(d_th, th.data(), sizeof(double) * h.V, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_g, 0, sizeof(double) * h.V, h.stream);
+        if (e == cudaSuccess) e = ctgb::launch_view_setup(h, d_th, nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h.stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e);
+            break;
+        }
+        const int K = h.max_batch;
+        float best = 1e30f;
+        ctgb::Tuning t = h.tune;
+        for (int kb : {1, 2, 4, 8}) {
+            if (kb > K) continue;
+            for (int sp : {1, 2, 4, 8}) {
+                const float ms = time_config(h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp); });
+                if (ms < best) {
+                    best = ms;
+                    t.fwd_kb = kb;
+                    t.fwd_split = sp;
+                }
+            }
+        }
+        best = 1e30f;
+        for (int kb : {1, 2, 4, 8}) {
+            if (kb > K) continue;
+            for (int sp : {1, 2, 4}) {
+                const float ms = time_config(h.stream, [&] { ctgb::launch_adjoint<T>(h, (T *)d_out, K, kb, sp); });
+                if (ms < best) {
+                    best = ms;
+                    t.adj_kb = kb;
+                    t.adj_split = sp;
+                }
+            }
+        }
+        best = 1e30f;
+        for (int sp : {1, 2, 4, 8}) {
+            const float ms = time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp); });
+            if (ms < best) {
+                best = ms;
+                t.der_split = sp;
+            }
+        }
+        e = cudaStreamSynchronize(h.stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e);
+            break;
+        }
+        h.tune = t;
+    } while (0);
+    cudaFree(d_th);
+    cudaFree(d_g);
+    cudaFree(d_out);
+    // the view table now holds the tuning angles; force a rebuild on the next call
+    cudaMemsetAsync(h.d_views, 0, sizeof(ctgb::ViewGeo) * h.V, h.stream);
+    return rc;
 }
 
 }  // namespace
@@ -135,6 +248,8 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
     h.stream = (cudaStream_t)cuda_stream;
     h.views_per_frame = vpf;
     h.nchunks = (h.B + ctgb::kChunk - 1) / ctgb::kChunk;
+    h.Pp = h.N + 4;
+    h.Pb = h.B + 4;
     int rc = CT_OK;
     do {
         cudaError_t e = cudaGetDevice(&h.device);
@@ -150,13 +265,17 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
             fcount[f] = vpf[f];
             for (int k = 0; k < vpf[f]; ++k) fov[v++] = f;
         }
-        const size_t img_elems = (size_t)h.max_batch * h.F * h.N * h.N;
+        const size_t pair_bytes = 2 * elem_size(h);
+        const size_t img_pairs = (size_t)h.max_batch * h.F * h.N * h.Pp;
+        const size_t sino_pairs = (size_t)h.max_batch * h.V * h.Pb;
         bool ok = cudaMalloc(&h.d_views, sizeof(ctgb::ViewGeo) * h.V) == cudaSuccess &&
                   cudaMalloc(&h.d_fov, sizeof(int) * h.V) == cudaSuccess &&
                   cudaMalloc(&h.d_fstart, sizeof(int) * h.F) == cudaSuccess &&
                   cudaMalloc(&h.d_fcount, sizeof(int) * h.F) == cudaSuccess &&
                   cudaMalloc(&h.d_flag, sizeof(int)) == cudaSuccess &&
-                  cudaMalloc(&h.d_xt, img_elems * elem_size(h)) == cudaSuccess &&
+                  cudaMalloc(&h.d_px, img_pairs * pair_bytes) == cudaSuccess &&
+                  cudaMalloc(&h.d_pt, img_pairs * pair_bytes) == cudaSuccess &&
+                  cudaMalloc(&h.d_yp, sino_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.V * h.nchunks) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
@@ -167,6 +286,10 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
         if (e == cudaSuccess) e = cudaMemcpy(h.d_fstart, fstart.data(), sizeof(int) * h.F, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h.d_fcount, fcount.data(), sizeof(int) * h.F, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(h.d_flag, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(h.d_views, 0, sizeof(ctgb::ViewGeo) * h.V);
+        if (e == cudaSuccess) e = cudaMemset(h.d_px, 0, img_pairs * pair_bytes);
+        if (e == cudaSuccess) e = cudaMemset(h.d_pt, 0, img_pairs * pair_bytes);
+        if (e == cudaSuccess) e = cudaMemset(h.d_yp, 0, sino_pairs * pair_bytes);
         if (e != cudaSuccess) {
             rc = cuda_fail(e);
             break;
@@ -177,6 +300,7 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
         delete H;
         return rc;
     }
+    default_tuning(h);
     *out = H;
     return CT_OK;
 }
@@ -192,39 +316,79 @@ void ct_destroy(ct_handle *H)
 int ct_forward(ct_handle *H, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
     if (!H || !theta || !X || !Y || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
-    return H->h.precision ? do_forward<double>(H, theta, delta, X, Y, batch)
-                          : do_forward<float>(H, theta, delta, X, Y, batch);
+    return H->h.precision ? do_forward<double>(H->h, theta, delta, X, Y, batch)
+                          : do_forward<float>(H->h, theta, delta, X, Y, batch);
 }
 
 int ct_adjoint(ct_handle *H, const double *theta, const double *delta, const void *Y, void *X, int batch)
 {
     if (!H || !theta || !X || !Y || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
-    return H->h.precision ? do_adjoint<double>(H, theta, delta, Y, X, batch)
-                          : do_adjoint<float>(H, theta, delta, Y, X, batch);
+    return H->h.precision ? do_adjoint<double>(H->h, theta, delta, Y, X, batch)
+                          : do_adjoint<float>(H->h, theta, delta, Y, X, batch);
 }
 
 int ct_jac(ct_handle *H, const double *theta, const double *delta, const void *x, const double *dtheta,
            const double *ddelta, void *dy)
 {
     if (!H || !theta || !x || !dtheta || !dy) return CT_ERR_ARG;
-    return H->h.precision ? do_jac<double>(H, theta, delta, x, dtheta, ddelta, dy)
-                          : do_jac<float>(H, theta, delta, x, dtheta, ddelta, dy);
+    return H->h.precision ? do_jac<double>(H->h, theta, delta, x, dtheta, ddelta, dy)
+                          : do_jac<float>(H->h, theta, delta, x, dtheta, ddelta, dy);
 }
 
 int ct_jacT(ct_handle *H, const double *theta, const double *delta, const void *x, const void *r, double *gtheta,
             double *gdelta)
 {
     if (!H || !theta || !x || !r || !gtheta) return CT_ERR_ARG;
-    return H->h.precision ? do_jacT<double>(H, theta, delta, x, r, gtheta, gdelta)
-                          : do_jacT<float>(H, theta, delta, x, r, gtheta, gdelta);
+    return H->h.precision ? do_jacT<double>(H->h, theta, delta, x, r, gtheta, gdelta)
+                          : do_jacT<float>(H->h, theta, delta, x, r, gtheta, gdelta);
 }
 
 int ct_gn_terms(ct_handle *H, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
                 double *grad, double *jnorm2, double *fval)
 {
     if (!H || !theta || !x || !bdata || !grad || !jnorm2) return CT_ERR_ARG;
-    return H->h.precision ? do_gn<double>(H, theta, delta, x, bdata, res, grad, jnorm2, fval)
-                          : do_gn<float>(H, theta, delta, x, bdata, res, grad, jnorm2, fval);
+    return H->h.precision ? do_gn<double>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval)
+                          : do_gn<float>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval);
+}
+
+int ct_set_stream(ct_handle *H, void *cuda_stream)
+{
+    if (!H) return CT_ERR_ARG;
+    H->h.stream = (cudaStream_t)cuda_stream;
+    return CT_OK;
+}
+
+int ct_autotune(ct_handle *H)
+{
+    if (!H) return CT_ERR_ARG;
+    return H->h.precision ? autotune_impl<double>(H->h) : autotune_impl<float>(H->h);
+}
+
+int ct_get_tuning(ct_handle *H, int32_t *out5)
+{
+    if (!H || !out5) return CT_ERR_ARG;
+    const ctgb::Tuning &t = H->h.tune;
+    out5[0] = t.fwd_kb;
+    out5[1] = t.fwd_split;
+    out5[2] = t.adj_kb;
+    out5[3] = t.adj_split;
+    out5[4] = t.der_split;
+    return CT_OK;
+}
+
+int ct_set_tuning(ct_handle *H, const int32_t *in5)
+{
+    if (!H || !in5) return CT_ERR_ARG;
+    auto pow2 = [](int x, int hi) { return x >= 1 && x <= hi && (x & (x - 1)) == 0; };
+    if (!pow2(in5[0], 8) || !pow2(in5[1], 8) || !pow2(in5[2], 8) || !pow2(in5[3], 4) || !pow2(in5[4], 8))
+        return CT_ERR_ARG;
+    ctgb::Tuning &t = H->h.tune;
+    t.fwd_kb = in5[0];
+    t.fwd_split = in5[1];
+    t.adj_kb = in5[2];
+    t.adj_split = in5[3];
+    t.der_split = in5[4];
+    return CT_OK;
 }
 
 int ct_status(ct_handle *H)

@@ -16,6 +16,14 @@
 // odd-sized image meets the centre pixel exactly) stay exact.  That matters
 // for the angle derivative, whose interpolation slope jumps at every cell
 // boundary.
+//
+// Pair layouts.  The ray kernels read an image as "pairs": element c of row
+// r holds (X[r][c], X[r][c+1]) for c = -2 .. N+1 (stored at c + 2, pitch
+// Pp = N + 4 pairs), zero outside the image.  One 8-byte load then fetches
+// both interpolation taps, and clamping the cell to [-2, N] keeps every load
+// in bounds while rays outside the image read exact zeros.  The transpose
+// operator reads sinograms the same way: pair b of view v holds
+// (Y[v][b], Y[v][b+1]) for b = -2 .. B+1 (stored at b + 2, pitch Pb = B + 4).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,70 +34,75 @@
 namespace ctgb {
 
 constexpr int kFracBits = 48;
-constexpr double kFixScale = 281474976710656.0;        // 2^48
-constexpr double kFixInv = 1.0 / 281474976710656.0;    // 2^-48
-constexpr int kMaxN = 4096;                            // keeps |q| * 2^48 inside int64
-constexpr int kChunk = 32;                             // bins per warp work item
-constexpr int kTile = 16;                              // adjoint pixel tile side
+constexpr double kFixScale = 281474976710656.0;  // 2^48
+constexpr int kMaxN = 4096;                      // keeps |q| * 2^48 inside int64
+constexpr int kChunk = 32;                       // bins per warp work item
+constexpr int kTile = 16;                        // transpose-operator pixel tile side
+constexpr double kAllRowsBelow = 4e-3;           // |qr| below this: march every row
 
-enum ViewFlags : int { kAllRows = 1 };
+enum ViewFlags : int { kAllRows = 1, kValid = 2 };
 
-// Per-view constants, rebuilt on the device from (theta, delta) by every
-// call (angles change between Gauss-Newton steps).
+// Per-view constants, rebuilt on the device from (theta, delta) whenever the
+// angle or offset of the view changed since the previous call.
 struct __align__(16) ViewGeo {
-    long long Qc, Qb, Qh;   // h + phi*qb, qb, qr/2 in fixed point
-    double alo, ahi, gam;   // rows with -1 < q < N lie between alo + b*gam and ahi + b*gam
-    double beta0, c, s;     // pixel-driven transpose: bin coordinate of pixel (i,j) = beta0 + j*c - i*s
-    double sb0d;            // s_b = sb0d + b (FP64 form)
-    float w;                // 1/|cos| or 1/|sin|
-    float dw;               // d w / d theta
-    float gs, gh, gr;       // dq/dtheta (b, r) = (s_b*gs + gh) + r*gr
-    float qbf;              // dq/ddelta = qb
-    float sb0;              // s_b = sb0 + b
-    int mode;               // 0: rows of X, 1: rows of X^T
+    long long Qc, Qb, Qh;  // h + phi*qb, qb, qr/2 in fixed point
+    double beta0, c, s;    // transpose: bin coordinate of pixel (i,j) = beta0 + j*c - i*s
+    double th, dl;         // the (theta, delta) the constants were built from
+    double sb0d;           // s_b = sb0d + b (FP64 form)
+    float alo, ahi, gam;   // rows with -1 < q < N lie between alo + b*gam and ahi + b*gam
+    float w;               // 1/|cos| or 1/|sin|
+    float dw;              // d w / d theta
+    float gs, gh, gr;      // dq/dtheta (b, r) = (s_b*gs + gh) + r*gr
+    float qbf;             // dq/ddelta = qb
+    float sb0;             // s_b = sb0 + b
+    int mode;              // 0: rows of X, 1: rows of X^T
     int frame;
     int flags;
-    int n0;                 // integer part of the bin-centre offset -(B-1)/2 + delta
+    int n0;                // integer part of the bin-centre offset -(B-1)/2 + delta
+};
+
+// Launch shapes.  kb: images (or sinograms) per lane; split: warps sharing
+// one ray (row segments, combined in shared memory) or thread groups sharing
+// one pixel tile (view subsets, combined in shared memory).
+struct Tuning {
+    int fwd_kb = 8, fwd_split = 2;  // forward projection of a batch
+    int adj_kb = 8, adj_split = 2;  // transpose of a batch
+    int der_split = 4;              // JVP / VJP / Gauss-Newton terms (one image)
 };
 
 struct Handle {
     int N = 0, B = 0, V = 0, F = 1, max_batch = 1, precision = 0, device = 0;
+    int Pp = 0, Pb = 0;  // pair pitches
     cudaStream_t stream = nullptr;
     std::vector<int> views_per_frame;
     ViewGeo *d_views = nullptr;
-    int *d_fov = nullptr;       // frame of each view
-    int *d_fstart = nullptr;    // first view of each frame
-    int *d_fcount = nullptr;    // views of each frame
-    int *d_flag = nullptr;      // device-side status bits
-    void *d_xt = nullptr;       // transposed images, max_batch * F * N * N elements
+    int *d_fov = nullptr;     // frame of each view
+    int *d_fstart = nullptr;  // first view of each frame
+    int *d_fcount = nullptr;  // views of each frame
+    int *d_flag = nullptr;    // device-side status bits
+    void *d_px = nullptr;     // pair images, rows of X:   max_batch * F * N * Pp pairs
+    void *d_pt = nullptr;     // pair images, rows of X^T: max_batch * F * N * Pp pairs
+    void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
     double *d_partial = nullptr;  // per (view, chunk) reduction partials, 4 per item
     int nchunks = 0;              // ceil(B / kChunk)
     int num_sms = 0;
+    Tuning tune;
 };
 
-// Kernel launchers (implemented in ct_kernels.cu).  All launch on h.stream.
+// Kernel launchers.  All launch on h.stream and return the launch status.
 cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta);
 
-template <typename T>
-cudaError_t launch_transpose(const Handle &h, const T *X, T *XT, int nimg);
+template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg);
+template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino);
 
+template <typename T> cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split);
+template <typename T> cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split);
 template <typename T>
-cudaError_t launch_forward(const Handle &h, const T *X, const T *XT, T *Y, int batch);
-
+cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split);
 template <typename T>
-cudaError_t launch_adjoint(const Handle &h, const T *Y, T *X, int batch);
-
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split);
 template <typename T>
-cudaError_t launch_jvp(const Handle &h, const T *X, const T *XT, const double *dtheta,
-                       const double *ddelta, T *dY);
-
-// mode 0: J^T r (theta and, if gdelta != null, delta); mode 1: Gauss-Newton terms.
-template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *X, const T *XT, const T *R, double *gtheta,
-                       double *gdelta);
-
-template <typename T>
-cudaError_t launch_gn(const Handle &h, const T *X, const T *XT, const T *bdata, T *res,
-                      double *grad, double *jnorm2, double *fval);
+cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval,
+                      int split);
 
 }  // namespace ctgb

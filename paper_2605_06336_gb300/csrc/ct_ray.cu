@@ -1,0 +1,510 @@
+// Ray-driven kernels of the angle-dependent Joseph operator (sm_103a).
+//
+//   k_view_setup  per-view constants from (theta, delta), FP64 -> fixed point
+//   k_pairs_img   X -> pair layouts of X and X^T (zero padded)
+//   k_pairs_sino  Y -> pair layout of the sinogram (zero padded)
+//   k_ray         one warp per 32 consecutive rays of one view (optionally
+//                 SPLIT warps per ray group, each marching a row segment):
+//                   FWD  Y = H X for KB images at once
+//                   JVP  dY = J_theta dtheta (+ J_delta ddelta)
+//                   VJP  J_theta^T r (and J_delta^T r), per-view partials
+//                   GN   residual, J^T r, |J_v|^2, f_v partials
+//   k_finalize    per-view sums of the partials in a fixed order
+//
+// Forward model: Joseph rule on a parallel-beam geometry with per-view angle
+// theta_v and detector offset delta_v (the CT operator of Sec. 6.2, with the
+// per-parameter derivatives H_{p_i} u of Alg. "UPDATE-PARAM").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "ct_device.cuh"
+#include "ct_internal.cuh"
+
+namespace ctgb {
+namespace {
+
+// ---------------------------------------------------------------------------
+// per-view setup
+// ---------------------------------------------------------------------------
+__global__ void k_view_setup(const double *__restrict__ theta, const double *__restrict__ delta,
+                             const int *__restrict__ fov, int V, int N, int B, ViewGeo *__restrict__ out,
+                             int *__restrict__ flag)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    double th = theta[v];
+    double dl = delta ? delta[v] : 0.0;
+    ViewGeo *gp = out + v;
+    if ((gp->flags & kValid) && __double_as_longlong(gp->th) == __double_as_longlong(th) &&
+        __double_as_longlong(gp->dl) == __double_as_longlong(dl))
+        return;  // unchanged since the last call
+    const double th_in = th, dl_in = dl;
+    int bad = 0;
+    if (!isfinite(th) || !isfinite(dl)) {
+        *flag = 1;  // every writer stores the same value
+        th = 0.0;
+        dl = 0.0;
+        bad = 1;
+    }
+    double s, c;
+    sincos(th, &s, &c);
+    const double h = 0.5 * (N - 1);
+    const double sb0 = -0.5 * (B - 1) + dl;
+    ViewGeo g;
+    double q0, qb, qr;
+    if (fabs(c) >= fabs(s)) {  // one sample per image row
+        const double ic = 1.0 / c;
+        const double ic2 = ic * ic;
+        g.mode = 0;
+        qb = ic;
+        qr = s * ic;
+        q0 = (sb0 - h * s) * ic + h;
+        g.w = (float)fabs(ic);
+        g.dw = (float)(copysign(1.0, c) * s * ic2);
+        g.gs = (float)(s * ic2);
+        g.gh = (float)(-h * ic2);
+        g.gr = (float)ic2;
+    } else {  // one sample per image column (rows of X^T)
+        const double is = 1.0 / s;
+        const double is2 = is * is;
+        g.mode = 1;
+        qb = -is;
+        qr = c * is;
+        q0 = h - (sb0 + h * c) * is;
+        g.w = (float)fabs(is);
+        g.dw = (float)(-copysign(1.0, s) * c * is2);
+        g.gs = (float)(c * is2);
+        g.gh = (float)(h * is2);
+        g.gr = (float)(-is2);
+    }
+    // Fixed-point line anchored at the image centre with an integer bin offset.
+    const double n0 = floor(sb0);
+    g.n0 = (int)n0;
+    g.Qc = __double2ll_rn(h * kFixScale) + __double2ll_rn((sb0 - n0) * qb * kFixScale);
+    g.Qb = __double2ll_rn(qb * kFixScale);
+    g.Qh = __double2ll_rn(qr * 0.5 * kFixScale);
+    g.qbf = (float)qb;
+    g.sb0 = (float)sb0;
+    g.sb0d = sb0;
+    int flags = kValid;
+    if (fabs(qr) < kAllRowsBelow) {
+        flags |= kAllRows;
+        g.alo = g.ahi = g.gam = 0.0f;
+    } else {
+        const double iqr = 1.0 / qr;
+        g.alo = (float)((-1.0 - q0) * iqr);
+        g.ahi = (float)(((double)N - q0) * iqr);
+        g.gam = (float)(-qb * iqr);
+    }
+    g.flags = bad ? (flags & ~kValid) : flags;  // a bad view is rebuilt (and reported) every call
+    g.beta0 = h * (s - c) - dl + 0.5 * (B - 1);
+    g.c = c;
+    g.s = s;
+    g.th = th_in;
+    g.dl = dl_in;
+    g.frame = fov ? fov[v] : 0;
+    *gp = g;
+}
+
+// ---------------------------------------------------------------------------
+// pair layouts
+// ---------------------------------------------------------------------------
+// Tile of 32 rows x 32 pairs.  PX[img][r][cp] = (X[r][c], X[r][c+1]) and
+// PT[img][r][cp] = (X[c][r], X[c+1][r]) with c = cp - 2, zero outside.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair_t<T> *__restrict__ PX,
+                                                   pair_t<T> *__restrict__ PT, int N, int Pp, int nimg)
+{
+    __shared__ T a[32][34];   // a[i][j] = X[r0 + i][c0 + j]
+    __shared__ T bt[33][33];  // bt[i][j] = X[c0 + i][r0 + j]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int cp0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = cp0 - 2;
+    for (int img = blockIdx.z; img < nimg; img += gridDim.z) {
+        const T *src = X + (size_t)img * N * N;
+        __syncthreads();
+        for (int i = ty; i < 32; i += 8) {
+            const int r = r0 + i;
+            for (int j = tx; j < 33; j += 32) {
+                const int c = c0 + j;
+                a[i][j] = (r < N && c >= 0 && c < N) ? src[(size_t)r * N + c] : T(0);
+            }
+        }
+        for (int i = ty; i < 33; i += 8) {
+            const int rr = c0 + i, cc = r0 + tx;
+            bt[i][tx] = (rr >= 0 && rr < N && cc < N) ? src[(size_t)rr * N + cc] : T(0);
+        }
+        __syncthreads();
+        pair_t<T> *px = PX + (size_t)img * N * Pp;
+        pair_t<T> *pt = PT + (size_t)img * N * Pp;
+        for (int i = ty; i < 32; i += 8) {
+            const int r = r0 + i, cp = cp0 + tx;
+            if (r < N && cp < Pp) {
+                pair_t<T> p;
+                p.x = a[i][tx];
+                p.y = a[i][tx + 1];
+                px[(size_t)r * Pp + cp] = p;
+                pair_t<T> q;
+                q.x = bt[tx][i];
+                q.y = bt[tx + 1][i];
+                pt[(size_t)r * Pp + cp] = q;
+            }
+        }
+    }
+}
+
+// YP[row][bp] = (Y[row][bp - 2], Y[row][bp - 1]), zero outside [0, B).
+template <typename T>
+__global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP, int B, int Pb, long long total)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long row = idx / Pb;
+        const int bp = (int)(idx - row * Pb);
+        const int b0 = bp - 2, b1 = bp - 1;
+        const T *y = Y + row * B;
+        pair_t<T> p;
+        p.x = (b0 >= 0 && b0 < B) ? y[b0] : T(0);
+        p.y = (b1 >= 0 && b1 < B) ? y[b1] : T(0);
+        YP[idx] = p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ray march
+// ---------------------------------------------------------------------------
+enum RayMode { kFwd = 0, kJvp = 1, kVjp = 2, kGn = 3 };
+
+template <typename T> struct RayArgs {
+    const ViewGeo *vg;
+    int V, N, B, nchunks, Pp;
+    const pair_t<T> *PX, *PT;
+    long long pimg_stride;  // pairs per batch element (F * N * Pp)
+    int kbase, ngroups;
+    T *Y;                   // FWD: [batch][V*B]; JVP: dY
+    long long sino_stride;
+    const double *dtheta, *ddelta;
+    const T *R;             // VJP: r; GN: data b
+    T *res;                 // GN: residual (nullable)
+    double *partial;        // VJP / GN
+};
+
+// Warp-uniform row range [rlo, rhi] covering every row where one of the
+// warp's rays has -1 < q < N; rows added by the union or by the two-row
+// margin read exact zeros.
+__device__ __forceinline__ void warp_rows(const ViewGeo &g, int b, bool active, int N, int &rlo, int &rhi)
+{
+    if (g.flags & kAllRows) {
+        rlo = 0;
+        rhi = N - 1;
+        return;
+    }
+    const float r1 = fmaf((float)b, g.gam, g.alo);
+    const float r2 = fmaf((float)b, g.gam, g.ahi);
+    const float lo = fminf(fmaxf(fminf(r1, r2) - 2.0f, 0.0f), (float)N);
+    const float hi = fmaxf(fminf(fmaxf(r1, r2) + 2.0f, (float)(N - 1)), -1.0f);
+    int l = (int)floorf(lo), u = (int)ceilf(hi);
+    if (!active) {
+        l = N;
+        u = -1;
+    }
+    rlo = __reduce_min_sync(0xffffffffu, l);
+    rhi = __reduce_max_sync(0xffffffffu, u);
+}
+
+template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
+__global__ void __launch_bounds__(32 * SPLIT) k_ray(RayArgs<T> a)
+{
+    using P2 = pair_t<T>;
+    constexpr int NACC = (MODE == kFwd) ? KB : 3;
+    __shared__ T red[SPLIT > 1 ? SPLIT : 1][NACC][32];
+    const int lane = threadIdx.x & 31;
+    const int seg = threadIdx.x >> 5;
+    const int N = a.N;
+    const int total = a.ngroups * a.V * a.nchunks;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int chunk = item % a.nchunks;
+        const int t = item / a.nchunks;
+        const int v = t % a.V;
+        const int grp = t / a.V;
+        const ViewGeo &g = a.vg[v];
+        const int b = chunk * kChunk + lane;
+        const bool active = b < a.B;
+        int rlo, rhi;
+        warp_rows(g, b, active, N, rlo, rhi);
+        const int len = rhi - rlo + 1;
+        const int per = (len + SPLIT - 1) / SPLIT;
+        const int r0 = rlo + seg * per;
+        const int r1 = min(rhi, r0 + per - 1);
+        long long Q = line_at(g, b, r0, N);
+        const long long dQ = 2 * g.Qh;
+        const int k0 = a.kbase + grp * KB;
+        const P2 *img = (g.mode ? a.PT : a.PX) + (size_t)g.frame * N * a.Pp + (size_t)k0 * a.pimg_stride +
+                        (size_t)r0 * a.Pp + 2;
+        T acc[NACC];
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) acc[k] = T(0);
+        if constexpr (MODE == kFwd) {
+#pragma unroll 4
+            for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ) {
+                const int cell = min(max(cell_of(Q), -2), N);
+                const T f = frac_of(Q, T());
+                const T omf = T(1) - f;
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    const P2 p = __ldg(img + (size_t)k * a.pimg_stride + cell);
+                    acc[k] = fma(omf, p.x, fma(f, p.y, acc[k]));
+                }
+            }
+        } else {
+            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta,
+            // acc[2] = sum of slopes (offset derivative)
+            const T g0 = fma(GeoT<T>::sb(g, b), GeoT<T>::gs(g), GeoT<T>::gh(g, N));
+            const T gr = GeoT<T>::gr(g);
+            T rf = (T)r0;
+#pragma unroll 4
+            for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ, rf += T(1)) {
+                const int cell = min(max(cell_of(Q), -2), N);
+                const T f = frac_of(Q, T());
+                const P2 p = __ldg(img + cell);
+                const T d = p.y - p.x;
+                acc[0] += fma(f, d, p.x);
+                acc[1] = fma(d, fma(rf, gr, g0), acc[1]);
+                if (OFFS) acc[2] += d;
+            }
+        }
+        if constexpr (SPLIT > 1) {
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) red[seg][k][lane] = acc[k];
+            __syncthreads();
+            if (seg == 0) {
+#pragma unroll
+                for (int k = 0; k < NACC; ++k) {
+                    T s = red[0][k][lane];
+#pragma unroll
+                    for (int q = 1; q < SPLIT; ++q) s += red[q][k][lane];
+                    acc[k] = s;
+                }
+            }
+        }
+        if (seg == 0) {
+            const T wv = GeoT<T>::w(g);
+            if constexpr (MODE == kFwd) {
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < KB; ++k)
+                        a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = wv * acc[k];
+                }
+            } else {
+                const T jt = fma(GeoT<T>::dw(g), acc[0], wv * acc[1]);
+                const T jd = wv * GeoT<T>::qb(g) * acc[2];
+                if constexpr (MODE == kJvp) {
+                    if (active) {
+                        T out = (T)a.dtheta[v] * jt;
+                        if (OFFS) out = fma((T)a.ddelta[v], jd, out);
+                        a.Y[(size_t)v * a.B + b] = out;
+                    }
+                } else if constexpr (MODE == kVjp) {
+                    double pt = 0.0, pd = 0.0;
+                    if (active) {
+                        const T r = a.R[(size_t)v * a.B + b];
+                        pt = (double)(r * jt);
+                        if (OFFS) pd = (double)(r * jd);
+                    }
+                    pt = warp_sum(pt);
+                    if (OFFS) pd = warp_sum(pd);
+                    if (lane == 0) {
+                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                        p[0] = pt;
+                        p[1] = pd;
+                    }
+                } else {  // kGn
+                    double pg = 0.0, pj = 0.0, pf = 0.0;
+                    if (active) {
+                        const T rr = wv * acc[0] - a.R[(size_t)v * a.B + b];
+                        if (a.res) a.res[(size_t)v * a.B + b] = rr;
+                        pg = (double)rr * (double)jt;
+                        pj = (double)jt * (double)jt;
+                        pf = (double)rr * (double)rr;
+                    }
+                    pg = warp_sum(pg);
+                    pj = warp_sum(pj);
+                    pf = warp_sum(pf);
+                    if (lane == 0) {
+                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                        p[0] = pg;
+                        p[1] = pj;
+                        p[2] = pf;
+                    }
+                }
+            }
+        }
+        if constexpr (SPLIT > 1) __syncthreads();  // red[] is reused by the next item
+    }
+}
+
+// out_q[v] = scale_q * sum_c partial[v][c][q], summed in chunk order.
+__global__ void k_finalize(const double *__restrict__ partial, int V, int nchunks, double *out0, double *out1,
+                           double *out2, double scale2)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const double *p = partial + (size_t)v * nchunks * 4;
+    for (int k = 0; k < nchunks; ++k) {
+        s0 += p[4 * k + 0];
+        s1 += p[4 * k + 1];
+        s2 += p[4 * k + 2];
+    }
+    if (out0) out0[v] = s0;
+    if (out1) out1[v] = s1;
+    if (out2) out2[v] = scale2 * s2;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+template <typename T> RayArgs<T> base_args(const Handle &h)
+{
+    RayArgs<T> a{};
+    a.vg = h.d_views;
+    a.V = h.V;
+    a.N = h.N;
+    a.B = h.B;
+    a.nchunks = h.nchunks;
+    a.Pp = h.Pp;
+    a.PX = (const pair_t<T> *)h.d_px;
+    a.PT = (const pair_t<T> *)h.d_pt;
+    a.pimg_stride = (long long)h.F * h.N * h.Pp;
+    a.kbase = 0;
+    a.ngroups = 1;
+    a.sino_stride = (long long)h.V * h.B;
+    return a;
+}
+
+template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
+cudaError_t run_ray(const Handle &h, const RayArgs<T> &a)
+{
+    auto kern = k_ray<T, MODE, OFFS, KB, SPLIT>;
+    const long long items = (long long)a.ngroups * a.V * a.nchunks;
+    const int grid = persistent_grid(kern, 32 * SPLIT, 0, items, h.num_sms);
+    kern<<<grid, 32 * SPLIT, 0, h.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE, bool OFFS, int KB>
+cudaError_t run_ray_split(const Handle &h, const RayArgs<T> &a, int split)
+{
+    switch (split) {
+    case 1: return run_ray<T, MODE, OFFS, KB, 1>(h, a);
+    case 2: return run_ray<T, MODE, OFFS, KB, 2>(h, a);
+    case 4: return run_ray<T, MODE, OFFS, KB, 4>(h, a);
+    default: return run_ray<T, MODE, OFFS, KB, 8>(h, a);
+    }
+}
+
+template <typename T>
+cudaError_t fwd_groups(const Handle &h, RayArgs<T> a, int kb, int split)
+{
+    switch (kb) {
+    case 1: return run_ray_split<T, kFwd, false, 1>(h, a, split);
+    case 2: return run_ray_split<T, kFwd, false, 2>(h, a, split);
+    case 4: return run_ray_split<T, kFwd, false, 4>(h, a, split);
+    default: return run_ray_split<T, kFwd, false, 8>(h, a, split);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta)
+{
+    const int threads = 128;
+    k_view_setup<<<(h.V + threads - 1) / threads, threads, 0, h.stream>>>(theta, delta, h.d_fov, h.V, h.N, h.B,
+                                                                           h.d_views, h.d_flag);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg)
+{
+    dim3 grid((h.Pp + 31) / 32, (h.N + 31) / 32, std::min(nimg, 65535));
+    k_pairs_img<T><<<grid, 256, 0, h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp, nimg);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino)
+{
+    const long long total = (long long)nsino * h.V * h.Pb;
+    const int threads = 256;
+    const long long blocks = std::min<long long>((total + threads - 1) / threads, (long long)h.num_sms * 16);
+    k_pairs_sino<T><<<(int)std::max<long long>(1, blocks), threads, 0, h.stream>>>(Y, (pair_t<T> *)h.d_yp, h.B,
+                                                                                     h.Pb, total);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split)
+{
+    RayArgs<T> a = base_args<T>(h);
+    a.Y = Y;
+    int k = 0;
+    for (int width : {8, 4, 2, 1}) {
+        if (width > kb) continue;
+        const int groups = (batch - k) / width;
+        if (groups == 0) continue;
+        a.kbase = k;
+        a.ngroups = groups;
+        cudaError_t e = fwd_groups<T>(h, a, width, split);
+        if (e != cudaSuccess) return e;
+        k += groups * width;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split)
+{
+    RayArgs<T> a = base_args<T>(h);
+    a.Y = dY;
+    a.dtheta = dtheta;
+    a.ddelta = ddelta;
+    return ddelta ? run_ray_split<T, kJvp, true, 1>(h, a, split) : run_ray_split<T, kJvp, false, 1>(h, a, split);
+}
+
+template <typename T>
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split)
+{
+    RayArgs<T> a = base_args<T>(h);
+    a.R = R;
+    a.partial = h.d_partial;
+    cudaError_t e = gdelta ? run_ray_split<T, kVjp, true, 1>(h, a, split)
+                           : run_ray_split<T, kVjp, false, 1>(h, a, split);
+    if (e != cudaSuccess) return e;
+    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval, int split)
+{
+    RayArgs<T> a = base_args<T>(h);
+    a.R = bdata;
+    a.res = res;
+    a.partial = h.d_partial;
+    cudaError_t e = run_ray_split<T, kGn, false, 1>(h, a, split);
+    if (e != cudaSuccess) return e;
+    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5);
+    return cudaGetLastError();
+}
+
+#define CTGB_RAY_INSTANTIATE(T)                                                                             \
+    template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int);                              \
+    template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int);                             \
+    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int);                            \
+    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int);          \
+    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int);                \
+    template cudaError_t launch_gn<T>(const Handle &, const T *, T *, double *, double *, double *, int);
+
+CTGB_RAY_INSTANTIATE(float)
+CTGB_RAY_INSTANTIATE(double)
+
+}  // namespace ctgb

@@ -77,11 +77,16 @@ def load_library(path: str | None = None):
     lib.ct_jacT.argtypes = [P, P, P, P, P, P, P]
     lib.ct_gn_terms.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.ct_status.argtypes = [P]
+    lib.ct_set_stream.argtypes = [P, P]
+    lib.ct_autotune.argtypes = [P]
+    lib.ct_get_tuning.argtypes = [P, P]
+    lib.ct_set_tuning.argtypes = [P, P]
     lib.ct_strerror.argtypes = [I]
     lib.ct_strerror.restype = ctypes.c_char_p
     lib.ct_last_cuda_error.argtypes = []
     lib.ct_last_cuda_error.restype = ctypes.c_char_p
-    for f in ("ct_init", "ct_forward", "ct_adjoint", "ct_jac", "ct_jacT", "ct_gn_terms", "ct_status"):
+    for f in ("ct_init", "ct_forward", "ct_adjoint", "ct_jac", "ct_jacT", "ct_gn_terms", "ct_status",
+              "ct_set_stream", "ct_autotune", "ct_get_tuning", "ct_set_tuning"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -148,6 +153,25 @@ def ct_gn_terms(h, theta, delta, x, bdata, res, grad, jnorm2, fval):
 
 def ct_status(h):
     return load_library().ct_status(h)
+
+
+def ct_set_stream(h, stream=None):
+    _check(load_library().ct_set_stream(h, _stream_ptr(stream)), "ct_set_stream")
+
+
+def ct_autotune(h):
+    _check(load_library().ct_autotune(h), "ct_autotune")
+
+
+def ct_get_tuning(h):
+    buf = (ctypes.c_int32 * 5)()
+    _check(load_library().ct_get_tuning(h, buf), "ct_get_tuning")
+    return list(buf)
+
+
+def ct_set_tuning(h, values):
+    buf = (ctypes.c_int32 * 5)(*[int(v) for v in values])
+    _check(load_library().ct_set_tuning(h, buf), "ct_set_tuning")
 
 
 # --- tensor-level wrapper ---------------------------------------------------
@@ -243,3 +267,18 @@ class CTOperator:
 
     def status(self):
         return ct_status(self.h)
+
+    def autotune(self):
+        ct_autotune(self.h)
+        return ct_get_tuning(self.h)
+
+    @property
+    def tuning(self):
+        return ct_get_tuning(self.h)
+
+    @tuning.setter
+    def tuning(self, values):
+        ct_set_tuning(self.h, values)
+
+    def set_stream(self, stream=None):
+        ct_set_stream(self.h, stream)

@@ -199,6 +199,40 @@ def test_large_image_sampled_views(ct):
     assert rel(host(op.adjoint(dev(y, torch.float32), th)), oracle.adjoint(g, theta, y)) <= 1e-5
 
 
+@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1], [2, 4, 2, 2, 2], [8, 8, 8, 4, 8], [4, 2, 1, 4, 4]])
+def test_results_do_not_depend_on_launch_shapes(ct, tuning):
+    N, B, vpf = 40, 59, [7, 13]
+    V = sum(vpf)
+    rng = np.random.default_rng(21)
+    theta = synth.random_angles(V, rng)
+    delta = rng.normal(0, 0.5, V)
+    X = rng.uniform(size=(11, 2 * N * N))
+    Y = rng.standard_normal((11, V * B))
+    dth = rng.standard_normal(V)
+    g = oracle.Geometry(N, B, V, vpf)
+    op = ct.CTOperator(N, B, V, vpf, max_batch=11, dtype=torch.float32)
+    op.tuning = tuning
+    assert op.tuning == tuning
+    th, dl = dev(theta), dev(delta)
+    assert rel(host(op.forward(dev(X, torch.float32), th, dl)), oracle.forward(g, theta, X, delta)) <= 1e-5
+    assert rel(host(op.adjoint(dev(Y, torch.float32), th, dl)), oracle.adjoint(g, theta, Y, delta)) <= 1e-5
+    assert rel(host(op.jac(dev(X[0], torch.float32), th, dev(dth), dl)),
+               oracle.jac(g, theta, X[0], dth, delta)) <= 1e-5
+    gt = host(op.jacT(dev(X[0], torch.float32), th, dev(Y[0], torch.float32), dl))
+    assert rel(gt, oracle.jacT(g, theta, X[0], Y[0], delta)[0]) <= 1e-5
+
+
+def test_autotune_picks_valid_shapes(ct):
+    w = synth.make_workload("C2")
+    op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
+    t = op.autotune()
+    assert len(t) == 5 and all(x in (1, 2, 4, 8) for x in t)
+    th = dev(w.theta_true)
+    x = w.images.reshape(1, -1)
+    g = oracle.Geometry(w.N, w.B, w.V)
+    assert rel(host(op.forward(dev(x, torch.float32), th)), oracle.forward(g, w.theta_true, x)) <= 1e-5
+
+
 def test_argument_errors(ct):
     op = ct.CTOperator(16, 23, 4, max_batch=2)
     th = dev(np.zeros(4))
