@@ -166,6 +166,69 @@ int ct_autotune(ct_handle *h);
 int ct_get_tuning(ct_handle *h, int32_t *out5);
 int ct_set_tuning(ct_handle *h, const int32_t *in5);
 
+/* ------------------------------------------------------------------------
+ * NL-RMM-GKS (alternating form) on the handle's geometry.
+ * ------------------------------------------------------------------------ */
+#define NLRMM_MAX_HIST 256
+
+typedef struct {
+    int32_t k_min;          /* compressed basis size (Sec. 6 default 5); 2 <= k_min <= 17 */
+    int32_t k_max;          /* enlarged basis size (default 25); k_min < k_max <= 62 */
+    int32_t outer_iters;    /* outer iteration limit */
+    int32_t maxiter_p;      /* Gauss-Newton iterations per outer iteration (default 3) */
+    int32_t max_halvings;   /* Armijo backtracking halvings (default 20) */
+    int32_t lam_iters;      /* bisection steps of the discrepancy principle (default 60) */
+    int32_t update_theta;   /* 0: angles fixed (the solve is RMM-GKS) */
+    int32_t stop_on_convergence; /* stop when du < tol_u and dtheta < tol_p */
+    double eps;             /* smoothing of the l1 term, P = diag((z^2 + eps^2)^(-1/4)) (default 1e-3) */
+    double tol1;            /* Enlarge stops when |u_new - u_old| <= tol1 |u_old| (default 1e-3) */
+    double tau;             /* discrepancy safety factor (default 1.01) */
+    double noise_norm;      /* |e| for the discrepancy principle (required unless lam_fix > 0) */
+    double lam_fix;         /* > 0: fixed lambda instead of the discrepancy principle */
+    double lam_lo, lam_hi;  /* log10 bracket of lambda (default -10, 10) */
+    double c1, beta, alpha0;/* Armijo constants (default 1e-4, 0.5, 1) */
+    double mu_rel;          /* damping mu = mu_rel * max_v |J_v|^2 (default 1e-8) */
+    double tol_u, tol_p;    /* outer stopping tolerances (default 1e-3, 1e-4) */
+} nlrmm_opts;
+
+typedef struct {
+    int32_t outer_done;     /* outer iterations run */
+    int32_t converged;      /* stopping rule met */
+    int32_t breakdown;      /* a Cholesky pivot was clamped or a residual vanished */
+    int32_t enlarge_steps[NLRMM_MAX_HIST];
+    double lambda[NLRMM_MAX_HIST];   /* lambda of the last Enlarge step */
+    double du[NLRMM_MAX_HIST];       /* |u_{k+1} - u_k| / |u_k| */
+    double dtheta[NLRMM_MAX_HIST];   /* |theta_{k+1} - theta_k| */
+    double rre[NLRMM_MAX_HIST];      /* |u - x_true| / |x_true| (-1 without x_true) */
+    double ms[NLRMM_MAX_HIST];       /* wall time of the outer iteration, milliseconds */
+} nlrmm_stats;
+
+/* Fill *opts with the defaults above. */
+void nlrmm_default_opts(nlrmm_opts *opts);
+
+/*
+ * Joint reconstruction min_{u,theta} 1/2 |H(theta) u - b|^2 + lambda |Psi u|_1
+ * (Eq. (4.1)) by alternating NL-RMM-GKS (Alg. "NL-RMM-GKS" without the
+ * high-lambda solve): per outer iteration one Enlarge (<= k_max - k_min
+ * MM-GKS steps, lambda by the discrepancy principle on the projected
+ * problem) and one Compress of the generalized Krylov basis at the current
+ * angles, then per-view damped Gauss-Newton with Armijo backtracking on the
+ * angles (Alg. "UPDATE-PARAM"), then the normal-equation residual appended
+ * to the basis.  Psi = forward differences per frame.  The basis starts
+ * from k_min Golub-Kahan steps on b and u starts at zero.
+ *   b [n_views][B] (device, handle precision); theta_inout [n_views] device
+ *   double, initial angles in, estimated angles out; delta [n_views] or NULL
+ *   (fixed offsets); x_out [n_frames][N][N] device; x_true (nullable) for
+ *   the RRE history; stats (host, nullable).
+ * Operators run in the handle's precision; every small matrix is FP64 on the
+ * device.  Allocates its workspace (about (k_max + 2)(n + m) elements) on
+ * entry and frees it on return; synchronises the handle's stream.  Returns
+ * CT_OK, CT_ERR_NOCONV (iteration limit reached with stopping enabled;
+ * outputs valid), CT_ERR_ARG, CT_ERR_OOM or CT_ERR_CUDA.
+ */
+int nlrmm_gks_solve(ct_handle *h, const void *b, double *theta_inout, const double *delta, void *x_out,
+                    const void *x_true, const nlrmm_opts *opts, nlrmm_stats *stats);
+
 /*
  * Synchronise the handle's stream and report device-side conditions found
  * since the last ct_status: CT_ERR_NAN if a non-finite angle or offset was

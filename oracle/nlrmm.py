@@ -1,0 +1,321 @@
+"""FP64 reference of the NL-RMM-GKS solver (AltMin form), written step by step.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Uses the oracle
+operators of this package and numpy's QR / SVD / solve as library steps.
+
+Passages followed:
+  * MM weights P = diag((z^2 + eps^2)^(-1/4)), z = Psi u, and the quadratic
+    majorant (Eq. (3.1)-(3.2), Sec. 3.1);
+  * generalized Krylov projection: QR of H V and P Psi V, the reduced
+    problem (Eq. (3.4)), the normal-equation residual appended to V
+    (Eq. (3.5)-(3.6));
+  * Alg. "Enlarge" and Alg. "Compress" (supplementary Sec. S1.2) and
+    Alg. "RMM-GKS" (Sec. 3.3);
+  * Alg. "UPDATE-PARAM" (damped Gauss-Newton + Armijo backtracking, Sec. 4.1.2);
+  * Alg. "NL-RMM-GKS" (Sec. 4.3) without the optional high-lambda solve.
+
+Readings where the paper is silent (also listed in the design notes):
+  * Psi = forward differences without wrap, horizontal then vertical, per frame;
+  * eps = 1e-3; tol_1 = 1e-3;
+  * lambda by the discrepancy principle on the projected problem:
+    ||H V y(lambda) - b||^2 = (tau * noise_norm)^2, tau = 1.01, bisection in
+    log10(lambda) over [-10, 10] with 60 halvings; if the target is below the
+    smallest reachable residual lambda = 1e-10, if above the largest 1e10;
+  * GKB start vector b, k_min steps, each new right vector reorthogonalized
+    twice against the previous ones;
+  * one Enlarge + Compress per outer iteration; Enlarge starts from the basis
+    carried over (k_min + 1 columns after the residual append) and stops after
+    s = k_max - k_min steps or when ||u_new - u_old|| <= tol_1 ||u_old||;
+  * Compress uses the columns of V that R_H, R_Psi were formed from (the last
+    appended residual has no R entry yet): top k_min - 1 right singular
+    vectors of [R_H; sqrt(lambda) R_Psi], then the normalized part of u
+    orthogonal to them (skipped if it vanishes);
+  * per-view angles make J^T J diagonal: the Gauss-Newton step is per view,
+    d_v = -g_v / (|J_v|^2 + mu) with mu = 1e-8 max_v |J_v|^2, and the Armijo
+    backtracking (c1 = 1e-4, beta = 1/2, alpha_bar = 1, at most 20 halvings,
+    no step if none is accepted) is applied to each view's own data term;
+    3 Gauss-Newton iterations per outer iteration;
+  * the residual appended at the end of an outer iteration uses the operator
+    of that iteration's angles (H_k of Alg. "NL-RMM-GKS");
+  * u^(0) = 0; the relative-change tests are skipped while ||u_old|| = 0;
+  * outer stop: ||du|| / ||u|| < tol_u and ||dtheta|| < tol_p, or the
+    iteration limit.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Geometry, adjoint, dsample, forward
+
+
+# ---------------------------------------------------------------------------
+# regularization operator Psi (finite differences, Sec. 2.2)
+# ---------------------------------------------------------------------------
+def psi(g: Geometry, u: np.ndarray) -> np.ndarray:
+    U = u.reshape(g.F, g.N, g.N)
+    dx = U[:, :, 1:] - U[:, :, :-1]
+    dy = U[:, 1:, :] - U[:, :-1, :]
+    return np.concatenate([dx.ravel(), dy.ravel()])
+
+
+def psi_t(g: Geometry, z: np.ndarray) -> np.ndarray:
+    F, N = g.F, g.N
+    nx = F * N * (N - 1)
+    dx = z[:nx].reshape(F, N, N - 1)
+    dy = z[nx:].reshape(F, N - 1, N)
+    U = np.zeros((F, N, N))
+    U[:, :, 1:] += dx
+    U[:, :, :-1] -= dx
+    U[:, 1:, :] += dy
+    U[:, :-1, :] -= dy
+    return U.ravel()
+
+
+def mm_weights(z: np.ndarray, eps: float) -> np.ndarray:
+    """Diagonal of P^2 = (z^2 + eps^2)^(-1/2) (P itself has exponent -1/4)."""
+    return 1.0 / np.sqrt(z * z + eps * eps)
+
+
+def objective(g, theta, delta, u, b, lam, eps):
+    """J_{eps,lambda}(u, theta) = 1/2 ||H u - b||^2 + lambda sum sqrt((Psi u)^2 + eps^2)."""
+    r = forward(g, theta, u, delta) - b
+    z = psi(g, u)
+    return 0.5 * r @ r + lam * np.sum(np.sqrt(z * z + eps * eps))
+
+
+def majorant(g, theta, delta, u, uk, b, lam, eps):
+    """Q(u | u_k): the quadratic majorant of J_{eps,lambda} at u_k (Eq. (3.2)), constant included."""
+    r = forward(g, theta, u, delta) - b
+    zk = psi(g, uk)
+    sk = np.sqrt(zk * zk + eps * eps)
+    z = psi(g, u)
+    # sqrt(t^2 + eps^2) <= sk + (t^2 - zk^2) / (2 sk) by concavity of sqrt
+    return 0.5 * r @ r + lam * np.sum(sk + (z * z - zk * zk) / (2 * sk))
+
+
+def cgs2(V: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """r - V V^T r, applied twice (classical Gram-Schmidt with reorthogonalization)."""
+    if V.shape[1] == 0:
+        return r
+    r = r - V @ (V.T @ r)
+    return r - V @ (V.T @ r)
+
+
+@dataclass
+class Options:
+    k_min: int = 5
+    k_max: int = 25
+    eps: float = 1e-3
+    tol1: float = 1e-3
+    tau: float = 1.01
+    noise_norm: float | None = None
+    lam_fix: float | None = None
+    lam_lo: float = -10.0
+    lam_hi: float = 10.0
+    lam_iters: int = 60
+    maxiter_p: int = 3
+    c1: float = 1e-4
+    beta: float = 0.5
+    alpha0: float = 1.0
+    max_halvings: int = 20
+    mu_rel: float = 1e-8
+    outer_iters: int = 20
+    tol_u: float = 1e-3
+    tol_p: float = 1e-4
+    update_theta: bool = True
+    stop_on_convergence: bool = True
+    fixed_weights: np.ndarray | None = None   # freeze P^2 (pins only)
+
+
+@dataclass
+class History:
+    lam: list = field(default_factory=list)
+    rre: list = field(default_factory=list)
+    angle_err: list = field(default_factory=list)
+    du: list = field(default_factory=list)
+    dtheta: list = field(default_factory=list)
+    enlarge_steps: list = field(default_factory=list)
+    objective: list = field(default_factory=list)
+
+
+class NLRMMGKS:
+    """Alternating NL-RMM-GKS on the oracle operator."""
+
+    def __init__(self, g: Geometry, b: np.ndarray, opts: Options, delta=None):
+        self.g, self.b, self.o, self.delta = g, np.asarray(b, float), opts, delta
+        self.bnorm2 = float(self.b @ self.b)
+
+    # -- operator wrappers ------------------------------------------------
+    def H(self, theta, x):
+        return forward(self.g, theta, x, self.delta)
+
+    def HT(self, theta, y):
+        return adjoint(self.g, theta, y, self.delta)
+
+    # -- lambda by the discrepancy principle on the projected problem -------
+    def projected_residual2(self, RH, RP, QHb, lam):
+        M = RH.T @ RH + lam * (RP.T @ RP)
+        y = np.linalg.solve(M, RH.T @ QHb)
+        out = RH @ y - QHb
+        return out @ out + (self.bnorm2 - QHb @ QHb), y
+
+    def choose_lambda(self, RH, RP, QHb):
+        o = self.o
+        if o.lam_fix is not None:
+            return o.lam_fix
+        target = (o.tau * o.noise_norm) ** 2
+        lo, hi = o.lam_lo, o.lam_hi
+        if self.projected_residual2(RH, RP, QHb, 10.0 ** lo)[0] >= target:
+            return 10.0 ** lo
+        if self.projected_residual2(RH, RP, QHb, 10.0 ** hi)[0] <= target:
+            return 10.0 ** hi
+        for _ in range(o.lam_iters):
+            mid = 0.5 * (lo + hi)
+            if self.projected_residual2(RH, RP, QHb, 10.0 ** mid)[0] < target:
+                lo = mid
+            else:
+                hi = mid
+        return 10.0 ** (0.5 * (lo + hi))
+
+    # -- initial basis: Golub-Kahan bidiagonalization ----------------------
+    def gkb(self, theta, k):
+        b = self.b
+        u = b / np.linalg.norm(b)
+        v = self.HT(theta, u)
+        alpha = np.linalg.norm(v)
+        v = v / alpha
+        V = [v]
+        for _ in range(1, k):
+            p = self.H(theta, v) - alpha * u
+            beta = np.linalg.norm(p)
+            u = p / beta
+            q = self.HT(theta, u) - beta * v
+            q = cgs2(np.stack(V, 1), q)
+            alpha = np.linalg.norm(q)
+            v = q / alpha
+            V.append(v)
+        return np.stack(V, 1)
+
+    # -- Alg. "Enlarge" -----------------------------------------------------
+    def enlarge(self, theta, V, HV, u0, s):
+        o, g, b = self.o, self.g, self.b
+        u_old = u0
+        lam = None
+        RH = RP = None
+        steps = 0
+        for _ in range(s):
+            w = o.fixed_weights if o.fixed_weights is not None else mm_weights(psi(g, u_old), o.eps)
+            p = np.sqrt(w)
+            QH, RH = np.linalg.qr(HV)
+            PsiV = np.stack([psi(g, V[:, j]) for j in range(V.shape[1])], 1)
+            _, RP = np.linalg.qr(p[:, None] * PsiV)
+            QHb = QH.T @ b
+            lam = self.choose_lambda(RH, RP, QHb)
+            y = np.linalg.solve(RH.T @ RH + lam * (RP.T @ RP), RH.T @ QHb)
+            u = V @ y
+            r = self.HT(theta, self.H(theta, u) - b) + lam * psi_t(g, w * psi(g, u))
+            r = cgs2(V, r)
+            nr = np.linalg.norm(r)
+            steps += 1
+            used = V.shape[1]
+            if nr > 0:
+                vn = r / nr
+                V = np.concatenate([V, vn[:, None]], 1)
+                HV = np.concatenate([HV, self.H(theta, vn)[:, None]], 1)
+            nu = np.linalg.norm(u_old)
+            stop = nr == 0 or (nu > 0 and np.linalg.norm(u - u_old) <= o.tol1 * nu)
+            u_old = u
+            if stop:
+                break
+        return u_old, lam, V, HV, RH, RP, used, steps
+
+    # -- Alg. "Compress" ------------------------------------------------------
+    def compress(self, V, RH, RP, used, lam, u):
+        k_min = self.o.k_min
+        M = np.vstack([RH, np.sqrt(lam) * RP])
+        _, _, Wt = np.linalg.svd(M, full_matrices=False)
+        W = Wt[: k_min - 1].T
+        Vt = V[:, :used] @ W
+        un = u - Vt @ (Vt.T @ u)
+        nn = np.linalg.norm(un)
+        if nn > 1e-14 * max(np.linalg.norm(u), 1e-300):
+            return np.concatenate([Vt, (un / nn)[:, None]], 1)
+        return Vt
+
+    # -- Alg. "UPDATE-PARAM" (per view) ---------------------------------------
+    def view_terms(self, theta, u):
+        g = self.g
+        r = (self.H(theta, u) - self.b).reshape(g.V, g.B)
+        dt, _ = dsample(g, theta, u, self.delta)
+        dt = dt.reshape(g.V, g.B)
+        return (r * dt).sum(1), (dt * dt).sum(1), 0.5 * (r * r).sum(1)
+
+    def view_f(self, theta, u):
+        g = self.g
+        r = (self.H(theta, u) - self.b).reshape(g.V, g.B)
+        return 0.5 * (r * r).sum(1)
+
+    def update_param(self, theta, u):
+        o = self.o
+        theta = theta.copy()
+        for _ in range(o.maxiter_p):
+            grad, jn2, f0 = self.view_terms(theta, u)
+            mu = o.mu_rel * max(float(jn2.max()), 1e-300)
+            d = -grad / (jn2 + mu)
+            alpha = np.full(theta.shape, o.alpha0)
+            active = np.ones(theta.shape, bool)
+            for _h in range(o.max_halvings + 1):
+                ft = self.view_f(theta + alpha * d, u)
+                ok = ft <= f0 + o.c1 * alpha * grad * d
+                active &= ~ok
+                if not active.any():
+                    break
+                alpha[active] *= o.beta
+            alpha[active] = 0.0  # no acceptable step for these views
+            theta = theta + alpha * d
+        return theta
+
+    # -- residual of the normal equations appended to V -----------------------
+    def residual_direction(self, theta, u, lam, V):
+        g = self.g
+        w = self.o.fixed_weights if self.o.fixed_weights is not None else mm_weights(psi(g, u), self.o.eps)
+        r = self.HT(theta, self.H(theta, u) - self.b) + lam * psi_t(g, w * psi(g, u))
+        r = cgs2(V, r)
+        nr = np.linalg.norm(r)
+        return r / nr if nr > 0 else None
+
+    # -- Alg. "NL-RMM-GKS" -------------------------------------------------------
+    def solve(self, theta0, u_true=None, theta_true=None, callback=None):
+        o, g = self.o, self.g
+        theta = np.array(theta0, float)
+        u = np.zeros(g.n)
+        V = self.gkb(theta, o.k_min)
+        hist = History()
+        s = o.k_max - o.k_min
+        lam = None
+        for it in range(o.outer_iters):
+            HV = np.stack([self.H(theta, V[:, j]) for j in range(V.shape[1])], 1)
+            u_new, lam, Vg, _, RH, RP, used, steps = self.enlarge(theta, V, HV, u, s)
+            Vk = self.compress(Vg, RH, RP, used, lam, u_new)
+            theta_new = self.update_param(theta, u_new) if o.update_theta else theta.copy()
+            vn = self.residual_direction(theta, u_new, lam, Vk)
+            V = Vk if vn is None else np.concatenate([Vk, vn[:, None]], 1)
+            nu = np.linalg.norm(u)
+            du = np.linalg.norm(u_new - u) / nu if nu > 0 else np.inf
+            dth = float(np.linalg.norm(theta_new - theta))
+            hist.lam.append(lam)
+            hist.du.append(du)
+            hist.dtheta.append(dth)
+            hist.enlarge_steps.append(steps)
+            if u_true is not None:
+                hist.rre.append(float(np.linalg.norm(u_new - u_true) / np.linalg.norm(u_true)))
+            if theta_true is not None:
+                hist.angle_err.append(float(np.linalg.norm(theta_new - theta_true) / np.linalg.norm(theta_true)))
+            u, theta = u_new, theta_new
+            if callback:
+                callback(it, u, theta, V, lam)
+            if o.stop_on_convergence and du < o.tol_u and dth < o.tol_p:
+                break
+        return u, theta, hist

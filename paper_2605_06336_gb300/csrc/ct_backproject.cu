@@ -42,6 +42,7 @@ template <typename T> struct AdjArgs {
     int kbase, ngroups;
     T *X;
     long long img_stride;    // F * N * N
+    const int *skip;         // whole launch is a no-op when *skip != 0 (nullable)
 };
 
 template <typename T, int KB, int SPLIT>
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(256 * SPLIT) k_adjoint(AdjArgs<T> a)
     const int tiles = a.tps * a.tps;
     const int total = a.ngroups * a.F * tiles;
     const int N = a.N;
+    if (a.skip && *a.skip) return;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int tile = item % tiles;
         const int t2 = item / tiles;
@@ -151,9 +153,11 @@ cudaError_t run_adj_split(const Handle &h, const AdjArgs<T> &a, int split)
 
 }  // namespace
 
-template <typename T> cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split)
+template <typename T>
+cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip)
 {
     AdjArgs<T> a{};
+    a.skip = skip;
     a.vg = h.d_views;
     a.fstart = h.d_fstart;
     a.fcount = h.d_fcount;
@@ -186,7 +190,7 @@ template <typename T> cudaError_t launch_adjoint(const Handle &h, T *X, int batc
     return cudaSuccess;
 }
 
-template cudaError_t launch_adjoint<float>(const Handle &, float *, int, int, int);
-template cudaError_t launch_adjoint<double>(const Handle &, double *, int, int, int);
+template cudaError_t launch_adjoint<float>(const Handle &, float *, int, int, int, const int *);
+template cudaError_t launch_adjoint<double>(const Handle &, double *, int, int, int, const int *);
 
 }  // namespace ctgb

@@ -90,19 +90,26 @@ struct Handle {
 };
 
 // Kernel launchers.  All launch on h.stream and return the launch status.
-cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta);
+// `skip` (nullable, device) lets a caller that runs a fixed launch sequence
+// (the solver's predicated Enlarge steps) turn a launch into a no-op: when
+// *skip != 0 the kernel returns at once.
+cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta,
+                              const int *skip = nullptr);
 
-template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg);
-template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino);
+template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip = nullptr);
+template <typename T>
+cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip = nullptr);
 
-template <typename T> cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split);
-template <typename T> cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split);
+template <typename T>
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, const int *skip = nullptr);
+template <typename T>
+cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip = nullptr);
 template <typename T>
 cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split);
 template <typename T>
 cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split);
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval,
-                      int split);
+                      int split, const int *view_mask = nullptr, const int *skip = nullptr);
 
 }  // namespace ctgb

@@ -30,10 +30,10 @@ namespace {
 // ---------------------------------------------------------------------------
 __global__ void k_view_setup(const double *__restrict__ theta, const double *__restrict__ delta,
                              const int *__restrict__ fov, int V, int N, int B, ViewGeo *__restrict__ out,
-                             int *__restrict__ flag)
+                             int *__restrict__ flag, const int *__restrict__ skip)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
+    if (v >= V || (skip && *skip)) return;
     double th = theta[v];
     double dl = delta ? delta[v] : 0.0;
     ViewGeo *gp = out + v;
@@ -115,8 +115,10 @@ __global__ void k_view_setup(const double *__restrict__ theta, const double *__r
 // PT[img][r][cp] = (X[c][r], X[c+1][r]) with c = cp - 2, zero outside.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair_t<T> *__restrict__ PX,
-                                                   pair_t<T> *__restrict__ PT, int N, int Pp, int nimg)
+                                                   pair_t<T> *__restrict__ PT, int N, int Pp, int nimg,
+                                                   const int *__restrict__ skip)
 {
+    if (skip && *skip) return;
     __shared__ T a[32][34];   // a[i][j] = X[r0 + i][c0 + j]
     __shared__ T bt[33][33];  // bt[i][j] = X[c0 + i][r0 + j]
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -156,8 +158,10 @@ __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair
 
 // YP[row][bp] = (Y[row][bp - 2], Y[row][bp - 1]), zero outside [0, B).
 template <typename T>
-__global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP, int B, int Pb, long long total)
+__global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP, int B, int Pb, long long total,
+                             const int *__restrict__ skip)
 {
+    if (skip && *skip) return;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long row = idx / Pb;
@@ -188,6 +192,8 @@ template <typename T> struct RayArgs {
     const T *R;             // VJP: r; GN: data b
     T *res;                 // GN: residual (nullable)
     double *partial;        // VJP / GN
+    const int *view_mask;   // GN: views with mask 0 are skipped (nullable)
+    const int *skip;        // whole launch is a no-op when *skip != 0 (nullable)
 };
 
 // Warp-uniform row range [rlo, rhi] covering every row where one of the
@@ -223,11 +229,13 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray(RayArgs<T> a)
     const int seg = threadIdx.x >> 5;
     const int N = a.N;
     const int total = a.ngroups * a.V * a.nchunks;
+    if (a.skip && *a.skip) return;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int chunk = item % a.nchunks;
         const int t = item / a.nchunks;
         const int v = t % a.V;
         const int grp = t / a.V;
+        if (MODE == kGn && a.view_mask && a.view_mask[v] == 0) continue;  // uniform per CTA
         const ViewGeo &g = a.vg[v];
         const int b = chunk * kChunk + lane;
         const bool active = b < a.B;
@@ -346,10 +354,11 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray(RayArgs<T> a)
 
 // out_q[v] = scale_q * sum_c partial[v][c][q], summed in chunk order.
 __global__ void k_finalize(const double *__restrict__ partial, int V, int nchunks, double *out0, double *out1,
-                           double *out2, double scale2)
+                           double *out2, double scale2, const int *__restrict__ view_mask,
+                           const int *__restrict__ skip)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
+    if (v >= V || (skip && *skip) || (view_mask && view_mask[v] == 0)) return;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     const double *p = partial + (size_t)v * nchunks * 4;
     for (int k = 0; k < nchunks; ++k) {
@@ -417,35 +426,38 @@ cudaError_t fwd_groups(const Handle &h, RayArgs<T> a, int kb, int split)
 
 }  // namespace
 
-cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta)
+cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta, const int *skip)
 {
     const int threads = 128;
     k_view_setup<<<(h.V + threads - 1) / threads, threads, 0, h.stream>>>(theta, delta, h.d_fov, h.V, h.N, h.B,
-                                                                           h.d_views, h.d_flag);
+                                                                           h.d_views, h.d_flag, skip);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg)
+template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip)
 {
     dim3 grid((h.Pp + 31) / 32, (h.N + 31) / 32, std::min(nimg, 65535));
-    k_pairs_img<T><<<grid, 256, 0, h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp, nimg);
+    k_pairs_img<T><<<grid, 256, 0, h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp, nimg,
+                                               skip);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino)
+template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip)
 {
     const long long total = (long long)nsino * h.V * h.Pb;
     const int threads = 256;
     const long long blocks = std::min<long long>((total + threads - 1) / threads, (long long)h.num_sms * 16);
     k_pairs_sino<T><<<(int)std::max<long long>(1, blocks), threads, 0, h.stream>>>(Y, (pair_t<T> *)h.d_yp, h.B,
-                                                                                     h.Pb, total);
+                                                                                     h.Pb, total, skip);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split)
+template <typename T>
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, const int *skip)
 {
     RayArgs<T> a = base_args<T>(h);
     a.Y = Y;
+    a.skip = skip;
     int k = 0;
     for (int width : {8, 4, 2, 1}) {
         if (width > kb) continue;
@@ -479,30 +491,36 @@ cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdel
     cudaError_t e = gdelta ? run_ray_split<T, kVjp, true, 1>(h, a, split)
                            : run_ray_split<T, kVjp, false, 1>(h, a, split);
     if (e != cudaSuccess) return e;
-    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0);
+    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0,
+                                                        nullptr, nullptr);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval, int split)
+cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval, int split,
+                      const int *view_mask, const int *skip)
 {
     RayArgs<T> a = base_args<T>(h);
     a.R = bdata;
     a.res = res;
     a.partial = h.d_partial;
+    a.view_mask = view_mask;
+    a.skip = skip;
     cudaError_t e = run_ray_split<T, kGn, false, 1>(h, a, split);
     if (e != cudaSuccess) return e;
-    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5);
+    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5,
+                                                        view_mask, skip);
     return cudaGetLastError();
 }
 
 #define CTGB_RAY_INSTANTIATE(T)                                                                             \
-    template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int);                              \
-    template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int);                             \
-    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int);                            \
+    template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int, const int *);                 \
+    template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int, const int *);                \
+    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, const int *);               \
     template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int);          \
     template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int);                \
-    template cudaError_t launch_gn<T>(const Handle &, const T *, T *, double *, double *, double *, int);
+    template cudaError_t launch_gn<T>(const Handle &, const T *, T *, double *, double *, double *, int,    \
+                                      const int *, const int *);
 
 CTGB_RAY_INSTANTIATE(float)
 CTGB_RAY_INSTANTIATE(double)

@@ -1,0 +1,534 @@
+// nlrmm_gks_solve: the alternating NL-RMM-GKS driver on the GPU.
+//
+// Algorithms followed: "NL-RMM-GKS" (Sec. 4.3, without the optional
+// high-lambda solve), "RMM-GKS" (Sec. 3.3) with "Enlarge" and "Compress"
+// (supplementary Sec. S1.2), "UPDATE-PARAM" (Sec. 4.1.2).  Operators are the
+// ct kernels of this library in the handle's precision; every small matrix
+// (k <= 64) is FP64 on the device.
+//
+// Differences from the printed form, none of which changes the iterates in
+// exact arithmetic:
+//   * R_H and R_Psi enter the reduced problem and the Compress SVD only as
+//     R_H^T R_H = (HV)^T HV, R_Psi^T R_Psi = (P Psi V)^T (P Psi V) and
+//     R_H^T Q_H^T b = (HV)^T b, so those FP64 Gram products are formed
+//     directly; (HV)^T HV and (HV)^T b grow by one row per Enlarge step.
+//   * lambda is found on the generalized eigenbasis of the two Gram
+//     matrices, where the projected discrepancy is a closed-form sum.
+//   * H u is formed as (HV) y (no extra projection per step).
+//   * An Enlarge step is a fixed launch sequence predicated on a device stop
+//     flag (no host round trip inside Enlarge).
+//   * With per-view angles J^T J is diagonal, so the Gauss-Newton step and
+//     its Armijo backtracking are per view.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ctgb.h"
+#include "ct_internal.cuh"
+#include "ct_solver_kernels.cuh"
+
+struct ct_handle {
+    ctgb::Handle h;
+};
+
+namespace {
+
+using namespace ctgb;
+using namespace ctgb::solver;
+
+thread_local char g_solver_msg[256] = "";
+
+#define SV_CUDA(call)                                                                                     \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) {                                                                          \
+            std::snprintf(g_solver_msg, sizeof(g_solver_msg), "%s:%d %s", __FILE__, __LINE__,             \
+                          cudaGetErrorString(e_));                                                        \
+            return CT_ERR_CUDA;                                                                           \
+        }                                                                                                 \
+    } while (0)
+
+#define SV_TRY(expr)                  \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != CT_OK) return rc_; \
+    } while (0)
+
+constexpr int kThreads = 256;
+
+template <typename T> struct Solver {
+    Handle &h;
+    const nlrmm_opts &o;
+    const T *b;
+    const double *delta;
+    long long n = 0, m = 0, ne = 0;
+    int KC = 0;         // basis capacity (columns)
+    int gram_blocks = 0;
+    std::vector<void *> allocs;
+    // device buffers
+    T *V = nullptr, *HV = nullptr, *u = nullptr, *uold = nullptr, *uprev = nullptr, *w = nullptr, *res = nullptr,
+      *Vtmp = nullptr;
+    double *GH = nullptr, *GP = nullptr, *cvec = nullptr, *y = nullptr, *W = nullptr, *dots = nullptr,
+           *part_gram = nullptr, *part_dot = nullptr, *part_n = nullptr, *norms = nullptr, *norms2 = nullptr,
+           *scal = nullptr;
+    double *th_k = nullptr, *th_n = nullptr, *th_t = nullptr, *d = nullptr, *alpha = nullptr, *g = nullptr,
+           *j2 = nullptr, *f0 = nullptr, *ft = nullptr, *scratch_v = nullptr;
+    int *ctl = nullptr, *active = nullptr;
+    int *h_ctl = nullptr;       // pinned mirror of ctl
+    double *h_scal = nullptr;   // pinned mirror of small results
+
+    Solver(Handle &h_, const nlrmm_opts &o_, const T *b_, const double *delta_) : h(h_), o(o_), b(b_), delta(delta_) {}
+
+    ~Solver()
+    {
+        for (void *p : allocs) cudaFree(p);
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_scal) cudaFreeHost(h_scal);
+    }
+
+    template <typename U> int alloc(U *&p, size_t count)
+    {
+        void *q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(1, count) * sizeof(U)) != cudaSuccess) {
+            cudaGetLastError();
+            return CT_ERR_OOM;
+        }
+        allocs.push_back(q);
+        p = (U *)q;
+        return CT_OK;
+    }
+
+    int grid_for(long long len) const
+    {
+        return (int)std::max<long long>(1, std::min<long long>((len + kThreads - 1) / kThreads, 8LL * h.num_sms));
+    }
+
+    int setup()
+    {
+        n = (long long)h.F * h.N * h.N;
+        m = (long long)h.V * h.B;
+        ne = 2LL * h.F * h.N * (h.N - 1);
+        KC = o.k_max + 2;
+        const int tiles = ((h.N + 31) / 32) * ((h.N + (sizeof(T) == 4 ? 8 : 4) - 1) / (sizeof(T) == 4 ? 8 : 4)) * h.F;
+        gram_blocks = std::min(tiles, 2 * h.num_sms);
+        SV_TRY(alloc(V, (size_t)KC * n));
+        SV_TRY(alloc(HV, (size_t)KC * m));
+        SV_TRY(alloc(u, n));
+        SV_TRY(alloc(uold, n));
+        SV_TRY(alloc(uprev, n));
+        SV_TRY(alloc(w, ne));
+        SV_TRY(alloc(res, m));
+        SV_TRY(alloc(Vtmp, (size_t)o.k_min * n));
+        SV_TRY(alloc(GH, kKMax * kKMax));
+        SV_TRY(alloc(GP, kKMax * kKMax));
+        SV_TRY(alloc(cvec, kKMax + 2));
+        SV_TRY(alloc(y, kKMax + 2));
+        SV_TRY(alloc(W, kKMax * kKMax));
+        SV_TRY(alloc(dots, kKMax + 2));
+        SV_TRY(alloc(part_gram, (size_t)gram_blocks * kGramPairs));
+        SV_TRY(alloc(part_dot, (size_t)kRedBlocks * (kKMax + 2)));
+        SV_TRY(alloc(part_n, (size_t)kRedBlocks * 3));
+        SV_TRY(alloc(norms, 3));
+        SV_TRY(alloc(norms2, 3));
+        SV_TRY(alloc(scal, kScalCount));
+        for (double **p : {&th_k, &th_n, &th_t, &d, &alpha, &g, &j2, &f0, &ft, &scratch_v}) SV_TRY(alloc(*p, h.V));
+        SV_TRY(alloc(ctl, kCtlCount));
+        SV_TRY(alloc(active, h.V));
+        if (cudaMallocHost(&h_ctl, sizeof(int) * kCtlCount) != cudaSuccess ||
+            cudaMallocHost(&h_scal, sizeof(double) * 16) != cudaSuccess) {
+            cudaGetLastError();
+            return CT_ERR_OOM;
+        }
+        SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
+        SV_CUDA(cudaMemsetAsync(GP, 0, sizeof(double) * kKMax * kKMax, h.stream));
+        SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
+        SV_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kScalCount, h.stream));
+        const size_t small_smem = sizeof(SmallShared);
+        SV_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+        SV_CUDA(cudaFuncSetAttribute(k_compress_basis, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)small_smem));
+        SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, sizeof(T) == 4 ? 8 : 4>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem(kKMax)));
+        return CT_OK;
+    }
+
+    static size_t gram_smem(int k)
+    {
+        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
+        return (size_t)k * (2 * TR * 32 + 1) * sizeof(T);
+    }
+
+    T *col(T *base, long long len, int j) const { return base + (long long)j * len; }
+
+    // ---- building blocks --------------------------------------------------
+    // out[0..k) = A[:, 0..k)^T x  (+ out[k] = x2 . x when x2 != null)
+    int dots_into(const T *A, long long len, int k, const T *x, const T *x2, double *out, const int *stop)
+    {
+        k_dots<T><<<kRedBlocks, kThreads, 0, h.stream>>>(A, len, len, k, x, x2, part_dot, stop);
+        k_dots_reduce<<<1, kKMax + 2, 0, h.stream>>>(part_dot, kRedBlocks, k + (x2 ? 1 : 0), out, stop);
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // norms3 of (a, b): {|a|^2, |a-b|^2, |b|^2}
+    int norms3(const T *a, const T *bb, long long len, double *out, const int *stop)
+    {
+        k_norms3<T><<<kRedBlocks, kThreads, 0, h.stream>>>(a, bb, len, part_n, stop);
+        k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, out, stop);
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // r <- r - V[:, :k] V[:, :k]^T r, twice
+    int cgs2(T *r, int k, const int *stop)
+    {
+        if (k == 0) return CT_OK;
+        for (int pass = 0; pass < 2; ++pass) {
+            SV_TRY(dots_into(V, n, k, r, nullptr, dots, stop));
+            k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, dots, r, T(1), T(-1), nullptr, T(0),
+                                                                stop);
+        }
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // HV[:, j0:j0+cnt) = H(theta) V[:, j0:j0+cnt), in chunks of max_batch columns
+    int project(const double *theta, int j0, int cnt, const int *stop)
+    {
+        SV_CUDA(launch_view_setup(h, theta, delta, stop));
+        for (int j = j0; j < j0 + cnt; j += h.max_batch) {
+            const int nb = std::min(h.max_batch, j0 + cnt - j);
+            SV_CUDA(launch_pairs_img<T>(h, col(V, n, j), nb * h.F, stop));
+            SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, stop));
+        }
+        return CT_OK;
+    }
+
+    // out = H(theta)^T yin  (n vector)
+    int backproject(const double *theta, const T *yin, T *out, const int *stop)
+    {
+        SV_CUDA(launch_view_setup(h, theta, delta, stop));
+        SV_CUDA(launch_pairs_sino<T>(h, yin, 1, stop));
+        SV_CUDA(launch_adjoint<T>(h, out, 1, h.tune.adj_kb, h.tune.adj_split, stop));
+        return CT_OK;
+    }
+
+    int sync_ctl()
+    {
+        SV_CUDA(cudaMemcpyAsync(h_ctl, ctl, sizeof(int) * kCtlCount, cudaMemcpyDeviceToHost, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        return CT_OK;
+    }
+
+    int read_doubles(const double *src, int cnt, double *dst)
+    {
+        SV_CUDA(cudaMemcpyAsync(h_scal, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        std::memcpy(dst, h_scal, sizeof(double) * cnt);
+        return CT_OK;
+    }
+
+    // ---- Golub-Kahan bidiagonalization start basis --------------------------
+    int gkb(const double *theta, int k)
+    {
+        double nb[3];
+        SV_TRY(norms3(b, nullptr, m, norms, nullptr));
+        SV_TRY(read_doubles(norms, 3, nb));
+        const double bn = std::sqrt(nb[0]);
+        if (!(bn > 0.0)) return CT_ERR_ARG;
+        // ubuf (m) = b / |b| ; v = H^T ubuf
+        T *ubuf = res;
+        SV_CUDA(cudaMemcpyAsync(ubuf, b, sizeof(T) * m, cudaMemcpyDeviceToDevice, h.stream));
+        scale(ubuf, m, 1.0 / bn);
+        SV_TRY(backproject(theta, ubuf, col(V, n, 0), nullptr));
+        double nv[3];
+        SV_TRY(norms3(col(V, n, 0), nullptr, n, norms, nullptr));
+        SV_TRY(read_doubles(norms, 3, nv));
+        double alpha_ = std::sqrt(nv[0]);
+        scale(col(V, n, 0), n, 1.0 / alpha_);
+        for (int j = 1; j < k; ++j) {
+            // p = H v_{j-1} - alpha u ; beta = |p| ; u = p / beta
+            SV_TRY(project(theta, j - 1, 1, nullptr));
+            axpby(ubuf, col(HV, m, j - 1), m, -alpha_, 1.0);  // ubuf = HV[:, j-1] - alpha * ubuf
+            SV_TRY(norms3(ubuf, nullptr, m, norms, nullptr));
+            SV_TRY(read_doubles(norms, 3, nv));
+            const double beta_ = std::sqrt(nv[0]);
+            scale(ubuf, m, 1.0 / beta_);
+            // q = H^T u - beta v_{j-1}, reorthogonalized
+            SV_TRY(backproject(theta, ubuf, col(V, n, j), nullptr));
+            axpby(col(V, n, j), col(V, n, j - 1), n, 1.0, -beta_);  // V_j = V_j - beta V_{j-1}
+            SV_TRY(cgs2(col(V, n, j), j, nullptr));
+            SV_TRY(norms3(col(V, n, j), nullptr, n, norms, nullptr));
+            SV_TRY(read_doubles(norms, 3, nv));
+            alpha_ = std::sqrt(nv[0]);
+            scale(col(V, n, j), n, 1.0 / alpha_);
+        }
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // small elementwise helpers (host-known scalars)
+    void scale(T *x, long long len, double s)
+    {
+        k_gemv<T><<<grid_for(len), kThreads, 0, h.stream>>>(x, len, len, 0, y, x, (T)s, T(0), nullptr, T(0),
+                                                              nullptr);
+    }
+    // x = a*x + c*z
+    void axpby(T *x, const T *z, long long len, double a, double c)
+    {
+        k_gemv<T><<<grid_for(len), kThreads, 0, h.stream>>>(x, len, len, 0, y, x, (T)a, T(0), z, (T)c, nullptr);
+    }
+
+    // ---- one predicated Enlarge step with kc basis columns ------------------
+    int enlarge_step(const double *theta, int kc)
+    {
+        const int *stop = ctl + kStop;
+        const int gblk = gram_blocks;
+        // P^2 from the previous iterate
+        k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(uold, w, h.N, h.F, o.eps, stop);
+        // G_P = (P Psi V)^T (P Psi V)
+        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
+        k_gram_psi<T, TR><<<gblk, kThreads, gram_smem(kc), h.stream>>>(V, n, kc, w, h.N, h.F, part_gram, stop);
+        k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gblk, kc, GP, stop);
+        // lambda and the reduced solution
+        const double target = (o.tau * o.noise_norm) * (o.tau * o.noise_norm);
+        k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
+                                                                     o.lam_lo, o.lam_hi, o.lam_iters, y, scal, ctl);
+        // u = V y ; res = (HV) y - b
+        k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, kc, y, u, T(0), T(1), nullptr, T(0), stop);
+        k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, kc, y, res, T(0), T(1), b, T(-1), stop);
+        SV_CUDA(cudaGetLastError());
+        // r = H^T res + lambda Psi^T P^2 Psi u, written straight into the next basis column
+        T *r = col(V, n, kc);
+        SV_TRY(backproject(theta, res, r, stop));
+        k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(r, u, w, scal, h.N, h.F, stop);
+        SV_TRY(cgs2(r, kc, stop));
+        SV_TRY(norms3(r, nullptr, n, norms2, stop));        // |r|^2
+        SV_TRY(norms3(u, uold, n, norms, stop));            // |u|^2, |u - u_old|^2, |u_old|^2
+        k_step_decide<<<1, 1, 0, h.stream>>>(norms2, norms, o.tol1, ctl, scal);
+        k_normalize<T><<<grid_for(n), kThreads, 0, h.stream>>>(r, n, norms2, stop);
+        // H v_new and the new row of (HV)^T HV, (HV)^T b
+        SV_TRY(project(theta, kc, 1, stop));
+        SV_TRY(dots_into(HV, m, kc + 1, col(HV, m, kc), b, dots, stop));
+        k_gh_append<<<1, kKMax + 2, 0, h.stream>>>(dots, kc, GH, cvec, stop);
+        SV_CUDA(cudaMemcpyAsync(uold, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));  // (u_old = u)
+        k_step_commit<<<1, 1, 0, h.stream>>>(ctl);
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    double bnorm2 = 0.0;
+
+    int full_gram(int kc)
+    {
+        // (HV)^T HV and (HV)^T b from scratch
+        for (int j = 0; j < kc; ++j) {
+            SV_TRY(dots_into(HV, m, j + 1, col(HV, m, j), b, dots, nullptr));
+            k_gh_append<<<1, kKMax + 2, 0, h.stream>>>(dots, j, GH, cvec, nullptr);
+        }
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // ---- Gauss-Newton / Armijo per view ---------------------------------------
+    int update_param(const T *uimg)
+    {
+        SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        for (int it = 0; it < o.maxiter_p; ++it) {
+            SV_CUDA(launch_view_setup(h, th_n, delta));
+            SV_CUDA(launch_pairs_img<T>(h, uimg, h.F));
+            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split));
+            k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
+                                                     ctl);
+            for (int hv = 0; hv <= o.max_halvings; ++hv) {
+                SV_CUDA(launch_view_setup(h, th_t, delta));
+                SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, active));
+                k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, th_n, h.V, o.c1, o.beta, alpha, th_t, active, ctl,
+                                                   hv == o.max_halvings ? 1 : 0);
+                SV_TRY(sync_ctl());
+                if (h_ctl[kActive] == 0) break;
+            }
+            SV_CUDA(cudaMemcpyAsync(th_n, th_t, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        }
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // ---- the whole solve ---------------------------------------------------------
+    int run(double *theta_io, void *x_out, const T *x_true, nlrmm_stats *st)
+    {
+        SV_TRY(setup());
+        double nb[3];
+        SV_TRY(norms3(b, nullptr, m, norms, nullptr));
+        SV_TRY(read_doubles(norms, 3, nb));
+        bnorm2 = nb[0];
+        double xt2 = 0.0;
+        if (x_true) {
+            SV_TRY(norms3(x_true, nullptr, n, norms, nullptr));
+            SV_TRY(read_doubles(norms, 3, nb));
+            xt2 = nb[0];
+        }
+        SV_CUDA(cudaMemcpyAsync(th_k, theta_io, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        SV_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * n, h.stream));
+        SV_CUDA(cudaMemsetAsync(uold, 0, sizeof(T) * n, h.stream));
+        SV_CUDA(cudaMemsetAsync(uprev, 0, sizeof(T) * n, h.stream));
+        SV_TRY(gkb(th_k, o.k_min));
+        int kc = o.k_min;
+        const int s = o.k_max - o.k_min;
+        int rc_final = CT_ERR_NOCONV;
+        if (st) {
+            std::memset(st, 0, sizeof(*st));
+        }
+        for (int it = 0; it < o.outer_iters; ++it) {
+            const auto t0 = std::chrono::steady_clock::now();
+            // H(theta_k) V and its Gram data
+            SV_TRY(project(th_k, 0, kc, nullptr));
+            SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
+            SV_TRY(full_gram(kc));
+            SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
+            // Enlarge: s predicated steps
+            for (int step = 0; step < s && kc + step + 1 < KC; ++step) SV_TRY(enlarge_step(th_k, kc + step));
+            SV_TRY(sync_ctl());
+            const int steps = h_ctl[kSteps];
+            const int k_used = kc + steps - 1;  // columns the last reduced problem used
+            // Compress
+            const int keep = std::min(o.k_min - 1, k_used);
+            k_compress_basis<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, GP, k_used, scal, keep, W);
+            k_gemm_small<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k_used, W, keep, Vtmp, n);
+            SV_CUDA(cudaMemcpyAsync(V, Vtmp, sizeof(T) * n * keep, cudaMemcpyDeviceToDevice, h.stream));
+            SV_TRY(dots_into(V, n, keep, u, nullptr, dots, nullptr));
+            k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, keep, dots, col(V, n, keep), T(0), T(-1), u,
+                                                                T(1), nullptr);
+            SV_TRY(norms3(col(V, n, keep), u, n, norms, nullptr));
+            double nu[3];
+            SV_TRY(read_doubles(norms, 3, nu));
+            kc = keep;
+            if (std::sqrt(nu[0]) > 1e-14 * std::max(std::sqrt(nu[2]), 1e-300)) {
+                scale(col(V, n, keep), n, 1.0 / std::sqrt(nu[0]));
+                kc = keep + 1;
+            }
+            // parameter update
+            if (o.update_theta) {
+                SV_TRY(update_param(u));
+            } else {
+                SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+            }
+            // residual of the normal equations at H_k, new weights, appended to V
+            k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.eps, nullptr);
+            SV_CUDA(launch_view_setup(h, th_k, delta));
+            SV_CUDA(launch_pairs_img<T>(h, u, h.F));
+            SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split));
+            axpby(res, b, m, 1.0, -1.0);
+            SV_TRY(backproject(th_k, res, col(V, n, kc), nullptr));
+            k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(col(V, n, kc), u, w, scal, h.N, h.F, nullptr);
+            SV_TRY(cgs2(col(V, n, kc), kc, nullptr));
+            SV_TRY(norms3(col(V, n, kc), nullptr, n, norms2, nullptr));
+            // convergence data
+            SV_TRY(norms3(u, uprev, n, norms, nullptr));
+            double du3[3], dr[3], lam_now[1];
+            SV_TRY(read_doubles(norms, 3, du3));
+            SV_TRY(read_doubles(norms2, 3, dr));
+            SV_TRY(read_doubles(scal + kLam, 1, lam_now));
+            if (dr[0] > 0.0) {
+                scale(col(V, n, kc), n, 1.0 / std::sqrt(dr[0]));
+                kc += 1;
+            }
+            k_norms3<double><<<kRedBlocks, kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
+            k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, norms, nullptr);
+            double dth3[3];
+            SV_TRY(read_doubles(norms, 3, dth3));
+            double rre = -1.0;
+            if (x_true) {
+                SV_TRY(norms3(u, x_true, n, norms, nullptr));
+                double e3[3];
+                SV_TRY(read_doubles(norms, 3, e3));
+                rre = std::sqrt(e3[1] / std::max(xt2, 1e-300));
+            }
+            const double du = du3[2] > 0.0 ? std::sqrt(du3[1] / du3[2]) : INFINITY;
+            const double dth = std::sqrt(dth3[1]);
+            SV_CUDA(cudaMemcpyAsync(th_k, th_n, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+            SV_CUDA(cudaMemcpyAsync(uprev, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
+            SV_CUDA(cudaStreamSynchronize(h.stream));
+            const double ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (st) {
+                st->outer_done = it + 1;
+                if (it < NLRMM_MAX_HIST) {
+                    st->enlarge_steps[it] = steps;
+                    st->lambda[it] = lam_now[0];
+                    st->du[it] = du;
+                    st->dtheta[it] = dth;
+                    st->rre[it] = rre;
+                    st->ms[it] = ms;
+                }
+                st->breakdown |= h_ctl[kBreakdown];
+            }
+            if (o.stop_on_convergence && du < o.tol_u && dth < o.tol_p) {
+                rc_final = CT_OK;
+                if (st) st->converged = 1;
+                break;
+            }
+        }
+        if (!o.stop_on_convergence) rc_final = CT_OK;
+        SV_CUDA(cudaMemcpyAsync(x_out, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
+        SV_CUDA(cudaMemcpyAsync(theta_io, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        return rc_final;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void nlrmm_default_opts(nlrmm_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->k_min = 5;
+    o->k_max = 25;
+    o->outer_iters = 20;
+    o->maxiter_p = 3;
+    o->max_halvings = 20;
+    o->lam_iters = 60;
+    o->update_theta = 1;
+    o->stop_on_convergence = 1;
+    o->eps = 1e-3;
+    o->tol1 = 1e-3;
+    o->tau = 1.01;
+    o->noise_norm = 0.0;
+    o->lam_fix = 0.0;
+    o->lam_lo = -10.0;
+    o->lam_hi = 10.0;
+    o->c1 = 1e-4;
+    o->beta = 0.5;
+    o->alpha0 = 1.0;
+    o->mu_rel = 1e-8;
+    o->tol_u = 1e-3;
+    o->tol_p = 1e-4;
+}
+
+int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const double *delta, void *x_out,
+                    const void *x_true, const nlrmm_opts *opts, nlrmm_stats *stats)
+{
+    if (!H || !b || !theta_inout || !x_out || !opts) return CT_ERR_ARG;
+    const nlrmm_opts &o = *opts;
+    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min - 1 > 16 ||
+        o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
+        !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
+        return CT_ERR_ARG;
+    ctgb::Handle &h = H->h;
+    if (h.precision) {
+        Solver<double> s(h, o, (const double *)b, delta);
+        return s.run(theta_inout, x_out, (const double *)x_true, stats);
+    }
+    Solver<float> s(h, o, (const float *)b, delta);
+    return s.run(theta_inout, x_out, (const float *)x_true, stats);
+}
+
+}  // extern "C"

@@ -1,0 +1,741 @@
+// Device kernels of the NL-RMM-GKS driver (included by ct_solver.cu only).
+//
+// Vectors of the image space have n = F*N*N entries, of the data space
+// m = V*B entries; a basis V (and H V) is stored column by column, each column
+// contiguous, in the working precision T.  Small matrices (k <= kKMax) are
+// FP64.  Every kernel that belongs to a predicated Enlarge step takes the
+// device flag `stop` and returns at once when it is set, so a fixed launch
+// sequence can run without host round trips.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "ct_device.cuh"
+
+namespace ctgb {
+namespace solver {
+
+constexpr int kKMax = 64;       // largest basis the FP64 small algebra handles
+constexpr int kRedBlocks = 128;  // fixed partial-sum grid of the tall-skinny reductions
+
+// control words (int) and scalars (double) living on the device
+enum Ctl { kStop = 0, kStopNext, kSteps, kActive, kBreakdown, kCtlCount };
+enum Scal { kLam = 0, kRnorm2, kDu2, kU2, kJreg, kBnorm2, kTmp0, kTmp1, kScalCount };
+
+__device__ __forceinline__ bool stopped(const int *stop) { return stop && *stop; }
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+
+// ---------------------------------------------------------------------------
+// block reductions (deterministic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+        sh[32] = s;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// ---------------------------------------------------------------------------
+// MM weights P^2 = (z^2 + eps^2)^(-1/2), z = Psi u (forward differences)
+// edge layout: [F][N][N-1] horizontal, then [F][N-1][N] vertical
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_weights(const T *__restrict__ u, T *__restrict__ w, int N, int F, double eps, const int *stop)
+{
+    if (stopped(stop)) return;
+    const long long nx = (long long)F * N * (N - 1);
+    const long long ne = 2 * nx;
+    const T e2 = (T)(eps * eps);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+        T z;
+        if (e < nx) {
+            const long long f = e / ((long long)N * (N - 1));
+            const long long rem = e - f * N * (N - 1);
+            const int i = (int)(rem / (N - 1)), j = (int)(rem % (N - 1));
+            const T *uf = u + f * N * N;
+            z = uf[(size_t)i * N + j + 1] - uf[(size_t)i * N + j];
+        } else {
+            const long long e2i = e - nx;
+            const long long f = e2i / ((long long)(N - 1) * N);
+            const long long rem = e2i - f * (N - 1) * N;
+            const int i = (int)(rem / N), j = (int)(rem % N);
+            const T *uf = u + f * N * N;
+            z = uf[(size_t)(i + 1) * N + j] - uf[(size_t)i * N + j];
+        }
+        w[e] = rsqrt_t<T>(z * z + e2);
+    }
+}
+
+// r += lambda * Psi^T (w .* Psi u)   (one thread per pixel)
+template <typename T>
+__global__ void k_add_reg(T *__restrict__ r, const T *__restrict__ u, const T *__restrict__ w,
+                          const double *__restrict__ scal, int N, int F, const int *stop)
+{
+    if (stopped(stop)) return;
+    const long long n = (long long)F * N * N;
+    const long long nx = (long long)F * N * (N - 1);
+    const T lam = (T)scal[kLam];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const long long f = p / ((long long)N * N);
+        const int rem = (int)(p - f * N * N);
+        const int i = rem / N, j = rem % N;
+        const T *uf = u + f * N * N;
+        const T *wx = w + f * N * (N - 1);
+        const T *wy = w + nx + f * (N - 1) * N;
+        const T c = uf[rem];
+        T acc = T(0);
+        if (j < N - 1) acc -= wx[i * (N - 1) + j] * (uf[rem + 1] - c);      // edge (i,j)-(i,j+1)
+        if (j > 0) acc += wx[i * (N - 1) + j - 1] * (c - uf[rem - 1]);      // edge (i,j-1)-(i,j)
+        if (i < N - 1) acc -= wy[i * N + j] * (uf[rem + N] - c);            // edge (i,j)-(i+1,j)
+        if (i > 0) acc += wy[(i - 1) * N + j] * (c - uf[rem - N]);          // edge (i-1,j)-(i,j)
+        r[p] += lam * acc;
+    }
+}
+
+// J_reg partial: sum_e sqrt(z_e^2 + eps^2) is 1/w_e; summed per block
+template <typename T>
+__global__ void k_reg_value(const T *__restrict__ w, long long ne, double *__restrict__ part)
+{
+    __shared__ double sh[33];
+    double s = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
+        s += 1.0 / (double)w[e];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// weighted Gram of Psi V:  G[a][b] = sum_e w_e (Psi v_a)_e (Psi v_b)_e,
+// a <= b < k.  A fixed grid of CTAs walks the tiles (TR x 32 pixels of one
+// frame) in a fixed order; for each tile the edges (right and down
+// neighbour of every pixel) of all k columns are formed in shared memory,
+// each thread sums its (a, b) entries over the tile's edges in T and adds the
+// tile sum to an FP64 register accumulator.  Per-CTA FP64 partials;
+// k_gram_reduce sums them in order.
+// ---------------------------------------------------------------------------
+constexpr int kGramPairs = kKMax * (kKMax + 1) / 2;
+constexpr int kGramSlots = (kGramPairs + 255) / 256;
+
+template <typename T, int TR>
+__global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long long n, int k,
+                                                  const T *__restrict__ w, int N, int F, double *__restrict__ part,
+                                                  const int *stop)
+{
+    if (stopped(stop)) return;
+    extern __shared__ unsigned char smem_raw[];
+    constexpr int TP = TR * 32;          // pixels per tile
+    constexpr int EP = 2 * TP + 1;       // padded edge pitch (conflict-free column reads)
+    T *E = reinterpret_cast<T *>(smem_raw);  // [k][EP]
+    const int tiles_x = (N + 31) / 32, tiles_y = (N + TR - 1) / TR;
+    const int ntiles = tiles_x * tiles_y * F;
+    const long long nx = (long long)F * N * (N - 1);
+    const int np = k * (k + 1) / 2;
+    double acc[kGramSlots];
+#pragma unroll
+    for (int q = 0; q < kGramSlots; ++q) acc[q] = 0.0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tile = t % (tiles_x * tiles_y);
+        const int f = t / (tiles_x * tiles_y);
+        const int i0 = (tile / tiles_x) * TR, j0 = (tile % tiles_x) * 32;
+        const T *wx = w + (long long)f * N * (N - 1);
+        const T *wy = w + nx + (long long)f * (N - 1) * N;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * TP; idx += blockDim.x) {
+            const int a = idx / TP, pix = idx % TP;
+            const int i = i0 + pix / 32, j = j0 + pix % 32;
+            T ex = T(0), ey = T(0);
+            if (i < N && j < N) {
+                const T *va = V + (long long)a * n + (long long)f * N * N;
+                const T c = va[(size_t)i * N + j];
+                if (j < N - 1) ex = (va[(size_t)i * N + j + 1] - c) * sqrt(wx[i * (N - 1) + j]);
+                if (i < N - 1) ey = (va[(size_t)(i + 1) * N + j] - c) * sqrt(wy[i * N + j]);
+            }
+            E[a * EP + 2 * pix] = ex;
+            E[a * EP + 2 * pix + 1] = ey;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kGramSlots; ++q) {
+            const int p = threadIdx.x + 256 * q;
+            if (p >= np) break;
+            // p -> (a, b) with a <= b, row-major over the upper triangle
+            int a = 0, rem = p;
+            while (rem >= k - a) {
+                rem -= k - a;
+                ++a;
+            }
+            const int b = a + rem;
+            const T *ea = E + a * EP, *eb = E + b * EP;
+            T s = T(0);
+#pragma unroll 8
+            for (int e = 0; e < 2 * TP; ++e) s = fma(ea[e], eb[e], s);
+            acc[q] += (double)s;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kGramSlots; ++q) {
+        const int p = threadIdx.x + 256 * q;
+        if (p < np) part[(long long)blockIdx.x * kGramPairs + p] = acc[q];
+    }
+}
+
+// G (ld kKMax, symmetric, k x k) = sum over nblk partials (fixed order).
+__global__ void k_gram_reduce(const double *__restrict__ part, int nblk, int k, double *__restrict__ G,
+                              const int *stop)
+{
+    if (stopped(stop)) return;
+    const int np = k * (k + 1) / 2;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nblk; ++c) s += part[(long long)c * kGramPairs + p];
+        int a = 0, rem = p;
+        while (rem >= k - a) {
+            rem -= k - a;
+            ++a;
+        }
+        const int b = a + rem;
+        G[a * kKMax + b] = s;
+        G[b * kKMax + a] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tall-skinny products: out[a] = sum_i A[a][i] * x[i] for a < k (A column-major
+// with column stride lda); x2 (nullable) adds out[k] = x . x2 .
+// kRedBlocks CTAs each own a contiguous slice; partials reduced in order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_dots(const T *__restrict__ A, long long len, long long lda, int k,
+                                              const T *__restrict__ x, const T *__restrict__ x2,
+                                              double *__restrict__ part, const int *stop)
+{
+    if (stopped(stop)) return;
+    __shared__ double sh[33];
+    const long long per = (len + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * per, hi = min(len, lo + per);
+    const int kk = k + (x2 ? 1 : 0);
+    for (int a = 0; a < kk; ++a) {
+        const T *col = (a < k) ? A + (long long)a * lda : x2;
+        double s = 0.0;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += (double)(col[i] * x[i]);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * (kKMax + 2) + a] = s;
+    }
+}
+
+// out[a] = scale * sum_c part[c][a] for a < kk (fixed order)
+__global__ void k_dots_reduce(const double *__restrict__ part, int nblk, int kk, double *__restrict__ out,
+                              const int *stop)
+{
+    if (stopped(stop)) return;
+    const int a = threadIdx.x;
+    if (a >= kk) return;
+    double s = 0.0;
+    for (int c = 0; c < nblk; ++c) s += part[(long long)c * (kKMax + 2) + a];
+    out[a] = s;
+}
+
+// out[i] = beta*out[i] + sgn * sum_a A[a][i] * y[a]  (+ bias[i] * bsgn)
+template <typename T>
+__global__ void k_gemv(const T *__restrict__ A, long long len, long long lda, int k, const double *__restrict__ y,
+                       T *__restrict__ out, T beta, T sgn, const T *__restrict__ bias, T bsgn, const int *stop)
+{
+    if (stopped(stop)) return;
+    __shared__ T ys[kKMax];
+    for (int a = threadIdx.x; a < k; a += blockDim.x) ys[a] = (T)y[a];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int a = 0; a < k; ++a) s = fma(A[(long long)a * lda + i], ys[a], s);
+        T o = beta == T(0) ? T(0) : beta * out[i];
+        o = fma(sgn, s, o);
+        if (bias) o = fma(bsgn, bias[i], o);
+        out[i] = o;
+    }
+}
+
+// out[c][i] = sum_a A[a][i] * W[a][c]   (W: kKMax x kKMax row-major, c < kc)
+template <typename T>
+__global__ void k_gemm_small(const T *__restrict__ A, long long len, long long lda, int k,
+                             const double *__restrict__ W, int kc, T *__restrict__ out, long long ldo)
+{
+    __shared__ T Ws[kKMax * 16];
+    for (int idx = threadIdx.x; idx < k * kc; idx += blockDim.x) Ws[idx] = (T)W[(idx / kc) * kKMax + idx % kc];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+        T acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = T(0);
+        for (int a = 0; a < k; ++a) {
+            const T v = A[(long long)a * lda + i];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < kc) acc[c] = fma(v, Ws[a * kc + c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < kc) out[(long long)c * ldo + i] = acc[c];
+    }
+}
+
+// squared norms of three vectors: a (|a|^2), a - b (|a - b|^2), b (|b|^2); per-block partials
+template <typename T>
+__global__ void k_norms3(const T *__restrict__ a, const T *__restrict__ b, long long len, double *__restrict__ part,
+                         const int *stop)
+{
+    if (stopped(stop)) return;
+    __shared__ double sh[33];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+        const double x = (double)a[i];
+        const double y = b ? (double)b[i] : 0.0;
+        s0 += x * x;
+        s1 += (x - y) * (x - y);
+        s2 += y * y;
+    }
+    s0 = block_sum(s0, sh);
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 3 + 0] = s0;
+        part[blockIdx.x * 3 + 1] = s1;
+        part[blockIdx.x * 3 + 2] = s2;
+    }
+}
+
+__global__ void k_norms3_reduce(const double *__restrict__ part, int nblk, double *__restrict__ out3,
+                                const int *stop)
+{
+    if (stopped(stop)) return;
+    if (threadIdx.x >= 3) return;
+    double s = 0.0;
+    for (int c = 0; c < nblk; ++c) s += part[c * 3 + threadIdx.x];
+    out3[threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Enlarge step bookkeeping: normalise the new direction, decide whether the
+// step is the last one (tol_1 test or a vanished residual).
+//   scal[kRnorm2] = |r|^2, norms3 = {|u|^2, |u - u_old|^2, |u_old|^2}
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_normalize(T *__restrict__ r, long long len, const double *__restrict__ rn2, const int *stop)
+{
+    if (stopped(stop)) return;
+    const double nr = sqrt(*rn2);
+    const T inv = nr > 0.0 ? (T)(1.0 / nr) : T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+        r[i] *= inv;
+}
+
+__global__ void k_step_decide(const double *__restrict__ rn2, const double *__restrict__ norms3, double tol1,
+                              int *__restrict__ ctl, double *__restrict__ scal)
+{
+    if (ctl[kStop]) return;
+    const double uold2 = norms3[2];
+    const bool small = uold2 > 0.0 && sqrt(norms3[1]) <= tol1 * sqrt(uold2);
+    const bool vanished = !(*rn2 > 0.0);
+    ctl[kSteps] += 1;
+    scal[kDu2] = norms3[1];
+    scal[kU2] = uold2;
+    ctl[kStopNext] = (small || vanished) ? 1 : 0;
+    if (vanished) ctl[kBreakdown] = 1;
+}
+
+// Append row/column kc of (HV)^T HV and entry kc of (HV)^T b from
+// dots = {HV[:, j] . h_new for j <= kc, b . h_new}.
+__global__ void k_gh_append(const double *__restrict__ dots, int kc, double *__restrict__ GH,
+                            double *__restrict__ cvec, const int *stop)
+{
+    if (stopped(stop)) return;
+    const int j = threadIdx.x;
+    if (j <= kc) {
+        GH[kc * kKMax + j] = dots[j];
+        GH[j * kKMax + kc] = dots[j];
+    }
+    if (j == 0) cvec[kc] = dots[kc + 1];
+}
+
+__global__ void k_step_commit(int *__restrict__ ctl)
+{
+    if (ctl[kStop]) return;
+    if (ctl[kStopNext]) ctl[kStop] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 small algebra in one CTA (k <= kKMax).  Matrices in shared memory with
+// leading dimension kKMax + 1.
+// ---------------------------------------------------------------------------
+constexpr int kLd = kKMax + 1;
+
+// Cholesky A = L L^T in place (lower triangle); pivots clamped at tiny*A00.
+__device__ void chol(double *A, int k, int *bad)
+{
+    for (int j = 0; j < k; ++j) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double d = A[j * kLd + j];
+            const double floor_ = 1e-300 + 1e-15 * fabs(A[0]);
+            if (!(d > floor_)) {
+                d = floor_;
+                *bad = 1;
+            }
+            A[j * kLd + j] = sqrt(d);
+        }
+        __syncthreads();
+        const double dj = A[j * kLd + j];
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[i * kLd + j] /= dj;
+        __syncthreads();
+        const int m = k - j - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            const int i = j + 1 + idx / m, l = j + 1 + idx % m;
+            if (l <= i) A[i * kLd + l] -= A[i * kLd + j] * A[l * kLd + j];
+        }
+    }
+    __syncthreads();
+}
+
+// X := L^{-1} X for ncol columns of X (one thread per column)
+__device__ void trsm_lower(const double *L, double *X, int k, int ncol)
+{
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        for (int i = 0; i < k; ++i) {
+            double s = X[i * kLd + c];
+            for (int l = 0; l < i; ++l) s -= L[i * kLd + l] * X[l * kLd + c];
+            X[i * kLd + c] = s / L[i * kLd + i];
+        }
+    }
+    __syncthreads();
+}
+
+// Cyclic Jacobi eigen-decomposition of the symmetric k x k matrix A
+// (overwritten; its diagonal ends as the eigenvalues), eigenvectors in the
+// columns of U.  Parallel round-robin ordering of the (p, q) rotations.
+__device__ void jacobi_eig(double *A, double *U, int k, double *cs, double *sn, int *pp, int *qq, double *sh)
+{
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int i = idx / k, j = idx % k;
+        U[i * kLd + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int kp = (k + 1) & ~1;  // even number of players, index k is a bye when k is odd
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+            const int i = idx / k, j = idx % k;
+            const double v = A[i * kLd + j];
+            tot += v * v;
+            if (i != j) off += v * v;
+        }
+        off = block_sum(off, sh);
+        tot = block_sum(tot, sh);
+        if (!(off > 1e-30 * tot)) break;
+        for (int round = 0; round < kp - 1; ++round) {
+            for (int i = threadIdx.x; i < kp / 2; i += blockDim.x) {
+                int p, q;
+                if (i == 0) {
+                    p = kp - 1;
+                    q = round;
+                } else {
+                    p = (round + i) % (kp - 1);
+                    q = (round - i + (kp - 1)) % (kp - 1);
+                }
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                pp[i] = p;
+                qq[i] = q;
+                double c = 1.0, s = 0.0;
+                if (q < k) {
+                    const double apq = A[p * kLd + q];
+                    if (apq != 0.0) {
+                        const double tau = (A[q * kLd + q] - A[p * kLd + p]) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                cs[i] = c;
+                sn[i] = s;
+            }
+            __syncthreads();
+            const int npair = kp / 2;
+            for (int idx = threadIdx.x; idx < npair * k; idx += blockDim.x) {  // rows p, q
+                const int i = idx / k, j = idx % k;
+                const int p = pp[i], q = qq[i];
+                if (q >= k) continue;
+                const double c = cs[i], s = sn[i];
+                const double ap = A[p * kLd + j], aq = A[q * kLd + j];
+                A[p * kLd + j] = c * ap - s * aq;
+                A[q * kLd + j] = s * ap + c * aq;
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < npair * k; idx += blockDim.x) {  // columns p, q (and U)
+                const int i = idx / k, j = idx % k;
+                const int p = pp[i], q = qq[i];
+                if (q >= k) continue;
+                const double c = cs[i], s = sn[i];
+                const double ap = A[j * kLd + p], aq = A[j * kLd + q];
+                A[j * kLd + p] = c * ap - s * aq;
+                A[j * kLd + q] = s * ap + c * aq;
+                const double up = U[j * kLd + p], uq = U[j * kLd + q];
+                U[j * kLd + p] = c * up - s * uq;
+                U[j * kLd + q] = s * up + c * uq;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+}
+
+struct SmallShared {
+    double A[kKMax * kLd];
+    double B[kKMax * kLd];
+    double U[kKMax * kLd];
+    double vec[4][kKMax + 1];
+    double cs[kKMax / 2 + 1], sn[kKMax / 2 + 1];
+    int pp[kKMax / 2 + 1], qq[kKMax / 2 + 1];
+    double sh[40];
+    int bad;
+};
+
+// Reduced problem of one Enlarge step:
+//   G_H = (H V)^T (H V), c = (H V)^T b (both maintained incrementally),
+//   G_P = (P Psi V)^T (P Psi V).
+// With G_H = L L^T and L^{-1} G_P L^{-T} = U diag(sig) U^T the normal
+// equations (G_H + lambda G_P) y = c have y = L^{-T} U diag(1/(1 + lambda
+// sig)) U^T L^{-1} c, and the projected residual |H V y - b|^2 =
+// |b|^2 - sum_i chat_i^2 (1 - (lambda sig_i / (1 + lambda sig_i))^2),
+// chat = U^T L^{-1} c -- the same quantity as the QR form
+// |R_H y - Q_H^T b|^2 + |b|^2 - |Q_H^T b|^2 of the reduced problem.
+// lambda: fixed, or the discrepancy principle by bisection in log10(lambda).
+__global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ GH, const double *__restrict__ cvec,
+                                                     const double *__restrict__ GP, int k, double bnorm2,
+                                                     double target, double lam_fix, double lam_lo, double lam_hi,
+                                                     int lam_iters, double *__restrict__ y, double *__restrict__ scal,
+                                                     int *__restrict__ ctl)
+{
+    if (ctl[kStop]) return;
+    extern __shared__ unsigned char smem_raw[];
+    SmallShared &S = *reinterpret_cast<SmallShared *>(smem_raw);
+    if (threadIdx.x == 0) S.bad = 0;
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int i = idx / k, j = idx % k;
+        S.A[i * kLd + j] = GH[i * kKMax + j];
+        S.B[i * kLd + j] = GP[i * kKMax + j];
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) S.vec[0][i] = cvec[i];
+    __syncthreads();
+    chol(S.A, k, &S.bad);                    // A = L (lower)
+    trsm_lower(S.A, S.B, k, k);              // B = L^{-1} G_P
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {  // U = B^T (scratch)
+        const int i = idx / k, j = idx % k;
+        S.U[i * kLd + j] = S.B[j * kLd + i];
+    }
+    __syncthreads();
+    trsm_lower(S.A, S.U, k, k);              // U = L^{-1} G_P L^{-T}
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {  // symmetrize into B
+        const int i = idx / k, j = idx % k;
+        S.B[i * kLd + j] = 0.5 * (S.U[i * kLd + j] + S.U[j * kLd + i]);
+    }
+    // chat = U^T L^{-1} c  (vec[1] = L^{-1} c)
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < k; ++i) {
+            double s = S.vec[0][i];
+            for (int l = 0; l < i; ++l) s -= S.A[i * kLd + l] * S.vec[1][l];
+            S.vec[1][i] = s / S.A[i * kLd + i];
+        }
+    }
+    __syncthreads();
+    jacobi_eig(S.B, S.U, k, S.cs, S.sn, S.pp, S.qq, S.sh);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s += S.U[l * kLd + i] * S.vec[1][l];
+        S.vec[2][i] = s;                          // chat
+        S.vec[3][i] = fmax(S.B[i * kLd + i], 0.0);  // sigma
+    }
+    __syncthreads();
+    double lam;
+    if (lam_fix > 0.0) {
+        lam = lam_fix;
+    } else {
+        // phi(lambda) evaluated by warp 0
+        auto phi = [&](double l) {
+            double s = 0.0;
+            if (threadIdx.x < 32) {
+                for (int i = threadIdx.x; i < k; i += 32) {
+                    const double q = l * S.vec[3][i] / (1.0 + l * S.vec[3][i]);
+                    s += S.vec[2][i] * S.vec[2][i] * (1.0 - q * q);
+                }
+                s = warp_sum(s);
+            }
+            return bnorm2 - s;
+        };
+        double lo = lam_lo, hi = lam_hi;
+        if (threadIdx.x < 32) {
+            if (phi(pow(10.0, lo)) >= target) {
+                hi = lo;
+            } else if (phi(pow(10.0, hi)) <= target) {
+                lo = hi;
+            } else {
+                for (int it = 0; it < lam_iters; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    if (phi(pow(10.0, mid)) < target) lo = mid;
+                    else hi = mid;
+                }
+            }
+            if (threadIdx.x == 0) S.sh[0] = (lo == hi) ? pow(10.0, lo) : pow(10.0, 0.5 * (lo + hi));
+        }
+        __syncthreads();
+        lam = S.sh[0];
+    }
+    // y = L^{-T} U diag(t) chat
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s += S.U[i * kLd + l] * S.vec[2][l] / (1.0 + lam * S.vec[3][l]);
+        S.vec[0][i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = k - 1; i >= 0; --i) {
+            double s = S.vec[0][i];
+            for (int l = i + 1; l < k; ++l) s -= S.A[l * kLd + i] * S.vec[1][l];
+            S.vec[1][i] = s / S.A[i * kLd + i];
+        }
+        scal[kLam] = lam;
+        if (S.bad) ctl[kBreakdown] = 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = S.vec[1][i];
+}
+
+// Compress: right singular vectors of [R_H; sqrt(lambda) R_P] are the
+// eigenvectors of G_H + lambda G_P; W (row-major, ld kKMax) receives the
+// keep = k_min - 1 of largest eigenvalue, ordered by decreasing eigenvalue
+// (ties by index), each signed so its largest-magnitude entry is positive.
+__global__ void __launch_bounds__(256) k_compress_basis(const double *__restrict__ GH, const double *__restrict__ GP,
+                                                        int k, const double *__restrict__ scal, int keep,
+                                                        double *__restrict__ W)
+{
+    extern __shared__ unsigned char smem_raw[];
+    SmallShared &S = *reinterpret_cast<SmallShared *>(smem_raw);
+    const double lam = scal[kLam];
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int i = idx / k, j = idx % k;
+        S.A[i * kLd + j] = GH[i * kKMax + j] + lam * GP[i * kKMax + j];
+    }
+    __syncthreads();
+    jacobi_eig(S.A, S.U, k, S.cs, S.sn, S.pp, S.qq, S.sh);
+    if (threadIdx.x == 0) {  // selection of the `keep` largest eigenvalues
+        bool used[kKMax];
+        for (int i = 0; i < k; ++i) used[i] = false;
+        for (int c = 0; c < keep && c < k; ++c) {
+            int best = -1;
+            for (int i = 0; i < k; ++i)
+                if (!used[i] && (best < 0 || S.A[i * kLd + i] > S.A[best * kLd + best])) best = i;
+            used[best] = true;
+            S.vec[0][c] = (double)best;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < keep && c < k; c += blockDim.x) {
+        const int src = (int)S.vec[0][c];
+        int arg = 0;
+        double big = 0.0;
+        for (int i = 0; i < k; ++i) {
+            const double v = fabs(S.U[i * kLd + src]);
+            if (v > big) {
+                big = v;
+                arg = i;
+            }
+        }
+        const double sgn = S.U[arg * kLd + src] < 0.0 ? -1.0 : 1.0;
+        for (int i = 0; i < k; ++i) W[i * kKMax + c] = sgn * S.U[i * kLd + src];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Newton per view (diagonal J^T J): direction and Armijo bookkeeping
+// ---------------------------------------------------------------------------
+// mu = mu_rel * max_v |J_v|^2; d_v = -g_v / (|J_v|^2 + mu); alpha = alpha0;
+// theta_trial = theta + alpha d; every view active.
+__global__ void k_gn_direction(const double *__restrict__ g, const double *__restrict__ j2, int V, double mu_rel,
+                               double alpha0, const double *__restrict__ theta, double *__restrict__ d,
+                               double *__restrict__ alpha, double *__restrict__ theta_trial, int *__restrict__ active,
+                               int *__restrict__ ctl)
+{
+    __shared__ double sh[40];
+    double mx = 0.0;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) mx = fmax(mx, j2[v]);
+    // block max
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sh[i]);
+        sh[32] = m;
+    }
+    __syncthreads();
+    const double mu = mu_rel * fmax(sh[32], 1e-300);
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        const double dv = -g[v] / (j2[v] + mu);
+        d[v] = dv;
+        alpha[v] = alpha0;
+        theta_trial[v] = theta[v] + alpha0 * dv;
+        active[v] = 1;
+    }
+    if (threadIdx.x == 0) ctl[kActive] = V;
+}
+
+// Armijo test for the views still searching; shrinks alpha of the failures.
+__global__ void k_armijo(const double *__restrict__ f0, const double *__restrict__ ft, const double *__restrict__ g,
+                         const double *__restrict__ d, const double *__restrict__ theta, int V, double c1, double beta,
+                         double *__restrict__ alpha, double *__restrict__ theta_trial, int *__restrict__ active,
+                         int *__restrict__ ctl, int last)
+{
+    __shared__ int cnt[32];
+    int mine = 0;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        if (!active[v]) continue;
+        if (ft[v] <= f0[v] + c1 * alpha[v] * g[v] * d[v]) {
+            active[v] = 0;
+        } else if (last) {  // no acceptable step: keep the old angle
+            active[v] = 0;
+            alpha[v] = 0.0;
+            theta_trial[v] = theta[v];
+        } else {
+            alpha[v] *= beta;
+            theta_trial[v] = theta[v] + alpha[v] * d[v];
+            ++mine;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += cnt[i];
+        ctl[kActive] = t;
+    }
+}
+
+}  // namespace solver
+}  // namespace ctgb

@@ -51,6 +51,32 @@ class ct_geom(ctypes.Structure):
     ]
 
 
+NLRMM_MAX_HIST = 256
+
+
+class nlrmm_opts(ctypes.Structure):
+    _fields_ = [
+        ("k_min", ctypes.c_int32), ("k_max", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+        ("maxiter_p", ctypes.c_int32), ("max_halvings", ctypes.c_int32), ("lam_iters", ctypes.c_int32),
+        ("update_theta", ctypes.c_int32), ("stop_on_convergence", ctypes.c_int32),
+        ("eps", ctypes.c_double), ("tol1", ctypes.c_double), ("tau", ctypes.c_double),
+        ("noise_norm", ctypes.c_double), ("lam_fix", ctypes.c_double), ("lam_lo", ctypes.c_double),
+        ("lam_hi", ctypes.c_double), ("c1", ctypes.c_double), ("beta", ctypes.c_double),
+        ("alpha0", ctypes.c_double), ("mu_rel", ctypes.c_double), ("tol_u", ctypes.c_double),
+        ("tol_p", ctypes.c_double),
+    ]
+
+
+class nlrmm_stats(ctypes.Structure):
+    _fields_ = [
+        ("outer_done", ctypes.c_int32), ("converged", ctypes.c_int32), ("breakdown", ctypes.c_int32),
+        ("enlarge_steps", ctypes.c_int32 * NLRMM_MAX_HIST),
+        ("lambda_", ctypes.c_double * NLRMM_MAX_HIST), ("du", ctypes.c_double * NLRMM_MAX_HIST),
+        ("dtheta", ctypes.c_double * NLRMM_MAX_HIST), ("rre", ctypes.c_double * NLRMM_MAX_HIST),
+        ("ms", ctypes.c_double * NLRMM_MAX_HIST),
+    ]
+
+
 _lib = None
 
 
@@ -81,6 +107,10 @@ def load_library(path: str | None = None):
     lib.ct_autotune.argtypes = [P]
     lib.ct_get_tuning.argtypes = [P, P]
     lib.ct_set_tuning.argtypes = [P, P]
+    lib.nlrmm_default_opts.argtypes = [P]
+    lib.nlrmm_default_opts.restype = None
+    lib.nlrmm_gks_solve.argtypes = [P, P, P, P, P, P, P, P]
+    lib.nlrmm_gks_solve.restype = ctypes.c_int
     lib.ct_strerror.argtypes = [I]
     lib.ct_strerror.restype = ctypes.c_char_p
     lib.ct_last_cuda_error.argtypes = []
@@ -172,6 +202,31 @@ def ct_get_tuning(h):
 def ct_set_tuning(h, values):
     buf = (ctypes.c_int32 * 5)(*[int(v) for v in values])
     _check(load_library().ct_set_tuning(h, buf), "ct_set_tuning")
+
+
+def nlrmm_default_opts(**overrides):
+    o = nlrmm_opts()
+    load_library().nlrmm_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def nlrmm_gks_solve(h, b, theta_inout, delta, x_out, x_true=None, opts=None, **overrides):
+    """Run the GPU NL-RMM-GKS driver; returns (status code, stats dict)."""
+    o = opts if opts is not None else nlrmm_default_opts(**overrides)
+    st = nlrmm_stats()
+    rc = load_library().nlrmm_gks_solve(h, _p(b), _p(theta_inout), _p(delta), _p(x_out), _p(x_true),
+                                        ctypes.byref(o), ctypes.byref(st))
+    if rc not in (CT_OK, CT_ERR_NOCONV):
+        raise CTError(rc, "nlrmm_gks_solve")
+    k = min(st.outer_done, NLRMM_MAX_HIST)
+    stats = {"rc": rc, "outer_done": st.outer_done, "converged": bool(st.converged), "breakdown": bool(st.breakdown),
+             "enlarge_steps": list(st.enlarge_steps[:k]), "lambda": list(st.lambda_[:k]), "du": list(st.du[:k]),
+             "dtheta": list(st.dtheta[:k]), "rre": list(st.rre[:k]), "ms": list(st.ms[:k])}
+    return rc, stats
 
 
 # --- tensor-level wrapper ---------------------------------------------------
@@ -282,3 +337,13 @@ class CTOperator:
 
     def set_stream(self, stream=None):
         ct_set_stream(self.h, stream)
+
+    def solve(self, b, theta0, delta=None, x_true=None, **opts):
+        """NL-RMM-GKS: returns (x, theta, stats).  theta0 is not modified."""
+        self._chk(b, self.m, "b")
+        theta = self._ang(theta0, "theta0").clone()
+        x = torch.empty(self.n, dtype=self.dtype, device=b.device)
+        if x_true is not None:
+            self._chk(x_true, self.n, "x_true")
+        _, stats = nlrmm_gks_solve(self.h, b, theta, self._ang(delta, "delta"), x, x_true, **opts)
+        return x, theta, stats

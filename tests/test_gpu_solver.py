@@ -1,0 +1,104 @@
+"""GPU NL-RMM-GKS driver (nlrmm_gks_solve through the C ABI) against the FP64 oracle solver.
+
+* FP64 operators: per-iteration lambda, final image and angles match the oracle's
+  iterates (tolerances below), with the Enlarge early stop disabled so both sides
+  take the same number of steps;
+* FP32 operators + FP64 small algebra: the final relative reconstruction error
+  matches the oracle's within 1e-3 (relative) on the 64^2 / 90-view workload;
+* fixed angles reduce the solve to RMM-GKS (angles returned unchanged).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import nlrmm
+from paper_2605_06336_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ct():
+    from paper_2605_06336_gb300 import ct as ctmod
+    ctmod.load_library()
+    return ctmod
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def problem(N, V, seed, noise=0.01, sigma_deg=0.5):
+    rng = np.random.default_rng(seed)
+    g = oracle.Geometry(N, synth.n_bins(N), V)
+    th_nom = np.sort(synth.random_angles(V, rng))
+    th_true = th_nom + rng.normal(0, math.radians(sigma_deg), V)
+    u_true = synth.rasterize(N, synth.random_ellipses(N, 4, rng)).ravel()
+    b_true = oracle.forward(g, th_true, u_true)
+    e = rng.standard_normal(g.m)
+    e *= noise * np.linalg.norm(b_true) / np.linalg.norm(e)
+    return g, th_nom, th_true, u_true, b_true + e, float(np.linalg.norm(e))
+
+
+def test_fp64_solver_follows_the_oracle_iterates(ct):
+    g, th_nom, th_true, u_true, b, nn = problem(32, 40, seed=1)
+    kw = dict(k_min=5, k_max=15, outer_iters=4, tol1=0.0, stop_on_convergence=0)
+    o = nlrmm.Options(noise_norm=nn, k_min=5, k_max=15, outer_iters=4, tol1=0.0, stop_on_convergence=False)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true, theta_true=th_true)
+    op = ct.CTOperator(g.N, g.B, g.V, max_batch=8, dtype=torch.float64)
+    x, th, st = op.solve(dev(b), dev(th_nom), x_true=dev(u_true), noise_norm=nn, **kw)
+    assert st["outer_done"] == 4
+    assert st["enlarge_steps"] == h_o.enlarge_steps
+    np.testing.assert_allclose(st["lambda"], h_o.lam, rtol=1e-7)
+    np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-7)
+    xu = x.cpu().numpy()
+    assert np.linalg.norm(xu - u_o) <= 1e-7 * np.linalg.norm(u_o)
+    # the Gauss-Newton quotient -g/|J|^2 amplifies the ~1e-8 image differences
+    assert np.max(np.abs(th.cpu().numpy() - th_o)) <= 1e-8
+
+
+def test_fp32_solver_reaches_the_oracle_reconstruction_error(ct):
+    w = synth.make_workload("C1")
+    g = oracle.Geometry(w.N, w.B, w.V)
+    u_true = w.images.reshape(-1)
+    b_true = oracle.forward(g, w.theta_true, u_true)
+    e = w.noise_dir * (w.noise_level * np.linalg.norm(b_true) / np.linalg.norm(w.noise_dir))
+    b = b_true + e
+    nn = float(np.linalg.norm(e))
+    o = nlrmm.Options(noise_norm=nn, outer_iters=w.outer_iters, stop_on_convergence=False)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(w.theta_nominal, u_true=u_true, theta_true=w.theta_true)
+    op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
+    x, th, st = op.solve(dev(b, torch.float32), dev(w.theta_nominal), x_true=dev(u_true, torch.float32),
+                         noise_norm=nn, outer_iters=w.outer_iters, stop_on_convergence=0)
+    rre_gpu = st["rre"][-1]
+    rre_orc = h_o.rre[-1]
+    assert abs(rre_gpu - rre_orc) <= 1e-3 * rre_orc, (rre_gpu, rre_orc)
+    ang_gpu = np.linalg.norm(th.cpu().numpy() - w.theta_true) / np.linalg.norm(w.theta_true)
+    ang_orc = h_o.angle_err[-1]
+    assert ang_gpu <= 1.05 * ang_orc, (ang_gpu, ang_orc)
+
+
+def test_fixed_angles_is_rmm_gks(ct):
+    g, th_nom, th_true, u_true, b, nn = problem(24, 30, seed=2)
+    o = nlrmm.Options(noise_norm=nn, k_min=4, k_max=12, outer_iters=3, tol1=0.0, stop_on_convergence=False,
+                      update_theta=False)
+    u_o, _, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom)
+    op = ct.CTOperator(g.N, g.B, g.V, max_batch=4, dtype=torch.float64)
+    th0 = dev(th_nom)
+    x, th, st = op.solve(dev(b), th0, noise_norm=nn, k_min=4, k_max=12, outer_iters=3, tol1=0.0,
+                         stop_on_convergence=0, update_theta=0)
+    assert torch.equal(th, th0)
+    assert np.linalg.norm(x.cpu().numpy() - u_o) <= 1e-7 * np.linalg.norm(u_o)
+
+
+def test_solver_argument_errors(ct):
+    op = ct.CTOperator(16, 23, 8, max_batch=2, dtype=torch.float32)
+    b = torch.zeros(8 * 23, device="cuda")
+    th = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(ct.CTError):
+        op.solve(b, th, noise_norm=1.0, k_max=80)       # basis above the FP64 small-algebra limit
+    with pytest.raises(ct.CTError):
+        op.solve(b, th)                                 # no noise level and no fixed lambda

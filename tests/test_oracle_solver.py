@@ -1,0 +1,187 @@
+"""Pins of the FP64 NL-RMM-GKS oracle against mathematics it must satisfy.
+
+* Psi is the stacked Kronecker finite-difference operator and Psi^T its transpose;
+* the MM majorant touches J at u_k and lies above it (properties (i), (iii), Sec. 3.1);
+* with fixed lambda and fixed weights the generalized Krylov iteration reaches
+  the dense normal-equation solution once V spans the image space;
+* fixed-lambda Enlarge steps never increase J_{eps,lambda} (Lemma on image descent);
+* after Compress u lies in span(V) and V has orthonormal columns;
+* the discrepancy-principle lambda hits the target residual;
+* the per-view Gauss-Newton / Armijo update reaches the brute-force minimizer of a
+  single view's misfit;
+* a small alternating solve reduces both the image and the angle error.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle import nlrmm
+from paper_2605_06336_gb300 import synth
+
+
+def small_problem(N=16, V=12, noise=0.01, seed=0, sigma_deg=0.5):
+    rng = np.random.default_rng(seed)
+    g = oracle.Geometry(N, synth.n_bins(N), V)
+    th_nom = np.sort(rng.uniform(0, math.pi, V))
+    th_true = th_nom + rng.normal(0, math.radians(sigma_deg), V)
+    u_true = synth.rasterize(N, synth.random_ellipses(N, 3, rng)).ravel()
+    b_true = oracle.forward(g, th_true, u_true)
+    e = rng.standard_normal(g.m)
+    e *= noise * np.linalg.norm(b_true) / np.linalg.norm(e)
+    return g, th_nom, th_true, u_true, b_true + e, np.linalg.norm(e)
+
+
+def test_psi_is_the_kronecker_difference_operator():
+    g = oracle.Geometry(7, 11, 3, views_per_frame=[1, 2])
+    N = g.N
+    L = sp.diags([-np.ones(N - 1), np.ones(N - 1)], [0, 1], shape=(N - 1, N))
+    I = sp.identity(N)
+    Psi1 = sp.vstack([sp.kron(I, L), sp.kron(L, I)])   # horizontal then vertical, row-major image
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(g.n)
+    z = nlrmm.psi(g, u)
+    U = u.reshape(g.F, N * N)
+    nx = N * (N - 1)
+    for f in range(g.F):
+        ref = Psi1 @ U[f]
+        np.testing.assert_allclose(z[f * nx:(f + 1) * nx], ref[:nx], atol=1e-14)
+        np.testing.assert_allclose(z[g.F * nx + f * nx: g.F * nx + (f + 1) * nx], ref[nx:], atol=1e-14)
+    y = rng.standard_normal(z.size)
+    assert abs(z @ y - u @ nlrmm.psi_t(g, y)) < 1e-12 * np.linalg.norm(z) * np.linalg.norm(y)
+
+
+def test_majorant_touches_and_majorizes():
+    g, th, _, u_true, b, _ = small_problem(N=12, V=8)
+    rng = np.random.default_rng(2)
+    uk = u_true + 0.1 * rng.standard_normal(g.n)
+    lam, eps = 0.7, 1e-2
+    Jk = nlrmm.objective(g, th, None, uk, b, lam, eps)
+    assert abs(nlrmm.majorant(g, th, None, uk, uk, b, lam, eps) - Jk) <= 1e-12 * abs(Jk)
+    for _ in range(20):
+        u = uk + rng.standard_normal(g.n) * rng.uniform(0.01, 2)
+        assert nlrmm.majorant(g, th, None, u, uk, b, lam, eps) >= nlrmm.objective(g, th, None, u, b, lam, eps) - 1e-9
+
+
+def test_full_krylov_space_gives_the_dense_solution():
+    g, th, _, _, b, nn = small_problem(N=10, V=10)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 2.0, 2 * g.N * (g.N - 1))
+    lam = 0.3
+    opts = nlrmm.Options(k_min=3, k_max=3 + g.n + 5, tol1=0.0, lam_fix=lam, fixed_weights=w)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    V = s.gkb(th, opts.k_min)
+    HV = np.stack([s.H(th, V[:, j]) for j in range(V.shape[1])], 1)
+    u, *_ = s.enlarge(th, V, HV, np.zeros(g.n), opts.k_max - opts.k_min)
+    A = oracle.dense_matrix(g, th)
+    E = np.eye(g.n)
+    PsiM = np.stack([nlrmm.psi(g, E[:, j]) for j in range(g.n)], 1)
+    M = A.T @ A + lam * PsiM.T @ (w[:, None] * PsiM)
+    u_ref = np.linalg.solve(M, A.T @ b)
+    assert np.linalg.norm(u - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+
+
+def test_fixed_lambda_enlarge_steps_decrease_the_objective():
+    g, th, _, _, b, _ = small_problem(N=16, V=12, seed=4)
+    lam, eps = 0.05, 1e-3
+    opts = nlrmm.Options(k_min=5, k_max=25, tol1=0.0, lam_fix=lam, eps=eps)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    V = s.gkb(th, opts.k_min)
+    HV = np.stack([s.H(th, V[:, j]) for j in range(V.shape[1])], 1)
+    u = np.zeros(g.n)
+    J = [nlrmm.objective(g, th, None, u, b, lam, eps)]
+    for _ in range(12):
+        u, _, V, HV, *_ = s.enlarge(th, V, HV, u, 1)
+        J.append(nlrmm.objective(g, th, None, u, b, lam, eps))
+    assert all(J[i + 1] <= J[i] * (1 + 1e-12) for i in range(len(J) - 1)), J
+    assert J[-1] < 0.5 * J[0]
+
+
+def test_compress_keeps_u_in_the_span_and_orthonormality():
+    g, th, _, _, b, nn = small_problem(N=16, V=12, seed=5)
+    opts = nlrmm.Options(k_min=5, k_max=15, noise_norm=nn, tol1=0.0)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    V = s.gkb(th, opts.k_min)
+    assert np.abs(V.T @ V - np.eye(V.shape[1])).max() < 1e-12
+    HV = np.stack([s.H(th, V[:, j]) for j in range(V.shape[1])], 1)
+    u, lam, Vg, _, RH, RP, used, _ = s.enlarge(th, V, HV, np.zeros(g.n), 10)
+    assert np.abs(Vg.T @ Vg - np.eye(Vg.shape[1])).max() < 1e-11
+    Vk = s.compress(Vg, RH, RP, used, lam, u)
+    assert Vk.shape[1] == opts.k_min
+    assert np.abs(Vk.T @ Vk - np.eye(Vk.shape[1])).max() < 1e-12
+    assert np.linalg.norm(u - Vk @ (Vk.T @ u)) <= 1e-12 * np.linalg.norm(u)
+
+
+def test_discrepancy_principle_hits_the_target():
+    g, th, _, _, b, nn = small_problem(N=16, V=12, seed=6, noise=0.05)
+    opts = nlrmm.Options(noise_norm=nn)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    V = s.gkb(th, 30)
+    HV = np.stack([s.H(th, V[:, j]) for j in range(V.shape[1])], 1)
+    QH, RH = np.linalg.qr(HV)
+    PsiV = np.stack([nlrmm.psi(g, V[:, j]) for j in range(V.shape[1])], 1)
+    _, RP = np.linalg.qr(PsiV)
+    QHb = QH.T @ b
+    lam = s.choose_lambda(RH, RP, QHb)
+    target = (opts.tau * nn) ** 2
+    assert 1e-10 < lam < 1e10
+    phi, y = s.projected_residual2(RH, RP, QHb, lam)
+    assert abs(phi - target) <= 1e-8 * target
+    # the same residual computed in the full space
+    r = HV @ y - b
+    assert abs(r @ r - phi) <= 1e-9 * target
+
+
+def test_gauss_newton_reaches_the_single_view_minimizer():
+    N = 24
+    g = oracle.Geometry(N, synth.n_bins(N), 1)
+    rng = np.random.default_rng(7)
+    u = synth.rasterize(N, synth.random_ellipses(N, 4, rng)).ravel()
+    th_true = np.array([0.61])
+    b = oracle.forward(g, th_true, u)
+    opts = nlrmm.Options(maxiter_p=1)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    th = th_true + math.radians(0.8)
+    for _ in range(25):
+        th = s.update_param(th, u)
+    # brute force: golden-section search of f(theta) around the start
+    f = lambda t: float(s.view_f(np.array([t]), u)[0])
+    lo, hi = th_true[0] - math.radians(2), th_true[0] + math.radians(2)
+    gr = (math.sqrt(5) - 1) / 2
+    a, c = hi - gr * (hi - lo), lo + gr * (hi - lo)
+    for _ in range(80):
+        if f(a) < f(c):
+            hi = c
+        else:
+            lo = a
+        a, c = hi - gr * (hi - lo), lo + gr * (hi - lo)
+    t_min = 0.5 * (lo + hi)
+    assert abs(th[0] - t_min) <= 1e-6
+    assert abs(th[0] - th_true[0]) <= 1e-6
+    assert f(th[0]) <= f(th_true[0] + math.radians(0.8))
+
+
+def test_armijo_never_increases_a_view_misfit():
+    g, th_nom, th_true, u_true, b, _ = small_problem(N=20, V=15, seed=8, sigma_deg=1.0)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1))
+    th = th_nom.copy()
+    f_prev = s.view_f(th, u_true)
+    for _ in range(4):
+        th = s.update_param(th, u_true)
+        f = s.view_f(th, u_true)
+        assert np.all(f <= f_prev + 1e-12)
+        f_prev = f
+
+
+@pytest.mark.slow
+def test_small_alternating_solve_reduces_errors():
+    g, th_nom, th_true, u_true, b, nn = small_problem(N=32, V=30, seed=9, sigma_deg=0.5)
+    opts = nlrmm.Options(noise_norm=nn, outer_iters=8, stop_on_convergence=False)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    u, th, hist = s.solve(th_nom, u_true=u_true, theta_true=th_true)
+    e0 = np.linalg.norm(th_nom - th_true)
+    assert np.linalg.norm(th - th_true) < 0.5 * e0
+    assert hist.rre[-1] < hist.rre[0]
+    assert hist.rre[-1] < 0.5
