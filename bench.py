@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solver", action="store_true", help="skip the NL-RMM-GKS comparison")
+    ap.add_argument("--solver-iters", type=int, default=30)
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes 'fkb,fsplit,akb,asplit,jsplit' instead of autotuning")
     return ap.parse_args()
@@ -183,6 +185,48 @@ def run_reference(args):
                              "sample": f"{n} steps of H, H^T, J, J^T on one 256^2 image, 180x363 sinogram"},
             "e2e": {"value": val, "unit": "GSamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def solver_comparison(w, dev, outer_iters):
+    """NL-RMM-GKS on the workload: FP32 operators + FP64 small algebra + batched
+    basis projection against the plain FP64 GPU form, same data, same options."""
+    import torch
+    from paper_2605_06336_gb300 import ct
+    N, B, V = w.N, w.B, w.V
+    u_true = torch.tensor(w.images.reshape(-1), dtype=torch.float64, device=dev)
+    th_true = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
+    op64 = ct.CTOperator(N, B, V, max_batch=8, dtype=torch.float64)
+    b_true = op64.forward(u_true, th_true)
+    e = torch.tensor(w.noise_dir, dtype=torch.float64, device=dev)
+    e *= w.noise_level * b_true.norm() / e.norm()
+    b64 = b_true + e
+    nn = float(e.norm())
+    th0 = torch.tensor(w.theta_nominal, dtype=torch.float64, device=dev)
+    out = {}
+    for name, dt in (("fp64_plain", torch.float64), ("fp32_batched", torch.float32)):
+        op = op64 if dt == torch.float64 else ct.CTOperator(N, B, V, max_batch=8, dtype=dt)
+        op.autotune()
+        bb = b64.to(dt)
+        xt = u_true.to(dt)
+        op.solve(bb, th0, x_true=xt, noise_norm=nn, outer_iters=2, stop_on_convergence=0)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, th, st = op.solve(bb, th0, x_true=xt, noise_norm=nn, outer_iters=outer_iters, stop_on_convergence=0)
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms = e0.elapsed_time(e1)
+        ang = float((th - th_true).norm() / th_true.norm())
+        out[name] = {"total_ms": total_ms, "ms_per_outer_iter": total_ms / outer_iters,
+                     "final_rre": st["rre"][-1], "rel_angle_err": ang,
+                     "max_abs_angle_err_deg": float((th - th_true).abs().max()) * 180 / math.pi,
+                     "enlarge_steps": sum(st["enlarge_steps"])}
+    a, b_ = out["fp64_plain"], out["fp32_batched"]
+    out["equal_error"] = abs(b_["final_rre"] - a["final_rre"]) <= 1e-3 * a["final_rre"]
+    out["speedup_fp32_vs_fp64"] = a["total_ms"] / b_["total_ms"]
+    out["outer_iters"] = outer_iters
+    out["initial_max_abs_angle_err_deg"] = float(np.abs(w.theta_nominal - w.theta_true).max()) * 180 / math.pi
+    return out
 
 
 def cpu_baseline(w, seconds):
@@ -346,6 +390,9 @@ def main():
     sm_mhz = SM_MAX_MHZ_NOMINAL
     peak = NUM_SMS * LSU_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     peaks, src = measured_peaks()
+    solver = None
+    if not args.no_solver and world == 1:
+        solver = solver_comparison(w, dev, args.solver_iters)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, args.cpu_seconds)
@@ -366,6 +413,7 @@ def main():
                               f"{NUM_SMS} SMs x {LSU_BYTES_PER_CLK_SM} B/clk L1 data path x {sm_mhz:.0f} MHz",
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": "derived (unit counts x nominal max clock)"},
         "cpu_baseline": cpu,
+        "solver": solver,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "tuning": dict(zip(["fwd_images_per_lane", "fwd_warps_per_ray", "adj_images_per_thread",

@@ -85,7 +85,7 @@ void ct_destroy(ct_handle *h);
 
 /*
  * Y = H(theta, delta) X for a batch of `batch` images (forward projection
- * "H u" of every MM-GKS step, Eq. (3.3), Alg. "Enlarge").
+ * "H u" in the residual of every MM-GKS step, Eq. (3.6), Alg. "Enlarge").
  *   theta  [n_views] radians; delta [n_views] bins or NULL (zero offsets)
  *   X      [batch][n_frames][N][N]      Y [batch][n_views][B]
  */
@@ -95,7 +95,7 @@ int ct_forward(ct_handle *h, const double *theta, const double *delta,
 /*
  * X = H(theta, delta)^T Y, the exact transpose of ct_forward in gather form
  * (one thread per pixel, no atomics); used in the residual
- * H^T (H u - b) + lambda Psi^T P^2 Psi u of every MM-GKS step (Eq. (3.5)).
+ * H^T (H u - b) + lambda Psi^T P^2 Psi u of every MM-GKS step (Eq. (3.6)).
  *   Y [batch][n_views][B]  ->  X [batch][n_frames][N][N]
  */
 int ct_adjoint(ct_handle *h, const double *theta, const double *delta,

@@ -7,8 +7,8 @@ Passages followed:
   * MM weights P = diag((z^2 + eps^2)^(-1/4)), z = Psi u, and the quadratic
     majorant (Eq. (3.1)-(3.2), Sec. 3.1);
   * generalized Krylov projection: QR of H V and P Psi V, the reduced
-    problem (Eq. (3.4)), the normal-equation residual appended to V
-    (Eq. (3.5)-(3.6));
+    problem (Eq. (3.4)-(3.5)), the normal-equation residual appended to V
+    (Eq. (3.6)-(3.7));
   * Alg. "Enlarge" and Alg. "Compress" (supplementary Sec. S1.2) and
     Alg. "RMM-GKS" (Sec. 3.3);
   * Alg. "UPDATE-PARAM" (damped Gauss-Newton + Armijo backtracking, Sec. 4.1.2);

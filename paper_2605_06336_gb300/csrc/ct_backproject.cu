@@ -12,7 +12,7 @@
 // most two bins, floor(beta) and floor(beta) + 1, read as one sinogram pair.
 // beta is split into an FP64 tile anchor (integer + fraction, once per tile
 // and view) plus a small FP32 in-tile offset.  This is the residual step
-// H^T (H u - b) of every MM-GKS iteration (Eq. (3.5), Alg. "Enlarge").
+// H^T (H u - b) of every MM-GKS iteration (Eq. (3.6), Alg. "Enlarge").
 #include <cuda_runtime.h>
 
 #include <algorithm>
