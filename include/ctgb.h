@@ -229,6 +229,38 @@ void nlrmm_default_opts(nlrmm_opts *opts);
 int nlrmm_gks_solve(ct_handle *h, const void *b, double *theta_inout, const double *delta, void *x_out,
                     const void *x_true, const nlrmm_opts *opts, nlrmm_stats *stats);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free transposed Jacobian (this entry point has no counterpart in
+ * the paper; it exists for callers that cannot allocate device memory).
+ * ------------------------------------------------------------------------ */
+#define CTGB_NOALLOC_MAX_N 256      /* image side */
+#define CTGB_NOALLOC_MAX_VIEWS 512  /* views */
+#define CTGB_NOALLOC_MAX_BINS 1024  /* detector bins */
+
+/*
+ * Same result as ct_jacT (float32, one frame) without a handle and without
+ * allocating: for callers that cannot call cudaMalloc, such as a host
+ * application that owns all device memory through its own pool, or a
+ * service whose device-memory budget is fixed after start-up.
+ *   N, B, n_views   geometry (as in ct_geom), at most the CTGB_NOALLOC_MAX_*
+ *                   limits above; larger sizes return CT_ERR_ARG
+ *   theta, delta    [n_views] device double (delta may be NULL)
+ *   x               [N][N] device float image;  r [n_views][B] device float
+ *   gtheta, gdelta  [n_views] device double outputs (gdelta may be NULL)
+ *   cuda_stream     cudaStream_t the kernels run on (NULL = legacy default)
+ * The workspace is a file-scope device array of about 1.7 MB compiled into
+ * the library, so every GPU that loads the library holds it until the
+ * process exits.  The first call made on a device looks up that array's
+ * device address (cudaGetSymbolAddress) for the device current at the call;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that may overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  Returns CT_OK,
+ * CT_ERR_ARG or CT_ERR_CUDA; asynchronous, like ct_jacT.
+ */
+int ct_jacT_noalloc(int32_t N, int32_t B, int32_t n_views, const double *theta, const double *delta,
+                    const float *x, const float *r, double *gtheta, double *gdelta, void *cuda_stream);
+
 /*
  * Synchronise the handle's stream and report device-side conditions found
  * since the last ct_status: CT_ERR_NAN if a non-finite angle or offset was

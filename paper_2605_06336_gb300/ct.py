@@ -107,6 +107,8 @@ def load_library(path: str | None = None):
     lib.ct_autotune.argtypes = [P]
     lib.ct_get_tuning.argtypes = [P, P]
     lib.ct_set_tuning.argtypes = [P, P]
+    lib.ct_jacT_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P, P]
+    lib.ct_jacT_noalloc.restype = ctypes.c_int
     lib.nlrmm_default_opts.argtypes = [P]
     lib.nlrmm_default_opts.restype = None
     lib.nlrmm_gks_solve.argtypes = [P, P, P, P, P, P, P, P]
@@ -202,6 +204,19 @@ def ct_get_tuning(h):
 def ct_set_tuning(h, values):
     buf = (ctypes.c_int32 * 5)(*[int(v) for v in values])
     _check(load_library().ct_set_tuning(h, buf), "ct_set_tuning")
+
+
+NOALLOC_MAX_N, NOALLOC_MAX_VIEWS, NOALLOC_MAX_BINS = 256, 512, 1024
+
+
+def ct_jacT_noalloc(N, B, n_views, theta, delta, x, r, gtheta, gdelta, stream=None):
+    """ct_jacT without a handle or any device allocation (for callers that cannot
+    allocate); the workspace is a static device array, so sizes are capped."""
+    if N > NOALLOC_MAX_N or B > NOALLOC_MAX_BINS or n_views > NOALLOC_MAX_VIEWS:
+        raise ValueError(f"ct_jacT_noalloc: N={N}, B={B}, views={n_views} exceed the limits "
+                         f"{NOALLOC_MAX_N}/{NOALLOC_MAX_BINS}/{NOALLOC_MAX_VIEWS} of its static workspace")
+    _check(load_library().ct_jacT_noalloc(int(N), int(B), int(n_views), _p(theta), _p(delta), _p(x), _p(r),
+                                          _p(gtheta), _p(gdelta), _stream_ptr(stream)), "ct_jacT_noalloc")
 
 
 def nlrmm_default_opts(**overrides):
