@@ -149,22 +149,24 @@ int ct_set_stream(ct_handle *h, void *cuda_stream);
 
 /*
  * Pick launch shapes for this handle's geometry by timing the candidates on
- * its stream: images per lane (1, 2, 4, 8) and warps per ray group (1, 2, 4,
- * 8) for the forward projection at max_batch, images per thread and view
- * groups per pixel tile (1, 2, 4) for the transpose, warps per ray group for
- * the Jacobian kernels.  Synchronises; allocates and frees scratch buffers;
+ * its stream: images per lane (1, 2, 4, 8), warps per ray (1, 2, 4, 8) and
+ * neighbouring views per CTA (1, 2, 4, 8) for the forward projection at
+ * max_batch, images per thread and view groups per pixel tile (1, 2, 4) for
+ * the transpose, warps per ray and views per CTA for the Jacobian kernels.  Synchronises; allocates and frees scratch buffers;
  * must not run during stream capture.  Results of every operator are
  * independent of the chosen shapes up to floating-point summation order.
  */
 int ct_autotune(ct_handle *h);
 
 /*
- * Read / set the launch shapes: {fwd images per lane, fwd warps per ray
- * group, transpose images per thread, transpose view groups, Jacobian warps
- * per ray group}; each a power of two, at most 8 (view groups at most 4).
+ * Read / set the launch shapes, 7 values: {fwd images per lane, fwd warps
+ * per ray (row segments), fwd views per CTA, transpose images per thread,
+ * transpose view groups per pixel tile, Jacobian warps per ray, Jacobian
+ * views per CTA}; each a power of two, at most 8 (view groups at most 4),
+ * warps per ray x views per CTA at most 16.
  */
-int ct_get_tuning(ct_handle *h, int32_t *out5);
-int ct_set_tuning(ct_handle *h, const int32_t *in5);
+int ct_get_tuning(ct_handle *h, int32_t *out7);
+int ct_set_tuning(ct_handle *h, const int32_t *in7);
 
 /* ------------------------------------------------------------------------
  * NL-RMM-GKS (alternating form) on the handle's geometry.

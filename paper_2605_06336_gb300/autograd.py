@@ -1,0 +1,60 @@
+"""torch.autograd.Function over the C-ABI operators.
+
+``CTProject.apply(x, theta, delta, op)`` returns H(theta, delta) x through
+``ct_forward``; its backward returns
+    dL/dx     = H^T g                (ct_adjoint, the gather transpose)
+    dL/dtheta = J_theta(x)^T g       (ct_jacT)
+    dL/ddelta = J_delta(x)^T g       (ct_jacT)
+for the incoming gradient g.  Those are the gradient components
+[grad_p J]_i = (H_{p_i} u)^T (H u - b) of the appendix lemma on the
+Lipschitz gradient when the loss is 1/2 |H u - b|^2.  Everything runs in the
+library's kernels; nothing is differentiated by torch itself.
+"""
+from __future__ import annotations
+
+import torch
+
+from .ct import CTOperator
+
+
+class CTProject(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, theta, delta, op: CTOperator):
+        y = op.forward(x.contiguous(), theta.detach().contiguous(),
+                       None if delta is None else delta.detach().contiguous())
+        ctx.op = op
+        ctx.has_delta = delta is not None
+        ctx.save_for_backward(x, theta, delta if delta is not None else theta.new_empty(0))
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, theta, delta = ctx.saved_tensors
+        op = ctx.op
+        d = delta if ctx.has_delta else None
+        gy = gy.contiguous()
+        gx = gth = gdl = None
+        if ctx.needs_input_grad[0]:
+            gx = op.adjoint(gy, theta, d)
+        if ctx.needs_input_grad[1] or (ctx.has_delta and ctx.needs_input_grad[2]):
+            xs = x.reshape(-1, op.n)
+            gs = gy.reshape(-1, op.m)
+            gth = torch.zeros(op.V, dtype=torch.float64, device=x.device)
+            gdl = torch.zeros(op.V, dtype=torch.float64, device=x.device) if ctx.has_delta else None
+            for k in range(xs.shape[0]):  # one Jacobian per image of the batch
+                if ctx.has_delta:
+                    gt, gd = op.jacT(xs[k].contiguous(), theta, gs[k].contiguous(), d, want_delta=True)
+                    gdl += gd
+                else:
+                    gt = op.jacT(xs[k].contiguous(), theta, gs[k].contiguous(), None)
+                gth += gt
+            if not ctx.needs_input_grad[1]:
+                gth = None
+            if not (ctx.has_delta and ctx.needs_input_grad[2]):
+                gdl = None
+        return gx, gth, gdl, None
+
+
+def project(x, theta, op: CTOperator, delta=None):
+    """y = H(theta, delta) x, differentiable in x, theta and delta."""
+    return CTProject.apply(x, theta, delta, op)

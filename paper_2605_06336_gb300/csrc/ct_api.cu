@@ -40,12 +40,14 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_fstart);
     cudaFree(h.d_fcount);
     cudaFree(h.d_flag);
+    cudaFree(h.d_order);
+    cudaFree(h.d_changed);
     cudaFree(h.d_px);
     cudaFree(h.d_pt);
     cudaFree(h.d_yp);
     cudaFree(h.d_partial);
     h.d_views = nullptr;
-    h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = nullptr;
+    h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = h.d_changed = nullptr;
     h.d_px = h.d_pt = h.d_yp = nullptr;
     h.d_partial = nullptr;
 }
@@ -55,7 +57,7 @@ int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const 
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F));
-    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split));
+    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw));
     return CT_OK;
 }
 
@@ -74,7 +76,7 @@ int do_jac(ctgb::Handle &h, const double *theta, const double *delta, const void
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
-    CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split));
+    CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split, h.tune.der_vw));
     return CT_OK;
 }
 
@@ -84,7 +86,7 @@ int do_jacT(ctgb::Handle &h, const double *theta, const double *delta, const voi
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
-    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split));
+    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split, h.tune.der_vw));
     return CT_OK;
 }
 
@@ -94,7 +96,7 @@ int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void 
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
-    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split));
+    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw));
     return CT_OK;
 }
 
@@ -109,6 +111,8 @@ void default_tuning(ctgb::Handle &h)
     h.tune.fwd_split = rays >= 16LL * h.num_sms ? 2 : 4;
     h.tune.adj_split = 2;
     h.tune.der_split = rays >= 32LL * h.num_sms ? 2 : 4;
+    h.tune.fwd_vw = 2;
+    h.tune.der_vw = 2;
 }
 
 // Time one configuration: median of `reps` launches after one warm-up.
@@ -168,11 +172,16 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         for (int kb : {1, 2, 4, 8}) {
             if (kb > K) continue;
             for (int sp : {1, 2, 4, 8}) {
-                const float ms = time_config(h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp); });
-                if (ms < best) {
-                    best = ms;
-                    t.fwd_kb = kb;
-                    t.fwd_split = sp;
+                for (int vw : {1, 2, 4, 8}) {
+                    if (sp * vw > 16) continue;
+                    const float ms =
+                        time_config(h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw); });
+                    if (ms < best) {
+                        best = ms;
+                        t.fwd_kb = kb;
+                        t.fwd_split = sp;
+                        t.fwd_vw = vw;
+                    }
                 }
             }
         }
@@ -190,10 +199,15 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         }
         best = 1e30f;
         for (int sp : {1, 2, 4, 8}) {
-            const float ms = time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp); });
-            if (ms < best) {
-                best = ms;
-                t.der_split = sp;
+            for (int vw : {1, 2, 4, 8}) {
+                if (sp * vw > 16) continue;
+                const float ms =
+                    time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp, vw); });
+                if (ms < best) {
+                    best = ms;
+                    t.der_split = sp;
+                    t.der_vw = vw;
+                }
             }
         }
         e = cudaStreamSynchronize(h.stream);
@@ -273,6 +287,8 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
                   cudaMalloc(&h.d_fstart, sizeof(int) * h.F) == cudaSuccess &&
                   cudaMalloc(&h.d_fcount, sizeof(int) * h.F) == cudaSuccess &&
                   cudaMalloc(&h.d_flag, sizeof(int)) == cudaSuccess &&
+                  cudaMalloc(&h.d_order, sizeof(int) * h.V) == cudaSuccess &&
+                  cudaMalloc(&h.d_changed, sizeof(int)) == cudaSuccess &&
                   cudaMalloc(&h.d_px, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_pt, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_yp, sino_pairs * pair_bytes) == cudaSuccess &&
@@ -286,6 +302,7 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
         if (e == cudaSuccess) e = cudaMemcpy(h.d_fstart, fstart.data(), sizeof(int) * h.F, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h.d_fcount, fcount.data(), sizeof(int) * h.F, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(h.d_flag, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(h.d_changed, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(h.d_views, 0, sizeof(ctgb::ViewGeo) * h.V);
         if (e == cudaSuccess) e = cudaMemset(h.d_px, 0, img_pairs * pair_bytes);
         if (e == cudaSuccess) e = cudaMemset(h.d_pt, 0, img_pairs * pair_bytes);
@@ -364,30 +381,35 @@ int ct_autotune(ct_handle *H)
     return H->h.precision ? autotune_impl<double>(H->h) : autotune_impl<float>(H->h);
 }
 
-int ct_get_tuning(ct_handle *H, int32_t *out5)
+int ct_get_tuning(ct_handle *H, int32_t *out7)
 {
-    if (!H || !out5) return CT_ERR_ARG;
+    if (!H || !out7) return CT_ERR_ARG;
     const ctgb::Tuning &t = H->h.tune;
-    out5[0] = t.fwd_kb;
-    out5[1] = t.fwd_split;
-    out5[2] = t.adj_kb;
-    out5[3] = t.adj_split;
-    out5[4] = t.der_split;
+    out7[0] = t.fwd_kb;
+    out7[1] = t.fwd_split;
+    out7[2] = t.fwd_vw;
+    out7[3] = t.adj_kb;
+    out7[4] = t.adj_split;
+    out7[5] = t.der_split;
+    out7[6] = t.der_vw;
     return CT_OK;
 }
 
-int ct_set_tuning(ct_handle *H, const int32_t *in5)
+int ct_set_tuning(ct_handle *H, const int32_t *in7)
 {
-    if (!H || !in5) return CT_ERR_ARG;
+    if (!H || !in7) return CT_ERR_ARG;
     auto pow2 = [](int x, int hi) { return x >= 1 && x <= hi && (x & (x - 1)) == 0; };
-    if (!pow2(in5[0], 8) || !pow2(in5[1], 8) || !pow2(in5[2], 8) || !pow2(in5[3], 4) || !pow2(in5[4], 8))
+    if (!pow2(in7[0], 8) || !pow2(in7[1], 8) || !pow2(in7[2], 8) || !pow2(in7[3], 8) || !pow2(in7[4], 4) ||
+        !pow2(in7[5], 8) || !pow2(in7[6], 8) || in7[1] * in7[2] > 16 || in7[5] * in7[6] > 16)
         return CT_ERR_ARG;
     ctgb::Tuning &t = H->h.tune;
-    t.fwd_kb = in5[0];
-    t.fwd_split = in5[1];
-    t.adj_kb = in5[2];
-    t.adj_split = in5[3];
-    t.der_split = in5[4];
+    t.fwd_kb = in7[0];
+    t.fwd_split = in7[1];
+    t.fwd_vw = in7[2];
+    t.adj_kb = in7[3];
+    t.adj_split = in7[4];
+    t.der_split = in7[5];
+    t.der_vw = in7[6];
     return CT_OK;
 }
 

@@ -64,10 +64,12 @@ struct __align__(16) ViewGeo {
 // Launch shapes.  kb: images (or sinograms) per lane; split: warps sharing
 // one ray (row segments, combined in shared memory) or thread groups sharing
 // one pixel tile (view subsets, combined in shared memory).
+// vw: view slots per CTA for the ray kernels (neighbouring views of the
+// sorted view order, sharing the image band in L1).
 struct Tuning {
-    int fwd_kb = 8, fwd_split = 2;  // forward projection of a batch
-    int adj_kb = 8, adj_split = 2;  // transpose of a batch
-    int der_split = 4;              // JVP / VJP / Gauss-Newton terms (one image)
+    int fwd_kb = 8, fwd_split = 2, fwd_vw = 1;  // forward projection of a batch
+    int adj_kb = 8, adj_split = 2;              // transpose of a batch
+    int der_split = 4, der_vw = 1;              // JVP / VJP / Gauss-Newton terms (one image)
 };
 
 struct Handle {
@@ -80,6 +82,8 @@ struct Handle {
     int *d_fstart = nullptr;  // first view of each frame
     int *d_fcount = nullptr;  // views of each frame
     int *d_flag = nullptr;    // device-side status bits
+    int *d_order = nullptr;   // view order of the ray kernels (sorted by axis and slope)
+    int *d_changed = nullptr; // set when a view's constants were rebuilt (order is stale)
     void *d_px = nullptr;     // pair images, rows of X:   max_batch * F * N * Pp pairs
     void *d_pt = nullptr;     // pair images, rows of X^T: max_batch * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
@@ -101,15 +105,15 @@ template <typename T>
 cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip = nullptr);
 
 template <typename T>
-cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, const int *skip = nullptr);
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, const int *skip = nullptr);
 template <typename T>
 cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip = nullptr);
 template <typename T>
-cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split);
+cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw);
 template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split);
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw);
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval,
-                      int split, const int *view_mask = nullptr, const int *skip = nullptr);
+                      int split, int vw, const int *view_mask = nullptr, const int *skip = nullptr);
 
 }  // namespace ctgb

@@ -30,7 +30,7 @@ namespace {
 // ---------------------------------------------------------------------------
 __global__ void k_view_setup(const double *__restrict__ theta, const double *__restrict__ delta,
                              const int *__restrict__ fov, int V, int N, int B, ViewGeo *__restrict__ out,
-                             int *__restrict__ flag, const int *__restrict__ skip)
+                             int *__restrict__ flag, const int *__restrict__ skip, int *__restrict__ changed)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V || (skip && *skip)) return;
@@ -40,6 +40,7 @@ __global__ void k_view_setup(const double *__restrict__ theta, const double *__r
     if ((gp->flags & kValid) && __double_as_longlong(gp->th) == __double_as_longlong(th) &&
         __double_as_longlong(gp->dl) == __double_as_longlong(dl))
         return;  // unchanged since the last call
+    if (changed) *changed = 1;  // every writer stores the same value
     const double th_in = th, dl_in = dl;
     int bad = 0;
     if (!isfinite(th) || !isfinite(dl)) {
@@ -106,6 +107,35 @@ __global__ void k_view_setup(const double *__restrict__ theta, const double *__r
     g.dl = dl_in;
     g.frame = fov ? fov[v] : 0;
     *gp = g;
+}
+
+// View order for the ray kernels: views sorted by marching axis, then by ray
+// slope qr (ties by index), so that consecutive entries sweep nearly the same
+// image band.  One CTA; runs only when a view changed since the last sort.
+constexpr int kOrderMaxV = 4096;
+__global__ void __launch_bounds__(1024) k_view_order(const ViewGeo *__restrict__ vg, int V, int *__restrict__ order,
+                                                     int *__restrict__ changed, const int *__restrict__ skip)
+{
+    if ((skip && *skip) || !*changed) return;
+    __shared__ float key[kOrderMaxV];
+    if (V > kOrderMaxV) {
+        for (int i = threadIdx.x; i < V; i += blockDim.x) order[i] = i;
+    } else {
+        for (int i = threadIdx.x; i < V; i += blockDim.x)
+            key[i] = (float)(vg[i].mode * 4.0 + 1.0 + (double)vg[i].Qh * (2.0 / kFixScale));
+        __syncthreads();
+        for (int i = threadIdx.x; i < V; i += blockDim.x) {
+            const float ki = key[i];
+            int rank = 0;
+            for (int j = 0; j < V; ++j) {
+                const float kj = key[j];
+                rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+            }
+            order[rank] = i;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *changed = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -194,6 +224,8 @@ template <typename T> struct RayArgs {
     double *partial;        // VJP / GN
     const int *view_mask;   // GN: views with mask 0 are skipped (nullable)
     const int *skip;        // whole launch is a no-op when *skip != 0 (nullable)
+    const int *order;       // view order (nullable: identity)
+    int VW;                 // view slots per CTA
 };
 
 // Warp-uniform row range [rlo, rhi] covering every row where one of the
@@ -219,84 +251,101 @@ __device__ __forceinline__ void warp_rows(const ViewGeo &g, int b, bool active, 
     rhi = __reduce_max_sync(0xffffffffu, u);
 }
 
+// One CTA = VW view slots x SPLIT row segments, all on the same 32-bin chunk.
+// The view slots take VW consecutive entries of the view order (views sorted
+// by marching axis and ray slope), so the warps of a CTA sweep nearly the
+// same image band row by row and share it in L1.  SPLIT warps march
+// consecutive row segments of the same rays and are combined in shared memory
+// in a fixed order.
 template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
-__global__ void __launch_bounds__(32 * SPLIT) k_ray(RayArgs<T> a)
+__global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
 {
     using P2 = pair_t<T>;
     constexpr int NACC = (MODE == kFwd) ? KB : 3;
-    __shared__ T red[SPLIT > 1 ? SPLIT : 1][NACC][32];
+    extern __shared__ unsigned char ray_smem[];
+    T *red = reinterpret_cast<T *>(ray_smem);  // [VW][SPLIT][NACC][32], only when SPLIT > 1
     const int lane = threadIdx.x & 31;
-    const int seg = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int seg = warp % SPLIT;
+    const int slot = warp / SPLIT;
+    const int VW = a.VW;
     const int N = a.N;
-    const int total = a.ngroups * a.V * a.nchunks;
+    const int ngv = (a.V + VW - 1) / VW;
+    const int total = a.ngroups * ngv * a.nchunks;
     if (a.skip && *a.skip) return;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int chunk = item % a.nchunks;
         const int t = item / a.nchunks;
-        const int v = t % a.V;
-        const int grp = t / a.V;
-        if (MODE == kGn && a.view_mask && a.view_mask[v] == 0) continue;  // uniform per CTA
-        const ViewGeo &g = a.vg[v];
+        const int vgi = t % ngv;
+        const int grp = t / ngv;
+        const int pos = vgi * VW + slot;
+        const int v = pos < a.V ? (a.order ? a.order[pos] : pos) : -1;
+        const bool live = v >= 0 && !(MODE == kGn && a.view_mask && a.view_mask[v] == 0);  // warp-uniform
+        const ViewGeo &g = a.vg[live ? v : 0];
         const int b = chunk * kChunk + lane;
-        const bool active = b < a.B;
-        int rlo, rhi;
-        warp_rows(g, b, active, N, rlo, rhi);
-        const int len = rhi - rlo + 1;
-        const int per = (len + SPLIT - 1) / SPLIT;
-        const int r0 = rlo + seg * per;
-        const int r1 = min(rhi, r0 + per - 1);
-        long long Q = line_at(g, b, r0, N);
-        const long long dQ = 2 * g.Qh;
+        const bool active = live && b < a.B;
         const int k0 = a.kbase + grp * KB;
-        const P2 *img = (g.mode ? a.PT : a.PX) + (size_t)g.frame * N * a.Pp + (size_t)k0 * a.pimg_stride +
-                        (size_t)r0 * a.Pp + 2;
         T acc[NACC];
 #pragma unroll
         for (int k = 0; k < NACC; ++k) acc[k] = T(0);
-        if constexpr (MODE == kFwd) {
+        if (live) {
+            int rlo, rhi;
+            warp_rows(g, b, b < a.B, N, rlo, rhi);
+            const int len = rhi - rlo + 1;
+            const int per = (len + SPLIT - 1) / SPLIT;
+            const int r0 = rlo + seg * per;
+            const int r1 = min(rhi, r0 + per - 1);
+            long long Q = line_at(g, b, r0, N);
+            const long long dQ = 2 * g.Qh;
+            const P2 *img = (g.mode ? a.PT : a.PX) + (size_t)g.frame * N * a.Pp + (size_t)k0 * a.pimg_stride +
+                            (size_t)r0 * a.Pp + 2;
+            if constexpr (MODE == kFwd) {
 #pragma unroll 4
-            for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ) {
-                const int cell = min(max(cell_of(Q), -2), N);
-                const T f = frac_of(Q, T());
-                const T omf = T(1) - f;
+                for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ) {
+                    const int cell = min(max(cell_of(Q), -2), N);
+                    const T f = frac_of(Q, T());
+                    const T omf = T(1) - f;
 #pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    const P2 p = __ldg(img + (size_t)k * a.pimg_stride + cell);
-                    acc[k] = fma(omf, p.x, fma(f, p.y, acc[k]));
+                    for (int k = 0; k < KB; ++k) {
+                        const P2 p = __ldg(img + (size_t)k * a.pimg_stride + cell);
+                        acc[k] = fma(omf, p.x, fma(f, p.y, acc[k]));
+                    }
                 }
-            }
-        } else {
-            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta,
-            // acc[2] = sum of slopes (offset derivative)
-            const T g0 = fma(GeoT<T>::sb(g, b), GeoT<T>::gs(g), GeoT<T>::gh(g, N));
-            const T gr = GeoT<T>::gr(g);
-            T rf = (T)r0;
+            } else {
+                // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta,
+                // acc[2] = sum of slopes (offset derivative)
+                const T g0 = fma(GeoT<T>::sb(g, b), GeoT<T>::gs(g), GeoT<T>::gh(g, N));
+                const T gr = GeoT<T>::gr(g);
+                T rf = (T)r0;
 #pragma unroll 4
-            for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ, rf += T(1)) {
-                const int cell = min(max(cell_of(Q), -2), N);
-                const T f = frac_of(Q, T());
-                const P2 p = __ldg(img + cell);
-                const T d = p.y - p.x;
-                acc[0] += fma(f, d, p.x);
-                acc[1] = fma(d, fma(rf, gr, g0), acc[1]);
-                if (OFFS) acc[2] += d;
+                for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ, rf += T(1)) {
+                    const int cell = min(max(cell_of(Q), -2), N);
+                    const T f = frac_of(Q, T());
+                    const P2 p = __ldg(img + cell);
+                    const T d = p.y - p.x;
+                    acc[0] += fma(f, d, p.x);
+                    acc[1] = fma(d, fma(rf, gr, g0), acc[1]);
+                    if (OFFS) acc[2] += d;
+                }
             }
         }
         if constexpr (SPLIT > 1) {
+            T *mine = red + ((size_t)(slot * SPLIT + seg) * NACC) * 32;
 #pragma unroll
-            for (int k = 0; k < NACC; ++k) red[seg][k][lane] = acc[k];
+            for (int k = 0; k < NACC; ++k) mine[k * 32 + lane] = acc[k];
             __syncthreads();
             if (seg == 0) {
+                const T *base = red + ((size_t)slot * SPLIT * NACC) * 32;
 #pragma unroll
                 for (int k = 0; k < NACC; ++k) {
-                    T s = red[0][k][lane];
+                    T s = base[k * 32 + lane];
 #pragma unroll
-                    for (int q = 1; q < SPLIT; ++q) s += red[q][k][lane];
+                    for (int q = 1; q < SPLIT; ++q) s += base[(q * NACC + k) * 32 + lane];
                     acc[k] = s;
                 }
             }
         }
-        if (seg == 0) {
+        if (seg == 0 && live) {
             const T wv = GeoT<T>::w(g);
             if constexpr (MODE == kFwd) {
                 if (active) {
@@ -389,6 +438,8 @@ template <typename T> RayArgs<T> base_args(const Handle &h)
     a.kbase = 0;
     a.ngroups = 1;
     a.sino_stride = (long long)h.V * h.B;
+    a.order = h.d_order;
+    a.VW = 1;
     return a;
 }
 
@@ -396,9 +447,12 @@ template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
 cudaError_t run_ray(const Handle &h, const RayArgs<T> &a)
 {
     auto kern = k_ray<T, MODE, OFFS, KB, SPLIT>;
-    const long long items = (long long)a.ngroups * a.V * a.nchunks;
-    const int grid = persistent_grid(kern, 32 * SPLIT, 0, items, h.num_sms);
-    kern<<<grid, 32 * SPLIT, 0, h.stream>>>(a);
+    constexpr int NACC = (MODE == kFwd) ? KB : 3;
+    const int threads = 32 * SPLIT * a.VW;
+    const size_t smem = SPLIT > 1 ? (size_t)a.VW * SPLIT * NACC * 32 * sizeof(T) : 0;
+    const long long items = (long long)a.ngroups * ((a.V + a.VW - 1) / a.VW) * a.nchunks;
+    const int grid = persistent_grid(kern, threads, smem, items, h.num_sms);
+    kern<<<grid, threads, smem, h.stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -430,7 +484,8 @@ cudaError_t launch_view_setup(const Handle &h, const double *theta, const double
 {
     const int threads = 128;
     k_view_setup<<<(h.V + threads - 1) / threads, threads, 0, h.stream>>>(theta, delta, h.d_fov, h.V, h.N, h.B,
-                                                                           h.d_views, h.d_flag, skip);
+                                                                           h.d_views, h.d_flag, skip, h.d_changed);
+    if (h.d_order && h.d_changed) k_view_order<<<1, 1024, 0, h.stream>>>(h.d_views, h.V, h.d_order, h.d_changed, skip);
     return cudaGetLastError();
 }
 
@@ -453,11 +508,12 @@ template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y,
 }
 
 template <typename T>
-cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, const int *skip)
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, const int *skip)
 {
     RayArgs<T> a = base_args<T>(h);
     a.Y = Y;
     a.skip = skip;
+    a.VW = vw;
     int k = 0;
     for (int width : {8, 4, 2, 1}) {
         if (width > kb) continue;
@@ -473,9 +529,10 @@ cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, 
 }
 
 template <typename T>
-cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split)
+cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw)
 {
     RayArgs<T> a = base_args<T>(h);
+    a.VW = vw;
     a.Y = dY;
     a.dtheta = dtheta;
     a.ddelta = ddelta;
@@ -483,9 +540,10 @@ cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddel
 }
 
 template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split)
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw)
 {
     RayArgs<T> a = base_args<T>(h);
+    a.VW = vw;
     a.R = R;
     a.partial = h.d_partial;
     cudaError_t e = gdelta ? run_ray_split<T, kVjp, true, 1>(h, a, split)
@@ -498,9 +556,10 @@ cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdel
 
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval, int split,
-                      const int *view_mask, const int *skip)
+                      int vw, const int *view_mask, const int *skip)
 {
     RayArgs<T> a = base_args<T>(h);
+    a.VW = vw;
     a.R = bdata;
     a.res = res;
     a.partial = h.d_partial;
@@ -516,11 +575,11 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
 #define CTGB_RAY_INSTANTIATE(T)                                                                             \
     template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int, const int *);                 \
     template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int, const int *);                \
-    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, const int *);               \
-    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int);          \
-    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int);                \
+    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, const int *);          \
+    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int);     \
+    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int);           \
     template cudaError_t launch_gn<T>(const Handle &, const T *, T *, double *, double *, double *, int,    \
-                                      const int *, const int *);
+                                      int, const int *, const int *);
 
 CTGB_RAY_INSTANTIATE(float)
 CTGB_RAY_INSTANTIATE(double)

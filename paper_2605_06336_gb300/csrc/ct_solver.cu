@@ -62,7 +62,7 @@ thread_local char g_solver_msg[256] = "";
 constexpr int kThreads = 256;
 
 template <typename T> struct Solver {
-    Handle &h;
+    Handle h;  // copy of the caller's handle, running on the solver's private stream
     const nlrmm_opts &o;
     const T *b;
     const double *delta;
@@ -81,14 +81,28 @@ template <typename T> struct Solver {
     int *ctl = nullptr, *active = nullptr;
     int *h_ctl = nullptr;       // pinned mirror of ctl
     double *h_scal = nullptr;   // pinned mirror of small results
+    int *h_stop = nullptr;      // host-mapped mirror of the Enlarge stop flag
+    int *d_stop = nullptr;      // its device address
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::vector<cudaGraphExec_t> step_graph;  // one captured Enlarge step per basis size
+    bool use_graphs = true;
 
-    Solver(Handle &h_, const nlrmm_opts &o_, const T *b_, const double *delta_) : h(h_), o(o_), b(b_), delta(delta_) {}
+    Solver(const Handle &h_, cudaStream_t s_, const nlrmm_opts &o_, const T *b_, const double *delta_)
+        : h(h_), o(o_), b(b_), delta(delta_)
+    {
+        h.stream = s_;
+    }
 
     ~Solver()
     {
+        for (cudaGraphExec_t g : step_graph)
+            if (g) cudaGraphExecDestroy(g);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         for (void *p : allocs) cudaFree(p);
         if (h_ctl) cudaFreeHost(h_ctl);
         if (h_scal) cudaFreeHost(h_scal);
+        if (h_stop) cudaFreeHost(h_stop);
     }
 
     template <typename U> int alloc(U *&p, size_t count)
@@ -140,10 +154,16 @@ template <typename T> struct Solver {
         SV_TRY(alloc(ctl, kCtlCount));
         SV_TRY(alloc(active, h.V));
         if (cudaMallocHost(&h_ctl, sizeof(int) * kCtlCount) != cudaSuccess ||
-            cudaMallocHost(&h_scal, sizeof(double) * 16) != cudaSuccess) {
+            cudaMallocHost(&h_scal, sizeof(double) * 16) != cudaSuccess ||
+            cudaHostAlloc(&h_stop, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
             return CT_ERR_OOM;
         }
+        SV_CUDA(cudaHostGetDevicePointer((void **)&d_stop, h_stop, 0));
+        *(volatile int *)h_stop = 0;
+        SV_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        SV_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        step_graph.assign(KC + 1, nullptr);
         SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_CUDA(cudaMemsetAsync(GP, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
@@ -204,7 +224,7 @@ template <typename T> struct Solver {
         for (int j = j0; j < j0 + cnt; j += h.max_batch) {
             const int nb = std::min(h.max_batch, j0 + cnt - j);
             SV_CUDA(launch_pairs_img<T>(h, col(V, n, j), nb * h.F, stop));
-            SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, stop));
+            SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, stop));
         }
         return CT_OK;
     }
@@ -317,9 +337,35 @@ template <typename T> struct Solver {
         SV_TRY(dots_into(HV, m, kc + 1, col(HV, m, kc), b, dots, stop));
         k_gh_append<<<1, kKMax + 2, 0, h.stream>>>(dots, kc, GH, cvec, stop);
         SV_CUDA(cudaMemcpyAsync(uold, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));  // (u_old = u)
-        k_step_commit<<<1, 1, 0, h.stream>>>(ctl);
+        k_step_commit<<<1, 1, 0, h.stream>>>(ctl, d_stop);
         SV_CUDA(cudaGetLastError());
         return CT_OK;
+    }
+
+    // One Enlarge step: replay the captured graph for this basis size (capture
+    // it on first use); launch eagerly if capture is not available.
+    int run_step(int kc)
+    {
+        if (use_graphs && !step_graph[kc]) {
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            int rc = ok ? enlarge_step(th_k, kc) : CT_ERR_CUDA;
+            if (ok) ok = cudaStreamEndCapture(h.stream, &g) == cudaSuccess && rc == CT_OK;
+            cudaGraphExec_t ge = nullptr;
+            if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            if (!ok) {
+                cudaGetLastError();
+                use_graphs = false;  // fall back to plain launches for the rest of the solve
+            } else {
+                step_graph[kc] = ge;
+            }
+        }
+        if (use_graphs) {
+            SV_CUDA(cudaGraphLaunch(step_graph[kc], h.stream));
+            return CT_OK;
+        }
+        return enlarge_step(th_k, kc);
     }
 
     double bnorm2 = 0.0;
@@ -342,12 +388,12 @@ template <typename T> struct Solver {
         for (int it = 0; it < o.maxiter_p; ++it) {
             SV_CUDA(launch_view_setup(h, th_n, delta));
             SV_CUDA(launch_pairs_img<T>(h, uimg, h.F));
-            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split));
+            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw));
             k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
                                                      ctl);
             for (int hv = 0; hv <= o.max_halvings; ++hv) {
                 SV_CUDA(launch_view_setup(h, th_t, delta));
-                SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, active));
+                SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw, active));
                 k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, th_n, h.V, o.c1, o.beta, alpha, th_t, active, ctl,
                                                    hv == o.max_halvings ? 1 : 0);
                 SV_TRY(sync_ctl());
@@ -391,8 +437,17 @@ template <typename T> struct Solver {
             SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
             SV_TRY(full_gram(kc));
             SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
-            // Enlarge: s predicated steps
-            for (int step = 0; step < s && kc + step + 1 < KC; ++step) SV_TRY(enlarge_step(th_k, kc + step));
+            SV_CUDA(cudaStreamSynchronize(h.stream));
+            *(volatile int *)h_stop = 0;
+            // Enlarge: predicated steps issued one step ahead of the device's stop decision
+            for (int step = 0; step < s && kc + step + 1 < KC; ++step) {
+                if (step >= 2) {
+                    SV_CUDA(cudaEventSynchronize(ev[step & 1]));
+                    if (*(volatile int *)h_stop) break;
+                }
+                SV_TRY(run_step(kc + step));
+                SV_CUDA(cudaEventRecord(ev[step & 1], h.stream));
+            }
             SV_TRY(sync_ctl());
             const int steps = h_ctl[kSteps];
             const int k_used = kc + steps - 1;  // columns the last reduced problem used
@@ -422,7 +477,7 @@ template <typename T> struct Solver {
             k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.eps, nullptr);
             SV_CUDA(launch_view_setup(h, th_k, delta));
             SV_CUDA(launch_pairs_img<T>(h, u, h.F));
-            SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split));
+            SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw));
             axpby(res, b, m, 1.0, -1.0);
             SV_TRY(backproject(th_k, res, col(V, n, kc), nullptr));
             k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(col(V, n, kc), u, w, scal, h.N, h.F, nullptr);
@@ -523,12 +578,30 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
         return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
-    if (h.precision) {
-        Solver<double> s(h, o, (const double *)b, delta);
-        return s.run(theta_inout, x_out, (const double *)x_true, stats);
+    // The solve runs on a private stream ordered after the work already queued
+    // on the handle's stream; it synchronises before returning.
+    cudaStream_t ps = nullptr;
+    cudaEvent_t e0 = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(e0, h.stream) != cudaSuccess || cudaStreamWaitEvent(ps, e0, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        if (ps) cudaStreamDestroy(ps);
+        return CT_ERR_CUDA;
     }
-    Solver<float> s(h, o, (const float *)b, delta);
-    return s.run(theta_inout, x_out, (const float *)x_true, stats);
+    int rc;
+    if (h.precision) {
+        Solver<double> s(h, ps, o, (const double *)b, delta);
+        rc = s.run(theta_inout, x_out, (const double *)x_true, stats);
+    } else {
+        Solver<float> s(h, ps, o, (const float *)b, delta);
+        rc = s.run(theta_inout, x_out, (const float *)x_true, stats);
+    }
+    cudaStreamSynchronize(ps);
+    cudaEventDestroy(e0);
+    cudaStreamDestroy(ps);
+    return rc;
 }
 
 }  // extern "C"

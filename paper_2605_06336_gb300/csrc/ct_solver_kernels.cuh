@@ -370,10 +370,12 @@ __global__ void k_gh_append(const double *__restrict__ dots, int kc, double *__r
     if (j == 0) cvec[kc] = dots[kc + 1];
 }
 
-__global__ void k_step_commit(int *__restrict__ ctl)
+// Ends a step: raises the stop flag when the step decided so, and mirrors
+// it to host-mapped memory (nullable) for the host's issue loop.
+__global__ void k_step_commit(int *__restrict__ ctl, volatile int *__restrict__ stop_mirror)
 {
-    if (ctl[kStop]) return;
-    if (ctl[kStopNext]) ctl[kStop] = 1;
+    if (!ctl[kStop] && ctl[kStopNext]) ctl[kStop] = 1;
+    if (stop_mirror) *stop_mirror = ctl[kStop];
 }
 
 // ---------------------------------------------------------------------------

@@ -195,14 +195,18 @@ def ct_autotune(h):
     _check(load_library().ct_autotune(h), "ct_autotune")
 
 
+TUNING_FIELDS = ("fwd_images_per_lane", "fwd_warps_per_ray", "fwd_views_per_cta", "adj_images_per_thread",
+                 "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta")
+
+
 def ct_get_tuning(h):
-    buf = (ctypes.c_int32 * 5)()
+    buf = (ctypes.c_int32 * 7)()
     _check(load_library().ct_get_tuning(h, buf), "ct_get_tuning")
     return list(buf)
 
 
 def ct_set_tuning(h, values):
-    buf = (ctypes.c_int32 * 5)(*[int(v) for v in values])
+    buf = (ctypes.c_int32 * 7)(*[int(v) for v in values])
     _check(load_library().ct_set_tuning(h, buf), "ct_set_tuning")
 
 
