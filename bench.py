@@ -229,6 +229,37 @@ def solver_comparison(w, dev, outer_iters):
     return out
 
 
+def graph_op_timing(op, calls, reps, flush):
+    """Device time of each operator call alone: every call captured in its own
+    CUDA graph and replayed `reps` times (L2 flushed before each replay,
+    outside the events).  Returns mean ms per call, one per entry of `calls`."""
+    import torch
+    out = []
+    for call in calls:
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            op.set_stream(side)
+            call()
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.cuda.graph(g):
+            op.set_stream(torch.cuda.current_stream())
+            call()
+        op.set_stream(torch.cuda.current_stream())
+        cur = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        g.replay()
+        for a, b in evs:
+            flush.zero_()
+            a.record(cur)
+            g.replay()
+            b.record(cur)
+        torch.cuda.synchronize()
+        out.append(float(np.mean([a.elapsed_time(b) for a, b in evs])))
+    return out
+
+
 def graph_step_timing(op, step, steps, flush, stream_ctx):
     """Capture `step` (a sequence of C-ABI calls) in a CUDA graph and time replays,
     flushing L2 between replays outside the events.  Returns ms per step."""
@@ -450,10 +481,14 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant operator call
+    # ---- roofline of the dominant operator call: device time of each call alone (own graph)
     steps_img = interp_steps_per_image(w)
     op_names = ["forward_K8", "adjoint_K8", "jac", "jacT"]
-    mean_ms = per_op.mean(axis=0)
+    calls = [lambda: ct.ct_forward(op.h, theta, None, X, Y, K),
+             lambda: ct.ct_adjoint(op.h, theta, None, Ys, Xa, K),
+             lambda: ct.ct_jac(op.h, theta, None, X[0], dth, None, dy),
+             lambda: ct.ct_jacT(op.h, theta, None, X[0], Y[0], gt, None)]
+    mean_ms = np.array(graph_op_timing(op, calls, 200, flush))
     dom = int(np.argmax(mean_ms))
     units = {0: K * steps_img, 1: K * steps_img, 2: steps_img, 3: steps_img}
     gather_bytes = 8.0 * units[dom]          # two FP32 pixels (or bins) per interpolation
@@ -483,6 +518,8 @@ def main():
                    "launch": "step captured once in a CUDA graph and replayed (value); eager launches under 'eager'",
                    "parallelism": f"replicas x{world}"},
         "per_op_ms": dict(zip(op_names, [float(x) for x in mean_ms])),
+        "per_op_ms_note": "device time of each call (all its kernels) replayed alone from a CUDA graph, L2 flushed",
+        "per_op_ms_eager": dict(zip(op_names, [float(x) for x in per_op.mean(axis=0)])),
         "roofline": {"bound": "alu", "kernel": op_names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "basis": "8 B of gathered FP32 operands per interpolation step x steps per launch; peak = "

@@ -231,6 +231,27 @@ void nlrmm_default_opts(nlrmm_opts *opts);
 int nlrmm_gks_solve(ct_handle *h, const void *b, double *theta_inout, const double *delta, void *x_out,
                     const void *x_true, const nlrmm_opts *opts, nlrmm_stats *stats);
 
+/*
+ * VarPro reduced objective on a fixed basis (Sec. 4.2, Alg.
+ * "UPDATE-PARAM-VarPro"): with the image restricted to span(V) and the MM
+ * weights frozen,
+ *   f(theta) = min_y 1/2 |H(theta) V y - b|^2 + lam/2 |P Psi V y|^2,
+ *   P^2 = diag((z^2 + eps^2)^(-1/2)), z = Psi u_w   (u_w == NULL: P = I),
+ * and its gradient grad[v] = d f / d theta_v.  y is optimal for every theta,
+ * so the gradient is J_theta(u)^T (H(theta) u - b) at u = V y (the
+ * Golub-Pereyra / envelope form): one batched projection of V, the FP64
+ * reduced solve and one transposed-Jacobian pass; nothing of the inner solve
+ * is kept between calls.
+ *   b [n_views][B]; theta, delta [n_views] device double (delta nullable);
+ *   V [k][n_frames][N][N] device, k <= 62 columns; u_w [n_frames][N][N] or NULL;
+ *   fval: one device double; grad [n_views] device double or NULL;
+ *   u_out [n_frames][N][N] device or NULL.
+ * Allocates and frees its workspace; synchronises.  CT_OK, CT_ERR_ARG,
+ * CT_ERR_OOM or CT_ERR_CUDA.
+ */
+int nlrmm_varpro(ct_handle *h, const void *b, const double *theta, const double *delta, const void *V, int k,
+                 double lam, const void *u_w, double eps, double *fval, double *grad, void *u_out);
+
 /* ------------------------------------------------------------------------
  * Allocation-free transposed Jacobian (this entry point has no counterpart in
  * the paper; it exists for callers that cannot allocate device memory).

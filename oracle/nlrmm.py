@@ -319,3 +319,33 @@ class NLRMMGKS:
             if o.stop_on_convergence and du < o.tol_u and dth < o.tol_p:
                 break
         return u, theta, hist
+
+
+# ---------------------------------------------------------------------------
+# VarPro reduced objective on a fixed basis (Sec. 4.2, Alg. "UPDATE-PARAM-VarPro")
+# ---------------------------------------------------------------------------
+def varpro_objective(g: Geometry, b, theta, V, lam, w=None, delta=None):
+    """f(theta) = min_y 1/2 |H(theta) V y - b|^2 + lam/2 |P Psi V y|^2 with P^2 = diag(w)
+    (w = None: P = I), solved through the QR factors of H V and P Psi V as in the
+    reduced problem (3.5).  Returns (f, y, u = V y)."""
+    HV = np.stack([forward(g, theta, V[:, j], delta) for j in range(V.shape[1])], 1)
+    PsiV = np.stack([psi(g, V[:, j]) for j in range(V.shape[1])], 1)
+    if w is not None:
+        PsiV = np.sqrt(w)[:, None] * PsiV
+    QH, RH = np.linalg.qr(HV)
+    _, RP = np.linalg.qr(PsiV)
+    y = np.linalg.solve(RH.T @ RH + lam * (RP.T @ RP), RH.T @ (QH.T @ b))
+    r = HV @ y - b
+    s = PsiV @ y
+    return 0.5 * r @ r + 0.5 * lam * s @ s, y, V @ y
+
+
+def varpro_gradient(g: Geometry, b, theta, V, lam, w=None, delta=None):
+    """grad_theta f: y is optimal for every theta, so by the Golub-Pereyra
+    (envelope) argument the reduced gradient is J_theta(u)^T (H(theta) u - b)
+    with u = V y(theta), the data-term gradient (H_{p_i} u)^T (H u - b)."""
+    from . import jacT
+    f, y, u = varpro_objective(g, b, theta, V, lam, w, delta)
+    r = forward(g, theta, u, delta) - b
+    gt, _ = jacT(g, theta, u, r, delta)
+    return gt, f, u

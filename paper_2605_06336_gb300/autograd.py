@@ -58,3 +58,31 @@ class CTProject(torch.autograd.Function):
 def project(x, theta, op: CTOperator, delta=None):
     """y = H(theta, delta) x, differentiable in x, theta and delta."""
     return CTProject.apply(x, theta, delta, op)
+
+
+class VarProObjective(torch.autograd.Function):
+    """f(theta) of the VarPro reduced problem on a fixed basis (Sec. 4.2).
+
+    The inner reduced solve is not stored: backward recomputes it at the
+    saved angles (checkpointing) through ``nlrmm_varpro``, whose gradient is
+    J_theta(u)^T (H u - b) at the optimal u = V y (envelope form).
+    """
+
+    @staticmethod
+    def forward(ctx, theta, op: CTOperator, b, V, lam, u_w=None, eps=1e-3):
+        f, _, _ = op.varpro(b, theta.detach().contiguous(), V, lam, u_w, eps, want_grad=False)
+        ctx.op, ctx.lam, ctx.eps = op, lam, eps
+        ctx.save_for_backward(theta, b, V, u_w if u_w is not None else theta.new_empty(0))
+        ctx.has_w = u_w is not None
+        return f.reshape(())
+
+    @staticmethod
+    def backward(ctx, gf):
+        theta, b, V, u_w = ctx.saved_tensors
+        _, grad, _ = ctx.op.varpro(b, theta.detach().contiguous(), V, ctx.lam, u_w if ctx.has_w else None, ctx.eps)
+        return gf * grad, None, None, None, None, None, None
+
+
+def varpro_objective(theta, op: CTOperator, b, V, lam, u_w=None, eps=1e-3):
+    """Differentiable VarPro reduced objective f(theta)."""
+    return VarProObjective.apply(theta, op, b, V, lam, u_w, eps)

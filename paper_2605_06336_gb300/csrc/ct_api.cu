@@ -56,7 +56,7 @@ template <typename T>
 int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F));
+    CT_CUDA(ctgb::launch_prep_forward<T>(h, (const T *)X, batch * h.F));
     CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw));
     return CT_OK;
 }
@@ -280,7 +280,7 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
             for (int k = 0; k < vpf[f]; ++k) fov[v++] = f;
         }
         const size_t pair_bytes = 2 * elem_size(h);
-        const size_t img_pairs = (size_t)h.max_batch * h.F * h.N * h.Pp;
+        const size_t img_pairs = (size_t)(h.max_batch + 1) * h.F * h.N * h.Pp;
         const size_t sino_pairs = (size_t)h.max_batch * h.V * h.Pb;
         bool ok = cudaMalloc(&h.d_views, sizeof(ctgb::ViewGeo) * h.V) == cudaSuccess &&
                   cudaMalloc(&h.d_fov, sizeof(int) * h.V) == cudaSuccess &&

@@ -90,23 +90,48 @@ __global__ void __launch_bounds__(256 * SPLIT) k_adjoint(AdjArgs<T> a)
                 s_idx[q] = make_int2((int)fl, v * a.Pb);
             }
             __syncthreads();
-#pragma unroll 4
-            for (int q = grpv; q < nv; q += SPLIT) {
+            // Views in blocks of U: the U*KB sinogram pairs of a block are loaded
+            // before any is used (memory-level parallelism for the gathers).
+            constexpr int U = KB >= 4 ? 2 : 4;
+            int q = grpv;
+            for (; q + (U - 1) * SPLIT < nv; q += U * SPLIT) {
+                T wa[U], wb[U];
+                P2 p[U][KB];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const V4 gv = s_geo[q + u * SPLIT];
+                    const int2 ix = s_idx[q + u * SPLIT];
+                    const T t = fma(fx, gv.x, fma(-fy, gv.y, gv.w));
+                    int mm;
+                    T fr;
+                    floor_split(t, mm, fr);
+                    const T wv = gv.z;
+                    wa[u] = wv * fmax(T(0), fma(-fr, wv, T(1)));      // bin floor(beta)
+                    wb[u] = wv * fmax(T(0), fma(fr, wv, T(1) - wv));  // bin floor(beta) + 1
+                    const P2 *row = yp + ix.y + (min(max(ix.x + mm, -2), a.B) + 2);
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) p[u][k] = __ldg(row + (size_t)k * a.ysino_stride);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) acc[k] = fma(wa[u], p[u][k].x, fma(wb[u], p[u][k].y, acc[k]));
+            }
+            for (; q < nv; q += SPLIT) {
                 const V4 gv = s_geo[q];
                 const int2 ix = s_idx[q];
                 const T t = fma(fx, gv.x, fma(-fy, gv.y, gv.w));
-                int m;
+                int mm;
                 T fr;
-                floor_split(t, m, fr);
+                floor_split(t, mm, fr);
                 const T wv = gv.z;
-                const T w0 = fmax(T(0), fma(-fr, wv, T(1)));       // bin floor(beta)
-                const T w1 = fmax(T(0), fma(fr, wv, T(1) - wv));   // bin floor(beta) + 1
-                const int bp = min(max(ix.x + m, -2), a.B) + 2;
-                const P2 *row = yp + ix.y + bp;
+                const T w0 = wv * fmax(T(0), fma(-fr, wv, T(1)));
+                const T w1 = wv * fmax(T(0), fma(fr, wv, T(1) - wv));
+                const P2 *row = yp + ix.y + (min(max(ix.x + mm, -2), a.B) + 2);
 #pragma unroll
                 for (int k = 0; k < KB; ++k) {
-                    const P2 p = __ldg(row + (size_t)k * a.ysino_stride);
-                    acc[k] = fma(wv, fma(w0, p.x, w1 * p.y), acc[k]);
+                    const P2 pk = __ldg(row + (size_t)k * a.ysino_stride);
+                    acc[k] = fma(w0, pk.x, fma(w1, pk.y, acc[k]));
                 }
             }
         }

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ct_internal.cuh"
 
@@ -89,14 +92,34 @@ template <> struct GeoT<double> {
     __device__ static double sb(const ViewGeo &g, int b) { return g.sb0d + (double)b; }
 };
 
+// Resident CTAs per SM of a kernel at a launch shape, queried once per
+// (kernel, threads, shared memory) and cached: the occupancy query is a host
+// API call that would otherwise cost several microseconds per launch.
+inline int resident_per_sm(const void *kernel, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t>, int> cache;
+    const auto key = std::make_tuple(kernel, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = per_sm;
+    return per_sm;
+}
+
 // Persistent grid: as many CTAs as are resident at once, capped by the work.
 template <typename K>
 inline int persistent_grid(K kernel, int threads, size_t smem, long long work_blocks, int num_sms)
 {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
+    const int per_sm = resident_per_sm((const void *)kernel, threads, smem);
     const long long cap = (long long)per_sm * num_sms;
     return (int)std::max<long long>(1, std::min(work_blocks, cap));
 }

@@ -84,8 +84,8 @@ struct Handle {
     int *d_flag = nullptr;    // device-side status bits
     int *d_order = nullptr;   // view order of the ray kernels (sorted by axis and slope)
     int *d_changed = nullptr; // set when a view's constants were rebuilt (order is stale)
-    void *d_px = nullptr;     // pair images, rows of X:   max_batch * F * N * Pp pairs
-    void *d_pt = nullptr;     // pair images, rows of X^T: max_batch * F * N * Pp pairs
+    void *d_px = nullptr;     // pair images, rows of X:   (max_batch + 1) * F * N * Pp pairs
+    void *d_pt = nullptr;     // pair images, rows of X^T: (max_batch + 1) * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
     double *d_partial = nullptr;  // per (view, chunk) reduction partials, 4 per item
     int nchunks = 0;              // ceil(B / kChunk)
@@ -103,6 +103,9 @@ cudaError_t launch_view_setup(const Handle &h, const double *theta, const double
 template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip = nullptr);
 template <typename T>
 cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip = nullptr);
+// Layout the forward projection reads (pair images of X and X^T).
+template <typename T>
+cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip = nullptr);
 
 template <typename T>
 cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, const int *skip = nullptr);

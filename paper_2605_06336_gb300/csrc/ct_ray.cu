@@ -299,16 +299,41 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
             const long long dQ = 2 * g.Qh;
             const P2 *img = (g.mode ? a.PT : a.PX) + (size_t)g.frame * N * a.Pp + (size_t)k0 * a.pimg_stride +
                             (size_t)r0 * a.Pp + 2;
+            // Rows are processed in blocks of U: all loads of a block are issued
+            // before any of them is used, so U*KB gathers are in flight per warp.
+            constexpr int U = (MODE == kFwd) ? (KB >= 4 ? 4 : 8) : 8;
+            const int pp = a.Pp;
             if constexpr (MODE == kFwd) {
-#pragma unroll 4
-                for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ) {
+                int r = r0;
+                for (; r + U - 1 <= r1; r += U) {
+                    P2 p[U][KB];
+                    T f[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const long long Qu = Q + (long long)u * dQ;
+                        const int cell = min(max(cell_of(Qu), -2), N);
+                        f[u] = frac_of(Qu, T());
+                        const P2 *row = img + (size_t)u * pp + cell;
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) p[u][k] = __ldg(row + (size_t)k * a.pimg_stride);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const T omf = T(1) - f[u];
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) acc[k] = fma(omf, p[u][k].x, fma(f[u], p[u][k].y, acc[k]));
+                    }
+                    img += (size_t)U * pp;
+                    Q += (long long)U * dQ;
+                }
+                for (; r <= r1; ++r, img += pp, Q += dQ) {
                     const int cell = min(max(cell_of(Q), -2), N);
-                    const T f = frac_of(Q, T());
-                    const T omf = T(1) - f;
+                    const T fr = frac_of(Q, T());
+                    const T omf = T(1) - fr;
 #pragma unroll
                     for (int k = 0; k < KB; ++k) {
-                        const P2 p = __ldg(img + (size_t)k * a.pimg_stride + cell);
-                        acc[k] = fma(omf, p.x, fma(f, p.y, acc[k]));
+                        const P2 q = __ldg(img + (size_t)k * a.pimg_stride + cell);
+                        acc[k] = fma(omf, q.x, fma(fr, q.y, acc[k]));
                     }
                 }
             } else {
@@ -317,13 +342,34 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
                 const T g0 = fma(GeoT<T>::sb(g, b), GeoT<T>::gs(g), GeoT<T>::gh(g, N));
                 const T gr = GeoT<T>::gr(g);
                 T rf = (T)r0;
-#pragma unroll 4
-                for (int r = r0; r <= r1; ++r, img += a.Pp, Q += dQ, rf += T(1)) {
+                int r = r0;
+                for (; r + U - 1 <= r1; r += U) {
+                    P2 p[U];
+                    T f[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const long long Qu = Q + (long long)u * dQ;
+                        const int cell = min(max(cell_of(Qu), -2), N);
+                        f[u] = frac_of(Qu, T());
+                        p[u] = __ldg(img + (size_t)u * pp + cell);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const T d = p[u].y - p[u].x;
+                        acc[0] += fma(f[u], d, p[u].x);
+                        acc[1] = fma(d, fma(rf + T(u), gr, g0), acc[1]);
+                        if (OFFS) acc[2] += d;
+                    }
+                    img += (size_t)U * pp;
+                    Q += (long long)U * dQ;
+                    rf += T(U);
+                }
+                for (; r <= r1; ++r, img += pp, Q += dQ, rf += T(1)) {
                     const int cell = min(max(cell_of(Q), -2), N);
-                    const T f = frac_of(Q, T());
-                    const P2 p = __ldg(img + cell);
-                    const T d = p.y - p.x;
-                    acc[0] += fma(f, d, p.x);
+                    const T fr = frac_of(Q, T());
+                    const P2 q = __ldg(img + cell);
+                    const T d = q.y - q.x;
+                    acc[0] += fma(fr, d, q.x);
                     acc[1] = fma(d, fma(rf, gr, g0), acc[1]);
                     if (OFFS) acc[2] += d;
                 }
@@ -497,6 +543,11 @@ template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, 
     return cudaGetLastError();
 }
 
+template <typename T> cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip)
+{
+    return launch_pairs_img<T>(h, X, nimg, skip);
+}
+
 template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip)
 {
     const long long total = (long long)nsino * h.V * h.Pb;
@@ -575,6 +626,7 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
 #define CTGB_RAY_INSTANTIATE(T)                                                                             \
     template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int, const int *);                 \
     template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int, const int *);                \
+    template cudaError_t launch_prep_forward<T>(const Handle &, const T *, int, const int *);              \
     template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, const int *);          \
     template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int);     \
     template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int);           \

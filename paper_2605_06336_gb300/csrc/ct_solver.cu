@@ -223,7 +223,7 @@ template <typename T> struct Solver {
         SV_CUDA(launch_view_setup(h, theta, delta, stop));
         for (int j = j0; j < j0 + cnt; j += h.max_batch) {
             const int nb = std::min(h.max_batch, j0 + cnt - j);
-            SV_CUDA(launch_pairs_img<T>(h, col(V, n, j), nb * h.F, stop));
+            SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop));
             SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, stop));
         }
         return CT_OK;
@@ -405,6 +405,47 @@ template <typename T> struct Solver {
         return CT_OK;
     }
 
+    // ---- VarPro reduced objective and gradient on a given basis -----------------
+    // f(theta) = min_y 1/2 |H(theta) V y - b|^2 + lambda/2 |P Psi V y|^2, and
+    // grad f = J_theta(V y)^T (H(theta) V y - b) (Golub-Pereyra envelope form).
+    int varpro(const double *theta, const T *Vin, int k, double lam, const T *u_w, double *fval, double *grad,
+               T *u_out)
+    {
+        SV_TRY(setup());
+        double nb[3];
+        SV_TRY(norms3(b, nullptr, m, norms, nullptr));
+        SV_TRY(read_doubles(norms, 3, nb));
+        bnorm2 = nb[0];
+        SV_CUDA(cudaMemcpyAsync(V, Vin, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h.stream));
+        SV_TRY(project(theta, 0, k, nullptr));
+        SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
+        SV_TRY(full_gram(k));
+        if (u_w) {
+            k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u_w, w, h.N, h.F, o.eps, nullptr);
+        } else {
+            k_fill<T><<<grid_for(ne), kThreads, 0, h.stream>>>(w, ne, T(1));
+        }
+        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
+        k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k), h.stream>>>(V, n, k, w, h.N, h.F, part_gram,
+                                                                            nullptr);
+        k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gram_blocks, k, GP, nullptr);
+        k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
+                                                                     1, y, scal, ctl);
+        k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, u, T(0), T(1), nullptr, T(0), nullptr);
+        k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);
+        SV_TRY(norms3(res, nullptr, m, norms, nullptr));
+        k_varpro_value<<<1, 1, 0, h.stream>>>(norms, GP, y, k, lam, fval);
+        SV_CUDA(cudaGetLastError());
+        if (grad) {
+            SV_CUDA(launch_view_setup(h, theta, delta));
+            SV_CUDA(launch_pairs_img<T>(h, u, h.F));
+            SV_CUDA(launch_vjp<T>(h, res, grad, nullptr, h.tune.der_split, h.tune.der_vw));
+        }
+        if (u_out) SV_CUDA(cudaMemcpyAsync(u_out, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        return CT_OK;
+    }
+
     // ---- the whole solve ---------------------------------------------------------
     int run(double *theta_io, void *x_out, const T *x_true, nlrmm_stats *st)
     {
@@ -476,7 +517,7 @@ template <typename T> struct Solver {
             // residual of the normal equations at H_k, new weights, appended to V
             k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.eps, nullptr);
             SV_CUDA(launch_view_setup(h, th_k, delta));
-            SV_CUDA(launch_pairs_img<T>(h, u, h.F));
+            SV_CUDA(launch_prep_forward<T>(h, u, h.F));
             SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw));
             axpby(res, b, m, 1.0, -1.0);
             SV_TRY(backproject(th_k, res, col(V, n, kc), nullptr));
@@ -597,6 +638,43 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
     } else {
         Solver<float> s(h, ps, o, (const float *)b, delta);
         rc = s.run(theta_inout, x_out, (const float *)x_true, stats);
+    }
+    cudaStreamSynchronize(ps);
+    cudaEventDestroy(e0);
+    cudaStreamDestroy(ps);
+    return rc;
+}
+
+int nlrmm_varpro(ct_handle *H, const void *b, const double *theta, const double *delta, const void *V, int k,
+                 double lam, const void *u_w, double eps, double *fval, double *grad, void *u_out)
+{
+    if (!H || !b || !theta || !V || !fval || k < 1 || k + 2 > ctgb::solver::kKMax || !(lam > 0.0) ||
+        (u_w && !(eps > 0.0)))
+        return CT_ERR_ARG;
+    ctgb::Handle &h = H->h;
+    nlrmm_opts o;
+    nlrmm_default_opts(&o);
+    o.k_min = 2;
+    o.k_max = k;
+    o.eps = eps > 0.0 ? eps : 1e-3;
+    o.lam_fix = lam;
+    cudaStream_t ps = nullptr;
+    cudaEvent_t e0 = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(e0, h.stream) != cudaSuccess || cudaStreamWaitEvent(ps, e0, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        if (ps) cudaStreamDestroy(ps);
+        return CT_ERR_CUDA;
+    }
+    int rc;
+    if (h.precision) {
+        Solver<double> s(h, ps, o, (const double *)b, delta);
+        rc = s.varpro(theta, (const double *)V, k, lam, (const double *)u_w, fval, grad, (double *)u_out);
+    } else {
+        Solver<float> s(h, ps, o, (const float *)b, delta);
+        rc = s.varpro(theta, (const float *)V, k, lam, (const float *)u_w, fval, grad, (float *)u_out);
     }
     cudaStreamSynchronize(ps);
     cudaEventDestroy(e0);

@@ -673,6 +673,22 @@ __global__ void __launch_bounds__(256) k_compress_basis(const double *__restrict
     }
 }
 
+// VarPro reduced objective f = 1/2 |res|^2 + lambda/2 y^T G_P y (one thread).
+__global__ void k_varpro_value(const double *__restrict__ norms3_res, const double *__restrict__ GP,
+                               const double *__restrict__ y, int k, double lam, double *__restrict__ fval)
+{
+    double q = 0.0;
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) q += y[i] * GP[i * kKMax + j] * y[j];
+    *fval = 0.5 * norms3_res[0] + 0.5 * lam * q;
+}
+
+template <typename T> __global__ void k_fill(T *__restrict__ x, long long len, T value)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+        x[i] = value;
+}
+
 // ---------------------------------------------------------------------------
 // Gauss-Newton per view (diagonal J^T J): direction and Armijo bookkeeping
 // ---------------------------------------------------------------------------

@@ -109,6 +109,8 @@ def load_library(path: str | None = None):
     lib.ct_set_tuning.argtypes = [P, P]
     lib.ct_jacT_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P, P]
     lib.ct_jacT_noalloc.restype = ctypes.c_int
+    lib.nlrmm_varpro.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_double, P, ctypes.c_double, P, P, P]
+    lib.nlrmm_varpro.restype = ctypes.c_int
     lib.nlrmm_default_opts.argtypes = [P]
     lib.nlrmm_default_opts.restype = None
     lib.nlrmm_gks_solve.argtypes = [P, P, P, P, P, P, P, P]
@@ -248,6 +250,11 @@ def nlrmm_gks_solve(h, b, theta_inout, delta, x_out, x_true=None, opts=None, **o
     return rc, stats
 
 
+def nlrmm_varpro(h, b, theta, delta, V, k, lam, u_w, eps, fval, grad=None, u_out=None):
+    _check(load_library().nlrmm_varpro(h, _p(b), _p(theta), _p(delta), _p(V), int(k), float(lam), _p(u_w),
+                                       float(eps), _p(fval), _p(grad), _p(u_out)), "nlrmm_varpro")
+
+
 # --- tensor-level wrapper ---------------------------------------------------
 
 class CTOperator:
@@ -356,6 +363,19 @@ class CTOperator:
 
     def set_stream(self, stream=None):
         ct_set_stream(self.h, stream)
+
+    def varpro(self, b, theta, V, lam, u_w=None, eps=1e-3, delta=None, want_grad=True):
+        """VarPro reduced objective on the basis V (k x n): returns (f, grad or None, u)."""
+        self._chk(b, self.m, "b")
+        self._chk(V, self.n, "V")
+        fval = torch.empty(1, dtype=torch.float64, device=b.device)
+        grad = torch.empty(self.V, dtype=torch.float64, device=b.device) if want_grad else None
+        u = torch.empty(self.n, dtype=self.dtype, device=b.device)
+        if u_w is not None:
+            self._chk(u_w, self.n, "u_w")
+        nlrmm_varpro(self.h, b, self._ang(theta, "theta"), self._ang(delta, "delta"), V.contiguous(),
+                     V.shape[0], lam, u_w, eps, fval, grad, u)
+        return fval[0], grad, u
 
     def solve(self, b, theta0, delta=None, x_true=None, **opts):
         """NL-RMM-GKS: returns (x, theta, stats).  theta0 is not modified."""

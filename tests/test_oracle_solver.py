@@ -185,3 +185,26 @@ def test_small_alternating_solve_reduces_errors():
     assert np.linalg.norm(th - th_true) < 0.5 * e0
     assert hist.rre[-1] < hist.rre[0]
     assert hist.rre[-1] < 0.5
+
+
+def test_varpro_reduced_gradient_matches_central_differences():
+    # smooth image and a basis of smooth vectors: few interpolation kinks change slope
+    g, th_nom, th_true, u_true, b, nn = small_problem(N=20, V=14, seed=11)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(noise_norm=nn))
+    V = s.gkb(th_nom, 6)
+    rng = np.random.default_rng(12)
+    w = rng.uniform(0.5, 2.0, 2 * g.N * (g.N - 1))
+    lam = 0.2
+    grad, f0, _ = nlrmm.varpro_gradient(g, b, th_nom, V, lam, w)
+    errs = {}
+    for h in (1e-4, 1e-5, 1e-6):
+        err = ref = 0.0
+        for _ in range(8):
+            d = rng.standard_normal(g.V)
+            fp = nlrmm.varpro_objective(g, b, th_nom + h * d, V, lam, w)[0]
+            fm = nlrmm.varpro_objective(g, b, th_nom - h * d, V, lam, w)[0]
+            err += abs((fp - fm) / (2 * h) - grad @ d)
+            ref += abs(grad @ d)
+        errs[h] = err / ref
+    assert errs[1e-4] < 5e-2, errs
+    assert errs[1e-6] < max(errs[1e-4] / 20, 1e-7), errs
