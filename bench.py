@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-solver", action="store_true", help="skip the NL-RMM-GKS comparison")
     ap.add_argument("--solver-iters", type=int, default=30)
     ap.add_argument("--tuning", default=None,
-                    help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw' instead of autotuning")
+                    help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw,fstage,jstage' instead of autotuning")
     return ap.parse_args()
 
 

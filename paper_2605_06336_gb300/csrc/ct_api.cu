@@ -46,10 +46,12 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_pt);
     cudaFree(h.d_yp);
     cudaFree(h.d_partial);
+    cudaFree(h.d_fpart);
     h.d_views = nullptr;
     h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = h.d_changed = nullptr;
     h.d_px = h.d_pt = h.d_yp = nullptr;
     h.d_partial = nullptr;
+    h.d_fpart = nullptr;
 }
 
 template <typename T>
@@ -57,7 +59,7 @@ int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const 
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_prep_forward<T>(h, (const T *)X, batch * h.F));
-    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw));
+    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
     return CT_OK;
 }
 
@@ -76,7 +78,7 @@ int do_jac(ctgb::Handle &h, const double *theta, const double *delta, const void
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
-    CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split, h.tune.der_vw));
+    CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
     return CT_OK;
 }
 
@@ -86,7 +88,7 @@ int do_jacT(ctgb::Handle &h, const double *theta, const double *delta, const voi
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
-    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split, h.tune.der_vw));
+    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
     return CT_OK;
 }
 
@@ -96,7 +98,22 @@ int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void 
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
-    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw));
+    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw,
+                                  h.tune.der_stage));
+    return CT_OK;
+}
+
+// Workspace of the band-staged forward with row segments per ray (three
+// partial sinogram batches), allocated the first time such a shape is set.
+int ensure_fwd_partials(ctgb::Handle &h)
+{
+    if (h.d_fpart || h.precision != 0) return CT_OK;
+    const size_t bytes = sizeof(float) * 3 * (size_t)h.max_batch * h.V * h.B;
+    if (cudaMalloc(&h.d_fpart, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h.d_fpart = nullptr;
+        return CT_ERR_OOM;
+    }
     return CT_OK;
 }
 
@@ -169,18 +186,37 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         const int K = h.max_batch;
         float best = 1e30f;
         ctgb::Tuning t = h.tune;
+        // L1-gather shapes (stage 0), then band-staged ones (FP32: stage = rows per block)
+        const bool fp32 = h.precision == 0;
         for (int kb : {1, 2, 4, 8}) {
             if (kb > K) continue;
             for (int sp : {1, 2, 4, 8}) {
                 for (int vw : {1, 2, 4, 8}) {
                     if (sp * vw > 16) continue;
                     const float ms =
-                        time_config(h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw); });
+                        time_config(h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, 0); });
                     if (ms < best) {
                         best = ms;
                         t.fwd_kb = kb;
                         t.fwd_split = sp;
                         t.fwd_vw = vw;
+                        t.fwd_stage = 0;
+                    }
+                }
+            }
+            for (int st : {4, 8}) {
+                for (int vw : {4, 8}) {
+                    for (int sp : {1, 2, 4}) {
+                        if (!fp32 || (sp > 1 && ensure_fwd_partials(h) != CT_OK)) continue;
+                        const float ms = time_config(
+                            h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, st); });
+                        if (ms < best) {
+                            best = ms;
+                            t.fwd_kb = kb;
+                            t.fwd_split = sp;
+                            t.fwd_vw = vw;
+                            t.fwd_stage = st;
+                        }
                     }
                 }
             }
@@ -202,11 +238,25 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
             for (int vw : {1, 2, 4, 8}) {
                 if (sp * vw > 16) continue;
                 const float ms =
-                    time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp, vw); });
+                    time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp, vw, 0); });
                 if (ms < best) {
                     best = ms;
                     t.der_split = sp;
                     t.der_vw = vw;
+                    t.der_stage = 0;
+                }
+            }
+        }
+        for (int st : {4, 8}) {
+            for (int vw : {4, 8}) {
+                if (!fp32) continue;
+                const float ms =
+                    time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, 1, vw, st); });
+                if (ms < best) {
+                    best = ms;
+                    t.der_split = 1;
+                    t.der_vw = vw;
+                    t.der_stage = st;
                 }
             }
         }
@@ -381,35 +431,40 @@ int ct_autotune(ct_handle *H)
     return H->h.precision ? autotune_impl<double>(H->h) : autotune_impl<float>(H->h);
 }
 
-int ct_get_tuning(ct_handle *H, int32_t *out7)
+int ct_get_tuning(ct_handle *H, int32_t *out)
 {
-    if (!H || !out7) return CT_ERR_ARG;
+    if (!H || !out) return CT_ERR_ARG;
     const ctgb::Tuning &t = H->h.tune;
-    out7[0] = t.fwd_kb;
-    out7[1] = t.fwd_split;
-    out7[2] = t.fwd_vw;
-    out7[3] = t.adj_kb;
-    out7[4] = t.adj_split;
-    out7[5] = t.der_split;
-    out7[6] = t.der_vw;
+    const int32_t v[CT_TUNING_COUNT] = {t.fwd_kb,    t.fwd_split, t.fwd_vw,    t.adj_kb,   t.adj_split,
+                                        t.der_split, t.der_vw,    t.fwd_stage, t.der_stage};
+    for (int i = 0; i < CT_TUNING_COUNT; ++i) out[i] = v[i];
     return CT_OK;
 }
 
-int ct_set_tuning(ct_handle *H, const int32_t *in7)
+int ct_set_tuning(ct_handle *H, const int32_t *in)
 {
-    if (!H || !in7) return CT_ERR_ARG;
+    if (!H || !in) return CT_ERR_ARG;
     auto pow2 = [](int x, int hi) { return x >= 1 && x <= hi && (x & (x - 1)) == 0; };
-    if (!pow2(in7[0], 8) || !pow2(in7[1], 8) || !pow2(in7[2], 8) || !pow2(in7[3], 8) || !pow2(in7[4], 4) ||
-        !pow2(in7[5], 8) || !pow2(in7[6], 8) || in7[1] * in7[2] > 16 || in7[5] * in7[6] > 16)
+    auto stage_ok = [](int st, int vw) { return st == 0 || ((st == 4 || st == 8) && (vw == 4 || vw == 8)); };
+    if (!pow2(in[0], 8) || !pow2(in[1], 8) || !pow2(in[2], 8) || !pow2(in[3], 8) || !pow2(in[4], 4) ||
+        !pow2(in[5], 8) || !pow2(in[6], 8) || (in[7] == 0 && in[1] * in[2] > 16) ||
+        (in[8] == 0 && in[5] * in[6] > 16) || !stage_ok(in[7], in[2]) || !stage_ok(in[8], in[6]) ||
+        (in[7] > 0 && in[1] > 4))
         return CT_ERR_ARG;
+    if (in[7] > 0 && in[1] > 1) {
+        const int rc = ensure_fwd_partials(H->h);
+        if (rc != CT_OK) return rc;
+    }
     ctgb::Tuning &t = H->h.tune;
-    t.fwd_kb = in7[0];
-    t.fwd_split = in7[1];
-    t.fwd_vw = in7[2];
-    t.adj_kb = in7[3];
-    t.adj_split = in7[4];
-    t.der_split = in7[5];
-    t.der_vw = in7[6];
+    t.fwd_kb = in[0];
+    t.fwd_split = in[1];
+    t.fwd_vw = in[2];
+    t.adj_kb = in[3];
+    t.adj_split = in[4];
+    t.der_split = in[5];
+    t.der_vw = in[6];
+    t.fwd_stage = in[7];
+    t.der_stage = in[8];
     return CT_OK;
 }
 

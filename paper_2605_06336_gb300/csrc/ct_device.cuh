@@ -92,6 +92,124 @@ template <> struct GeoT<double> {
     __device__ static double sb(const ViewGeo &g, int b) { return g.sb0d + (double)b; }
 };
 
+// ---------------------------------------------------------------------------
+// ray march arguments (ct_ray.cu, ct_band.cu)
+// ---------------------------------------------------------------------------
+enum RayMode { kFwd = 0, kJvp = 1, kVjp = 2, kGn = 3 };
+
+template <typename T> struct RayArgs {
+    const ViewGeo *vg;
+    int V, N, B, nchunks, Pp;
+    const pair_t<T> *PX, *PT;
+    long long pimg_stride;  // pairs per batch element (F * N * Pp)
+    int kbase, ngroups;
+    T *Y;                   // FWD: [batch][V*B]; JVP: dY
+    long long sino_stride;
+    const double *dtheta, *ddelta;
+    const T *R;             // VJP: r; GN: data b
+    T *res;                 // GN: residual (nullable)
+    double *partial;        // VJP / GN
+    const int *view_mask;   // GN: views with mask 0 are skipped (nullable)
+    const int *skip;        // whole launch is a no-op when *skip != 0 (nullable)
+    const int *order;       // view order (nullable: identity)
+    int VW;                 // view slots per CTA
+    int segs;               // band-staged forward: row segments per ray, one CTA each (1: whole rays)
+    T *fpart;               // segments 1..segs-1 of the band-staged forward (segment 0 goes to Y)
+    long long fpart_stride; // elements per segment in fpart
+};
+
+// Warp-uniform row range [rlo, rhi] covering every row where one of the
+// warp's rays has -1 < q < N; rows added by the union or by the two-row
+// margin read exact zeros.
+__device__ __forceinline__ void warp_rows(const ViewGeo &g, int b, bool active, int N, int &rlo, int &rhi)
+{
+    if (g.flags & kAllRows) {
+        rlo = 0;
+        rhi = N - 1;
+        return;
+    }
+    const float r1 = fmaf((float)b, g.gam, g.alo);
+    const float r2 = fmaf((float)b, g.gam, g.ahi);
+    const float lo = fminf(fmaxf(fminf(r1, r2) - 2.0f, 0.0f), (float)N);
+    const float hi = fmaxf(fminf(fmaxf(r1, r2) + 2.0f, (float)(N - 1)), -1.0f);
+    int l = (int)floorf(lo), u = (int)ceilf(hi);
+    if (!active) {
+        l = N;
+        u = -1;
+    }
+    rlo = __reduce_min_sync(0xffffffffu, l);
+    rhi = __reduce_max_sync(0xffffffffu, u);
+}
+
+// Per-ray output of a march: the forward stores w * sum for each image, the
+// JVP stores the directional derivative, the VJP and Gauss-Newton modes write
+// per-(view, chunk) partial sums reduced over the warp in a fixed order.
+template <typename T, int MODE, bool OFFS, int KB>
+__device__ __forceinline__ void ray_epilogue(const RayArgs<T> &a, const ViewGeo &g, int v, int b, bool active, int k0,
+                                             int chunk, int lane, const T (&acc)[(MODE == kFwd) ? KB : 3])
+{
+    const T wv = GeoT<T>::w(g);
+    if constexpr (MODE == kFwd) {
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = wv * acc[k];
+        }
+    } else {
+        const T jt = fma(GeoT<T>::dw(g), acc[0], wv * acc[1]);
+        const T jd = wv * GeoT<T>::qb(g) * acc[2];
+        if constexpr (MODE == kJvp) {
+            if (active) {
+                T out = (T)a.dtheta[v] * jt;
+                if (OFFS) out = fma((T)a.ddelta[v], jd, out);
+                a.Y[(size_t)v * a.B + b] = out;
+            }
+        } else if constexpr (MODE == kVjp) {
+            double pt = 0.0, pd = 0.0;
+            if (active) {
+                const T r = a.R[(size_t)v * a.B + b];
+                pt = (double)(r * jt);
+                if (OFFS) pd = (double)(r * jd);
+            }
+            pt = warp_sum(pt);
+            if (OFFS) pd = warp_sum(pd);
+            if (lane == 0) {
+                double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                p[0] = pt;
+                p[1] = pd;
+            }
+        } else {  // kGn
+            double pg = 0.0, pj = 0.0, pf = 0.0;
+            if (active) {
+                const T rr = wv * acc[0] - a.R[(size_t)v * a.B + b];
+                if (a.res) a.res[(size_t)v * a.B + b] = rr;
+                pg = (double)rr * (double)jt;
+                pj = (double)jt * (double)jt;
+                pf = (double)rr * (double)rr;
+            }
+            pg = warp_sum(pg);
+            pj = warp_sum(pj);
+            pf = warp_sum(pf);
+            if (lane == 0) {
+                double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                p[0] = pg;
+                p[1] = pj;
+                p[2] = pf;
+            }
+        }
+    }
+}
+
+// Band-staged FP32 ray march (ct_band.cu): the rows a CTA's rays cross are
+// staged in shared memory block by block.  a.VW in {4, 8} view slots, rb in
+// {4, 8} rows per staged block, kb in {1, 2, 4, 8} images (forward only).
+// Results are bit-identical to k_ray with one row segment per ray.
+bool band_shape_ok(int mode, int kb, int vw, int rb);
+cudaError_t run_ray_band(const Handle &h, const RayArgs<float> &a, int mode, bool offs, int kb, int rb);
+// Y[k][v][b] = w_v * (Y + P_1 + ... + P_{segs-1}), summed in segment order.
+cudaError_t launch_fwd_combine(const Handle &h, float *Y, const float *P, int segs, long long stride, int batch,
+                               const int *skip);
+
 // Resident CTAs per SM of a kernel at a launch shape, queried once per
 // (kernel, threads, shared memory) and cached: the occupancy query is a host
 // API call that would otherwise cost several microseconds per launch.

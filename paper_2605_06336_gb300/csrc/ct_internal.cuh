@@ -65,11 +65,16 @@ struct __align__(16) ViewGeo {
 // one ray (row segments, combined in shared memory) or thread groups sharing
 // one pixel tile (view subsets, combined in shared memory).
 // vw: view slots per CTA for the ray kernels (neighbouring views of the
-// sorted view order, sharing the image band in L1).
+// sorted view order, sharing the image band in L1 or shared memory).
+// stage: 0 = gather through L1; 4 or 8 = rows per block of the band-staged
+// FP32 march (vw 4 or 8).  There the forward's split is the number of CTAs
+// that share one ray (row segments, combined by a second kernel); the
+// derivative kernels march whole rays.
 struct Tuning {
     int fwd_kb = 8, fwd_split = 2, fwd_vw = 1;  // forward projection of a batch
     int adj_kb = 8, adj_split = 2;              // transpose of a batch
     int der_split = 4, der_vw = 1;              // JVP / VJP / Gauss-Newton terms (one image)
+    int fwd_stage = 0, der_stage = 0;
 };
 
 struct Handle {
@@ -88,6 +93,8 @@ struct Handle {
     void *d_pt = nullptr;     // pair images, rows of X^T: (max_batch + 1) * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
     double *d_partial = nullptr;  // per (view, chunk) reduction partials, 4 per item
+    void *d_fpart = nullptr;      // row-segment partial sinograms of the band-staged forward:
+                                  // 3 * max_batch * V * B elements, allocated when such a shape is set
     int nchunks = 0;              // ceil(B / kChunk)
     int num_sms = 0;
     Tuning tune;
@@ -107,16 +114,20 @@ cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int 
 template <typename T>
 cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip = nullptr);
 
+// stage > 0 (FP32 only): rows per shared-memory block of the band-staged
+// march (ct_band.cu); 0: gathers through L1.
 template <typename T>
-cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, const int *skip = nullptr);
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, int stage,
+                           const int *skip = nullptr);
 template <typename T>
 cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip = nullptr);
 template <typename T>
-cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw);
+cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw,
+                       int stage);
 template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw);
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw, int stage);
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval,
-                      int split, int vw, const int *view_mask = nullptr, const int *skip = nullptr);
+                      int split, int vw, int stage, const int *view_mask = nullptr, const int *skip = nullptr);
 
 }  // namespace ctgb

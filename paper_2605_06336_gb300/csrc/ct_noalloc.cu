@@ -104,6 +104,6 @@ extern "C" int ct_jacT_noalloc(int32_t N, int32_t B, int32_t n_views, const doub
         return CT_ERR_CUDA;
     if (ctgb::launch_view_setup(h, theta, delta) != cudaSuccess) return CT_ERR_CUDA;
     if (ctgb::launch_pairs_img<float>(h, x, 1) != cudaSuccess) return CT_ERR_CUDA;
-    if (ctgb::launch_vjp<float>(h, r, gtheta, gdelta, h.tune.der_split, 1) != cudaSuccess) return CT_ERR_CUDA;
+    if (ctgb::launch_vjp<float>(h, r, gtheta, gdelta, h.tune.der_split, 1, 0) != cudaSuccess) return CT_ERR_CUDA;
     return CT_OK;
 }

@@ -16,6 +16,8 @@
 // per-parameter derivatives H_{p_i} u of Alg. "UPDATE-PARAM").
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 
@@ -109,26 +111,27 @@ __global__ void k_view_setup(const double *__restrict__ theta, const double *__r
     *gp = g;
 }
 
-// View order for the ray kernels: views sorted by marching axis, then by ray
-// slope qr (ties by index), so that consecutive entries sweep nearly the same
-// image band.  One CTA; runs only when a view changed since the last sort.
+// View order for the ray kernels: views sorted by frame, then by marching
+// axis, then by ray slope qr (ties by index), so that consecutive entries
+// read the same image and sweep nearly the same band of it.  One CTA; runs
+// only when a view changed since the last sort.
 constexpr int kOrderMaxV = 4096;
 __global__ void __launch_bounds__(1024) k_view_order(const ViewGeo *__restrict__ vg, int V, int *__restrict__ order,
                                                      int *__restrict__ changed, const int *__restrict__ skip)
 {
     if ((skip && *skip) || !*changed) return;
-    __shared__ float key[kOrderMaxV];
+    __shared__ double key[kOrderMaxV];
     if (V > kOrderMaxV) {
         for (int i = threadIdx.x; i < V; i += blockDim.x) order[i] = i;
     } else {
         for (int i = threadIdx.x; i < V; i += blockDim.x)
-            key[i] = (float)(vg[i].mode * 4.0 + 1.0 + (double)vg[i].Qh * (2.0 / kFixScale));
+            key[i] = vg[i].frame * 8.0 + vg[i].mode * 4.0 + 1.0 + (double)vg[i].Qh * (2.0 / kFixScale);
         __syncthreads();
         for (int i = threadIdx.x; i < V; i += blockDim.x) {
-            const float ki = key[i];
+            const double ki = key[i];
             int rank = 0;
             for (int j = 0; j < V; ++j) {
-                const float kj = key[j];
+                const double kj = key[j];
                 rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
             }
             order[rank] = i;
@@ -208,49 +211,6 @@ __global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP
 // ---------------------------------------------------------------------------
 // ray march
 // ---------------------------------------------------------------------------
-enum RayMode { kFwd = 0, kJvp = 1, kVjp = 2, kGn = 3 };
-
-template <typename T> struct RayArgs {
-    const ViewGeo *vg;
-    int V, N, B, nchunks, Pp;
-    const pair_t<T> *PX, *PT;
-    long long pimg_stride;  // pairs per batch element (F * N * Pp)
-    int kbase, ngroups;
-    T *Y;                   // FWD: [batch][V*B]; JVP: dY
-    long long sino_stride;
-    const double *dtheta, *ddelta;
-    const T *R;             // VJP: r; GN: data b
-    T *res;                 // GN: residual (nullable)
-    double *partial;        // VJP / GN
-    const int *view_mask;   // GN: views with mask 0 are skipped (nullable)
-    const int *skip;        // whole launch is a no-op when *skip != 0 (nullable)
-    const int *order;       // view order (nullable: identity)
-    int VW;                 // view slots per CTA
-};
-
-// Warp-uniform row range [rlo, rhi] covering every row where one of the
-// warp's rays has -1 < q < N; rows added by the union or by the two-row
-// margin read exact zeros.
-__device__ __forceinline__ void warp_rows(const ViewGeo &g, int b, bool active, int N, int &rlo, int &rhi)
-{
-    if (g.flags & kAllRows) {
-        rlo = 0;
-        rhi = N - 1;
-        return;
-    }
-    const float r1 = fmaf((float)b, g.gam, g.alo);
-    const float r2 = fmaf((float)b, g.gam, g.ahi);
-    const float lo = fminf(fmaxf(fminf(r1, r2) - 2.0f, 0.0f), (float)N);
-    const float hi = fmaxf(fminf(fmaxf(r1, r2) + 2.0f, (float)(N - 1)), -1.0f);
-    int l = (int)floorf(lo), u = (int)ceilf(hi);
-    if (!active) {
-        l = N;
-        u = -1;
-    }
-    rlo = __reduce_min_sync(0xffffffffu, l);
-    rhi = __reduce_max_sync(0xffffffffu, u);
-}
-
 // One CTA = VW view slots x SPLIT row segments, all on the same 32-bin chunk.
 // The view slots take VW consecutive entries of the view order (views sorted
 // by marching axis and ray slope), so the warps of a CTA sweep nearly the
@@ -391,58 +351,7 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
                 }
             }
         }
-        if (seg == 0 && live) {
-            const T wv = GeoT<T>::w(g);
-            if constexpr (MODE == kFwd) {
-                if (active) {
-#pragma unroll
-                    for (int k = 0; k < KB; ++k)
-                        a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = wv * acc[k];
-                }
-            } else {
-                const T jt = fma(GeoT<T>::dw(g), acc[0], wv * acc[1]);
-                const T jd = wv * GeoT<T>::qb(g) * acc[2];
-                if constexpr (MODE == kJvp) {
-                    if (active) {
-                        T out = (T)a.dtheta[v] * jt;
-                        if (OFFS) out = fma((T)a.ddelta[v], jd, out);
-                        a.Y[(size_t)v * a.B + b] = out;
-                    }
-                } else if constexpr (MODE == kVjp) {
-                    double pt = 0.0, pd = 0.0;
-                    if (active) {
-                        const T r = a.R[(size_t)v * a.B + b];
-                        pt = (double)(r * jt);
-                        if (OFFS) pd = (double)(r * jd);
-                    }
-                    pt = warp_sum(pt);
-                    if (OFFS) pd = warp_sum(pd);
-                    if (lane == 0) {
-                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
-                        p[0] = pt;
-                        p[1] = pd;
-                    }
-                } else {  // kGn
-                    double pg = 0.0, pj = 0.0, pf = 0.0;
-                    if (active) {
-                        const T rr = wv * acc[0] - a.R[(size_t)v * a.B + b];
-                        if (a.res) a.res[(size_t)v * a.B + b] = rr;
-                        pg = (double)rr * (double)jt;
-                        pj = (double)jt * (double)jt;
-                        pf = (double)rr * (double)rr;
-                    }
-                    pg = warp_sum(pg);
-                    pj = warp_sum(pj);
-                    pf = warp_sum(pf);
-                    if (lane == 0) {
-                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
-                        p[0] = pg;
-                        p[1] = pj;
-                        p[2] = pf;
-                    }
-                }
-            }
-        }
+        if (seg == 0 && live) ray_epilogue<T, MODE, OFFS, KB>(a, g, v, b, active, k0, chunk, lane, acc);
         if constexpr (SPLIT > 1) __syncthreads();  // red[] is reused by the next item
     }
 }
@@ -486,6 +395,7 @@ template <typename T> RayArgs<T> base_args(const Handle &h)
     a.sino_stride = (long long)h.V * h.B;
     a.order = h.d_order;
     a.VW = 1;
+    a.segs = 1;
     return a;
 }
 
@@ -513,14 +423,25 @@ cudaError_t run_ray_split(const Handle &h, const RayArgs<T> &a, int split)
     }
 }
 
+// FP32 with a staged shape runs the band kernel (ct_band.cu); every other
+// case runs k_ray.
+template <typename T, int MODE, bool OFFS, int KB>
+cudaError_t run_ray_any(const Handle &h, const RayArgs<T> &a, int split, int stage)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        if (stage > 0 && band_shape_ok(MODE, KB, a.VW, stage)) return run_ray_band(h, a, MODE, OFFS, KB, stage);
+    }
+    return run_ray_split<T, MODE, OFFS, KB>(h, a, split);
+}
+
 template <typename T>
-cudaError_t fwd_groups(const Handle &h, RayArgs<T> a, int kb, int split)
+cudaError_t fwd_groups(const Handle &h, RayArgs<T> a, int kb, int split, int stage)
 {
     switch (kb) {
-    case 1: return run_ray_split<T, kFwd, false, 1>(h, a, split);
-    case 2: return run_ray_split<T, kFwd, false, 2>(h, a, split);
-    case 4: return run_ray_split<T, kFwd, false, 4>(h, a, split);
-    default: return run_ray_split<T, kFwd, false, 8>(h, a, split);
+    case 1: return run_ray_any<T, kFwd, false, 1>(h, a, split, stage);
+    case 2: return run_ray_any<T, kFwd, false, 2>(h, a, split, stage);
+    case 4: return run_ray_any<T, kFwd, false, 4>(h, a, split, stage);
+    default: return run_ray_any<T, kFwd, false, 8>(h, a, split, stage);
     }
 }
 
@@ -559,12 +480,20 @@ template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y,
 }
 
 template <typename T>
-cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, const int *skip)
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, int stage, const int *skip)
 {
     RayArgs<T> a = base_args<T>(h);
     a.Y = Y;
     a.skip = skip;
     a.VW = vw;
+    // band-staged FP32 march with `split` CTAs per ray: segment partials go to Y and d_fpart
+    const bool band = std::is_same<T, float>::value && stage > 0 && band_shape_ok(kFwd, 1, vw, stage);
+    if (band && split > 1) {
+        if (!h.d_fpart || split > 4) return cudaErrorInvalidValue;
+        a.segs = split;
+        a.fpart = (T *)h.d_fpart;
+        a.fpart_stride = (long long)h.max_batch * h.V * h.B;
+    }
     int k = 0;
     for (int width : {8, 4, 2, 1}) {
         if (width > kb) continue;
@@ -572,33 +501,37 @@ cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, 
         if (groups == 0) continue;
         a.kbase = k;
         a.ngroups = groups;
-        cudaError_t e = fwd_groups<T>(h, a, width, split);
+        cudaError_t e = fwd_groups<T>(h, a, width, split, stage);
         if (e != cudaSuccess) return e;
         k += groups * width;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (a.segs > 1) return launch_fwd_combine(h, Y, a.fpart, a.segs, a.fpart_stride, batch, skip);
     }
     return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw)
+cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw,
+                       int stage)
 {
     RayArgs<T> a = base_args<T>(h);
     a.VW = vw;
     a.Y = dY;
     a.dtheta = dtheta;
     a.ddelta = ddelta;
-    return ddelta ? run_ray_split<T, kJvp, true, 1>(h, a, split) : run_ray_split<T, kJvp, false, 1>(h, a, split);
+    return ddelta ? run_ray_any<T, kJvp, true, 1>(h, a, split, stage) : run_ray_any<T, kJvp, false, 1>(h, a, split, stage);
 }
 
 template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw)
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw, int stage)
 {
     RayArgs<T> a = base_args<T>(h);
     a.VW = vw;
     a.R = R;
     a.partial = h.d_partial;
-    cudaError_t e = gdelta ? run_ray_split<T, kVjp, true, 1>(h, a, split)
-                           : run_ray_split<T, kVjp, false, 1>(h, a, split);
+    cudaError_t e = gdelta ? run_ray_any<T, kVjp, true, 1>(h, a, split, stage)
+                           : run_ray_any<T, kVjp, false, 1>(h, a, split, stage);
     if (e != cudaSuccess) return e;
     k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0,
                                                         nullptr, nullptr);
@@ -607,7 +540,7 @@ cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdel
 
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval, int split,
-                      int vw, const int *view_mask, const int *skip)
+                      int vw, int stage, const int *view_mask, const int *skip)
 {
     RayArgs<T> a = base_args<T>(h);
     a.VW = vw;
@@ -616,7 +549,7 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
     a.partial = h.d_partial;
     a.view_mask = view_mask;
     a.skip = skip;
-    cudaError_t e = run_ray_split<T, kGn, false, 1>(h, a, split);
+    cudaError_t e = run_ray_any<T, kGn, false, 1>(h, a, split, stage);
     if (e != cudaSuccess) return e;
     k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5,
                                                         view_mask, skip);
@@ -627,11 +560,11 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
     template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int, const int *);                 \
     template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int, const int *);                \
     template cudaError_t launch_prep_forward<T>(const Handle &, const T *, int, const int *);              \
-    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, const int *);          \
-    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int);     \
-    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int);           \
+    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, int, const int *);     \
+    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int, int); \
+    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int, int);      \
     template cudaError_t launch_gn<T>(const Handle &, const T *, T *, double *, double *, double *, int,    \
-                                      int, const int *, const int *);
+                                      int, int, const int *, const int *);
 
 CTGB_RAY_INSTANTIATE(float)
 CTGB_RAY_INSTANTIATE(double)

@@ -224,7 +224,8 @@ template <typename T> struct Solver {
         for (int j = j0; j < j0 + cnt; j += h.max_batch) {
             const int nb = std::min(h.max_batch, j0 + cnt - j);
             SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop));
-            SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, stop));
+            SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
+                                      h.tune.fwd_stage, stop));
         }
         return CT_OK;
     }
@@ -388,12 +389,13 @@ template <typename T> struct Solver {
         for (int it = 0; it < o.maxiter_p; ++it) {
             SV_CUDA(launch_view_setup(h, th_n, delta));
             SV_CUDA(launch_pairs_img<T>(h, uimg, h.F));
-            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw));
+            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
             k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
                                                      ctl);
             for (int hv = 0; hv <= o.max_halvings; ++hv) {
                 SV_CUDA(launch_view_setup(h, th_t, delta));
-                SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw, active));
+                SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw,
+                                     h.tune.der_stage, active));
                 k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, th_n, h.V, o.c1, o.beta, alpha, th_t, active, ctl,
                                                    hv == o.max_halvings ? 1 : 0);
                 SV_TRY(sync_ctl());
@@ -439,7 +441,7 @@ template <typename T> struct Solver {
         if (grad) {
             SV_CUDA(launch_view_setup(h, theta, delta));
             SV_CUDA(launch_pairs_img<T>(h, u, h.F));
-            SV_CUDA(launch_vjp<T>(h, res, grad, nullptr, h.tune.der_split, h.tune.der_vw));
+            SV_CUDA(launch_vjp<T>(h, res, grad, nullptr, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
         }
         if (u_out) SV_CUDA(cudaMemcpyAsync(u_out, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
         SV_CUDA(cudaStreamSynchronize(h.stream));
@@ -518,7 +520,7 @@ template <typename T> struct Solver {
             k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.eps, nullptr);
             SV_CUDA(launch_view_setup(h, th_k, delta));
             SV_CUDA(launch_prep_forward<T>(h, u, h.F));
-            SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw));
+            SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
             axpby(res, b, m, 1.0, -1.0);
             SV_TRY(backproject(th_k, res, col(V, n, kc), nullptr));
             k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(col(V, n, kc), u, w, scal, h.N, h.F, nullptr);

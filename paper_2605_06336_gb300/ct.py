@@ -198,17 +198,19 @@ def ct_autotune(h):
 
 
 TUNING_FIELDS = ("fwd_images_per_lane", "fwd_warps_per_ray", "fwd_views_per_cta", "adj_images_per_thread",
-                 "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta")
+                 "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta", "fwd_staging", "jac_staging")
 
 
 def ct_get_tuning(h):
-    buf = (ctypes.c_int32 * 7)()
+    buf = (ctypes.c_int32 * len(TUNING_FIELDS))()
     _check(load_library().ct_get_tuning(h, buf), "ct_get_tuning")
     return list(buf)
 
 
 def ct_set_tuning(h, values):
-    buf = (ctypes.c_int32 * 7)(*[int(v) for v in values])
+    if len(values) != len(TUNING_FIELDS):
+        raise ValueError(f"expected {len(TUNING_FIELDS)} launch-shape values, got {len(values)}")
+    buf = (ctypes.c_int32 * len(TUNING_FIELDS))(*[int(v) for v in values])
     _check(load_library().ct_set_tuning(h, buf), "ct_set_tuning")
 
 
