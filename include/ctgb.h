@@ -153,9 +153,10 @@ int ct_set_stream(ct_handle *h, void *cuda_stream);
  * neighbouring views per CTA (1, 2, 4, 8) for the forward projection at
  * max_batch, images per thread and view groups per pixel tile (1, 2, 4) for
  * the transpose, warps per ray and views per CTA for the Jacobian kernels,
- * and (FP32 handles) the band-staged form of the forward and Jacobian
- * kernels with 4 or 8 views per CTA and 4 or 8 rows per shared-memory
- * block.  Synchronises; allocates and frees scratch buffers; must not run
+ * and (FP32 handles) the staged forms: the forward and Jacobian kernels
+ * with 4 or 8 views per CTA, 4 or 8 rows per shared-memory block and 1, 2
+ * or 4 CTAs per ray, the transpose with 8 or 16 views per block and 1, 2 or
+ * 4 CTAs per tile.  Synchronises; allocates and frees scratch buffers; must not run
  * during stream capture.  Results of every operator are independent of the
  * chosen shapes up to floating-point summation order.
  */
@@ -166,17 +167,22 @@ int ct_autotune(ct_handle *h);
  *   [0] forward images per lane, [1] forward warps per ray (row segments),
  *   [2] forward views per CTA, [3] transpose images per thread,
  *   [4] transpose view groups per pixel tile, [5] Jacobian warps per ray,
- *   [6] Jacobian views per CTA, [7] forward staging, [8] Jacobian staging.
+ *   [6] Jacobian views per CTA, [7] forward staging, [8] Jacobian staging,
+ *   [9] transpose staging.
  * [0]..[6] are powers of two, at most 8 (view groups at most 4), warps per
- * ray x views per CTA at most 16 (unstaged kernels).  A staging value is 0 (gathers through
- * L1) or 4 / 8 (rows per shared-memory block of the band-staged march,
- * which needs 4 or 8 views per CTA; FP64 handles ignore it).  With forward
- * staging, [1] is the number of CTAs sharing one ray (row segments, at most
- * 4; more than 1 allocates a workspace of 3 x max_batch x V x B floats the
- * first time, CT_ERR_OOM if that fails); the Jacobian kernels ignore [5]
- * when staged.  CT_ERR_ARG for any other value.
+ * ray x views per CTA at most 16 (unstaged kernels).  Forward / Jacobian
+ * staging is 0 (gathers through L1) or 4 / 8 (rows per shared-memory block of
+ * the band-staged march, which needs 4 or 8 views per CTA).  Transpose
+ * staging is 0 or 8 / 16 (views per shared-memory block of the staged
+ * transpose).  Staging applies to FP32 handles only.  With forward staging,
+ * [1] is the number of CTAs sharing one ray (row segments, at most 4); with
+ * transpose staging, [4] is the number of CTAs sharing one pixel tile (view
+ * subsets).  A value above 1 there allocates a workspace of
+ * 3 x max_batch x max(V x B, F x N x N) floats the first time (CT_ERR_OOM if
+ * that fails).  The Jacobian kernels ignore [5] when staged.  CT_ERR_ARG for
+ * any other value.
  */
-#define CT_TUNING_COUNT 9
+#define CT_TUNING_COUNT 10
 int ct_get_tuning(ct_handle *h, int32_t *out);
 int ct_set_tuning(ct_handle *h, const int32_t *in);
 

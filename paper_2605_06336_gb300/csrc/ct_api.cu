@@ -41,17 +41,16 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_fcount);
     cudaFree(h.d_flag);
     cudaFree(h.d_order);
-    cudaFree(h.d_changed);
     cudaFree(h.d_px);
     cudaFree(h.d_pt);
     cudaFree(h.d_yp);
     cudaFree(h.d_partial);
-    cudaFree(h.d_fpart);
+    cudaFree(h.d_segpart);
     h.d_views = nullptr;
-    h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = h.d_changed = nullptr;
+    h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = nullptr;
     h.d_px = h.d_pt = h.d_yp = nullptr;
     h.d_partial = nullptr;
-    h.d_fpart = nullptr;
+    h.d_segpart = nullptr;
 }
 
 template <typename T>
@@ -68,7 +67,7 @@ int do_adjoint(ctgb::Handle &h, const double *theta, const double *delta, const 
 {
     CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
     CT_CUDA(ctgb::launch_pairs_sino<T>(h, (const T *)Y, batch));
-    CT_CUDA(ctgb::launch_adjoint<T>(h, (T *)X, batch, h.tune.adj_kb, h.tune.adj_split));
+    CT_CUDA(ctgb::launch_adjoint<T>(h, (T *)X, batch, h.tune.adj_kb, h.tune.adj_split, h.tune.adj_stage));
     return CT_OK;
 }
 
@@ -103,15 +102,16 @@ int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void 
     return CT_OK;
 }
 
-// Workspace of the band-staged forward with row segments per ray (three
-// partial sinogram batches), allocated the first time such a shape is set.
-int ensure_fwd_partials(ctgb::Handle &h)
+// Workspace of the staged forward and transpose with several CTAs per ray or
+// pixel tile (segment partials), allocated the first time such a shape is set.
+int ensure_seg_partials(ctgb::Handle &h)
 {
-    if (h.d_fpart || h.precision != 0) return CT_OK;
-    const size_t bytes = sizeof(float) * 3 * (size_t)h.max_batch * h.V * h.B;
-    if (cudaMalloc(&h.d_fpart, bytes) != cudaSuccess) {
+    if (h.d_segpart || h.precision != 0) return CT_OK;
+    const size_t per = std::max((size_t)h.V * h.B, (size_t)h.F * h.N * h.N);
+    const size_t bytes = sizeof(float) * 3 * (size_t)h.max_batch * per;
+    if (cudaMalloc(&h.d_segpart, bytes) != cudaSuccess) {
         cudaGetLastError();
-        h.d_fpart = nullptr;
+        h.d_segpart = nullptr;
         return CT_ERR_OOM;
     }
     return CT_OK;
@@ -132,27 +132,37 @@ void default_tuning(ctgb::Handle &h)
     h.tune.der_vw = 2;
 }
 
-// Time one configuration: median of `reps` launches after one warm-up.
-template <typename F> float time_config(cudaStream_t s, F &&launch, int reps = 5)
+// Time one configuration: median over `reps` launches issued back to back
+// (the GPU never idles between them, so its clock stays up), after two
+// warm-up launches.
+template <typename F> float time_config(cudaStream_t s, F &&launch, int reps = 9)
 {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    std::vector<cudaEvent_t> ev(reps + 1);
+    for (auto &e : ev) cudaEventCreate(&e);
     launch();
-    std::vector<float> ms;
+    launch();
+    cudaEventRecord(ev[0], s);
     for (int r = 0; r < reps; ++r) {
-        cudaEventRecord(e0, s);
         launch();
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        ms.push_back(t);
+        cudaEventRecord(ev[r + 1], s);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEventSynchronize(ev[reps]);
+    std::vector<float> ms(reps);
+    for (int r = 0; r < reps; ++r) cudaEventElapsedTime(&ms[r], ev[r], ev[r + 1]);
+    for (auto &e : ev) cudaEventDestroy(e);
     std::sort(ms.begin(), ms.end());
     return ms[ms.size() / 2];
+}
+
+// About `target_ms` of back-to-back launches: the SM clock ramps up under
+// sustained load, and the candidates timed first would otherwise see a
+// lower clock than the later ones.
+template <typename F> void clock_warmup(cudaStream_t s, F &&launch, float target_ms = 150.0f)
+{
+    const float one = std::max(time_config(s, launch, 3), 1e-3f);
+    const int n = std::min(20000, (int)(target_ms / one) + 1);
+    for (int i = 0; i < n; ++i) launch();
+    cudaStreamSynchronize(s);
 }
 
 template <typename T> int autotune_impl(ctgb::Handle &h)
@@ -186,6 +196,9 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         const int K = h.max_batch;
         float best = 1e30f;
         ctgb::Tuning t = h.tune;
+        clock_warmup(h.stream, [&] {
+            ctgb::launch_forward<T>(h, (T *)d_out, K, t.fwd_kb, t.fwd_split, t.fwd_vw, 0);
+        });
         // L1-gather shapes (stage 0), then band-staged ones (FP32: stage = rows per block)
         const bool fp32 = h.precision == 0;
         for (int kb : {1, 2, 4, 8}) {
@@ -207,7 +220,7 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
             for (int st : {4, 8}) {
                 for (int vw : {4, 8}) {
                     for (int sp : {1, 2, 4}) {
-                        if (!fp32 || (sp > 1 && ensure_fwd_partials(h) != CT_OK)) continue;
+                        if (!fp32 || (sp > 1 && ensure_seg_partials(h) != CT_OK)) continue;
                         const float ms = time_config(
                             h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, st); });
                         if (ms < best) {
@@ -224,12 +237,18 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         best = 1e30f;
         for (int kb : {1, 2, 4, 8}) {
             if (kb > K) continue;
-            for (int sp : {1, 2, 4}) {
-                const float ms = time_config(h.stream, [&] { ctgb::launch_adjoint<T>(h, (T *)d_out, K, kb, sp); });
-                if (ms < best) {
-                    best = ms;
-                    t.adj_kb = kb;
-                    t.adj_split = sp;
+            for (int st : {0, 8, 16}) {
+                for (int sp : {1, 2, 4}) {
+                    if (st > 0 && (!fp32 || (sp > 1 && ensure_seg_partials(h) != CT_OK) || !ctgb::adj_band_ok(h, st, sp)))
+                        continue;
+                    const float ms =
+                        time_config(h.stream, [&] { ctgb::launch_adjoint<T>(h, (T *)d_out, K, kb, sp, st); });
+                    if (ms < best) {
+                        best = ms;
+                        t.adj_kb = kb;
+                        t.adj_split = sp;
+                        t.adj_stage = st;
+                    }
                 }
             }
         }
@@ -313,7 +332,7 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
     h.views_per_frame = vpf;
     h.nchunks = (h.B + ctgb::kChunk - 1) / ctgb::kChunk;
     h.Pp = h.N + 4;
-    h.Pb = h.B + 4;
+    h.Pb = (h.B + 5) & ~1;  // B + 4 rounded up to even: sinogram pair rows start on 16-byte boundaries
     int rc = CT_OK;
     do {
         cudaError_t e = cudaGetDevice(&h.device);
@@ -338,7 +357,6 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
                   cudaMalloc(&h.d_fcount, sizeof(int) * h.F) == cudaSuccess &&
                   cudaMalloc(&h.d_flag, sizeof(int)) == cudaSuccess &&
                   cudaMalloc(&h.d_order, sizeof(int) * h.V) == cudaSuccess &&
-                  cudaMalloc(&h.d_changed, sizeof(int)) == cudaSuccess &&
                   cudaMalloc(&h.d_px, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_pt, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_yp, sino_pairs * pair_bytes) == cudaSuccess &&
@@ -352,7 +370,6 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
         if (e == cudaSuccess) e = cudaMemcpy(h.d_fstart, fstart.data(), sizeof(int) * h.F, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(h.d_fcount, fcount.data(), sizeof(int) * h.F, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(h.d_flag, 0, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(h.d_changed, 0, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(h.d_views, 0, sizeof(ctgb::ViewGeo) * h.V);
         if (e == cudaSuccess) e = cudaMemset(h.d_px, 0, img_pairs * pair_bytes);
         if (e == cudaSuccess) e = cudaMemset(h.d_pt, 0, img_pairs * pair_bytes);
@@ -435,8 +452,8 @@ int ct_get_tuning(ct_handle *H, int32_t *out)
 {
     if (!H || !out) return CT_ERR_ARG;
     const ctgb::Tuning &t = H->h.tune;
-    const int32_t v[CT_TUNING_COUNT] = {t.fwd_kb,    t.fwd_split, t.fwd_vw,    t.adj_kb,   t.adj_split,
-                                        t.der_split, t.der_vw,    t.fwd_stage, t.der_stage};
+    const int32_t v[CT_TUNING_COUNT] = {t.fwd_kb, t.fwd_split, t.fwd_vw,    t.adj_kb,    t.adj_split,
+                                        t.der_split, t.der_vw, t.fwd_stage, t.der_stage, t.adj_stage};
     for (int i = 0; i < CT_TUNING_COUNT; ++i) out[i] = v[i];
     return CT_OK;
 }
@@ -449,10 +466,10 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
     if (!pow2(in[0], 8) || !pow2(in[1], 8) || !pow2(in[2], 8) || !pow2(in[3], 8) || !pow2(in[4], 4) ||
         !pow2(in[5], 8) || !pow2(in[6], 8) || (in[7] == 0 && in[1] * in[2] > 16) ||
         (in[8] == 0 && in[5] * in[6] > 16) || !stage_ok(in[7], in[2]) || !stage_ok(in[8], in[6]) ||
-        (in[7] > 0 && in[1] > 4))
+        (in[7] > 0 && in[1] > 4) || (in[9] != 0 && in[9] != 8 && in[9] != 16))
         return CT_ERR_ARG;
-    if (in[7] > 0 && in[1] > 1) {
-        const int rc = ensure_fwd_partials(H->h);
+    if ((in[7] > 0 && in[1] > 1) || (in[9] > 0 && in[4] > 1)) {
+        const int rc = ensure_seg_partials(H->h);
         if (rc != CT_OK) return rc;
     }
     ctgb::Tuning &t = H->h.tune;
@@ -465,6 +482,7 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
     t.der_vw = in[6];
     t.fwd_stage = in[7];
     t.der_stage = in[8];
+    t.adj_stage = in[9];
     return CT_OK;
 }
 

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "ct_device.cuh"
 #include "ct_internal.cuh"
@@ -179,8 +180,11 @@ cudaError_t run_adj_split(const Handle &h, const AdjArgs<T> &a, int split)
 }  // namespace
 
 template <typename T>
-cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip)
+cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, int stage, const int *skip)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (stage > 0 && adj_band_ok(h, stage, split)) return launch_adjoint_band(h, X, batch, kb, split, stage, skip);
+    }
     AdjArgs<T> a{};
     a.skip = skip;
     a.vg = h.d_views;
@@ -215,7 +219,7 @@ cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, 
     return cudaSuccess;
 }
 
-template cudaError_t launch_adjoint<float>(const Handle &, float *, int, int, int, const int *);
-template cudaError_t launch_adjoint<double>(const Handle &, double *, int, int, int, const int *);
+template cudaError_t launch_adjoint<float>(const Handle &, float *, int, int, int, int, const int *);
+template cudaError_t launch_adjoint<double>(const Handle &, double *, int, int, int, int, const int *);
 
 }  // namespace ctgb

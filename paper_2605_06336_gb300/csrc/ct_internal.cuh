@@ -23,7 +23,8 @@
 // both interpolation taps, and clamping the cell to [-2, N] keeps every load
 // in bounds while rays outside the image read exact zeros.  The transpose
 // operator reads sinograms the same way: pair b of view v holds
-// (Y[v][b], Y[v][b+1]) for b = -2 .. B+1 (stored at b + 2, pitch Pb = B + 4).
+// (Y[v][b], Y[v][b+1]) for b = -2 .. B+1 (stored at b + 2, pitch Pb = B + 4
+// rounded up to even, so that rows start on 16-byte boundaries).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -75,6 +76,8 @@ struct Tuning {
     int adj_kb = 8, adj_split = 2;              // transpose of a batch
     int der_split = 4, der_vw = 1;              // JVP / VJP / Gauss-Newton terms (one image)
     int fwd_stage = 0, der_stage = 0;
+    int adj_stage = 0;  // 0: gather through L1; 8 or 16: views per shared-memory block of the
+                        // staged FP32 transpose, whose adj_split is then CTAs per tile
 };
 
 struct Handle {
@@ -88,13 +91,13 @@ struct Handle {
     int *d_fcount = nullptr;  // views of each frame
     int *d_flag = nullptr;    // device-side status bits
     int *d_order = nullptr;   // view order of the ray kernels (sorted by axis and slope)
-    int *d_changed = nullptr; // set when a view's constants were rebuilt (order is stale)
     void *d_px = nullptr;     // pair images, rows of X:   (max_batch + 1) * F * N * Pp pairs
     void *d_pt = nullptr;     // pair images, rows of X^T: (max_batch + 1) * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
     double *d_partial = nullptr;  // per (view, chunk) reduction partials, 4 per item
-    void *d_fpart = nullptr;      // row-segment partial sinograms of the band-staged forward:
-                                  // 3 * max_batch * V * B elements, allocated when such a shape is set
+    void *d_segpart = nullptr;    // segment partials of the staged forward (sinograms) and transpose
+                                  // (images): 3 * max_batch * max(V * B, F * N * N) floats, allocated
+                                  // when a shape with several CTAs per ray or tile is set
     int nchunks = 0;              // ceil(B / kChunk)
     int num_sms = 0;
     Tuning tune;
@@ -120,7 +123,11 @@ template <typename T>
 cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, int stage,
                            const int *skip = nullptr);
 template <typename T>
-cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip = nullptr);
+cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, int stage,
+                           const int *skip = nullptr);
+// Staged FP32 transpose (ct_adj_band.cu); adj_band_ok tells whether a shape can run on this handle.
+bool adj_band_ok(const Handle &h, int stage, int segs);
+cudaError_t launch_adjoint_band(const Handle &h, float *X, int batch, int kb, int segs, int stage, const int *skip);
 template <typename T>
 cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw,
                        int stage);

@@ -1,6 +1,7 @@
 // Ray-driven kernels of the angle-dependent Joseph operator (sm_103a).
 //
-//   k_view_setup  per-view constants from (theta, delta), FP64 -> fixed point
+//   k_view_prep   per-view constants from (theta, delta), FP64 -> fixed point,
+//                 and the view order of the ray kernels
 //   k_pairs_img   X -> pair layouts of X and X^T (zero padded)
 //   k_pairs_sino  Y -> pair layout of the sinogram (zero padded)
 //   k_ray         one warp per 32 consecutive rays of one view (optionally
@@ -30,19 +31,18 @@ namespace {
 // ---------------------------------------------------------------------------
 // per-view setup
 // ---------------------------------------------------------------------------
-__global__ void k_view_setup(const double *__restrict__ theta, const double *__restrict__ delta,
-                             const int *__restrict__ fov, int V, int N, int B, ViewGeo *__restrict__ out,
-                             int *__restrict__ flag, const int *__restrict__ skip, int *__restrict__ changed)
+// Rebuilds the constants of view v when its (theta, delta) changed since the
+// last call; returns whether it did.
+__device__ bool view_setup_one(int v, const double *__restrict__ theta, const double *__restrict__ delta,
+                               const int *__restrict__ fov, int N, int B, ViewGeo *__restrict__ out,
+                               int *__restrict__ flag)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V || (skip && *skip)) return;
     double th = theta[v];
     double dl = delta ? delta[v] : 0.0;
     ViewGeo *gp = out + v;
     if ((gp->flags & kValid) && __double_as_longlong(gp->th) == __double_as_longlong(th) &&
         __double_as_longlong(gp->dl) == __double_as_longlong(dl))
-        return;  // unchanged since the last call
-    if (changed) *changed = 1;  // every writer stores the same value
+        return false;  // unchanged since the last call
     const double th_in = th, dl_in = dl;
     int bad = 0;
     if (!isfinite(th) || !isfinite(dl)) {
@@ -109,36 +109,47 @@ __global__ void k_view_setup(const double *__restrict__ theta, const double *__r
     g.dl = dl_in;
     g.frame = fov ? fov[v] : 0;
     *gp = g;
+    return true;
 }
 
-// View order for the ray kernels: views sorted by frame, then by marching
-// axis, then by ray slope qr (ties by index), so that consecutive entries
-// read the same image and sweep nearly the same band of it.  One CTA; runs
-// only when a view changed since the last sort.
+// Per-view setup and view order in one single-CTA launch.  The view order
+// of the ray kernels sorts the views by frame, then by marching axis, then
+// by ray slope qr (ties by index), so that consecutive entries read the same
+// image and sweep nearly the same band of it; it is rebuilt only when a view
+// changed.  Without an order buffer (nullable) only the constants are built.
 constexpr int kOrderMaxV = 4096;
-__global__ void __launch_bounds__(1024) k_view_order(const ViewGeo *__restrict__ vg, int V, int *__restrict__ order,
-                                                     int *__restrict__ changed, const int *__restrict__ skip)
+__global__ void __launch_bounds__(1024) k_view_prep(const double *__restrict__ theta, const double *__restrict__ delta,
+                                                    const int *__restrict__ fov, int V, int N, int B,
+                                                    ViewGeo *__restrict__ vg, int *__restrict__ flag,
+                                                    int *__restrict__ order, const int *__restrict__ skip)
 {
-    if ((skip && *skip) || !*changed) return;
+    __shared__ int s_changed;
     __shared__ double key[kOrderMaxV];
+    if (skip && *skip) return;
+    if (threadIdx.x == 0) s_changed = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) mine |= view_setup_one(v, theta, delta, fov, N, B, vg, flag);
+    if (mine) s_changed = 1;  // every writer stores the same value
+    __syncthreads();
+    if (!order || !s_changed) return;
+    __threadfence_block();  // the rebuilt constants are read below
     if (V > kOrderMaxV) {
         for (int i = threadIdx.x; i < V; i += blockDim.x) order[i] = i;
-    } else {
-        for (int i = threadIdx.x; i < V; i += blockDim.x)
-            key[i] = vg[i].frame * 8.0 + vg[i].mode * 4.0 + 1.0 + (double)vg[i].Qh * (2.0 / kFixScale);
-        __syncthreads();
-        for (int i = threadIdx.x; i < V; i += blockDim.x) {
-            const double ki = key[i];
-            int rank = 0;
-            for (int j = 0; j < V; ++j) {
-                const double kj = key[j];
-                rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
-            }
-            order[rank] = i;
-        }
+        return;
     }
+    for (int i = threadIdx.x; i < V; i += blockDim.x)
+        key[i] = vg[i].frame * 8.0 + vg[i].mode * 4.0 + 1.0 + (double)vg[i].Qh * (2.0 / kFixScale);
     __syncthreads();
-    if (threadIdx.x == 0) *changed = 0;
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+        const double ki = key[i];
+        int rank = 0;
+        for (int j = 0; j < V; ++j) {
+            const double kj = key[j];
+            rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+        }
+        order[rank] = i;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -356,23 +367,37 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
     }
 }
 
-// out_q[v] = scale_q * sum_c partial[v][c][q], summed in chunk order.
+// out_q[v] = scale_q * sum_c partial[v][c][q], summed in chunk order.  One
+// warp per view: the lanes load 32 chunks at a time in one round trip, and
+// the sums run over them in chunk order through shuffles.
 __global__ void k_finalize(const double *__restrict__ partial, int V, int nchunks, double *out0, double *out1,
                            double *out2, double scale2, const int *__restrict__ view_mask,
                            const int *__restrict__ skip)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V || (skip && *skip) || (view_mask && view_mask[v] == 0)) return;
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= V || (skip && *skip) || (view_mask && view_mask[v] == 0)) return;  // warp-uniform
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     const double *p = partial + (size_t)v * nchunks * 4;
-    for (int k = 0; k < nchunks; ++k) {
-        s0 += p[4 * k + 0];
-        s1 += p[4 * k + 1];
-        s2 += p[4 * k + 2];
+    for (int base = 0; base < nchunks; base += 32) {
+        double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+        if (base + lane < nchunks) {
+            q0 = p[4 * (base + lane) + 0];
+            q1 = p[4 * (base + lane) + 1];
+            q2 = p[4 * (base + lane) + 2];
+        }
+        const int n = min(32, nchunks - base);
+        for (int k = 0; k < n; ++k) {
+            s0 += __shfl_sync(0xffffffffu, q0, k);
+            s1 += __shfl_sync(0xffffffffu, q1, k);
+            s2 += __shfl_sync(0xffffffffu, q2, k);
+        }
     }
-    if (out0) out0[v] = s0;
-    if (out1) out1[v] = s1;
-    if (out2) out2[v] = scale2 * s2;
+    if (lane == 0) {
+        if (out0) out0[v] = s0;
+        if (out1) out1[v] = s1;
+        if (out2) out2[v] = scale2 * s2;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -449,10 +474,8 @@ cudaError_t fwd_groups(const Handle &h, RayArgs<T> a, int kb, int split, int sta
 
 cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta, const int *skip)
 {
-    const int threads = 128;
-    k_view_setup<<<(h.V + threads - 1) / threads, threads, 0, h.stream>>>(theta, delta, h.d_fov, h.V, h.N, h.B,
-                                                                           h.d_views, h.d_flag, skip, h.d_changed);
-    if (h.d_order && h.d_changed) k_view_order<<<1, 1024, 0, h.stream>>>(h.d_views, h.V, h.d_order, h.d_changed, skip);
+    k_view_prep<<<1, 1024, 0, h.stream>>>(theta, delta, h.d_fov, h.V, h.N, h.B, h.d_views, h.d_flag, h.d_order,
+                                          skip);
     return cudaGetLastError();
 }
 
@@ -486,12 +509,12 @@ cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, 
     a.Y = Y;
     a.skip = skip;
     a.VW = vw;
-    // band-staged FP32 march with `split` CTAs per ray: segment partials go to Y and d_fpart
+    // band-staged FP32 march with `split` CTAs per ray: segment partials go to Y and d_segpart
     const bool band = std::is_same<T, float>::value && stage > 0 && band_shape_ok(kFwd, 1, vw, stage);
     if (band && split > 1) {
-        if (!h.d_fpart || split > 4) return cudaErrorInvalidValue;
+        if (!h.d_segpart || split > 4) return cudaErrorInvalidValue;
         a.segs = split;
-        a.fpart = (T *)h.d_fpart;
+        a.fpart = (T *)h.d_segpart;
         a.fpart_stride = (long long)h.max_batch * h.V * h.B;
     }
     int k = 0;
@@ -533,7 +556,7 @@ cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdel
     cudaError_t e = gdelta ? run_ray_any<T, kVjp, true, 1>(h, a, split, stage)
                            : run_ray_any<T, kVjp, false, 1>(h, a, split, stage);
     if (e != cudaSuccess) return e;
-    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0,
+    k_finalize<<<(h.V + 7) / 8, 256, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0,
                                                         nullptr, nullptr);
     return cudaGetLastError();
 }
@@ -551,7 +574,7 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
     a.skip = skip;
     cudaError_t e = run_ray_any<T, kGn, false, 1>(h, a, split, stage);
     if (e != cudaSuccess) return e;
-    k_finalize<<<(h.V + 127) / 128, 128, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5,
+    k_finalize<<<(h.V + 7) / 8, 256, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5,
                                                         view_mask, skip);
     return cudaGetLastError();
 }

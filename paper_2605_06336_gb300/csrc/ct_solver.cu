@@ -235,7 +235,7 @@ template <typename T> struct Solver {
     {
         SV_CUDA(launch_view_setup(h, theta, delta, stop));
         SV_CUDA(launch_pairs_sino<T>(h, yin, 1, stop));
-        SV_CUDA(launch_adjoint<T>(h, out, 1, h.tune.adj_kb, h.tune.adj_split, stop));
+        SV_CUDA(launch_adjoint<T>(h, out, 1, h.tune.adj_kb, h.tune.adj_split, h.tune.adj_stage, stop));
         return CT_OK;
     }
 

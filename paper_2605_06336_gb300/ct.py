@@ -198,7 +198,8 @@ def ct_autotune(h):
 
 
 TUNING_FIELDS = ("fwd_images_per_lane", "fwd_warps_per_ray", "fwd_views_per_cta", "adj_images_per_thread",
-                 "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta", "fwd_staging", "jac_staging")
+                 "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta", "fwd_staging", "jac_staging",
+                 "adj_staging")
 
 
 def ct_get_tuning(h):

@@ -199,10 +199,10 @@ def test_large_image_sampled_views(ct):
     assert rel(host(op.adjoint(dev(y, torch.float32), th)), oracle.adjoint(g, theta, y)) <= 1e-5
 
 
-@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1, 1, 1, 0, 0], [2, 4, 2, 2, 2, 2, 4, 0, 0],
-                                    [8, 8, 2, 8, 4, 8, 2, 0, 0], [4, 2, 8, 1, 4, 4, 4, 0, 4],
-                                    [8, 1, 8, 8, 2, 1, 8, 8, 8], [4, 1, 4, 2, 2, 1, 4, 4, 8],
-                                    [2, 2, 8, 4, 1, 2, 8, 8, 4], [8, 1, 4, 1, 1, 1, 8, 4, 0]])
+@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1, 1, 1, 0, 0, 0], [2, 4, 2, 2, 2, 2, 4, 0, 0, 8],
+                                    [8, 8, 2, 8, 4, 8, 2, 0, 0, 16], [4, 2, 8, 1, 4, 4, 4, 0, 4, 0],
+                                    [8, 1, 8, 8, 2, 1, 8, 8, 8, 16], [4, 1, 4, 2, 2, 1, 4, 4, 8, 8],
+                                    [2, 2, 8, 4, 1, 2, 8, 8, 4, 16], [8, 1, 4, 1, 1, 1, 8, 4, 0, 8]])
 def test_results_do_not_depend_on_launch_shapes(ct, tuning):
     N, B, vpf = 40, 59, [7, 13]
     V = sum(vpf)
@@ -229,7 +229,8 @@ def test_autotune_picks_valid_shapes(ct):
     w = synth.make_workload("C2")
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
     t = op.autotune()
-    assert len(t) == 9 and all(x in (1, 2, 4, 8) for x in t[:7]) and t[7] in (0, 4, 8) and t[8] in (0, 4, 8)
+    assert len(t) == 10 and all(x in (1, 2, 4, 8) for x in t[:7]) and t[7] in (0, 4, 8) and t[8] in (0, 4, 8)
+    assert t[9] in (0, 8, 16)
     th = dev(w.theta_true)
     x = w.images.reshape(1, -1)
     g = oracle.Geometry(w.N, w.B, w.V)
