@@ -36,10 +36,41 @@ if ROOT not in sys.path:
 METRIC = "A/Aᵀ/Jθ GSamples/s + NL-RMM-GKS iter time vs FP64 GPU form at equal error"
 WORKLOAD = "C2"
 KBLOCK = 8
-# kernels per step: forward (view table, view order, pair layouts, march),
-# transpose (view table, view order, sinogram pairs, gather), JVP (table,
-# order, pairs, march), VJP (table, order, pairs, march, per-view sums)
-LAUNCHES_PER_STEP = 4 + 4 + 4 + 5  # each call also re-sorts the view order when angles changed
+# DRAM bytes per launch of the dominant kernels, from one ncu capture of
+# `python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-solver --tuning 4,4,1,8,2,2,1,0,0,0`,
+# keyed by the launch shape that selects the kernel; a shape that was not
+# profiled reports null.
+PROFILED_DRAM_BYTES = {
+    ("forward_K8", (4, 4, 1, 0)): 8.56e6,   # k_ray<float, 0, 0, 4, 4>: fwd kb, split, views/CTA, staging
+    ("adjoint_K8", (8, 2, 0)): 3.95e6,      # k_adjoint<float, 8, 2>: adj kb, view groups, staging
+}
+
+
+def launches_per_step(t):
+    """Kernels of one bench step at launch shapes t (the 10 ct_get_tuning values):
+    each of the 4 calls builds its view table (1); forward, J and J^T lay out
+    their image (1 each), the transpose its sinograms (1); the forward ray
+    kernel(s) over the 8-image block, the transpose, the JVP, the VJP and its
+    per-view reduction; staged shapes with several CTAs per ray / tile add a
+    combining kernel."""
+    fkb, fsplit, _, akb, asplit, _, _, fstage, _, astage = t
+    fwd = 0
+    k = 0
+    for width in (8, 4, 2, 1):
+        if width <= fkb and (KBLOCK - k) // width > 0:
+            fwd += 1
+            k += (KBLOCK - k) // width * width
+    fwd += 1 if (fstage > 0 and fsplit > 1) else 0
+    adj = 0
+    k = 0
+    for width in (8, 4, 2, 1):
+        if width <= akb and (KBLOCK - k) // width > 0:
+            adj += 1
+            k += (KBLOCK - k) // width * width
+    adj += 1 if (astage > 0 and asplit > 1) else 0
+    return 4 + 3 + 1 + fwd + adj + 1 + 1 + 1
+
+
 L2_FLUSH_BYTES = 512 * 1024 * 1024
 LSU_BYTES_PER_CLK_SM = 128          # L1/shared data path per SM per clock
 NUM_SMS = 152
@@ -57,7 +88,8 @@ def parse():
     ap.add_argument("--no-solver", action="store_true", help="skip the NL-RMM-GKS comparison")
     ap.add_argument("--solver-iters", type=int, default=30)
     ap.add_argument("--tuning", default=None,
-                    help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw,fstage,jstage' instead of autotuning")
+                    help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw,fstage,jstage,astage' "
+                         "(the ct_set_tuning values) instead of autotuning")
     return ap.parse_args()
 
 
@@ -489,10 +521,22 @@ def main():
              lambda: ct.ct_jac(op.h, theta, None, X[0], dth, None, dy),
              lambda: ct.ct_jacT(op.h, theta, None, X[0], Y[0], gt, None)]
     mean_ms = np.array(graph_op_timing(op, calls, 200, flush))
-    dom = int(np.argmax(mean_ms))
-    units = {0: K * steps_img, 1: K * steps_img, 2: steps_img, 3: steps_img}
-    gather_bytes = 8.0 * units[dom]          # two FP32 pixels (or bins) per interpolation
-    achieved = gather_bytes / (mean_ms[dom] * 1e-3) / 1e9
+    # the projection kernel alone, with its inputs as warm as in the step: the
+    # call followed by a rerun of its kernel (ct_forward_repeat /
+    # ct_adjoint_repeat), minus the call alone
+    def call_and_repeat(call, repeat):
+        def f():
+            call()
+            repeat()
+        return f
+    twice = graph_op_timing(op, [call_and_repeat(calls[0], lambda: ct.ct_forward_repeat(op.h, Y, K)),
+                                 call_and_repeat(calls[1], lambda: ct.ct_adjoint_repeat(op.h, Xa, K))], 200, flush)
+    kernel_ms = {"forward_K8": twice[0] - float(mean_ms[0]), "adjoint_K8": twice[1] - float(mean_ms[1])}
+    dom_name = max(kernel_ms, key=kernel_ms.get)
+    gather_bytes = 8.0 * K * steps_img       # two FP32 pixels (or bins) per interpolation step
+    achieved = gather_bytes / (kernel_ms[dom_name] * 1e-3) / 1e9
+    shape = tuple(tuning[i] for i in ((0, 1, 2, 7) if dom_name == "forward_K8" else (3, 4, 9)))
+    traffic = PROFILED_DRAM_BYTES.get((dom_name, shape))
     sm_mhz = SM_MAX_MHZ_NOMINAL
     peak = NUM_SMS * LSU_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     peaks, src = measured_peaks()
@@ -520,17 +564,22 @@ def main():
         "per_op_ms": dict(zip(op_names, [float(x) for x in mean_ms])),
         "per_op_ms_note": "device time of each call (all its kernels) replayed alone from a CUDA graph, L2 flushed",
         "per_op_ms_eager": dict(zip(op_names, [float(x) for x in per_op.mean(axis=0)])),
-        "roofline": {"bound": "alu", "kernel": op_names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "basis": "8 B of gathered FP32 operands per interpolation step x steps per launch; peak = "
-                              f"{NUM_SMS} SMs x {LSU_BYTES_PER_CLK_SM} B/clk L1 data path x {sm_mhz:.0f} MHz",
+        "kernel_ms": kernel_ms,
+        "kernel_ms_note": "projection kernel alone: graph of the call followed by ct_forward_repeat / "
+                          "ct_adjoint_repeat minus the graph of the call, L2 flushed before each replay",
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read+write)",
+                     "launch_ms": kernel_ms[dom_name],
+                     "basis": f"8 B of gathered FP32 operands per interpolation step x {K} x {steps_img} steps per "
+                              f"launch; peak = {NUM_SMS} SMs x {LSU_BYTES_PER_CLK_SM} B/clk L1 data path x "
+                              f"{sm_mhz:.0f} MHz",
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": "derived (unit counts x nominal max clock)"},
         "cpu_baseline": cpu,
         "solver": solver,
         "batched_frames": frames,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-        "gpu_launches_note": f"{LAUNCHES_PER_STEP} kernels per step in the replayed graph",
+        "gpu_launches": launches_per_step(tuning) * args.steps,
+        "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
         "tuning": dict(zip(ct.TUNING_FIELDS, tuning)),
         "clocks": clocks,
         "wall_s_timed_region": t_wall,

@@ -102,6 +102,20 @@ int ct_adjoint(ct_handle *h, const double *theta, const double *delta,
                const void *Y, void *X, int batch);
 
 /*
+ * Rerun only the projection kernel of the last ct_forward (ct_adjoint) call
+ * on this handle, on the angles, offsets and inputs that call laid out in
+ * the handle, writing Y (X) for its first `batch` images (sinograms).  For
+ * callers that need the same product again (and for timing the kernel
+ * alone).  No counterpart in the paper.  CT_ERR_ARG when batch exceeds that
+ * call's batch, or when any other call on the handle (ct_forward for
+ * ct_adjoint_repeat and the reverse, ct_jac, ct_jacT, ct_gn_terms,
+ * ct_autotune, the solvers) has run since.  Same layouts as ct_forward
+ * (ct_adjoint); the inputs of that call need not be alive any more.
+ */
+int ct_forward_repeat(ct_handle *h, void *Y, int batch);
+int ct_adjoint_repeat(ct_handle *h, void *X, int batch);
+
+/*
  * Angle (and offset) Jacobian-vector product of the forward projection at a
  * fixed image x: dy[v,b] = dtheta_v d(Hx)[v,b]/dtheta_v
  *                        + ddelta_v d(Hx)[v,b]/ddelta_v

@@ -167,25 +167,31 @@ template <typename F> void clock_warmup(cudaStream_t s, F &&launch, float target
 
 template <typename T> int autotune_impl(ctgb::Handle &h)
 {
-    // Representative inputs: evenly spaced angles, pair buffers as they are
-    // (values do not change the timing), a scratch output.
+    // Representative inputs: evenly spaced angles, zero images and sinograms
+    // (values do not change the timing), a scratch output.  Every candidate
+    // is timed together with the layout kernel that precedes it in an
+    // operator call, so its inputs are as warm in L2 as they are there.
     std::vector<double> th(h.V);
     for (int v = 0; v < h.V; ++v) th[v] = 3.14159265358979 * (v + 0.37) / h.V;
     double *d_th = nullptr, *d_g = nullptr;
-    void *d_out = nullptr;
+    void *d_out = nullptr, *d_in = nullptr;
     const size_t out_elems = std::max((size_t)h.max_batch * h.V * h.B, (size_t)h.max_batch * h.F * h.N * h.N);
     if (cudaMalloc(&d_th, sizeof(double) * h.V) != cudaSuccess ||
         cudaMalloc(&d_g, sizeof(double) * h.V) != cudaSuccess ||
-        cudaMalloc(&d_out, out_elems * sizeof(T)) != cudaSuccess) {
+        cudaMalloc(&d_out, out_elems * sizeof(T)) != cudaSuccess ||
+        cudaMalloc(&d_in, out_elems * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(d_th);
         cudaFree(d_g);
         cudaFree(d_out);
+        cudaFree(d_in);
         return CT_ERR_OOM;
     }
+    const T *X = (const T *)d_in;
     int rc = CT_OK;
     do {
         cudaError_t e = cudaMemcpy(d_th, th.data(), sizeof(double) * h.V, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_in, 0, out_elems * sizeof(T), h.stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_g, 0, sizeof(double) * h.V, h.stream);
         if (e == cudaSuccess) e = ctgb::launch_view_setup(h, d_th, nullptr);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h.stream);
@@ -197,6 +203,7 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         float best = 1e30f;
         ctgb::Tuning t = h.tune;
         clock_warmup(h.stream, [&] {
+            ctgb::launch_prep_forward<T>(h, X, K * h.F);
             ctgb::launch_forward<T>(h, (T *)d_out, K, t.fwd_kb, t.fwd_split, t.fwd_vw, 0);
         });
         // L1-gather shapes (stage 0), then band-staged ones (FP32: stage = rows per block)
@@ -206,8 +213,10 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
             for (int sp : {1, 2, 4, 8}) {
                 for (int vw : {1, 2, 4, 8}) {
                     if (sp * vw > 16) continue;
-                    const float ms =
-                        time_config(h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, 0); });
+                    const float ms = time_config(h.stream, [&] {
+                        ctgb::launch_prep_forward<T>(h, X, K * h.F);
+                        ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, 0);
+                    });
                     if (ms < best) {
                         best = ms;
                         t.fwd_kb = kb;
@@ -221,8 +230,10 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
                 for (int vw : {4, 8}) {
                     for (int sp : {1, 2, 4}) {
                         if (!fp32 || (sp > 1 && ensure_seg_partials(h) != CT_OK)) continue;
-                        const float ms = time_config(
-                            h.stream, [&] { ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, st); });
+                        const float ms = time_config(h.stream, [&] {
+                            ctgb::launch_prep_forward<T>(h, X, K * h.F);
+                            ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, st);
+                        });
                         if (ms < best) {
                             best = ms;
                             t.fwd_kb = kb;
@@ -241,8 +252,10 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
                 for (int sp : {1, 2, 4}) {
                     if (st > 0 && (!fp32 || (sp > 1 && ensure_seg_partials(h) != CT_OK) || !ctgb::adj_band_ok(h, st, sp)))
                         continue;
-                    const float ms =
-                        time_config(h.stream, [&] { ctgb::launch_adjoint<T>(h, (T *)d_out, K, kb, sp, st); });
+                    const float ms = time_config(h.stream, [&] {
+                        ctgb::launch_pairs_sino<T>(h, X, K);
+                        ctgb::launch_adjoint<T>(h, (T *)d_out, K, kb, sp, st);
+                    });
                     if (ms < best) {
                         best = ms;
                         t.adj_kb = kb;
@@ -256,8 +269,10 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         for (int sp : {1, 2, 4, 8}) {
             for (int vw : {1, 2, 4, 8}) {
                 if (sp * vw > 16) continue;
-                const float ms =
-                    time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp, vw, 0); });
+                const float ms = time_config(h.stream, [&] {
+                    ctgb::launch_pairs_img<T>(h, X, h.F);
+                    ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, sp, vw, 0);
+                });
                 if (ms < best) {
                     best = ms;
                     t.der_split = sp;
@@ -269,8 +284,10 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
         for (int st : {4, 8}) {
             for (int vw : {4, 8}) {
                 if (!fp32) continue;
-                const float ms =
-                    time_config(h.stream, [&] { ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, 1, vw, st); });
+                const float ms = time_config(h.stream, [&] {
+                    ctgb::launch_pairs_img<T>(h, X, h.F);
+                    ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, 1, vw, st);
+                });
                 if (ms < best) {
                     best = ms;
                     t.der_split = 1;
@@ -290,6 +307,7 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
     cudaFree(d_th);
     cudaFree(d_g);
     cudaFree(d_out);
+    cudaFree(d_in);
     // the view table now holds the tuning angles; force a rebuild on the next call
     cudaMemsetAsync(h.d_views, 0, sizeof(ctgb::ViewGeo) * h.V, h.stream);
     return rc;
@@ -400,21 +418,52 @@ void ct_destroy(ct_handle *H)
 int ct_forward(ct_handle *H, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
     if (!H || !theta || !X || !Y || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
-    return H->h.precision ? do_forward<double>(H->h, theta, delta, X, Y, batch)
-                          : do_forward<float>(H->h, theta, delta, X, Y, batch);
+    H->h.fwd_ready = H->h.adj_ready = 0;
+    const int rc = H->h.precision ? do_forward<double>(H->h, theta, delta, X, Y, batch)
+                                  : do_forward<float>(H->h, theta, delta, X, Y, batch);
+    if (rc == CT_OK) H->h.fwd_ready = batch;
+    return rc;
+}
+
+int ct_forward_repeat(ct_handle *H, void *Y, int batch)
+{
+    if (!H || !Y || batch < 1 || batch > H->h.fwd_ready) return CT_ERR_ARG;
+    ctgb::Handle &h = H->h;
+    if (h.precision)
+        CT_CUDA(ctgb::launch_forward<double>(h, (double *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
+                                             h.tune.fwd_stage));
+    else
+        CT_CUDA(ctgb::launch_forward<float>(h, (float *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
+                                            h.tune.fwd_stage));
+    return CT_OK;
+}
+
+int ct_adjoint_repeat(ct_handle *H, void *X, int batch)
+{
+    if (!H || !X || batch < 1 || batch > H->h.adj_ready) return CT_ERR_ARG;
+    ctgb::Handle &h = H->h;
+    if (h.precision)
+        CT_CUDA(ctgb::launch_adjoint<double>(h, (double *)X, batch, h.tune.adj_kb, h.tune.adj_split, h.tune.adj_stage));
+    else
+        CT_CUDA(ctgb::launch_adjoint<float>(h, (float *)X, batch, h.tune.adj_kb, h.tune.adj_split, h.tune.adj_stage));
+    return CT_OK;
 }
 
 int ct_adjoint(ct_handle *H, const double *theta, const double *delta, const void *Y, void *X, int batch)
 {
     if (!H || !theta || !X || !Y || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
-    return H->h.precision ? do_adjoint<double>(H->h, theta, delta, Y, X, batch)
-                          : do_adjoint<float>(H->h, theta, delta, Y, X, batch);
+    H->h.fwd_ready = H->h.adj_ready = 0;
+    const int rc = H->h.precision ? do_adjoint<double>(H->h, theta, delta, Y, X, batch)
+                                  : do_adjoint<float>(H->h, theta, delta, Y, X, batch);
+    if (rc == CT_OK) H->h.adj_ready = batch;
+    return rc;
 }
 
 int ct_jac(ct_handle *H, const double *theta, const double *delta, const void *x, const double *dtheta,
            const double *ddelta, void *dy)
 {
     if (!H || !theta || !x || !dtheta || !dy) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jac<double>(H->h, theta, delta, x, dtheta, ddelta, dy)
                           : do_jac<float>(H->h, theta, delta, x, dtheta, ddelta, dy);
 }
@@ -423,6 +472,7 @@ int ct_jacT(ct_handle *H, const double *theta, const double *delta, const void *
             double *gdelta)
 {
     if (!H || !theta || !x || !r || !gtheta) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jacT<double>(H->h, theta, delta, x, r, gtheta, gdelta)
                           : do_jacT<float>(H->h, theta, delta, x, r, gtheta, gdelta);
 }
@@ -431,6 +481,7 @@ int ct_gn_terms(ct_handle *H, const double *theta, const double *delta, const vo
                 double *grad, double *jnorm2, double *fval)
 {
     if (!H || !theta || !x || !bdata || !grad || !jnorm2) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_gn<double>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval)
                           : do_gn<float>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval);
 }
@@ -445,6 +496,7 @@ int ct_set_stream(ct_handle *H, void *cuda_stream)
 int ct_autotune(ct_handle *H)
 {
     if (!H) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? autotune_impl<double>(H->h) : autotune_impl<float>(H->h);
 }
 

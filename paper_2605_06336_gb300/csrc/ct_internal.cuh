@@ -99,6 +99,11 @@ struct Handle {
                                   // (images): 3 * max_batch * max(V * B, F * N * N) floats, allocated
                                   // when a shape with several CTAs per ray or tile is set
     int nchunks = 0;              // ceil(B / kChunk)
+    // Batch sizes whose forward (adjoint) inputs are still laid out in the
+    // handle from the last ct_forward (ct_adjoint) call: ct_forward_repeat
+    // (ct_adjoint_repeat) may rerun the projection kernel alone.  Any other
+    // call that may change the view table or the pair layouts clears them.
+    int fwd_ready = 0, adj_ready = 0;
     int num_sms = 0;
     Tuning tune;
 };

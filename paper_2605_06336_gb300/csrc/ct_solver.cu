@@ -621,6 +621,7 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
         return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
+    h.fwd_ready = h.adj_ready = 0;
     // The solve runs on a private stream ordered after the work already queued
     // on the handle's stream; it synchronises before returning.
     cudaStream_t ps = nullptr;
@@ -654,6 +655,7 @@ int nlrmm_varpro(ct_handle *H, const void *b, const double *theta, const double 
         (u_w && !(eps > 0.0)))
         return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
+    h.fwd_ready = h.adj_ready = 0;
     nlrmm_opts o;
     nlrmm_default_opts(&o);
     o.k_min = 2;

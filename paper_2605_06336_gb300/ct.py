@@ -99,6 +99,8 @@ def load_library(path: str | None = None):
     lib.ct_destroy.restype = None
     lib.ct_forward.argtypes = [P, P, P, P, P, I]
     lib.ct_adjoint.argtypes = [P, P, P, P, P, I]
+    lib.ct_forward_repeat.argtypes = [P, P, I]
+    lib.ct_adjoint_repeat.argtypes = [P, P, I]
     lib.ct_jac.argtypes = [P, P, P, P, P, P, P]
     lib.ct_jacT.argtypes = [P, P, P, P, P, P, P]
     lib.ct_gn_terms.argtypes = [P, P, P, P, P, P, P, P, P]
@@ -119,8 +121,8 @@ def load_library(path: str | None = None):
     lib.ct_strerror.restype = ctypes.c_char_p
     lib.ct_last_cuda_error.argtypes = []
     lib.ct_last_cuda_error.restype = ctypes.c_char_p
-    for f in ("ct_init", "ct_forward", "ct_adjoint", "ct_jac", "ct_jacT", "ct_gn_terms", "ct_status",
-              "ct_set_stream", "ct_autotune", "ct_get_tuning", "ct_set_tuning"):
+    for f in ("ct_init", "ct_forward", "ct_adjoint", "ct_forward_repeat", "ct_adjoint_repeat", "ct_jac", "ct_jacT",
+              "ct_gn_terms", "ct_status", "ct_set_stream", "ct_autotune", "ct_get_tuning", "ct_set_tuning"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -170,6 +172,14 @@ def ct_forward(h, theta, delta, X, Y, batch):
 
 def ct_adjoint(h, theta, delta, Y, X, batch):
     _check(load_library().ct_adjoint(h, _p(theta), _p(delta), _p(Y), _p(X), int(batch)), "ct_adjoint")
+
+
+def ct_forward_repeat(h, Y, batch):
+    _check(load_library().ct_forward_repeat(h, _p(Y), int(batch)), "ct_forward_repeat")
+
+
+def ct_adjoint_repeat(h, X, batch):
+    _check(load_library().ct_adjoint_repeat(h, _p(X), int(batch)), "ct_adjoint_repeat")
 
 
 def ct_jac(h, theta, delta, x, dtheta, ddelta, dy):

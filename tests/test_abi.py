@@ -20,7 +20,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("ct_init", "ct_forward", "ct_adjoint", "ct_jac", "ct_jacT", "ct_destroy", "ct_strerror"):
+    for required in ("ct_init", "ct_forward", "ct_adjoint", "ct_forward_repeat", "ct_adjoint_repeat", "ct_jac",
+                     "ct_jacT", "ct_destroy", "ct_strerror"):
         assert required in names
 
 

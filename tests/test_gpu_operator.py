@@ -251,3 +251,31 @@ def test_argument_errors(ct):
     op.forward(X[0], bad)
     assert op.status() == ct.CT_ERR_NAN
     assert op.status() == ct.CT_OK  # the flag is cleared once reported
+
+
+def test_repeat_reruns_the_projection_alone(ct):
+    """ct_forward_repeat / ct_adjoint_repeat reproduce the last call bit for bit
+    and refuse once another call may have changed the handle's layouts."""
+    N, B, V = 48, 68, 25
+    rng = np.random.default_rng(31)
+    theta = synth.random_angles(V, rng)
+    op = ct.CTOperator(N, B, V, max_batch=3, dtype=torch.float32)
+    th = dev(theta)
+    X = dev(rng.uniform(size=(3, N * N)), torch.float32)
+    Y = dev(rng.standard_normal((3, V * B)), torch.float32)
+    y0 = op.forward(X, th).clone()
+    y1 = torch.zeros_like(y0)
+    ct.ct_forward_repeat(op.h, y1, 3)
+    assert torch.equal(y0, y1)
+    x0 = op.adjoint(Y, th).clone()
+    x1 = torch.zeros_like(x0)
+    ct.ct_adjoint_repeat(op.h, x1, 2)
+    assert torch.equal(x0[:2], x1[:2]) and not x1[2].any()
+    for call in (lambda: ct.ct_forward_repeat(op.h, y1, 1),      # an adjoint ran since the forward
+                 lambda: ct.ct_adjoint_repeat(op.h, x1, 3 + 1)):  # larger than that call's batch
+        with pytest.raises(ct.CTError) as e:
+            call()
+        assert e.value.code == ct.CT_ERR_ARG
+    op.jac(X[0], th, dev(rng.standard_normal(V)))
+    with pytest.raises(ct.CTError):
+        ct.ct_adjoint_repeat(op.h, x1, 1)
