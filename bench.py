@@ -49,11 +49,11 @@ PROFILED_DRAM_BYTES = {
 
 def launches_per_step(t):
     """Kernels of one bench step at launch shapes t (the 10 ct_get_tuning values):
-    each of the 4 calls builds its view table (1); forward, J and J^T lay out
-    their image (1 each), the transpose its sinograms (1); the forward ray
-    kernel(s) over the 8-image block, the transpose, the JVP, the VJP and its
-    per-view reduction; staged shapes with several CTAs per ray / tile add a
-    combining kernel."""
+    forward, J and J^T lay out their image and the transpose its sinograms
+    (1 each; the same launch brings the view table up to date); the forward
+    ray kernel(s) over the 8-image block, the transpose, the JVP, the VJP and
+    its per-view reduction; staged shapes with several CTAs per ray / tile
+    add a combining kernel."""
     fkb, fsplit, _, akb, asplit, _, _, fstage, _, astage = t
     fwd = 0
     k = 0
@@ -69,7 +69,7 @@ def launches_per_step(t):
             adj += 1
             k += (KBLOCK - k) // width * width
     adj += 1 if (astage > 0 and asplit > 1) else 0
-    return 4 + 3 + 1 + fwd + adj + 1 + 1 + 1
+    return 3 + 1 + fwd + adj + 1 + 1 + 1
 
 
 L2_FLUSH_BYTES = 512 * 1024 * 1024

@@ -56,8 +56,7 @@ void free_all(ctgb::Handle &h)
 template <typename T>
 int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
-    CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_prep_forward<T>(h, (const T *)X, batch * h.F));
+    CT_CUDA(ctgb::launch_prep_forward<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
     CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
     return CT_OK;
 }
@@ -65,8 +64,7 @@ int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const 
 template <typename T>
 int do_adjoint(ctgb::Handle &h, const double *theta, const double *delta, const void *Y, void *X, int batch)
 {
-    CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_pairs_sino<T>(h, (const T *)Y, batch));
+    CT_CUDA(ctgb::launch_pairs_sino<T>(h, (const T *)Y, batch, nullptr, theta, delta));
     CT_CUDA(ctgb::launch_adjoint<T>(h, (T *)X, batch, h.tune.adj_kb, h.tune.adj_split, h.tune.adj_stage));
     return CT_OK;
 }
@@ -75,8 +73,7 @@ template <typename T>
 int do_jac(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const double *dtheta,
            const double *ddelta, void *dy)
 {
-    CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F, nullptr, theta, delta));
     CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
     return CT_OK;
 }
@@ -85,8 +82,7 @@ template <typename T>
 int do_jacT(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *r, double *gtheta,
             double *gdelta)
 {
-    CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F, nullptr, theta, delta));
     CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
     return CT_OK;
 }
@@ -95,8 +91,7 @@ template <typename T>
 int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
           double *grad, double *jnorm2, double *fval)
 {
-    CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F));
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F, nullptr, theta, delta));
     CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw,
                                   h.tune.der_stage));
     return CT_OK;

@@ -115,12 +115,18 @@ struct Handle {
 cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta,
                               const int *skip = nullptr);
 
-template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip = nullptr);
+// Layout kernels.  With theta non-null the same launch also runs the view-table
+// step of the call (what launch_view_setup does), in one extra CTA.
 template <typename T>
-cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip = nullptr);
+cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip = nullptr,
+                             const double *theta = nullptr, const double *delta = nullptr);
+template <typename T>
+cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip = nullptr,
+                              const double *theta = nullptr, const double *delta = nullptr);
 // Layout the forward projection reads (pair images of X and X^T).
 template <typename T>
-cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip = nullptr);
+cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip = nullptr,
+                                const double *theta = nullptr, const double *delta = nullptr);
 
 // stage > 0 (FP32 only): rows per shared-memory block of the band-staged
 // march (ct_band.cu); 0: gathers through L1.

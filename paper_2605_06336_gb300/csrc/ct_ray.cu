@@ -118,38 +118,53 @@ __device__ bool view_setup_one(int v, const double *__restrict__ theta, const do
 // image and sweep nearly the same band of it; it is rebuilt only when a view
 // changed.  Without an order buffer (nullable) only the constants are built.
 constexpr int kOrderMaxV = 4096;
-__global__ void __launch_bounds__(1024) k_view_prep(const double *__restrict__ theta, const double *__restrict__ delta,
-                                                    const int *__restrict__ fov, int V, int N, int B,
-                                                    ViewGeo *__restrict__ vg, int *__restrict__ flag,
-                                                    int *__restrict__ order, const int *__restrict__ skip)
+
+// What the view-table step of an operator call needs; `on` = 0: no step.
+struct ViewPrep {
+    const double *theta, *delta;
+    const int *fov;
+    int V, N, B, on;
+    ViewGeo *vg;
+    int *flag;
+    int *order;  // nullable: constants only
+};
+
+// The view-table step, run by one whole CTA; key: shared memory for
+// min(V, kOrderMaxV) doubles.
+__device__ void view_prep_block(const ViewPrep &p, double *key)
 {
     __shared__ int s_changed;
-    __shared__ double key[kOrderMaxV];
-    if (skip && *skip) return;
     if (threadIdx.x == 0) s_changed = 0;
     __syncthreads();
     int mine = 0;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) mine |= view_setup_one(v, theta, delta, fov, N, B, vg, flag);
+    for (int v = threadIdx.x; v < p.V; v += blockDim.x)
+        mine |= view_setup_one(v, p.theta, p.delta, p.fov, p.N, p.B, p.vg, p.flag);
     if (mine) s_changed = 1;  // every writer stores the same value
     __syncthreads();
-    if (!order || !s_changed) return;
-    __threadfence_block();  // the rebuilt constants are read below
-    if (V > kOrderMaxV) {
-        for (int i = threadIdx.x; i < V; i += blockDim.x) order[i] = i;
+    if (!p.order || !s_changed) return;
+    if (p.V > kOrderMaxV) {
+        for (int i = threadIdx.x; i < p.V; i += blockDim.x) p.order[i] = i;
         return;
     }
-    for (int i = threadIdx.x; i < V; i += blockDim.x)
-        key[i] = vg[i].frame * 8.0 + vg[i].mode * 4.0 + 1.0 + (double)vg[i].Qh * (2.0 / kFixScale);
+    for (int i = threadIdx.x; i < p.V; i += blockDim.x)
+        key[i] = p.vg[i].frame * 8.0 + p.vg[i].mode * 4.0 + 1.0 + (double)p.vg[i].Qh * (2.0 / kFixScale);
     __syncthreads();
-    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    for (int i = threadIdx.x; i < p.V; i += blockDim.x) {
         const double ki = key[i];
         int rank = 0;
-        for (int j = 0; j < V; ++j) {
+        for (int j = 0; j < p.V; ++j) {
             const double kj = key[j];
             rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
         }
-        order[rank] = i;
+        p.order[rank] = i;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_view_prep(ViewPrep p, const int *__restrict__ skip)
+{
+    __shared__ double key[kOrderMaxV];
+    if (skip && *skip) return;
+    view_prep_block(p, key);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,12 +172,19 @@ __global__ void __launch_bounds__(1024) k_view_prep(const double *__restrict__ t
 // ---------------------------------------------------------------------------
 // Tile of 32 rows x 32 pairs.  PX[img][r][cp] = (X[r][c], X[r][c+1]) and
 // PT[img][r][cp] = (X[c][r], X[c+1][r]) with c = cp - 2, zero outside.
+// With p.on, one extra column of CTAs is launched and its first CTA runs the
+// view-table step of the call (the two are independent).
 template <typename T>
 __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair_t<T> *__restrict__ PX,
-                                                   pair_t<T> *__restrict__ PT, int N, int Pp, int nimg,
+                                                   pair_t<T> *__restrict__ PT, int N, int Pp, int nimg, ViewPrep p,
                                                    const int *__restrict__ skip)
 {
+    extern __shared__ double prep_key[];
     if (skip && *skip) return;
+    if (p.on && blockIdx.x == gridDim.x - 1) {
+        if (blockIdx.y == 0 && blockIdx.z == 0) view_prep_block(p, prep_key);
+        return;
+    }
     __shared__ T a[32][34];   // a[i][j] = X[r0 + i][c0 + j]
     __shared__ T bt[33][33];  // bt[i][j] = X[c0 + i][r0 + j]
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -201,13 +223,20 @@ __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair
 }
 
 // YP[row][bp] = (Y[row][bp - 2], Y[row][bp - 1]), zero outside [0, B).
+// With p.on, the last CTA runs the view-table step of the call instead.
 template <typename T>
 __global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP, int B, int Pb, long long total,
-                             const int *__restrict__ skip)
+                             ViewPrep p, const int *__restrict__ skip)
 {
+    extern __shared__ double prep_key[];
     if (skip && *skip) return;
+    const int nblk = gridDim.x - (p.on ? 1 : 0);
+    if (p.on && blockIdx.x == nblk) {
+        view_prep_block(p, prep_key);
+        return;
+    }
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
+         idx += (long long)nblk * blockDim.x) {
         const long long row = idx / Pb;
         const int bp = (int)(idx - row * Pb);
         const int b0 = bp - 2, b1 = bp - 1;
@@ -472,33 +501,77 @@ cudaError_t fwd_groups(const Handle &h, RayArgs<T> a, int kb, int split, int sta
 
 }  // namespace
 
+namespace {
+
+ViewPrep view_prep_args(const Handle &h, const double *theta, const double *delta)
+{
+    ViewPrep p{};
+    p.theta = theta;
+    p.delta = delta;
+    p.fov = h.d_fov;
+    p.V = h.V;
+    p.N = h.N;
+    p.B = h.B;
+    p.on = theta != nullptr;
+    p.vg = h.d_views;
+    p.flag = h.d_flag;
+    p.order = h.d_order;
+    return p;
+}
+
+size_t prep_smem(const ViewPrep &p) { return p.on ? sizeof(double) * std::min(p.V, kOrderMaxV) : 0; }
+
+// The layout kernels may carry the view-table step in up to 32 KB of dynamic shared memory.
+template <typename K> cudaError_t allow_prep_smem(K kernel)
+{
+    static bool done = false;  // per kernel; the attribute is idempotent, so a race is harmless
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * kOrderMaxV));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+}  // namespace
+
 cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta, const int *skip)
 {
-    k_view_prep<<<1, 1024, 0, h.stream>>>(theta, delta, h.d_fov, h.V, h.N, h.B, h.d_views, h.d_flag, h.d_order,
-                                          skip);
+    k_view_prep<<<1, 1024, 0, h.stream>>>(view_prep_args(h, theta, delta), skip);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip)
+template <typename T>
+cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *skip, const double *theta,
+                             const double *delta)
 {
-    dim3 grid((h.Pp + 31) / 32, (h.N + 31) / 32, std::min(nimg, 65535));
-    k_pairs_img<T><<<grid, 256, 0, h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp, nimg,
-                                               skip);
+    const ViewPrep p = view_prep_args(h, theta, delta);
+    cudaError_t e = allow_prep_smem(k_pairs_img<T>);
+    if (e != cudaSuccess) return e;
+    dim3 grid((h.Pp + 31) / 32 + (p.on ? 1 : 0), (h.N + 31) / 32, std::max(1, std::min(nimg, 65535)));
+    k_pairs_img<T><<<grid, 256, prep_smem(p), h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp,
+                                                          nimg, p, skip);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip)
+template <typename T>
+cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip, const double *theta,
+                                const double *delta)
 {
-    return launch_pairs_img<T>(h, X, nimg, skip);
+    return launch_pairs_img<T>(h, X, nimg, skip, theta, delta);
 }
 
-template <typename T> cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip)
+template <typename T>
+cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip, const double *theta,
+                              const double *delta)
 {
+    const ViewPrep p = view_prep_args(h, theta, delta);
+    cudaError_t e = allow_prep_smem(k_pairs_sino<T>);
+    if (e != cudaSuccess) return e;
     const long long total = (long long)nsino * h.V * h.Pb;
     const int threads = 256;
     const long long blocks = std::min<long long>((total + threads - 1) / threads, (long long)h.num_sms * 16);
-    k_pairs_sino<T><<<(int)std::max<long long>(1, blocks), threads, 0, h.stream>>>(Y, (pair_t<T> *)h.d_yp, h.B,
-                                                                                     h.Pb, total, skip);
+    k_pairs_sino<T><<<(int)std::max<long long>(1, blocks) + (p.on ? 1 : 0), threads, prep_smem(p), h.stream>>>(
+        Y, (pair_t<T> *)h.d_yp, h.B, h.Pb, total, p, skip);
     return cudaGetLastError();
 }
 
@@ -580,9 +653,12 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
 }
 
 #define CTGB_RAY_INSTANTIATE(T)                                                                             \
-    template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int, const int *);                 \
-    template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int, const int *);                \
-    template cudaError_t launch_prep_forward<T>(const Handle &, const T *, int, const int *);              \
+    template cudaError_t launch_pairs_img<T>(const Handle &, const T *, int, const int *, const double *,   \
+                                             const double *);                                              \
+    template cudaError_t launch_pairs_sino<T>(const Handle &, const T *, int, const int *, const double *,  \
+                                              const double *);                                             \
+    template cudaError_t launch_prep_forward<T>(const Handle &, const T *, int, const int *, const double *, \
+                                                const double *);                                           \
     template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, int, const int *);     \
     template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int, int); \
     template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int, int);      \

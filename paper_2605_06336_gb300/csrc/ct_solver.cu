@@ -220,10 +220,11 @@ template <typename T> struct Solver {
     // HV[:, j0:j0+cnt) = H(theta) V[:, j0:j0+cnt), in chunks of max_batch columns
     int project(const double *theta, int j0, int cnt, const int *stop)
     {
-        SV_CUDA(launch_view_setup(h, theta, delta, stop));
+        if (cnt <= 0) SV_CUDA(launch_view_setup(h, theta, delta, stop));
         for (int j = j0; j < j0 + cnt; j += h.max_batch) {
             const int nb = std::min(h.max_batch, j0 + cnt - j);
-            SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop));
+            // the first layout launch also brings the view table up to date
+            SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop, j == j0 ? theta : nullptr, delta));
             SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
                                       h.tune.fwd_stage, stop));
         }
@@ -233,8 +234,7 @@ template <typename T> struct Solver {
     // out = H(theta)^T yin  (n vector)
     int backproject(const double *theta, const T *yin, T *out, const int *stop)
     {
-        SV_CUDA(launch_view_setup(h, theta, delta, stop));
-        SV_CUDA(launch_pairs_sino<T>(h, yin, 1, stop));
+        SV_CUDA(launch_pairs_sino<T>(h, yin, 1, stop, theta, delta));
         SV_CUDA(launch_adjoint<T>(h, out, 1, h.tune.adj_kb, h.tune.adj_split, h.tune.adj_stage, stop));
         return CT_OK;
     }
@@ -387,8 +387,7 @@ template <typename T> struct Solver {
     {
         SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
         for (int it = 0; it < o.maxiter_p; ++it) {
-            SV_CUDA(launch_view_setup(h, th_n, delta));
-            SV_CUDA(launch_pairs_img<T>(h, uimg, h.F));
+            SV_CUDA(launch_pairs_img<T>(h, uimg, h.F, nullptr, th_n, delta));
             SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
             k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
                                                      ctl);
@@ -439,8 +438,7 @@ template <typename T> struct Solver {
         k_varpro_value<<<1, 1, 0, h.stream>>>(norms, GP, y, k, lam, fval);
         SV_CUDA(cudaGetLastError());
         if (grad) {
-            SV_CUDA(launch_view_setup(h, theta, delta));
-            SV_CUDA(launch_pairs_img<T>(h, u, h.F));
+            SV_CUDA(launch_pairs_img<T>(h, u, h.F, nullptr, theta, delta));
             SV_CUDA(launch_vjp<T>(h, res, grad, nullptr, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
         }
         if (u_out) SV_CUDA(cudaMemcpyAsync(u_out, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
@@ -518,8 +516,7 @@ template <typename T> struct Solver {
             }
             // residual of the normal equations at H_k, new weights, appended to V
             k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.eps, nullptr);
-            SV_CUDA(launch_view_setup(h, th_k, delta));
-            SV_CUDA(launch_prep_forward<T>(h, u, h.F));
+            SV_CUDA(launch_prep_forward<T>(h, u, h.F, nullptr, th_k, delta));
             SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
             axpby(res, b, m, 1.0, -1.0);
             SV_TRY(backproject(th_k, res, col(V, n, kc), nullptr));
