@@ -233,12 +233,15 @@ inline int resident_per_sm(const void *kernel, int threads, size_t smem)
     return per_sm;
 }
 
-// Persistent grid: as many CTAs as are resident at once, capped by the work.
+// Grid of a work-item kernel: one CTA per item, so that the hardware hands
+// items to SMs as CTAs finish (items differ in cost: chunks at the detector
+// edge carry short rays).  Very large item counts are folded into a grid of
+// 64 resident waves; the kernels loop over item += gridDim.x.
 template <typename K>
 inline int persistent_grid(K kernel, int threads, size_t smem, long long work_blocks, int num_sms)
 {
     const int per_sm = resident_per_sm((const void *)kernel, threads, smem);
-    const long long cap = (long long)per_sm * num_sms;
+    const long long cap = 64LL * per_sm * num_sms;
     return (int)std::max<long long>(1, std::min(work_blocks, cap));
 }
 
