@@ -538,6 +538,17 @@ def main():
     achieved = gather_bytes / (kernel_ms[dom_name] * 1e-3) / 1e9
     shape = tuple(tuning[i] for i in ((0, 1, 2, 7) if dom_name == "forward_K8" else (3, 4, 9)))
     traffic = PROFILED_DRAM_BYTES.get((dom_name, shape))
+    # Gather roofline: the same algorithmic bytes against the measured read
+    # bandwidth of the level that serves the gathers (ncu: the L1-gather
+    # forward misses L1 and hits L2; the staged kernels read shared memory,
+    # and the L1-gather transpose mostly hits L1, which shares its data path).
+    l2_gbs, smem_gbs = ct.ct_measure_peaks()
+    gather = {}
+    for name, staged in (("forward_K8", tuning[7] > 0), ("adjoint_K8", tuning[9] > 0)):
+        level = "smem" if staged else ("L2" if name == "forward_K8" else "L1")
+        pk = l2_gbs if level == "L2" else smem_gbs
+        ach = gather_bytes / (kernel_ms[name] * 1e-3) / 1e9
+        gather[name] = {"level": level, "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk}
     sm_mhz = SM_MAX_MHZ_NOMINAL
     peak = NUM_SMS * LSU_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
     peaks, src = measured_peaks()
@@ -575,6 +586,10 @@ def main():
                               f"launch; peak = {NUM_SMS} SMs x {LSU_BYTES_PER_CLK_SM} B/clk L1 data path x "
                               f"{sm_mhz:.0f} MHz",
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": "derived (unit counts x nominal max clock)"},
+        "gather_roofline": gather,
+        "gather_roofline_note": "algorithmic gather bytes per launch / kernel time against the read bandwidth of the "
+                                "level serving the gathers, measured on this GPU by ct_measure_peaks "
+                                f"(L2 {l2_gbs:.0f} GB/s, shared memory {smem_gbs:.0f} GB/s)",
         "cpu_baseline": cpu,
         "solver": solver,
         "batched_frames": frames,

@@ -200,6 +200,19 @@ int ct_autotune(ct_handle *h);
 int ct_get_tuning(ct_handle *h, int32_t *out);
 int ct_set_tuning(ct_handle *h, const int32_t *in);
 
+/*
+ * Measure, on the current device, the read bandwidth of the two on-chip
+ * levels that serve the operators' gathers (a microbenchmark with no
+ * counterpart in the paper; it gives the measured denominators of the
+ * gather roofline):
+ *   *l2_read_gbs    float4 loads that bypass L1 over a 48 MB buffer held
+ *                   in L2, all SMs, GB/s;
+ *   *smem_read_gbs  conflict-free 16-byte shared-memory loads, all SMs, GB/s.
+ * Best of 5 timed launches each.  Allocates and frees 48 MB; synchronises a
+ * private stream.  CT_ERR_ARG for null outputs, CT_ERR_OOM, CT_ERR_CUDA.
+ */
+int ct_measure_peaks(double *l2_read_gbs, double *smem_read_gbs);
+
 /* ------------------------------------------------------------------------
  * NL-RMM-GKS (alternating form) on the handle's geometry.
  * ------------------------------------------------------------------------ */

@@ -100,6 +100,8 @@ def load_library(path: str | None = None):
     lib.ct_forward.argtypes = [P, P, P, P, P, I]
     lib.ct_adjoint.argtypes = [P, P, P, P, P, I]
     lib.ct_forward_repeat.argtypes = [P, P, I]
+    lib.ct_measure_peaks.argtypes = [P, P]
+    lib.ct_measure_peaks.restype = ctypes.c_int
     lib.ct_adjoint_repeat.argtypes = [P, P, I]
     lib.ct_jac.argtypes = [P, P, P, P, P, P, P]
     lib.ct_jacT.argtypes = [P, P, P, P, P, P, P]
@@ -172,6 +174,13 @@ def ct_forward(h, theta, delta, X, Y, batch):
 
 def ct_adjoint(h, theta, delta, Y, X, batch):
     _check(load_library().ct_adjoint(h, _p(theta), _p(delta), _p(Y), _p(X), int(batch)), "ct_adjoint")
+
+
+def ct_measure_peaks():
+    """(L2 read GB/s, shared-memory read GB/s) measured on the current device."""
+    l2, sm = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ct_measure_peaks(ctypes.byref(l2), ctypes.byref(sm)), "ct_measure_peaks")
+    return l2.value, sm.value
 
 
 def ct_forward_repeat(h, Y, batch):
