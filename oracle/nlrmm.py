@@ -12,7 +12,8 @@ Passages followed:
   * Alg. "Enlarge" and Alg. "Compress" (supplementary Sec. S1.2) and
     Alg. "RMM-GKS" (Sec. 3.3);
   * Alg. "UPDATE-PARAM" (damped Gauss-Newton + Armijo backtracking, Sec. 4.1.2);
-  * Alg. "NL-RMM-GKS" (Sec. 4.3) without the optional high-lambda solve.
+  * Alg. "NL-RMM-GKS" (Sec. 4.3) without the optional high-lambda solve;
+  * Alg. "s-NL-RMM-GKS" (Sec. 5) over blocks of views (``stream_solve``).
 
 Readings where the paper is silent (also listed in the design notes):
   * Psi = forward differences without wrap, horizontal then vertical, per frame;
@@ -349,3 +350,64 @@ def varpro_gradient(g: Geometry, b, theta, V, lam, w=None, delta=None):
     r = forward(g, theta, u, delta) - b
     gt, _ = jacT(g, theta, u, r, delta)
     return gt, f, u
+
+
+# ---------------------------------------------------------------------------
+# Alg. "s-NL-RMM-GKS" (Sec. 5): streaming over measurement blocks
+# ---------------------------------------------------------------------------
+def stream_solve(blocks, theta0, passes, u_true=None, theta_true=None, tol_u=None, tol_p=None, callback=None):
+    """Streaming NL-RMM-GKS over blocks of views (Sec. 2.4 block setup, Sec. 5).
+
+    ``blocks``: one NLRMMGKS per block j (its views' geometry, b_j, options
+    with that block's noise norm); all share the image size.  ``theta0``: the
+    blocks' initial angles.  Each pass visits the blocks in order; a visit is
+    one RMM-GKS cycle (Enlarge + Compress) on block j's data started from the
+    carried image and compressed basis, then UPDATE-PARAM for block j's
+    angles; the compressed basis is carried to the next block.  After each
+    pass the change of u and of all angles over the pass is checked against
+    tol_u / tol_p (the options of block 1 when not given).
+
+    Readings: V^(0)_kmin is the GKB basis of block 1 (b_1, k_min steps); no
+    residual is appended after the parameter update (the printed algorithm
+    has none: the first Enlarge step of the next block appends that block's
+    residual); the optional high-lambda solve is off.
+    Returns (u, thetas, history) with one history entry per pass;
+    ``callback(pass, j, u, V, thetas)`` after each block visit.
+    """
+    o1 = blocks[0].o
+    tol_u = o1.tol_u if tol_u is None else tol_u
+    tol_p = o1.tol_p if tol_p is None else tol_p
+    thetas = [np.array(t, float) for t in theta0]
+    n = blocks[0].g.n
+    u = np.zeros(n)
+    V = blocks[0].gkb(thetas[0], o1.k_min)
+    hist = History()
+    for _ in range(passes):
+        u_start = u.copy()
+        th_start = [t.copy() for t in thetas]
+        steps_pass = 0
+        lam = None
+        for j, blk in enumerate(blocks):
+            th = thetas[j]
+            HV = np.stack([blk.H(th, V[:, c]) for c in range(V.shape[1])], 1)
+            u, lam, Vg, _, RH, RP, used, steps = blk.enlarge(th, V, HV, u, blk.o.k_max - blk.o.k_min)
+            V = blk.compress(Vg, RH, RP, used, lam, u)
+            thetas[j] = blk.update_param(th, u) if blk.o.update_theta else th.copy()
+            steps_pass += steps
+            if callback:
+                callback(len(hist.du), j, u, V, thetas)
+        nu = np.linalg.norm(u_start)
+        du = np.linalg.norm(u - u_start) / nu if nu > 0 else np.inf
+        dth = float(np.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(thetas, th_start))))
+        hist.lam.append(lam)
+        hist.du.append(du)
+        hist.dtheta.append(dth)
+        hist.enlarge_steps.append(steps_pass)
+        if u_true is not None:
+            hist.rre.append(float(np.linalg.norm(u - u_true) / np.linalg.norm(u_true)))
+        if theta_true is not None:
+            err = np.concatenate([a - b for a, b in zip(thetas, theta_true)])
+            hist.angle_err.append(float(np.linalg.norm(err) / np.linalg.norm(np.concatenate(theta_true))))
+        if o1.stop_on_convergence and du < tol_u and dth < tol_p:
+            break
+    return u, thetas, hist

@@ -9,7 +9,12 @@
 * the discrepancy-principle lambda hits the target residual;
 * the per-view Gauss-Newton / Armijo update reaches the brute-force minimizer of a
   single view's misfit;
-* a small alternating solve reduces both the image and the angle error.
+* a small alternating solve reduces both the image and the angle error;
+* streaming (Alg. "s-NL-RMM-GKS"): a block visit with fixed lambda and weights and
+  a basis that reaches the image space returns the dense solution of that
+  block's own problem, whatever basis and image it was started from; the
+  carried compressed basis contains the image; a small streaming solve reduces
+  both errors.
 """
 import math
 
@@ -208,3 +213,80 @@ def test_varpro_reduced_gradient_matches_central_differences():
         errs[h] = err / ref
     assert errs[1e-4] < 5e-2, errs
     assert errs[1e-6] < max(errs[1e-4] / 20, 1e-7), errs
+
+
+def _blocks(g, th, b, nblocks, opts_for):
+    """Split the views of (g, th, b) into nblocks consecutive blocks."""
+    idx = np.array_split(np.arange(g.V), nblocks)
+    bv = b.reshape(g.V, g.B)
+    out = []
+    for j, ix in enumerate(idx):
+        gj = oracle.Geometry(g.N, g.B, len(ix))
+        out.append((nlrmm.NLRMMGKS(gj, bv[ix].ravel(), opts_for(j, ix)), th[ix]))
+    return out
+
+
+def test_stream_visit_solves_its_own_block_problem():
+    g, th, _, _, b, _ = small_problem(N=10, V=10, seed=21)
+    rng = np.random.default_rng(22)
+    w = rng.uniform(0.5, 2.0, 2 * g.N * (g.N - 1))
+    lam = 0.3
+    opts = lambda j, ix: nlrmm.Options(k_min=3, k_max=3 + g.n + 5, tol1=0.0, lam_fix=lam, fixed_weights=w,
+                                       update_theta=False, stop_on_convergence=False)
+    blocks = _blocks(g, th, b, 2, opts)
+    E = np.eye(g.n)
+    PsiM = np.stack([nlrmm.psi(g, E[:, j]) for j in range(g.n)], 1)
+    seen = []
+
+    def cb(p, j, u, V, thetas):
+        blk, thj = blocks[j]
+        A = oracle.dense_matrix(blk.g, thj)
+        M = A.T @ A + lam * PsiM.T @ (w[:, None] * PsiM)
+        u_ref = np.linalg.solve(M, A.T @ blk.b)
+        seen.append(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+
+    nlrmm.stream_solve([s for s, _ in blocks], [t for _, t in blocks], passes=2, callback=cb)
+    assert len(seen) == 4 and max(seen) <= 1e-8, seen
+
+
+def test_stream_carries_the_image_in_the_basis():
+    g, th, _, _, b, nn = small_problem(N=16, V=12, seed=23)
+    opts = lambda j, ix: nlrmm.Options(k_min=5, k_max=15, noise_norm=nn / math.sqrt(3), stop_on_convergence=False)
+    blocks = _blocks(g, th, b, 3, opts)
+    checks = []
+
+    def cb(p, j, u, V, thetas):
+        checks.append((np.linalg.norm(u - V @ (V.T @ u)) / np.linalg.norm(u), np.abs(V.T @ V - np.eye(V.shape[1])).max(),
+                       V.shape[1]))
+
+    nlrmm.stream_solve([s for s, _ in blocks], [t for _, t in blocks], passes=2, callback=cb)
+    assert len(checks) == 6
+    for resid, orth, k in checks:
+        assert resid <= 1e-12 and orth <= 1e-12 and k == 5
+
+
+@pytest.mark.slow
+def test_small_streaming_solve_reduces_errors():
+    rng = np.random.default_rng(24)
+    N, V, nb = 32, 30, 3
+    g = oracle.Geometry(N, synth.n_bins(N), V)
+    th_nom = np.sort(rng.uniform(0, math.pi, V))
+    th_true = th_nom + rng.normal(0, math.radians(0.5), V)
+    perm = rng.permutation(V)  # views drawn into blocks without replacement
+    u_true = synth.rasterize(N, synth.random_ellipses(N, 3, rng)).ravel()
+    b_true = oracle.forward(g, th_true, u_true).reshape(V, -1)
+    e = rng.standard_normal(b_true.shape)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    blocks, th0, tht = [], [], []
+    for ix in np.array_split(perm, nb):
+        ix = np.sort(ix)
+        gj = oracle.Geometry(N, g.B, len(ix))
+        o = nlrmm.Options(noise_norm=float(np.linalg.norm(e[ix])), stop_on_convergence=False)
+        blocks.append(nlrmm.NLRMMGKS(gj, (b_true[ix] + e[ix]).ravel(), o))
+        th0.append(th_nom[ix])
+        tht.append(th_true[ix])
+    u, th, hist = nlrmm.stream_solve(blocks, th0, passes=6, u_true=u_true, theta_true=tht)
+    err0 = np.linalg.norm(np.concatenate(th0) - np.concatenate(tht))
+    assert np.linalg.norm(np.concatenate(th) - np.concatenate(tht)) < 0.6 * err0
+    assert all(hist.rre[i + 1] <= hist.rre[i] for i in range(len(hist.rre) - 1)), hist.rre
+    assert hist.rre[-1] < 0.5 * hist.rre[0]
