@@ -277,6 +277,39 @@ int nlrmm_gks_solve(ct_handle *h, const void *b, double *theta_inout, const doub
                     const void *x_true, const nlrmm_opts *opts, nlrmm_stats *stats);
 
 /*
+ * Streaming NL-RMM-GKS over blocks of views (Alg. "s-NL-RMM-GKS", Sec. 5,
+ * blocks as in Sec. 2.4): each pass visits the blocks in order; a visit is
+ * one Enlarge + Compress on block j's data, started from the carried image
+ * and compressed basis, then per-view Gauss-Newton with Armijo on block j's
+ * angles; the compressed basis (k_min columns) goes on to the next block.
+ * Passes repeat until the image and all angles change less than tol_u /
+ * tol_p over a pass, or outer_iters passes.  The first basis is k_min
+ * Golub-Kahan steps on block 0's data; u starts at zero; no residual is
+ * appended after a parameter update (the next block's first Enlarge step
+ * appends its own).
+ *   blocks [nblocks]      host array of handles, one per block (its views);
+ *                         same N, n_frames, precision and device; each
+ *                         keeps its own launch shapes
+ *   b [nblocks]           host array of device [V_j][B] data
+ *   theta_inout [nblocks] host array of device [V_j] double angles, updated
+ *   delta                 host array of device [V_j] offsets (entries may be
+ *                         NULL) or NULL: no offsets
+ *   noise_norms [nblocks] host, |e_j| for block j's discrepancy principle
+ *                         (NULL allowed when opts->lam_fix > 0)
+ *   x_out [n_frames][N][N] device; x_true nullable, for the RRE history
+ *   stats                 one entry per pass: Enlarge steps summed over the
+ *                         blocks, lambda of the last block, du, dtheta (all
+ *                         blocks), rre, ms
+ * Workspace about (k_max + 2)(n + max_j m_j) elements, allocated on entry and
+ * freed on return; runs on a private stream ordered after every block's
+ * stream and synchronises it.  CT_OK, CT_ERR_NOCONV, CT_ERR_ARG, CT_ERR_OOM,
+ * CT_ERR_CUDA.
+ */
+int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const *b, double *const *theta_inout,
+                       const double *const *delta, const double *noise_norms, void *x_out, const void *x_true,
+                       const nlrmm_opts *opts, nlrmm_stats *stats);
+
+/*
  * VarPro reduced objective on a fixed basis (Sec. 4.2, Alg.
  * "UPDATE-PARAM-VarPro"): with the image restricted to span(V) and the MM
  * weights frozen,

@@ -86,9 +86,12 @@ template <typename T> struct Solver {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::vector<cudaGraphExec_t> step_graph;  // one captured Enlarge step per basis size
     bool use_graphs = true;
+    double noise = 0.0;      // noise norm of the discrepancy principle for the bound data
+    long long m_cap = 0;     // streaming: capacities over all blocks (0: this handle's)
+    int v_cap = 0;
 
     Solver(const Handle &h_, cudaStream_t s_, const nlrmm_opts &o_, const T *b_, const double *delta_)
-        : h(h_), o(o_), b(b_), delta(delta_)
+        : h(h_), o(o_), b(b_), delta(delta_), noise(o_.noise_norm)
     {
         h.stream = s_;
     }
@@ -130,13 +133,15 @@ template <typename T> struct Solver {
         KC = o.k_max + 2;
         const int tiles = ((h.N + 31) / 32) * ((h.N + (sizeof(T) == 4 ? 8 : 4) - 1) / (sizeof(T) == 4 ? 8 : 4)) * h.F;
         gram_blocks = std::min(tiles, 2 * h.num_sms);
+        const long long m_all = std::max(m, m_cap);
+        const int v_all = std::max(h.V, v_cap);
         SV_TRY(alloc(V, (size_t)KC * n));
-        SV_TRY(alloc(HV, (size_t)KC * m));
+        SV_TRY(alloc(HV, (size_t)KC * m_all));
         SV_TRY(alloc(u, n));
         SV_TRY(alloc(uold, n));
         SV_TRY(alloc(uprev, n));
         SV_TRY(alloc(w, ne));
-        SV_TRY(alloc(res, m));
+        SV_TRY(alloc(res, m_all));
         SV_TRY(alloc(Vtmp, (size_t)o.k_min * n));
         SV_TRY(alloc(GH, kKMax * kKMax));
         SV_TRY(alloc(GP, kKMax * kKMax));
@@ -150,9 +155,9 @@ template <typename T> struct Solver {
         SV_TRY(alloc(norms, 3));
         SV_TRY(alloc(norms2, 3));
         SV_TRY(alloc(scal, kScalCount));
-        for (double **p : {&th_k, &th_n, &th_t, &d, &alpha, &g, &j2, &f0, &ft, &scratch_v}) SV_TRY(alloc(*p, h.V));
+        for (double **p : {&th_k, &th_n, &th_t, &d, &alpha, &g, &j2, &f0, &ft, &scratch_v}) SV_TRY(alloc(*p, v_all));
         SV_TRY(alloc(ctl, kCtlCount));
-        SV_TRY(alloc(active, h.V));
+        SV_TRY(alloc(active, v_all));
         if (cudaMallocHost(&h_ctl, sizeof(int) * kCtlCount) != cudaSuccess ||
             cudaMallocHost(&h_scal, sizeof(double) * 16) != cudaSuccess ||
             cudaHostAlloc(&h_stop, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
@@ -317,7 +322,7 @@ template <typename T> struct Solver {
         k_gram_psi<T, TR><<<gblk, kThreads, gram_smem(kc), h.stream>>>(V, n, kc, w, h.N, h.F, part_gram, stop);
         k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gblk, kc, GP, stop);
         // lambda and the reduced solution
-        const double target = (o.tau * o.noise_norm) * (o.tau * o.noise_norm);
+        const double target = (o.tau * noise) * (o.tau * noise);
         k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
                                                                      o.lam_lo, o.lam_hi, o.lam_iters, y, scal, ctl);
         // u = V y ; res = (HV) y - b
@@ -446,6 +451,170 @@ template <typename T> struct Solver {
         return CT_OK;
     }
 
+    // ---- streaming (Alg. "s-NL-RMM-GKS", Sec. 5) --------------------------------
+    // Bind block j: its handle (views, layouts, launch shapes) on the solver's
+    // stream, its data, offsets and noise norm.  Basis, image and the small
+    // algebra state stay.
+    int bind(const Handle &hj, const T *bj, const double *deltaj, double noise_j)
+    {
+        const cudaStream_t s_ = h.stream;
+        h = hj;
+        h.stream = s_;
+        b = bj;
+        delta = deltaj;
+        noise = noise_j;
+        m = (long long)h.V * h.B;
+        double nb[3];
+        SV_TRY(norms3(b, nullptr, m, norms, nullptr));
+        SV_TRY(read_doubles(norms, 3, nb));
+        bnorm2 = nb[0];
+        return CT_OK;
+    }
+
+    // One visit of the bound block: an RMM-GKS cycle (Enlarge + Compress) from
+    // the carried image and basis (kc columns), then UPDATE-PARAM for the
+    // block's angles theta_j (device, updated in place).  |theta change|^2 is
+    // added to *dth2.
+    int visit(double *theta_j, int &kc, int &steps_out, double &lam_out, double *dth2)
+    {
+        SV_CUDA(cudaMemcpyAsync(th_k, theta_j, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        SV_TRY(project(th_k, 0, kc, nullptr));
+        SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
+        SV_TRY(full_gram(kc));
+        SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        *(volatile int *)h_stop = 0;
+        const int s_steps = o.k_max - o.k_min;
+        for (int step = 0; step < s_steps && kc + step + 1 < KC; ++step) {
+            if (step >= 2) {
+                SV_CUDA(cudaEventSynchronize(ev[step & 1]));
+                if (*(volatile int *)h_stop) break;
+            }
+            SV_TRY(run_step(kc + step));
+            SV_CUDA(cudaEventRecord(ev[step & 1], h.stream));
+        }
+        SV_TRY(sync_ctl());
+        steps_out = h_ctl[kSteps];
+        const int k_used = kc + steps_out - 1;
+        SV_TRY(compress(k_used, kc));
+        if (o.update_theta) {
+            SV_TRY(update_param(u));
+        } else {
+            SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        }
+        k_norms3<double><<<kRedBlocks, kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
+        k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, norms, nullptr);
+        double dth3[3], lam_now[1];
+        SV_TRY(read_doubles(norms, 3, dth3));
+        SV_TRY(read_doubles(scal + kLam, 1, lam_now));
+        *dth2 += dth3[1];
+        lam_out = lam_now[0];
+        SV_CUDA(cudaMemcpyAsync(theta_j, th_n, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        return CT_OK;
+    }
+
+    // Compress: the k_min - 1 leading directions of the reduced problem on the
+    // k_used columns, then the normalized part of u outside them; kc = the
+    // columns kept.
+    int compress(int k_used, int &kc)
+    {
+        const int keep = std::min(o.k_min - 1, k_used);
+        k_compress_basis<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, GP, k_used, scal, keep, W);
+        k_gemm_small<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k_used, W, keep, Vtmp, n);
+        SV_CUDA(cudaMemcpyAsync(V, Vtmp, sizeof(T) * n * keep, cudaMemcpyDeviceToDevice, h.stream));
+        SV_TRY(dots_into(V, n, keep, u, nullptr, dots, nullptr));
+        k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, keep, dots, col(V, n, keep), T(0), T(-1), u,
+                                                            T(1), nullptr);
+        SV_TRY(norms3(col(V, n, keep), u, n, norms, nullptr));
+        double nu[3];
+        SV_TRY(read_doubles(norms, 3, nu));
+        kc = keep;
+        if (std::sqrt(nu[0]) > 1e-14 * std::max(std::sqrt(nu[2]), 1e-300)) {
+            scale(col(V, n, keep), n, 1.0 / std::sqrt(nu[0]));
+            kc = keep + 1;
+        }
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // Alg. "s-NL-RMM-GKS": passes over the blocks, each block visited once per
+    // pass, until the image and all angles change less than tol_u / tol_p
+    // over a pass (or outer_iters passes).  The first basis is the GKB basis
+    // of block 0.  Statistics are per pass.
+    int stream_run(int nb, const Handle *const *hs, const T *const *bs, double *const *thetas,
+                   const double *const *deltas, const double *noises, void *x_out, const T *x_true,
+                   nlrmm_stats *st)
+    {
+        for (int j = 0; j < nb; ++j) {
+            m_cap = std::max(m_cap, (long long)hs[j]->V * hs[j]->B);
+            v_cap = std::max(v_cap, hs[j]->V);
+        }
+        use_graphs = false;  // a captured Enlarge step would hold one block's buffers
+        SV_TRY(setup());
+        double xt2 = 0.0, nb3[3];
+        if (x_true) {
+            SV_TRY(norms3(x_true, nullptr, n, norms, nullptr));
+            SV_TRY(read_doubles(norms, 3, nb3));
+            xt2 = nb3[0];
+        }
+        SV_TRY(bind(*hs[0], bs[0], deltas ? deltas[0] : nullptr, noises ? noises[0] : 0.0));
+        SV_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * n, h.stream));
+        SV_CUDA(cudaMemsetAsync(uold, 0, sizeof(T) * n, h.stream));
+        SV_CUDA(cudaMemsetAsync(uprev, 0, sizeof(T) * n, h.stream));
+        SV_TRY(gkb(thetas[0], o.k_min));
+        int kc = o.k_min;
+        int rc_final = CT_ERR_NOCONV;
+        if (st) std::memset(st, 0, sizeof(*st));
+        for (int pass = 0; pass < o.outer_iters; ++pass) {
+            const auto t0 = std::chrono::steady_clock::now();
+            SV_CUDA(cudaMemcpyAsync(uprev, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
+            double dth2 = 0.0, lam = 0.0;
+            int steps_pass = 0;
+            for (int j = 0; j < nb; ++j) {
+                SV_TRY(bind(*hs[j], bs[j], deltas ? deltas[j] : nullptr, noises ? noises[j] : 0.0));
+                int steps = 0;
+                SV_TRY(visit(thetas[j], kc, steps, lam, &dth2));
+                steps_pass += steps;
+            }
+            SV_TRY(norms3(u, uprev, n, norms, nullptr));
+            double du3[3];
+            SV_TRY(read_doubles(norms, 3, du3));
+            double rre = -1.0;
+            if (x_true) {
+                SV_TRY(norms3(u, x_true, n, norms, nullptr));
+                double e3[3];
+                SV_TRY(read_doubles(norms, 3, e3));
+                rre = std::sqrt(e3[1] / std::max(xt2, 1e-300));
+            }
+            const double du = du3[2] > 0.0 ? std::sqrt(du3[1] / du3[2]) : INFINITY;
+            const double dth = std::sqrt(dth2);
+            SV_CUDA(cudaStreamSynchronize(h.stream));
+            const double ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (st) {
+                st->outer_done = pass + 1;
+                if (pass < NLRMM_MAX_HIST) {
+                    st->enlarge_steps[pass] = steps_pass;
+                    st->lambda[pass] = lam;
+                    st->du[pass] = du;
+                    st->dtheta[pass] = dth;
+                    st->rre[pass] = rre;
+                    st->ms[pass] = ms;
+                }
+                st->breakdown |= h_ctl[kBreakdown];
+            }
+            if (o.stop_on_convergence && du < o.tol_u && dth < o.tol_p) {
+                rc_final = CT_OK;
+                if (st) st->converged = 1;
+                break;
+            }
+        }
+        if (!o.stop_on_convergence) rc_final = CT_OK;
+        SV_CUDA(cudaMemcpyAsync(x_out, u, sizeof(T) * n, cudaMemcpyDeviceToDevice, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        return rc_final;
+    }
+
     // ---- the whole solve ---------------------------------------------------------
     int run(double *theta_io, void *x_out, const T *x_true, nlrmm_stats *st)
     {
@@ -493,21 +662,7 @@ template <typename T> struct Solver {
             const int steps = h_ctl[kSteps];
             const int k_used = kc + steps - 1;  // columns the last reduced problem used
             // Compress
-            const int keep = std::min(o.k_min - 1, k_used);
-            k_compress_basis<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, GP, k_used, scal, keep, W);
-            k_gemm_small<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k_used, W, keep, Vtmp, n);
-            SV_CUDA(cudaMemcpyAsync(V, Vtmp, sizeof(T) * n * keep, cudaMemcpyDeviceToDevice, h.stream));
-            SV_TRY(dots_into(V, n, keep, u, nullptr, dots, nullptr));
-            k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, keep, dots, col(V, n, keep), T(0), T(-1), u,
-                                                                T(1), nullptr);
-            SV_TRY(norms3(col(V, n, keep), u, n, norms, nullptr));
-            double nu[3];
-            SV_TRY(read_doubles(norms, 3, nu));
-            kc = keep;
-            if (std::sqrt(nu[0]) > 1e-14 * std::max(std::sqrt(nu[2]), 1e-300)) {
-                scale(col(V, n, keep), n, 1.0 / std::sqrt(nu[0]));
-                kc = keep + 1;
-            }
+            SV_TRY(compress(k_used, kc));
             // parameter update
             if (o.update_theta) {
                 SV_TRY(update_param(u));
@@ -638,6 +793,62 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
     } else {
         Solver<float> s(h, ps, o, (const float *)b, delta);
         rc = s.run(theta_inout, x_out, (const float *)x_true, stats);
+    }
+    cudaStreamSynchronize(ps);
+    cudaEventDestroy(e0);
+    cudaStreamDestroy(ps);
+    return rc;
+}
+
+int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const *b, double *const *theta_inout,
+                       const double *const *delta, const double *noise_norms, void *x_out, const void *x_true,
+                       const nlrmm_opts *opts, nlrmm_stats *stats)
+{
+    if (!blocks || nblocks < 1 || !b || !theta_inout || !x_out || !opts) return CT_ERR_ARG;
+    const nlrmm_opts &o = *opts;
+    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min - 1 > 16 ||
+        o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
+        !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !noise_norms))
+        return CT_ERR_ARG;
+    std::vector<const ctgb::Handle *> hs(nblocks);
+    for (int j = 0; j < nblocks; ++j) {
+        if (!blocks[j] || !b[j] || !theta_inout[j]) return CT_ERR_ARG;
+        const ctgb::Handle &hj = blocks[j]->h;
+        const ctgb::Handle &h0 = blocks[0]->h;
+        if (hj.N != h0.N || hj.F != h0.F || hj.precision != h0.precision || hj.device != h0.device)
+            return CT_ERR_ARG;
+        if (o.lam_fix <= 0.0 && !(noise_norms[j] > 0.0)) return CT_ERR_ARG;
+        hs[j] = &hj;
+    }
+    for (int j = 0; j < nblocks; ++j) blocks[j]->h.fwd_ready = blocks[j]->h.adj_ready = 0;
+    ctgb::Handle &h = blocks[0]->h;
+    cudaStream_t ps = nullptr;
+    cudaEvent_t e0 = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        if (ps) cudaStreamDestroy(ps);
+        return CT_ERR_CUDA;
+    }
+    // ordered after the work already queued on every block's stream
+    for (int j = 0; j < nblocks; ++j) {
+        if (cudaEventRecord(e0, blocks[j]->h.stream) != cudaSuccess || cudaStreamWaitEvent(ps, e0, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(e0);
+            cudaStreamDestroy(ps);
+            return CT_ERR_CUDA;
+        }
+    }
+    int rc;
+    if (h.precision) {
+        Solver<double> s(h, ps, o, (const double *)b[0], delta ? delta[0] : nullptr);
+        rc = s.stream_run(nblocks, hs.data(), (const double *const *)b, theta_inout, delta, noise_norms, x_out,
+                          (const double *)x_true, stats);
+    } else {
+        Solver<float> s(h, ps, o, (const float *)b[0], delta ? delta[0] : nullptr);
+        rc = s.stream_run(nblocks, hs.data(), (const float *const *)b, theta_inout, delta, noise_norms, x_out,
+                          (const float *)x_true, stats);
     }
     cudaStreamSynchronize(ps);
     cudaEventDestroy(e0);

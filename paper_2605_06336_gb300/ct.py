@@ -119,6 +119,8 @@ def load_library(path: str | None = None):
     lib.nlrmm_default_opts.restype = None
     lib.nlrmm_gks_solve.argtypes = [P, P, P, P, P, P, P, P]
     lib.nlrmm_gks_solve.restype = ctypes.c_int
+    lib.nlrmm_stream_solve.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.nlrmm_stream_solve.restype = ctypes.c_int
     lib.ct_strerror.argtypes = [I]
     lib.ct_strerror.restype = ctypes.c_char_p
     lib.ct_last_cuda_error.argtypes = []
@@ -270,6 +272,45 @@ def nlrmm_gks_solve(h, b, theta_inout, delta, x_out, x_true=None, opts=None, **o
              "enlarge_steps": list(st.enlarge_steps[:k]), "lambda": list(st.lambda_[:k]), "du": list(st.du[:k]),
              "dtheta": list(st.dtheta[:k]), "rre": list(st.rre[:k]), "ms": list(st.ms[:k])}
     return rc, stats
+
+
+def nlrmm_stream_solve(handles, bs, thetas, deltas, noise_norms, x_out, x_true=None, opts=None, **overrides):
+    """Run the GPU streaming NL-RMM-GKS over blocks; returns (status code, stats dict per pass)."""
+    o = opts if opts is not None else nlrmm_default_opts(**overrides)
+    nb = len(handles)
+    if not (len(bs) == len(thetas) == nb) or (deltas is not None and len(deltas) != nb):
+        raise ValueError("one data vector, angle vector (and offset vector) per block")
+    Parr = ctypes.c_void_p * nb
+    hs = Parr(*[h for h in handles])
+    barr = Parr(*[_p(b) for b in bs])
+    tharr = Parr(*[_p(t) for t in thetas])
+    darr = None if deltas is None else Parr(*[_p(d) for d in deltas])
+    narr = None if noise_norms is None else (ctypes.c_double * nb)(*[float(x) for x in noise_norms])
+    st = nlrmm_stats()
+    rc = load_library().nlrmm_stream_solve(hs, nb, barr, tharr, darr, narr, _p(x_out), _p(x_true),
+                                           ctypes.byref(o), ctypes.byref(st))
+    if rc not in (CT_OK, CT_ERR_NOCONV):
+        raise CTError(rc, "nlrmm_stream_solve")
+    k = min(st.outer_done, NLRMM_MAX_HIST)
+    stats = {"rc": rc, "passes": st.outer_done, "converged": bool(st.converged), "breakdown": bool(st.breakdown),
+             "enlarge_steps": list(st.enlarge_steps[:k]), "lambda": list(st.lambda_[:k]), "du": list(st.du[:k]),
+             "dtheta": list(st.dtheta[:k]), "rre": list(st.rre[:k]), "ms": list(st.ms[:k])}
+    return rc, stats
+
+
+def stream_solve(ops, bs, thetas0, noise_norms, deltas=None, x_true=None, **opts):
+    """Streaming NL-RMM-GKS over blocks (one CTOperator per block, sharing the
+    image size): returns (x, thetas, stats).  thetas0 are not modified."""
+    op0 = ops[0]
+    for op, b in zip(ops, bs):
+        op._chk(b, op.m, "b")
+    thetas = [op._ang(t, "theta0").clone() for op, t in zip(ops, thetas0)]
+    dl = None if deltas is None else [op._ang(d, "delta") for op, d in zip(ops, deltas)]
+    x = torch.empty(op0.n, dtype=op0.dtype, device=bs[0].device)
+    if x_true is not None:
+        op0._chk(x_true, op0.n, "x_true")
+    _, stats = nlrmm_stream_solve([op.h for op in ops], bs, thetas, dl, noise_norms, x, x_true, **opts)
+    return x, thetas, stats
 
 
 def nlrmm_varpro(h, b, theta, delta, V, k, lam, u_w, eps, fval, grad=None, u_out=None):
