@@ -219,7 +219,7 @@ int ct_measure_peaks(double *l2_read_gbs, double *smem_read_gbs);
 #define NLRMM_MAX_HIST 256
 
 typedef struct {
-    int32_t k_min;          /* compressed basis size (Sec. 6 default 5); 2 <= k_min <= 17 */
+    int32_t k_min;          /* compressed basis size (Sec. 6 default 5); 2 <= k_min <= 32 */
     int32_t k_max;          /* enlarged basis size (default 25); k_min < k_max <= 62 */
     int32_t outer_iters;    /* outer iteration limit */
     int32_t maxiter_p;      /* Gauss-Newton iterations per outer iteration (default 3) */

@@ -520,7 +520,9 @@ template <typename T> struct Solver {
     {
         const int keep = std::min(o.k_min - 1, k_used);
         k_compress_basis<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, GP, k_used, scal, keep, W);
-        k_gemm_small<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k_used, W, keep, Vtmp, n);
+        for (int c0 = 0; c0 < keep; c0 += 16)  // 16 output columns per pass over V
+            k_gemm_small<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k_used, W + c0,
+                                                                    std::min(16, keep - c0), col(Vtmp, n, c0), n);
         SV_CUDA(cudaMemcpyAsync(V, Vtmp, sizeof(T) * n * keep, cudaMemcpyDeviceToDevice, h.stream));
         SV_TRY(dots_into(V, n, keep, u, nullptr, dots, nullptr));
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, keep, dots, col(V, n, keep), T(0), T(-1), u,
@@ -768,7 +770,7 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
 {
     if (!H || !b || !theta_inout || !x_out || !opts) return CT_ERR_ARG;
     const nlrmm_opts &o = *opts;
-    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min - 1 > 16 ||
+    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min > 32 ||
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
         return CT_ERR_ARG;
@@ -806,7 +808,7 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
 {
     if (!blocks || nblocks < 1 || !b || !theta_inout || !x_out || !opts) return CT_ERR_ARG;
     const nlrmm_opts &o = *opts;
-    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min - 1 > 16 ||
+    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min > 32 ||
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !noise_norms))
         return CT_ERR_ARG;
