@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true", help="skip the NL-RMM-GKS comparison")
     ap.add_argument("--solver-iters", type=int, default=30)
+    ap.add_argument("--stream-passes", type=int, default=2,
+                    help="passes of the streaming solve on the 2048^2 / 1440-view workload (0: skip)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw,fstage,jstage,astage' "
                          "(the ct_set_tuning values) instead of autotuning")
@@ -259,6 +261,59 @@ def solver_comparison(w, dev, outer_iters):
     out["speedup_fp32_vs_fp64"] = a["total_ms"] / b_["total_ms"]
     out["outer_iters"] = outer_iters
     out["initial_max_abs_angle_err_deg"] = float(np.abs(w.theta_nominal - w.theta_true).max()) * 180 / math.pi
+    return out
+
+
+def streaming_c5(dev, passes):
+    """Streaming NL-RMM-GKS (FP32 operators, FP64 small algebra) on the 2048^2 /
+    1440-view workload in its 12 random chunks of 120 views: one handle per
+    chunk, `passes` passes.  The data are H(theta_true) u_true from the FP64
+    GPU forward plus 0.5 % noise."""
+    import torch
+    from paper_2605_06336_gb300 import ct, synth
+    w = synth.make_workload("C5")
+    N, B = w.N, w.B
+    chunks = w.extra["chunks"]
+    u64 = torch.tensor(w.images.reshape(-1), dtype=torch.float64, device=dev)
+    bt = []
+    for ch in chunks:
+        op64 = ct.CTOperator(N, B, len(ch), max_batch=1, dtype=torch.float64)
+        bt.append(op64.forward(u64, torch.tensor(w.theta_true[ch], device=dev)).cpu().numpy())
+        op64.close()
+    nd = w.noise_dir.reshape(w.V, B)
+    scale = w.noise_level * math.sqrt(sum(float((x * x).sum()) for x in bt)) / np.linalg.norm(nd)
+    ops, bs, th0, nns, tuning = [], [], [], [], None
+    for j, ch in enumerate(chunks):
+        op = ct.CTOperator(N, B, len(ch), max_batch=4, dtype=torch.float32)
+        if tuning is None:
+            tuning = op.autotune()  # one geometry for every chunk
+        else:
+            op.tuning = tuning
+        e = scale * nd[ch].ravel()
+        bs.append(torch.tensor(bt[j] + e, dtype=torch.float32, device=dev))
+        th0.append(torch.tensor(w.theta_nominal[ch], device=dev))
+        nns.append(float(np.linalg.norm(e)))
+        ops.append(op)
+    k_min, k_max = 20, 60
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, th, st = ct.stream_solve(ops, bs, th0, nns, x_true=u64.float(), k_min=k_min, k_max=k_max,
+                                outer_iters=passes, stop_on_convergence=0)
+    wall = time.perf_counter() - t0
+    tht = np.concatenate([w.theta_true[ch] for ch in chunks])
+    thn = np.concatenate([w.theta_nominal[ch] for ch in chunks])
+    the = np.concatenate([t.cpu().numpy() for t in th])
+    rel = lambda a: float(np.linalg.norm(a - tht) / np.linalg.norm(tht))
+    out = {"workload": f"C5: {N}x{N}, {w.V} views in {len(chunks)} streamed chunks of {len(chunks[0])}, {B} bins, "
+                       f"{w.noise_level * 100:.1f}% noise",
+           "passes": st["passes"], "k_min": k_min, "k_max": k_max, "wall_s": wall, "ms_per_pass": st["ms"],
+           "enlarge_steps_per_pass": st["enlarge_steps"], "rre_per_pass": st["rre"], "lambda_last_block": st["lambda"],
+           "rel_angle_err_initial": rel(thn), "rel_angle_err_final": rel(the),
+           "tuning": dict(zip(ct.TUNING_FIELDS, tuning)),
+           "note": "basis capped at k_max = 60 (the FP64 small algebra holds at most 64 columns); "
+                   "data from the FP64 GPU forward"}
+    for op in ops:
+        op.close()
     return out
 
 
@@ -554,9 +609,11 @@ def main():
     peaks, src = measured_peaks()
     solver = None
     frames = None
+    streaming = None
     if not args.no_solver and world == 1:
         solver = solver_comparison(w, dev, args.solver_iters)
         frames = batched_frames(dev, min(args.steps, 200), flush)
+        streaming = streaming_c5(dev, args.stream_passes) if args.stream_passes > 0 else None
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, args.cpu_seconds)
@@ -593,6 +650,7 @@ def main():
         "cpu_baseline": cpu,
         "solver": solver,
         "batched_frames": frames,
+        "streaming": streaming,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step(tuning) * args.steps,
         "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
