@@ -13,7 +13,9 @@ Passages followed:
     Alg. "RMM-GKS" (Sec. 3.3);
   * Alg. "UPDATE-PARAM" (damped Gauss-Newton + Armijo backtracking, Sec. 4.1.2);
   * Alg. "NL-RMM-GKS" (Sec. 4.3) without the optional high-lambda solve;
-  * Alg. "s-NL-RMM-GKS" (Sec. 5) over blocks of views (``stream_solve``).
+  * Alg. "s-NL-RMM-GKS" (Sec. 5) over blocks of views (``stream_solve``);
+  * the dynamic form with ANISO-TV (operator D_1, Alg. "Dynamic NL-RMM-GKS"): Psi gains the
+    differences of consecutive frames (``Options.temporal``).
 
 Readings where the paper is silent (also listed in the design notes):
   * Psi = forward differences without wrap, horizontal then vertical, per frame;
@@ -54,23 +56,34 @@ from . import Geometry, adjoint, dsample, forward
 # ---------------------------------------------------------------------------
 # regularization operator Psi (finite differences, Sec. 2.2)
 # ---------------------------------------------------------------------------
-def psi(g: Geometry, u: np.ndarray) -> np.ndarray:
+def psi(g: Geometry, u: np.ndarray, temporal: bool = False) -> np.ndarray:
+    """Psi u: forward differences within each frame (horizontal block, then
+    vertical); with ``temporal`` also the difference of consecutive frames
+    (ANISO-TV: the operator D_1 = [I_nt (x) L_s; L_t (x) I_ns] of the dynamic
+    extension, Alg. "Dynamic NL-RMM-GKS")."""
     U = u.reshape(g.F, g.N, g.N)
     dx = U[:, :, 1:] - U[:, :, :-1]
     dy = U[:, 1:, :] - U[:, :-1, :]
-    return np.concatenate([dx.ravel(), dy.ravel()])
+    parts = [dx.ravel(), dy.ravel()]
+    if temporal and g.F > 1:
+        parts.append((U[1:] - U[:-1]).ravel())
+    return np.concatenate(parts)
 
 
-def psi_t(g: Geometry, z: np.ndarray) -> np.ndarray:
+def psi_t(g: Geometry, z: np.ndarray, temporal: bool = False) -> np.ndarray:
     F, N = g.F, g.N
     nx = F * N * (N - 1)
     dx = z[:nx].reshape(F, N, N - 1)
-    dy = z[nx:].reshape(F, N - 1, N)
+    dy = z[nx:2 * nx].reshape(F, N - 1, N)
     U = np.zeros((F, N, N))
     U[:, :, 1:] += dx
     U[:, :, :-1] -= dx
     U[:, 1:, :] += dy
     U[:, :-1, :] -= dy
+    if temporal and F > 1:
+        dt = z[2 * nx:].reshape(F - 1, N, N)
+        U[1:] += dt
+        U[:-1] -= dt
     return U.ravel()
 
 
@@ -79,19 +92,19 @@ def mm_weights(z: np.ndarray, eps: float) -> np.ndarray:
     return 1.0 / np.sqrt(z * z + eps * eps)
 
 
-def objective(g, theta, delta, u, b, lam, eps):
+def objective(g, theta, delta, u, b, lam, eps, temporal=False):
     """J_{eps,lambda}(u, theta) = 1/2 ||H u - b||^2 + lambda sum sqrt((Psi u)^2 + eps^2)."""
     r = forward(g, theta, u, delta) - b
-    z = psi(g, u)
+    z = psi(g, u, temporal)
     return 0.5 * r @ r + lam * np.sum(np.sqrt(z * z + eps * eps))
 
 
-def majorant(g, theta, delta, u, uk, b, lam, eps):
+def majorant(g, theta, delta, u, uk, b, lam, eps, temporal=False):
     """Q(u | u_k): the quadratic majorant of J_{eps,lambda} at u_k (Eq. (3.2)), constant included."""
     r = forward(g, theta, u, delta) - b
-    zk = psi(g, uk)
+    zk = psi(g, uk, temporal)
     sk = np.sqrt(zk * zk + eps * eps)
-    z = psi(g, u)
+    z = psi(g, u, temporal)
     # sqrt(t^2 + eps^2) <= sk + (t^2 - zk^2) / (2 sk) by concavity of sqrt
     return 0.5 * r @ r + lam * np.sum(sk + (z * z - zk * zk) / (2 * sk))
 
@@ -128,6 +141,7 @@ class Options:
     update_theta: bool = True
     stop_on_convergence: bool = True
     fixed_weights: np.ndarray | None = None   # freeze P^2 (pins only)
+    temporal: bool = False                    # ANISO-TV: add frame-to-frame differences to Psi
 
 
 @dataclass
@@ -207,16 +221,16 @@ class NLRMMGKS:
         RH = RP = None
         steps = 0
         for _ in range(s):
-            w = o.fixed_weights if o.fixed_weights is not None else mm_weights(psi(g, u_old), o.eps)
+            w = o.fixed_weights if o.fixed_weights is not None else mm_weights(psi(g, u_old, o.temporal), o.eps)
             p = np.sqrt(w)
             QH, RH = np.linalg.qr(HV)
-            PsiV = np.stack([psi(g, V[:, j]) for j in range(V.shape[1])], 1)
+            PsiV = np.stack([psi(g, V[:, j], o.temporal) for j in range(V.shape[1])], 1)
             _, RP = np.linalg.qr(p[:, None] * PsiV)
             QHb = QH.T @ b
             lam = self.choose_lambda(RH, RP, QHb)
             y = np.linalg.solve(RH.T @ RH + lam * (RP.T @ RP), RH.T @ QHb)
             u = V @ y
-            r = self.HT(theta, self.H(theta, u) - b) + lam * psi_t(g, w * psi(g, u))
+            r = self.HT(theta, self.H(theta, u) - b) + lam * psi_t(g, w * psi(g, u, o.temporal), o.temporal)
             r = cgs2(V, r)
             nr = np.linalg.norm(r)
             steps += 1
@@ -281,8 +295,9 @@ class NLRMMGKS:
     # -- residual of the normal equations appended to V -----------------------
     def residual_direction(self, theta, u, lam, V):
         g = self.g
-        w = self.o.fixed_weights if self.o.fixed_weights is not None else mm_weights(psi(g, u), self.o.eps)
-        r = self.HT(theta, self.H(theta, u) - self.b) + lam * psi_t(g, w * psi(g, u))
+        tm = self.o.temporal
+        w = self.o.fixed_weights if self.o.fixed_weights is not None else mm_weights(psi(g, u, tm), self.o.eps)
+        r = self.HT(theta, self.H(theta, u) - self.b) + lam * psi_t(g, w * psi(g, u, tm), tm)
         r = cgs2(V, r)
         nr = np.linalg.norm(r)
         return r / nr if nr > 0 else None
