@@ -236,6 +236,8 @@ typedef struct {
     double c1, beta, alpha0;/* Armijo constants (default 1e-4, 0.5, 1) */
     double mu_rel;          /* damping mu = mu_rel * max_v |J_v|^2 (default 1e-8) */
     double tol_u, tol_p;    /* outer stopping tolerances (default 1e-3, 1e-4) */
+    int32_t temporal;       /* 1: ANISO-TV, Psi also takes the difference of consecutive frames
+                               (operator D_1 of Alg. "Dynamic NL-RMM-GKS"); default 0 */
 } nlrmm_opts;
 
 typedef struct {
@@ -261,7 +263,8 @@ void nlrmm_default_opts(nlrmm_opts *opts);
  * problem) and one Compress of the generalized Krylov basis at the current
  * angles, then per-view damped Gauss-Newton with Armijo backtracking on the
  * angles (Alg. "UPDATE-PARAM"), then the normal-equation residual appended
- * to the basis.  Psi = forward differences per frame.  The basis starts
+ * to the basis.  Psi = forward differences per frame (with opts->temporal,
+ * also between consecutive frames: ANISO-TV).  The basis starts
  * from k_min Golub-Kahan steps on b and u starts at zero.
  *   b [n_views][B] (device, handle precision); theta_inout [n_views] device
  *   double, initial angles in, estimated angles out; delta [n_views] or NULL

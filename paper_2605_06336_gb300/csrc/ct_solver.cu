@@ -129,7 +129,7 @@ template <typename T> struct Solver {
     {
         n = (long long)h.F * h.N * h.N;
         m = (long long)h.V * h.B;
-        ne = 2LL * h.F * h.N * (h.N - 1);
+        ne = psi_edges(h.N, h.F, o.temporal);
         KC = o.k_max + 2;
         const int tiles = ((h.N + 31) / 32) * ((h.N + (sizeof(T) == 4 ? 8 : 4) - 1) / (sizeof(T) == 4 ? 8 : 4)) * h.F;
         gram_blocks = std::min(tiles, 2 * h.num_sms);
@@ -178,14 +178,15 @@ template <typename T> struct Solver {
         SV_CUDA(cudaFuncSetAttribute(k_compress_basis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)small_smem));
         SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, sizeof(T) == 4 ? 8 : 4>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem(kKMax)));
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem(kKMax, true)));
         return CT_OK;
     }
 
-    static size_t gram_smem(int k)
+    // k columns of the edges of one tile: 2 per pixel, 3 with the temporal edge (ANISO-TV)
+    static size_t gram_smem(int k, bool temporal)
     {
         constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        return (size_t)k * (2 * TR * 32 + 1) * sizeof(T);
+        return (size_t)k * ((temporal ? 3 : 2) * TR * 32 + 1) * sizeof(T);
     }
 
     T *col(T *base, long long len, int j) const { return base + (long long)j * len; }
@@ -316,10 +317,11 @@ template <typename T> struct Solver {
         const int *stop = ctl + kStop;
         const int gblk = gram_blocks;
         // P^2 from the previous iterate
-        k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(uold, w, h.N, h.F, o.eps, stop);
+        k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(uold, w, h.N, h.F, o.temporal, o.eps, stop);
         // G_P = (P Psi V)^T (P Psi V)
         constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        k_gram_psi<T, TR><<<gblk, kThreads, gram_smem(kc), h.stream>>>(V, n, kc, w, h.N, h.F, part_gram, stop);
+        k_gram_psi<T, TR><<<gblk, kThreads, gram_smem(kc, o.temporal && h.F > 1), h.stream>>>(V, n, kc, w, h.N, h.F, o.temporal, part_gram,
+                                                                      stop);
         k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gblk, kc, GP, stop);
         // lambda and the reduced solution
         const double target = (o.tau * noise) * (o.tau * noise);
@@ -332,7 +334,7 @@ template <typename T> struct Solver {
         // r = H^T res + lambda Psi^T P^2 Psi u, written straight into the next basis column
         T *r = col(V, n, kc);
         SV_TRY(backproject(theta, res, r, stop));
-        k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(r, u, w, scal, h.N, h.F, stop);
+        k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(r, u, w, scal, h.N, h.F, o.temporal, stop);
         SV_TRY(cgs2(r, kc, stop));
         SV_TRY(norms3(r, nullptr, n, norms2, stop));        // |r|^2
         SV_TRY(norms3(u, uold, n, norms, stop));            // |u|^2, |u - u_old|^2, |u_old|^2
@@ -427,12 +429,12 @@ template <typename T> struct Solver {
         SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_TRY(full_gram(k));
         if (u_w) {
-            k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u_w, w, h.N, h.F, o.eps, nullptr);
+            k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u_w, w, h.N, h.F, o.temporal, o.eps, nullptr);
         } else {
             k_fill<T><<<grid_for(ne), kThreads, 0, h.stream>>>(w, ne, T(1));
         }
         constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k), h.stream>>>(V, n, k, w, h.N, h.F, part_gram,
+        k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k, o.temporal && h.F > 1), h.stream>>>(V, n, k, w, h.N, h.F, o.temporal, part_gram,
                                                                             nullptr);
         k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gram_blocks, k, GP, nullptr);
         k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
@@ -672,12 +674,13 @@ template <typename T> struct Solver {
                 SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
             }
             // residual of the normal equations at H_k, new weights, appended to V
-            k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.eps, nullptr);
+            k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.temporal, o.eps, nullptr);
             SV_CUDA(launch_prep_forward<T>(h, u, h.F, nullptr, th_k, delta));
             SV_CUDA(launch_forward<T>(h, res, 1, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
             axpby(res, b, m, 1.0, -1.0);
             SV_TRY(backproject(th_k, res, col(V, n, kc), nullptr));
-            k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(col(V, n, kc), u, w, scal, h.N, h.F, nullptr);
+            k_add_reg<T><<<grid_for(n), kThreads, 0, h.stream>>>(col(V, n, kc), u, w, scal, h.N, h.F, o.temporal,
+                                                                nullptr);
             SV_TRY(cgs2(col(V, n, kc), kc, nullptr));
             SV_TRY(norms3(col(V, n, kc), nullptr, n, norms2, nullptr));
             // convergence data

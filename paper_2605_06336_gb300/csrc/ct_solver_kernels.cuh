@@ -51,14 +51,21 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 // ---------------------------------------------------------------------------
 // MM weights P^2 = (z^2 + eps^2)^(-1/2), z = Psi u (forward differences)
-// edge layout: [F][N][N-1] horizontal, then [F][N-1][N] vertical
+// edge layout: [F][N][N-1] horizontal, then [F][N-1][N] vertical, then (with
+// temporal: the ANISO-TV operator D_1) [F-1][N][N] frame f+1 minus frame f
 // ---------------------------------------------------------------------------
+inline long long psi_edges(int N, int F, int temporal)
+{
+    return 2LL * F * N * (N - 1) + (temporal && F > 1 ? (long long)(F - 1) * N * N : 0);
+}
+
 template <typename T>
-__global__ void k_weights(const T *__restrict__ u, T *__restrict__ w, int N, int F, double eps, const int *stop)
+__global__ void k_weights(const T *__restrict__ u, T *__restrict__ w, int N, int F, int temporal, double eps,
+                          const int *stop)
 {
     if (stopped(stop)) return;
     const long long nx = (long long)F * N * (N - 1);
-    const long long ne = 2 * nx;
+    const long long ne = 2 * nx + (temporal && F > 1 ? (long long)(F - 1) * N * N : 0);
     const T e2 = (T)(eps * eps);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
         T z;
@@ -68,27 +75,31 @@ __global__ void k_weights(const T *__restrict__ u, T *__restrict__ w, int N, int
             const int i = (int)(rem / (N - 1)), j = (int)(rem % (N - 1));
             const T *uf = u + f * N * N;
             z = uf[(size_t)i * N + j + 1] - uf[(size_t)i * N + j];
-        } else {
+        } else if (e < 2 * nx) {
             const long long e2i = e - nx;
             const long long f = e2i / ((long long)(N - 1) * N);
             const long long rem = e2i - f * (N - 1) * N;
             const int i = (int)(rem / N), j = (int)(rem % N);
             const T *uf = u + f * N * N;
             z = uf[(size_t)(i + 1) * N + j] - uf[(size_t)i * N + j];
+        } else {
+            const long long et = e - 2 * nx;  // = f * N * N + pixel
+            z = u[et + (long long)N * N] - u[et];
         }
         w[e] = rsqrt_t<T>(z * z + e2);
     }
 }
 
-// r += lambda * Psi^T (w .* Psi u)   (one thread per pixel)
+// r += lambda Psi^T P^2 Psi u  (lambda = scal[kLam])
 template <typename T>
 __global__ void k_add_reg(T *__restrict__ r, const T *__restrict__ u, const T *__restrict__ w,
-                          const double *__restrict__ scal, int N, int F, const int *stop)
+                          const double *__restrict__ scal, int N, int F, int temporal, const int *stop)
 {
     if (stopped(stop)) return;
     const long long n = (long long)F * N * N;
     const long long nx = (long long)F * N * (N - 1);
     const T lam = (T)scal[kLam];
+    const bool tm = temporal && F > 1;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const long long f = p / ((long long)N * N);
         const int rem = (int)(p - f * N * N);
@@ -102,6 +113,12 @@ __global__ void k_add_reg(T *__restrict__ r, const T *__restrict__ u, const T *_
         if (j > 0) acc += wx[i * (N - 1) + j - 1] * (c - uf[rem - 1]);      // edge (i,j-1)-(i,j)
         if (i < N - 1) acc -= wy[i * N + j] * (uf[rem + N] - c);            // edge (i,j)-(i+1,j)
         if (i > 0) acc += wy[(i - 1) * N + j] * (c - uf[rem - N]);          // edge (i-1,j)-(i,j)
+        if (tm) {
+            const T *wt = w + 2 * nx;                                       // [F-1][N*N]
+            const long long nn = (long long)N * N;
+            if (f < F - 1) acc -= wt[f * nn + rem] * (u[p + nn] - c);      // frame f -> f+1
+            if (f > 0) acc += wt[(f - 1) * nn + rem] * (c - u[p - nn]);    // frame f-1 -> f
+        }
         r[p] += lam * acc;
     }
 }
@@ -132,14 +149,15 @@ constexpr int kGramSlots = (kGramPairs + 255) / 256;
 
 template <typename T, int TR>
 __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long long n, int k,
-                                                  const T *__restrict__ w, int N, int F, double *__restrict__ part,
-                                                  const int *stop)
+                                                  const T *__restrict__ w, int N, int F, int temporal,
+                                                  double *__restrict__ part, const int *stop)
 {
     if (stopped(stop)) return;
     extern __shared__ unsigned char smem_raw[];
-    constexpr int TP = TR * 32;          // pixels per tile
-    constexpr int EP = 2 * TP + 1;       // padded edge pitch (conflict-free column reads)
-    T *E = reinterpret_cast<T *>(smem_raw);  // [k][EP]
+    constexpr int TP = TR * 32;                  // pixels per tile
+    const int EPP = (temporal && F > 1) ? 3 : 2;  // edges per pixel: right, down (, next frame)
+    const int EP = EPP * TP + 1;                 // padded edge pitch (conflict-free column reads)
+    T *E = reinterpret_cast<T *>(smem_raw);      // [k][EP]
     const int tiles_x = (N + 31) / 32, tiles_y = (N + TR - 1) / TR;
     const int ntiles = tiles_x * tiles_y * F;
     const long long nx = (long long)F * N * (N - 1);
@@ -153,19 +171,23 @@ __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long 
         const int i0 = (tile / tiles_x) * TR, j0 = (tile % tiles_x) * 32;
         const T *wx = w + (long long)f * N * (N - 1);
         const T *wy = w + nx + (long long)f * (N - 1) * N;
+        const T *wt = w + 2 * nx + (long long)f * N * N;  // temporal edges of frames (f, f + 1)
         __syncthreads();
         for (int idx = threadIdx.x; idx < k * TP; idx += blockDim.x) {
             const int a = idx / TP, pix = idx % TP;
             const int i = i0 + pix / 32, j = j0 + pix % 32;
-            T ex = T(0), ey = T(0);
+            T ex = T(0), ey = T(0), et = T(0);
             if (i < N && j < N) {
                 const T *va = V + (long long)a * n + (long long)f * N * N;
                 const T c = va[(size_t)i * N + j];
                 if (j < N - 1) ex = (va[(size_t)i * N + j + 1] - c) * sqrt(wx[i * (N - 1) + j]);
                 if (i < N - 1) ey = (va[(size_t)(i + 1) * N + j] - c) * sqrt(wy[i * N + j]);
+                if (EPP == 3 && f < F - 1)
+                    et = (va[(size_t)N * N + (size_t)i * N + j] - c) * sqrt(wt[(size_t)i * N + j]);
             }
-            E[a * EP + 2 * pix] = ex;
-            E[a * EP + 2 * pix + 1] = ey;
+            E[a * EP + EPP * pix] = ex;
+            E[a * EP + EPP * pix + 1] = ey;
+            if (EPP == 3) E[a * EP + EPP * pix + 2] = et;
         }
         __syncthreads();
 #pragma unroll
@@ -182,7 +204,7 @@ __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long 
             const T *ea = E + a * EP, *eb = E + b * EP;
             T s = T(0);
 #pragma unroll 8
-            for (int e = 0; e < 2 * TP; ++e) s = fma(ea[e], eb[e], s);
+            for (int e = 0; e < EPP * TP; ++e) s = fma(ea[e], eb[e], s);
             acc[q] += (double)s;
         }
     }

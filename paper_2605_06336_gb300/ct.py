@@ -63,7 +63,7 @@ class nlrmm_opts(ctypes.Structure):
         ("noise_norm", ctypes.c_double), ("lam_fix", ctypes.c_double), ("lam_lo", ctypes.c_double),
         ("lam_hi", ctypes.c_double), ("c1", ctypes.c_double), ("beta", ctypes.c_double),
         ("alpha0", ctypes.c_double), ("mu_rel", ctypes.c_double), ("tol_u", ctypes.c_double),
-        ("tol_p", ctypes.c_double),
+        ("tol_p", ctypes.c_double), ("temporal", ctypes.c_int32),
     ]
 
 

@@ -102,3 +102,43 @@ def test_solver_argument_errors(ct):
         op.solve(b, th, noise_norm=1.0, k_max=80)       # basis above the FP64 small-algebra limit
     with pytest.raises(ct.CTError):
         op.solve(b, th)                                 # no noise level and no fixed lambda
+
+
+def _moving_sequence(N=24, vpf=(6, 7, 6, 7), seed=41, sigma_deg=0.5):
+    rng = np.random.default_rng(seed)
+    F, V = len(vpf), sum(vpf)
+    ells = synth.random_ellipses(N, 3, rng)
+    u_true = np.stack([synth.rasterize(N, ells, shift=(0.5 * f, 0.0)) for f in range(F)]).ravel()
+    g = oracle.Geometry(N, synth.n_bins(N), V, views_per_frame=list(vpf))
+    th_nom = np.sort(synth.random_angles(V, rng))
+    th_true = th_nom + rng.normal(0, math.radians(sigma_deg), V)
+    b_true = oracle.forward(g, th_true, u_true)
+    e = rng.standard_normal(g.m)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    return g, list(vpf), th_nom, th_true, u_true, b_true + e, float(np.linalg.norm(e))
+
+
+def test_fp64_aniso_tv_solver_follows_the_oracle_iterates(ct):
+    """Dynamic NL-RMM-GKS with ANISO-TV (temporal differences in Psi) on 4 frames."""
+    g, vpf, th_nom, th_true, u_true, b, nn = _moving_sequence()
+    o = nlrmm.Options(noise_norm=nn, k_min=5, k_max=15, outer_iters=3, tol1=0.0, stop_on_convergence=False,
+                      temporal=True)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float64)
+    x, th, st = op.solve(dev(b), dev(th_nom), x_true=dev(u_true), noise_norm=nn, k_min=5, k_max=15, outer_iters=3,
+                         tol1=0.0, stop_on_convergence=0, temporal=1)
+    assert st["enlarge_steps"] == h_o.enlarge_steps
+    np.testing.assert_allclose(st["lambda"], h_o.lam, rtol=1e-7)
+    np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-7)
+    assert np.linalg.norm(x.cpu().numpy() - u_o) <= 1e-7 * np.linalg.norm(u_o)
+    assert np.max(np.abs(th.cpu().numpy() - th_o)) <= 1e-8
+
+
+def test_fp32_aniso_tv_solver_reaches_the_oracle_reconstruction_error(ct):
+    g, vpf, th_nom, th_true, u_true, b, nn = _moving_sequence(N=48, vpf=(12, 13, 12, 13, 12, 13), seed=42)
+    o = nlrmm.Options(noise_norm=nn, outer_iters=6, stop_on_convergence=False, temporal=True)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float32)
+    x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
+                         outer_iters=6, stop_on_convergence=0, temporal=1)
+    assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
