@@ -222,15 +222,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def solver_comparison(w, dev, outer_iters):
+def solver_comparison(w, dev, outer_iters, **extra):
     """NL-RMM-GKS on the workload: FP32 operators + FP64 small algebra + batched
-    basis projection against the plain FP64 GPU form, same data, same options."""
+    basis projection against the plain FP64 GPU form, same data, same options
+    (`extra`: further solver options, e.g. temporal=1 for ANISO-TV)."""
     import torch
     from paper_2605_06336_gb300 import ct
     N, B, V = w.N, w.B, w.V
     u_true = torch.tensor(w.images.reshape(-1), dtype=torch.float64, device=dev)
     th_true = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
-    op64 = ct.CTOperator(N, B, V, max_batch=8, dtype=torch.float64)
+    op64 = ct.CTOperator(N, B, V, w.views_per_frame, max_batch=8, dtype=torch.float64)
     b_true = op64.forward(u_true, th_true)
     e = torch.tensor(w.noise_dir, dtype=torch.float64, device=dev)
     e *= w.noise_level * b_true.norm() / e.norm()
@@ -239,15 +240,16 @@ def solver_comparison(w, dev, outer_iters):
     th0 = torch.tensor(w.theta_nominal, dtype=torch.float64, device=dev)
     out = {}
     for name, dt in (("fp64_plain", torch.float64), ("fp32_batched", torch.float32)):
-        op = op64 if dt == torch.float64 else ct.CTOperator(N, B, V, max_batch=8, dtype=dt)
+        op = op64 if dt == torch.float64 else ct.CTOperator(N, B, V, w.views_per_frame, max_batch=8, dtype=dt)
         op.autotune()
         bb = b64.to(dt)
         xt = u_true.to(dt)
-        op.solve(bb, th0, x_true=xt, noise_norm=nn, outer_iters=2, stop_on_convergence=0)  # warm-up
+        op.solve(bb, th0, x_true=xt, noise_norm=nn, outer_iters=2, stop_on_convergence=0, **extra)  # warm-up
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        x, th, st = op.solve(bb, th0, x_true=xt, noise_norm=nn, outer_iters=outer_iters, stop_on_convergence=0)
+        x, th, st = op.solve(bb, th0, x_true=xt, noise_norm=nn, outer_iters=outer_iters, stop_on_convergence=0,
+                             **extra)
         e1.record()
         torch.cuda.synchronize()
         total_ms = e0.elapsed_time(e1)
@@ -261,6 +263,13 @@ def solver_comparison(w, dev, outer_iters):
     out["speedup_fp32_vs_fp64"] = a["total_ms"] / b_["total_ms"]
     out["outer_iters"] = outer_iters
     out["initial_max_abs_angle_err_deg"] = float(np.abs(w.theta_nominal - w.theta_true).max()) * 180 / math.pi
+    if extra.get("temporal"):
+        # the same FP32 solve with spatial differences only, for the effect of the temporal coupling
+        op = ct.CTOperator(N, B, V, w.views_per_frame, max_batch=8, dtype=torch.float32)
+        op.autotune()
+        _, _, st = op.solve(b64.float(), th0, x_true=u_true.float(), noise_norm=nn, outer_iters=outer_iters,
+                            stop_on_convergence=0)
+        out["fp32_spatial_only_final_rre"] = st["rre"][-1]
     return out
 
 
@@ -610,10 +619,16 @@ def main():
     solver = None
     frames = None
     streaming = None
+    dynamic = None
     if not args.no_solver and world == 1:
         solver = solver_comparison(w, dev, args.solver_iters)
         frames = batched_frames(dev, min(args.steps, 200), flush)
         streaming = streaming_c5(dev, args.stream_passes) if args.stream_passes > 0 else None
+        wd = synth.make_workload("C4")
+        dynamic = solver_comparison(wd, dev, wd.outer_iters, temporal=1)
+        dynamic["workload"] = (f"C4: {wd.F} frames of {wd.N}x{wd.N} (phantom translating 1 px per frame), {wd.V} "
+                               f"golden-angle views ({min(wd.views_per_frame)}-{max(wd.views_per_frame)} per "
+                               f"frame), {wd.B} bins; ANISO-TV")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, args.cpu_seconds)
@@ -651,6 +666,7 @@ def main():
         "solver": solver,
         "batched_frames": frames,
         "streaming": streaming,
+        "dynamic_solver": dynamic,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step(tuning) * args.steps,
         "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
