@@ -38,12 +38,13 @@ WORKLOAD = "C2"
 KBLOCK = 8
 # DRAM bytes per launch of the dominant kernels, from ncu captures of
 # `python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-solver --tuning <shape>`
-# (4,4,1,8,2,2,1,0,0,0 and 4,4,1,8,4,2,2,0,0,16), keyed by the launch shape
+# (4,4,1,8,2,2,1,0,0,0, 4,4,1,8,4,2,2,0,0,16 and 4,4,1,8,4,4,1,0,0,8), keyed by the launch shape
 # that selects the kernel; a shape that was not profiled reports null.
 PROFILED_DRAM_BYTES = {
     ("forward_K8", (4, 4, 1, 0)): 8.56e6,   # k_ray<float, 0, 0, 4, 4>: fwd kb, split, views/CTA, staging
     ("adjoint_K8", (8, 2, 0)): 3.95e6,      # k_adjoint<float, 8, 2>: adj kb, view groups, staging
     ("adjoint_K8", (8, 4, 16)): 4.04e6,     # k_adj_band<8, 16>, 4 CTAs per tile
+    ("adjoint_K8", (8, 4, 8)): 4.04e6,      # k_adj_band<8, 8>, 4 CTAs per tile
 }
 
 
