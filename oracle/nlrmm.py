@@ -12,6 +12,10 @@ Passages followed:
   * Alg. "Enlarge" and Alg. "Compress" (supplementary Sec. S1.2) and
     Alg. "RMM-GKS" (Sec. 3.3);
   * Alg. "UPDATE-PARAM" (damped Gauss-Newton + Armijo backtracking, Sec. 4.1.2);
+  * Alg. "UPDATE-PARAM-VarPro" (Sec. 4.2): the reduced objective on the
+    compressed basis, its Gauss-Newton system (J_r^T J_r + lambda J_s^T J_s)
+    with Jacobian columns from the sensitivity equation, Armijo on the reduced
+    objective (``varpro_jacobians``, ``NLRMMGKS.update_param_varpro``);
   * Alg. "NL-RMM-GKS" (Sec. 4.3) without the optional high-lambda solve;
   * Alg. "s-NL-RMM-GKS" (Sec. 5) over blocks of views (``stream_solve``);
   * the dynamic form with ANISO-TV (operator D_1, Alg. "Dynamic NL-RMM-GKS"): Psi gains the
@@ -38,6 +42,13 @@ Readings where the paper is silent (also listed in the design notes):
     backtracking (c1 = 1e-4, beta = 1/2, alpha_bar = 1, at most 20 halvings,
     no step if none is accepted) is applied to each view's own data term;
     3 Gauss-Newton iterations per outer iteration;
+  * VarPro (Options.varpro): the basis is the compressed V^(k+1)_kmin of the
+    primary solve, lambda_hat = lambda^(k), B_hat = P Psi V with P^2 the MM
+    weights of u^(k+1); the Gauss-Newton matrix is damped by mu = 1e-8 times
+    its largest diagonal entry; the Armijo test is on the whole reduced
+    objective (the views are coupled through y); when no step is accepted
+    the angles stay and the remaining Gauss-Newton iterations are skipped;
+    u^(k+1) stays the image of the outer iteration;
   * the residual appended at the end of an outer iteration uses the operator
     of that iteration's angles (H_k of Alg. "NL-RMM-GKS");
   * u^(0) = 0; the relative-change tests are skipped while ||u_old|| = 0;
@@ -50,7 +61,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Geometry, adjoint, dsample, forward
+from . import Geometry, adjoint, dsample, forward, jac, jacT
 
 
 # ---------------------------------------------------------------------------
@@ -142,6 +153,7 @@ class Options:
     stop_on_convergence: bool = True
     fixed_weights: np.ndarray | None = None   # freeze P^2 (pins only)
     temporal: bool = False                    # ANISO-TV: add frame-to-frame differences to Psi
+    varpro: bool = False                      # parameter update by Alg. "UPDATE-PARAM-VarPro"
 
 
 @dataclass
@@ -292,6 +304,42 @@ class NLRMMGKS:
             theta = theta + alpha * d
         return theta
 
+    # -- Alg. "UPDATE-PARAM-VarPro" (Sec. 4.2) ----------------------------------
+    def update_param_varpro(self, theta, V, lam, w):
+        """maxiter_p Gauss-Newton steps on the reduced objective f(theta) on the
+        basis V with frozen weights w (P^2) and lambda_hat = lam."""
+        o, g = self.o, self.g
+        theta = np.array(theta, float)
+        for _ in range(o.maxiter_p):
+            Jr, Js, r, s, f0, u = varpro_jacobians(g, self.b, theta, V, lam, w, self.delta, o.temporal)
+            # gradient of J_{eps,lambda}(u_hat, theta) in theta: only the data term depends on theta
+            grad, _ = jacT(g, theta, u, r, self.delta)
+            A = Jr.T @ Jr + lam * (Js.T @ Js)
+            mu = o.mu_rel * max(float(np.max(np.diag(A))), 1e-300)
+            d = -np.linalg.solve(A + mu * np.eye(g.V), grad)
+            gd = float(grad @ d)
+            alpha = o.alpha0
+            accepted = False
+            for _h in range(o.max_halvings + 1):
+                ft = varpro_objective(g, self.b, theta + alpha * d, V, lam, w, self.delta, o.temporal)[0]
+                if ft <= f0 + o.c1 * alpha * gd:
+                    accepted = True
+                    break
+                alpha *= o.beta
+            if not accepted:
+                break  # no acceptable step: the angles stay
+            theta = theta + alpha * d
+        return theta
+
+    def param_update(self, theta, u, V, lam):
+        """UPDATE-PARAM of the outer iteration: per-view AltMin, or VarPro on
+        the compressed basis V with the MM weights of u."""
+        if not self.o.varpro:
+            return self.update_param(theta, u)
+        o = self.o
+        w = o.fixed_weights if o.fixed_weights is not None else mm_weights(psi(self.g, u, o.temporal), o.eps)
+        return self.update_param_varpro(theta, V, lam, w)
+
     # -- residual of the normal equations appended to V -----------------------
     def residual_direction(self, theta, u, lam, V):
         g = self.g
@@ -315,7 +363,7 @@ class NLRMMGKS:
             HV = np.stack([self.H(theta, V[:, j]) for j in range(V.shape[1])], 1)
             u_new, lam, Vg, _, RH, RP, used, steps = self.enlarge(theta, V, HV, u, s)
             Vk = self.compress(Vg, RH, RP, used, lam, u_new)
-            theta_new = self.update_param(theta, u_new) if o.update_theta else theta.copy()
+            theta_new = self.param_update(theta, u_new, Vk, lam) if o.update_theta else theta.copy()
             vn = self.residual_direction(theta, u_new, lam, Vk)
             V = Vk if vn is None else np.concatenate([Vk, vn[:, None]], 1)
             nu = np.linalg.norm(u)
@@ -340,12 +388,12 @@ class NLRMMGKS:
 # ---------------------------------------------------------------------------
 # VarPro reduced objective on a fixed basis (Sec. 4.2, Alg. "UPDATE-PARAM-VarPro")
 # ---------------------------------------------------------------------------
-def varpro_objective(g: Geometry, b, theta, V, lam, w=None, delta=None):
+def varpro_objective(g: Geometry, b, theta, V, lam, w=None, delta=None, temporal=False):
     """f(theta) = min_y 1/2 |H(theta) V y - b|^2 + lam/2 |P Psi V y|^2 with P^2 = diag(w)
     (w = None: P = I), solved through the QR factors of H V and P Psi V as in the
     reduced problem (3.5).  Returns (f, y, u = V y)."""
     HV = np.stack([forward(g, theta, V[:, j], delta) for j in range(V.shape[1])], 1)
-    PsiV = np.stack([psi(g, V[:, j]) for j in range(V.shape[1])], 1)
+    PsiV = np.stack([psi(g, V[:, j], temporal) for j in range(V.shape[1])], 1)
     if w is not None:
         PsiV = np.sqrt(w)[:, None] * PsiV
     QH, RH = np.linalg.qr(HV)
@@ -356,15 +404,46 @@ def varpro_objective(g: Geometry, b, theta, V, lam, w=None, delta=None):
     return 0.5 * r @ r + 0.5 * lam * s @ s, y, V @ y
 
 
-def varpro_gradient(g: Geometry, b, theta, V, lam, w=None, delta=None):
+def varpro_gradient(g: Geometry, b, theta, V, lam, w=None, delta=None, temporal=False):
     """grad_theta f: y is optimal for every theta, so by the Golub-Pereyra
     (envelope) argument the reduced gradient is J_theta(u)^T (H(theta) u - b)
     with u = V y(theta), the data-term gradient (H_{p_i} u)^T (H u - b)."""
-    from . import jacT
-    f, y, u = varpro_objective(g, b, theta, V, lam, w, delta)
+    f, y, u = varpro_objective(g, b, theta, V, lam, w, delta, temporal)
     r = forward(g, theta, u, delta) - b
     gt, _ = jacT(g, theta, u, r, delta)
     return gt, f, u
+
+
+def varpro_jacobians(g: Geometry, b, theta, V, lam, w=None, delta=None, temporal=False):
+    """Jacobians of the reduced residuals r(theta) = H(theta) V y(theta) - b and
+    s(theta) = P Psi V y(theta) of f = 1/2 |r|^2 + lam/2 |s|^2 (Sec. 4.2).
+
+    Column j (angle of view j) follows the sensitivity equation restricted to
+    span(V) (u_{p_j} = V y_j):
+        M y_j = -((H_j V)^T r + (H V)^T H_j u),  M = (HV)^T HV + lam (P Psi V)^T (P Psi V),
+        J_r[:, j] = H_j u + (H V) y_j,           J_s[:, j] = (P Psi V) y_j,
+    with H_j = dH/dtheta_j applied through the oracle's Jacobian (direction e_j).
+    One column at a time, dense.  Returns (J_r, J_s, r, s, f, u)."""
+    k = V.shape[1]
+    f, y, u = varpro_objective(g, b, theta, V, lam, w, delta, temporal)
+    HV = np.stack([forward(g, theta, V[:, c], delta) for c in range(k)], 1)
+    PsiV = np.stack([psi(g, V[:, c], temporal) for c in range(k)], 1)
+    if w is not None:
+        PsiV = np.sqrt(w)[:, None] * PsiV
+    r = HV @ y - b
+    s = PsiV @ y
+    M = HV.T @ HV + lam * (PsiV.T @ PsiV)
+    Jr = np.empty((r.size, g.V))
+    Js = np.empty((s.size, g.V))
+    for j in range(g.V):
+        e = np.zeros(g.V)
+        e[j] = 1.0
+        Hju = jac(g, theta, u, e, delta)
+        HjV = np.stack([jac(g, theta, V[:, c], e, delta) for c in range(k)], 1)
+        yj = -np.linalg.solve(M, HjV.T @ r + HV.T @ Hju)
+        Jr[:, j] = Hju + HV @ yj
+        Js[:, j] = PsiV @ yj
+    return Jr, Js, r, s, f, u
 
 
 # ---------------------------------------------------------------------------
@@ -407,7 +486,7 @@ def stream_solve(blocks, theta0, passes, u_true=None, theta_true=None, tol_u=Non
             HV = np.stack([blk.H(th, V[:, c]) for c in range(V.shape[1])], 1)
             u, lam, Vg, _, RH, RP, used, steps = blk.enlarge(th, V, HV, u, blk.o.k_max - blk.o.k_min)
             V = blk.compress(Vg, RH, RP, used, lam, u)
-            thetas[j] = blk.update_param(th, u) if blk.o.update_theta else th.copy()
+            thetas[j] = blk.param_update(th, u, V, lam) if blk.o.update_theta else th.copy()
             steps_pass += steps
             if callback:
                 callback(len(hist.du), j, u, V, thetas)
