@@ -238,6 +238,9 @@ typedef struct {
     double tol_u, tol_p;    /* outer stopping tolerances (default 1e-3, 1e-4) */
     int32_t temporal;       /* 1: ANISO-TV, Psi also takes the difference of consecutive frames
                                (operator D_1 of Alg. "Dynamic NL-RMM-GKS"); default 0 */
+    int32_t varpro;         /* 1: parameter update by Alg. "UPDATE-PARAM-VarPro" (Sec. 4.2) on the
+                               compressed basis (see nlrmm_varpro_update) instead of the per-view
+                               AltMin update; default 0 */
 } nlrmm_opts;
 
 typedef struct {
@@ -262,7 +265,9 @@ void nlrmm_default_opts(nlrmm_opts *opts);
  * MM-GKS steps, lambda by the discrepancy principle on the projected
  * problem) and one Compress of the generalized Krylov basis at the current
  * angles, then per-view damped Gauss-Newton with Armijo backtracking on the
- * angles (Alg. "UPDATE-PARAM"), then the normal-equation residual appended
+ * angles (Alg. "UPDATE-PARAM"; with opts->varpro, the VarPro update of
+ * nlrmm_varpro_update on the compressed basis with the MM weights of the new
+ * image and the last lambda), then the normal-equation residual appended
  * to the basis.  Psi = forward differences per frame (with opts->temporal,
  * also between consecutive frames: ANISO-TV).  The basis starts
  * from k_min Golub-Kahan steps on b and u starts at zero.
@@ -283,7 +288,8 @@ int nlrmm_gks_solve(ct_handle *h, const void *b, double *theta_inout, const doub
  * Streaming NL-RMM-GKS over blocks of views (Alg. "s-NL-RMM-GKS", Sec. 5,
  * blocks as in Sec. 2.4): each pass visits the blocks in order; a visit is
  * one Enlarge + Compress on block j's data, started from the carried image
- * and compressed basis, then per-view Gauss-Newton with Armijo on block j's
+ * and compressed basis, then per-view Gauss-Newton with Armijo (with
+ * opts->varpro: the VarPro update of nlrmm_varpro_update) on block j's
  * angles; the compressed basis (k_min columns) goes on to the next block.
  * Passes repeat until the image and all angles change less than tol_u /
  * tol_p over a pass, or outer_iters passes.  The first basis is k_min
@@ -332,6 +338,30 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
  */
 int nlrmm_varpro(ct_handle *h, const void *b, const double *theta, const double *delta, const void *V, int k,
                  double lam, const void *u_w, double eps, double *fval, double *grad, void *u_out);
+
+/*
+ * One VarPro parameter update (Alg. "UPDATE-PARAM-VarPro", Sec. 4.2) on a
+ * fixed basis: opts->maxiter_p damped Gauss-Newton steps on the reduced
+ * objective f(theta) of nlrmm_varpro, each followed by Armijo backtracking on
+ * f (c1, beta, alpha0, at most max_halvings halvings; when no step is
+ * accepted the angles stay and the update ends).  The Gauss-Newton matrix is
+ * J_r^T J_r + lam J_s^T J_s of the reduced residuals r = H(theta) V y(theta) - b
+ * and s = P Psi V y(theta), whose columns follow the sensitivity equation
+ * restricted to span(V); it is a diagonal plus a rank-2k term, damped by
+ * mu = mu_rel * its largest diagonal entry and solved by the Woodbury identity
+ * (FP64).  The gradient is J_theta(V y)^T r.  Per step: one projection of the
+ * k basis columns per evaluation of f, one JVP, k VJPs.
+ *   b [n_views][B]; theta_inout [n_views] device double, updated in place;
+ *   delta [n_views] device or NULL; V [k][n_frames][N][N] device, 1 <= k <= 32;
+ *   lam > 0; u_w [n_frames][N][N] device or NULL (P = I), eps > 0 with u_w;
+ *   opts: maxiter_p, max_halvings, c1, beta, alpha0, mu_rel, temporal are
+ *   read (NULL: defaults); f_hist (host, nullable): maxiter_p + 1 values,
+ *   f before the first step and after each step (repeated once the update ends).
+ * Allocates and frees its workspace; synchronises.  CT_OK, CT_ERR_ARG,
+ * CT_ERR_OOM or CT_ERR_CUDA.
+ */
+int nlrmm_varpro_update(ct_handle *h, const void *b, double *theta_inout, const double *delta, const void *V, int k,
+                        double lam, const void *u_w, double eps, const nlrmm_opts *opts, double *f_hist);
 
 /* ------------------------------------------------------------------------
  * Allocation-free transposed Jacobian (this entry point has no counterpart in

@@ -2,7 +2,8 @@
 //
 // Algorithms followed: "NL-RMM-GKS" (Sec. 4.3, without the optional
 // high-lambda solve), "RMM-GKS" (Sec. 3.3) with "Enlarge" and "Compress"
-// (supplementary Sec. S1.2), "UPDATE-PARAM" (Sec. 4.1.2).  Operators are the
+// (supplementary Sec. S1.2), "UPDATE-PARAM" (Sec. 4.1.2) or, with
+// opts.varpro, "UPDATE-PARAM-VarPro" (Sec. 4.2).  Operators are the
 // ct kernels of this library in the handle's precision; every small matrix
 // (k <= 64) is FP64 on the device.
 //
@@ -19,6 +20,9 @@
 //     flag (no host round trip inside Enlarge).
 //   * With per-view angles J^T J is diagonal, so the Gauss-Newton step and
 //     its Armijo backtracking are per view.
+//   * VarPro: the Gauss-Newton matrix of the reduced residuals is a diagonal
+//     plus a rank-2k term (k basis columns); it is never formed: the damped
+//     system is solved by the Woodbury identity with a 2k x 2k capacitance.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,6 +83,11 @@ template <typename T> struct Solver {
     double *th_k = nullptr, *th_n = nullptr, *th_t = nullptr, *d = nullptr, *alpha = nullptr, *g = nullptr,
            *j2 = nullptr, *f0 = nullptr, *ft = nullptr, *scratch_v = nullptr;
     int *ctl = nullptr, *active = nullptr;
+    // VarPro Gauss-Newton work (allocated on first use)
+    T *vp_a = nullptr, *vp_u = nullptr;
+    double *vp_E = nullptr, *vp_G = nullptr, *vp_Y = nullptr, *vp_idel = nullptr, *vp_ones = nullptr,
+           *vp_scal = nullptr;
+    int *vp_ctl = nullptr;
     int *h_ctl = nullptr;       // pinned mirror of ctl
     double *h_scal = nullptr;   // pinned mirror of small results
     int *h_stop = nullptr;      // host-mapped mirror of the Enlarge stop flag
@@ -413,6 +422,128 @@ template <typename T> struct Solver {
         return CT_OK;
     }
 
+    // ---- VarPro Gauss-Newton update (Alg. "UPDATE-PARAM-VarPro", Sec. 4.2) --------
+    int varpro_setup()
+    {
+        if (vp_a) return CT_OK;
+        const long long m_all = std::max(m, m_cap);
+        const int v_all = std::max(h.V, v_cap);
+        SV_TRY(alloc(vp_a, m_all));
+        SV_TRY(alloc(vp_u, n));
+        for (double **p : {&vp_E, &vp_G, &vp_Y}) SV_TRY(alloc(*p, (size_t)kVpMax * v_all));
+        SV_TRY(alloc(vp_idel, v_all));
+        SV_TRY(alloc(vp_ones, v_all));
+        SV_TRY(alloc(vp_scal, kScalCount));
+        SV_TRY(alloc(vp_ctl, kCtlCount));
+        k_fill<double><<<grid_for(v_all), kThreads, 0, h.stream>>>(vp_ones, v_all, 1.0);
+        SV_CUDA(cudaMemsetAsync(vp_ctl, 0, sizeof(int) * kCtlCount, h.stream));
+        SV_CUDA(cudaMemsetAsync(vp_scal, 0, sizeof(double) * kScalCount, h.stream));
+        SV_CUDA(cudaFuncSetAttribute(k_varpro_direction, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(VpShared)));
+        return CT_OK;
+    }
+
+    // f(theta) on V[:, :k] with G_P already formed: HV, (HV)^T HV, (HV)^T b,
+    // the fixed-lambda reduced solve y, u = V y (vp_u), res = HV y - b; f goes to *fslot
+    int varpro_eval(const double *theta, int k, double lam, double *fslot)
+    {
+        SV_TRY(project(theta, 0, k, nullptr));
+        SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
+        SV_TRY(full_gram(k));
+        k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
+                                                                     1, y, vp_scal, vp_ctl);
+        k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, vp_u, T(0), T(1), nullptr, T(0), nullptr);
+        k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);
+        SV_TRY(norms3(res, nullptr, m, norms, nullptr));
+        k_varpro_value<<<1, 1, 0, h.stream>>>(norms, GP, y, k, lam, fslot);
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
+    // maxiter_p damped Gauss-Newton steps on the reduced objective over the
+    // basis V[:, :k] with the weights in w and lambda_hat = lam, from
+    // theta_in; the angles reached go to theta_out (device, V).  Per step:
+    // f and its reduced solution at theta; a = J_theta(u) 1 (one JVP);
+    // per-view dots E, |a|^2, g; G by one VJP per basis column; the
+    // direction (k_varpro_direction); Armijo backtracking on f, each trial one
+    // more evaluation of f.  No accepted step ends the update.  f_hist
+    // (host, nullable): f before the first step and after each step.
+    int varpro_update(const double *theta_in, int k, double lam, double *theta_out, double *f_hist)
+    {
+        if (k < 1 || k > kVpMax) return CT_ERR_ARG;
+        SV_TRY(varpro_setup());
+        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
+        k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k, o.temporal && h.F > 1), h.stream>>>(
+            V, n, k, w, h.N, h.F, o.temporal, part_gram, nullptr);
+        k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gram_blocks, k, GP, nullptr);
+        SV_CUDA(cudaMemcpyAsync(th_n, theta_in, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        double f_last = 0.0;
+        for (int it = 0; it < o.maxiter_p; ++it) {
+            SV_TRY(varpro_eval(th_n, k, lam, vp_scal + kTmp0));
+            SV_CUDA(launch_pairs_img<T>(h, vp_u, h.F, nullptr, th_n, delta));
+            SV_CUDA(launch_jvp<T>(h, vp_ones, nullptr, vp_a, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
+            k_view_dots<T><<<std::min(h.V, 8 * h.num_sms), 128, 0, h.stream>>>(HV, m, k, vp_a, res, h.V, h.B, vp_E,
+                                                                               j2, g);
+            for (int c = 0; c < k; ++c) {
+                SV_CUDA(launch_pairs_img<T>(h, col(V, n, c), h.F, nullptr, nullptr, delta));
+                SV_CUDA(launch_vjp<T>(h, res, vp_G + (size_t)c * h.V, nullptr, h.tune.der_split, h.tune.der_vw,
+                                      h.tune.der_stage));
+            }
+            k_varpro_direction<<<1, 1024, sizeof(VpShared), h.stream>>>(GH, GP, lam, vp_E, vp_G, j2, g, k, h.V,
+                                                                        o.mu_rel, vp_Y, vp_idel, d, vp_scal + kTmp1,
+                                                                        ctl);
+            SV_CUDA(cudaGetLastError());
+            double fg[2];
+            SV_TRY(read_doubles(vp_scal + kTmp0, 2, fg));
+            const double f0 = fg[0], gd = fg[1];
+            if (it == 0 && f_hist) f_hist[0] = f0;
+            f_last = f0;
+            bool accepted = false;
+            double alpha = o.alpha0;
+            if (gd < 0.0) {
+                for (int hv = 0; hv <= o.max_halvings; ++hv) {
+                    k_theta_step<<<grid_for(h.V), kThreads, 0, h.stream>>>(th_n, d, alpha, h.V, th_t);
+                    SV_TRY(varpro_eval(th_t, k, lam, vp_scal + kRnorm2));
+                    double ft;
+                    SV_TRY(read_doubles(vp_scal + kRnorm2, 1, &ft));
+                    if (ft <= f0 + o.c1 * alpha * gd) {
+                        accepted = true;
+                        f_last = ft;
+                        break;
+                    }
+                    alpha *= o.beta;
+                }
+            }
+            if (!accepted) {
+                if (f_hist)
+                    for (int r = it + 1; r <= o.maxiter_p; ++r) f_hist[r] = f_last;
+                break;
+            }
+            if (f_hist) f_hist[it + 1] = f_last;
+            SV_CUDA(cudaMemcpyAsync(th_n, th_t, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        }
+        if (theta_out != th_n)
+            SV_CUDA(cudaMemcpyAsync(theta_out, th_n, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        SV_CUDA(cudaStreamSynchronize(h.stream));
+        return CT_OK;
+    }
+
+    // UPDATE-PARAM of an outer iteration (or block visit) after Compress left
+    // kc columns in V: per-view AltMin, or VarPro on the compressed basis with
+    // the MM weights of u and the lambda of the last Enlarge step.  th_k -> th_n.
+    int param_update(int kc)
+    {
+        if (!o.update_theta || (o.varpro && kc < 1)) {
+            SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+            return CT_OK;
+        }
+        if (!o.varpro) return update_param(u);
+        k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.temporal, o.eps, nullptr);
+        double lam;
+        SV_TRY(read_doubles(scal + kLam, 1, &lam));
+        return varpro_update(th_k, kc, lam, th_n, nullptr);
+    }
+
     // ---- VarPro reduced objective and gradient on a given basis -----------------
     // f(theta) = min_y 1/2 |H(theta) V y - b|^2 + lambda/2 |P Psi V y|^2, and
     // grad f = J_theta(V y)^T (H(theta) V y - b) (Golub-Pereyra envelope form).
@@ -499,11 +630,7 @@ template <typename T> struct Solver {
         steps_out = h_ctl[kSteps];
         const int k_used = kc + steps_out - 1;
         SV_TRY(compress(k_used, kc));
-        if (o.update_theta) {
-            SV_TRY(update_param(u));
-        } else {
-            SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
-        }
+        SV_TRY(param_update(kc));
         k_norms3<double><<<kRedBlocks, kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
         k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, norms, nullptr);
         double dth3[3], lam_now[1];
@@ -668,11 +795,7 @@ template <typename T> struct Solver {
             // Compress
             SV_TRY(compress(k_used, kc));
             // parameter update
-            if (o.update_theta) {
-                SV_TRY(update_param(u));
-            } else {
-                SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
-            }
+            SV_TRY(param_update(kc));
             // residual of the normal equations at H_k, new weights, appended to V
             k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.temporal, o.eps, nullptr);
             SV_CUDA(launch_prep_forward<T>(h, u, h.F, nullptr, th_k, delta));
@@ -893,6 +1016,63 @@ int nlrmm_varpro(ct_handle *H, const void *b, const double *theta, const double 
         Solver<float> s(h, ps, o, (const float *)b, delta);
         rc = s.varpro(theta, (const float *)V, k, lam, (const float *)u_w, fval, grad, (float *)u_out);
     }
+    cudaStreamSynchronize(ps);
+    cudaEventDestroy(e0);
+    cudaStreamDestroy(ps);
+    return rc;
+}
+
+int nlrmm_varpro_update(ct_handle *H, const void *b, double *theta_inout, const double *delta, const void *V, int k,
+                        double lam, const void *u_w, double eps, const nlrmm_opts *opts, double *f_hist)
+{
+    if (!H || !b || !theta_inout || !V || k < 1 || k > ctgb::solver::kVpMax || !(lam > 0.0) ||
+        (u_w && !(eps > 0.0)))
+        return CT_ERR_ARG;
+    nlrmm_opts o;
+    nlrmm_default_opts(&o);
+    if (opts) {
+        if (opts->maxiter_p < 0 || opts->max_halvings < 0 || !(opts->beta > 0.0 && opts->beta < 1.0) ||
+            !(opts->alpha0 > 0.0) || !(opts->mu_rel >= 0.0))
+            return CT_ERR_ARG;
+        o.maxiter_p = opts->maxiter_p;
+        o.max_halvings = opts->max_halvings;
+        o.c1 = opts->c1;
+        o.beta = opts->beta;
+        o.alpha0 = opts->alpha0;
+        o.mu_rel = opts->mu_rel;
+        o.temporal = opts->temporal;
+    }
+    ctgb::Handle &h = H->h;
+    h.fwd_ready = h.adj_ready = 0;
+    o.k_min = 2;
+    o.k_max = std::max(k, 3);
+    o.eps = u_w ? eps : 1e-3;
+    o.lam_fix = lam;
+    cudaStream_t ps = nullptr;
+    cudaEvent_t e0 = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(e0, h.stream) != cudaSuccess || cudaStreamWaitEvent(ps, e0, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        if (ps) cudaStreamDestroy(ps);
+        return CT_ERR_CUDA;
+    }
+    auto run = [&](auto tag) -> int {
+        using T = decltype(tag);
+        Solver<T> s(h, ps, o, (const T *)b, delta);
+        SV_TRY(s.setup());
+        SV_CUDA(cudaMemcpyAsync(s.V, V, sizeof(T) * s.n * k, cudaMemcpyDeviceToDevice, ps));
+        if (u_w) {
+            k_weights<T><<<s.grid_for(s.ne), kThreads, 0, ps>>>((const T *)u_w, s.w, h.N, h.F, o.temporal, o.eps,
+                                                                   nullptr);
+        } else {
+            k_fill<T><<<s.grid_for(s.ne), kThreads, 0, ps>>>(s.w, s.ne, T(1));
+        }
+        SV_CUDA(cudaGetLastError());
+        return s.varpro_update(theta_inout, k, lam, theta_inout, f_hist);
+    };
+    const int rc = h.precision ? run(double(0)) : run(float(0));
     cudaStreamSynchronize(ps);
     cudaEventDestroy(e0);
     cudaStreamDestroy(ps);

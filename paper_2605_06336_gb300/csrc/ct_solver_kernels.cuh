@@ -777,5 +777,212 @@ __global__ void k_armijo(const double *__restrict__ f0, const double *__restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// VarPro Gauss-Newton system (Sec. 4.2, Alg. "UPDATE-PARAM-VarPro")
+// ---------------------------------------------------------------------------
+// With the image restricted to span(V) (k columns), y(theta) the reduced
+// solution, u = V y, r = H V y - b, s = P Psi V y, the sensitivity equation
+// restricted to span(V) gives, for the angle of view j,
+//   M y_j = -(G[:, j] + E[:, j]),  M = (HV)^T HV + lambda (P Psi V)^T (P Psi V),
+//   G[c][j] = (H_j V_c)^T r,  E[c][j] = (H V_c)^T H_j u,
+// and the Jacobian columns J_r[:, j] = H_j u + (HV) y_j, J_s[:, j] = (P Psi V) y_j
+// (H_j = dH/dtheta_j, nonzero only in view j's samples).  Hence
+//   J_r^T J_r + lambda J_s^T J_s = diag(|H_j u|^2) + E^T Y + Y^T E + Y^T M Y,
+// a diagonal plus a rank-2k term: with U = [E; Y] (2k x V) and
+// S = [[0, I], [I, M]] it is diag + U^T S U.  The damped system
+// (diag + mu + U^T S U) d = -g is solved by the Woodbury identity with the
+// 2k x 2k capacitance S^{-1} + U D^{-1} U^T, S^{-1} = [[-M, I], [I, 0]]
+// (symmetric indefinite: Gaussian elimination with partial pivoting).
+constexpr int kVpMax = 32;  // basis columns of the VarPro Gauss-Newton system
+
+// Per-view dot products over view j's B samples: j2[j] = <a, a>_j,
+// g[j] = <a, r>_j, E[c][j] = <(HV)_c, a>_j, where a = J_theta(u) 1 holds
+// H_j u in view j's samples.  One CTA per view.
+template <typename T>
+__global__ void __launch_bounds__(128) k_view_dots(const T *__restrict__ HV, long long m, int k,
+                                                   const T *__restrict__ a, const T *__restrict__ r, int V, int B,
+                                                   double *__restrict__ E, double *__restrict__ j2,
+                                                   double *__restrict__ g)
+{
+    __shared__ double red[4];
+    for (int j = blockIdx.x; j < V; j += gridDim.x) {
+        const size_t off = (size_t)j * B;
+        for (int c = -2; c < k; ++c) {
+            const T *x = c == -2 ? a : (c == -1 ? r : HV + (size_t)c * m);
+            double s = 0.0;
+            for (int q = threadIdx.x; q < B; q += blockDim.x) s += (double)a[off + q] * (double)x[off + q];
+            s = warp_sum(s);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const double t = (red[0] + red[1]) + (red[2] + red[3]);
+                if (c == -2) j2[j] = t;
+                else if (c == -1) g[j] = t;
+                else E[(size_t)c * V + j] = t;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+struct VpShared {
+    double M[kVpMax * kLd];                    // (HV)^T HV + lambda (P Psi V)^T (P Psi V)
+    double L[kVpMax * kLd];                    // its Cholesky factor
+    double C[2 * kVpMax][2 * kVpMax + 2];      // capacitance | right-hand side
+    double z[2 * kVpMax];
+    double red[40];
+    double mu;
+    int bad, piv;
+};
+
+// The damped Gauss-Newton direction d = -(J^T J + mu I)^{-1} g of the VarPro
+// reduced objective, mu = mu_rel * max_j (J^T J)_jj, and gd = g . d.
+// Y (k x V) and idel (V) are global work arrays written and read by this CTA.
+// A numerically singular capacitance sets the breakdown flag and gives d = 0.
+__global__ void __launch_bounds__(1024) k_varpro_direction(const double *__restrict__ GH,
+                                                           const double *__restrict__ GP, double lam,
+                                                           const double *__restrict__ E, const double *__restrict__ G,
+                                                           const double *__restrict__ j2, const double *__restrict__ g,
+                                                           int k, int V, double mu_rel, double *Y, double *idel,
+                                                           double *__restrict__ d, double *__restrict__ gd_out,
+                                                           int *__restrict__ ctl)
+{
+    extern __shared__ unsigned char smem_raw[];
+    VpShared &S = *reinterpret_cast<VpShared *>(smem_raw);
+    const int tid = threadIdx.x, nt = blockDim.x, K = 2 * k;
+    if (tid == 0) S.bad = 0;
+    for (int idx = tid; idx < k * k; idx += nt) {
+        const int i = idx / k, l = idx % k;
+        const double v = GH[i * kKMax + l] + lam * GP[i * kKMax + l];
+        S.M[i * kLd + l] = v;
+        S.L[i * kLd + l] = v;
+    }
+    __syncthreads();
+    chol(S.L, k, &S.bad);
+    __syncthreads();
+    // Y[:, j] = -M^{-1} (G[:, j] + E[:, j]) by L z = -(G + E), L^T y = z; then
+    // (J^T J)_jj = |H_j u|^2 + 2 E[:, j] . y + y^T M y, with y^T M y = |z|^2
+    double dmax = 0.0;
+    for (int j = tid; j < V; j += nt) {
+        double z[kVpMax], yv[kVpMax];
+        double zz = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double s = -(G[(size_t)i * V + j] + E[(size_t)i * V + j]);
+            for (int l = 0; l < i; ++l) s -= S.L[i * kLd + l] * z[l];
+            z[i] = s / S.L[i * kLd + i];
+            zz += z[i] * z[i];
+        }
+        double ey = 0.0;
+        for (int i = k - 1; i >= 0; --i) {
+            double s = z[i];
+            for (int l = i + 1; l < k; ++l) s -= S.L[l * kLd + i] * yv[l];
+            yv[i] = s / S.L[i * kLd + i];
+            Y[(size_t)i * V + j] = yv[i];
+            ey += E[(size_t)i * V + j] * yv[i];
+        }
+        dmax = fmax(dmax, j2[j] + 2.0 * ey + zz);
+    }
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((tid & 31) == 0) S.red[tid >> 5] = dmax;
+    __syncthreads();
+    if (tid == 0) {
+        double mx = 0.0;
+        for (int i = 0; i < (nt >> 5); ++i) mx = fmax(mx, S.red[i]);
+        S.mu = mu_rel * fmax(mx, 1e-300);
+    }
+    __syncthreads();
+    for (int j = tid; j < V; j += nt) idel[j] = 1.0 / (j2[j] + S.mu);
+    __syncthreads();  // Y and idel are visible to the whole CTA
+    // capacitance C = S^{-1} + U D^{-1} U^T and right-hand side U D^{-1} g
+    for (int idx = tid; idx < K * (K + 1); idx += nt) {
+        const int p = idx / (K + 1), q = idx % (K + 1);
+        const double *up = p < k ? E + (size_t)p * V : Y + (size_t)(p - k) * V;
+        double s = 0.0;
+        if (q < K) {
+            const double *uq = q < k ? E + (size_t)q * V : Y + (size_t)(q - k) * V;
+            for (int j = 0; j < V; ++j) s += up[j] * uq[j] * idel[j];
+            if (p < k && q < k) s -= S.M[p * kLd + q];
+            else if (q == p + k || p == q + k) s += 1.0;
+        } else {
+            for (int j = 0; j < V; ++j) s += up[j] * g[j] * idel[j];
+        }
+        S.C[p][q] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double cmax = 0.0;
+        for (int p = 0; p < K; ++p)
+            for (int q = 0; q < K; ++q) cmax = fmax(cmax, fabs(S.C[p][q]));
+        S.red[32] = cmax;
+    }
+    __syncthreads();
+    const double cmax = S.red[32];
+    for (int p = 0; p < K; ++p) {
+        if (tid == 0) {
+            int best = p;
+            double bv = fabs(S.C[p][p]);
+            for (int i = p + 1; i < K; ++i)
+                if (fabs(S.C[i][p]) > bv) {
+                    bv = fabs(S.C[i][p]);
+                    best = i;
+                }
+            S.piv = best;
+            if (!(bv > 1e-300 + 1e-15 * cmax)) S.bad |= 2;
+        }
+        __syncthreads();
+        if (S.bad & 2) break;
+        const int pv = S.piv;
+        if (pv != p)
+            for (int c = tid; c <= K; c += nt) {
+                const double t = S.C[p][c];
+                S.C[p][c] = S.C[pv][c];
+                S.C[pv][c] = t;
+            }
+        __syncthreads();
+        for (int i = p + 1 + tid; i < K; i += nt) S.z[i] = S.C[i][p] / S.C[p][p];
+        __syncthreads();
+        const int rows = K - p - 1, cols = K - p;  // rows p+1.., columns p+1..K (right-hand side included)
+        for (int idx = tid; idx < rows * cols; idx += nt) {
+            const int i = p + 1 + idx / cols, c = p + 1 + idx % cols;
+            S.C[i][c] -= S.z[i] * S.C[p][c];
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && !(S.bad & 2)) {
+        for (int p = K - 1; p >= 0; --p) {
+            double s = S.C[p][K];
+            for (int c = p + 1; c < K; ++c) s -= S.C[p][c] * S.z[c];
+            S.z[p] = s / S.C[p][p];
+        }
+    }
+    __syncthreads();
+    const bool bad = (S.bad & 2) != 0;
+    // d = -(D^{-1} g - D^{-1} U^T C^{-1} U D^{-1} g)
+    double gd = 0.0;
+    for (int j = tid; j < V; j += nt) {
+        double dj = 0.0;
+        if (!bad) {
+            double s = 0.0;
+            for (int p = 0; p < k; ++p) s += E[(size_t)p * V + j] * S.z[p] + Y[(size_t)p * V + j] * S.z[k + p];
+            dj = -(g[j] - s) * idel[j];
+        }
+        d[j] = dj;
+        gd += g[j] * dj;
+    }
+    gd = block_sum(gd, S.red);
+    if (tid == 0) {
+        *gd_out = gd;
+        if (S.bad) ctl[kBreakdown] = 1;
+    }
+}
+
+// out = theta + alpha d
+__global__ void k_theta_step(const double *__restrict__ theta, const double *__restrict__ d, double alpha, int V,
+                             double *__restrict__ out)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+        out[v] = theta[v] + alpha * d[v];
+}
+
 }  // namespace solver
 }  // namespace ctgb

@@ -63,7 +63,7 @@ class nlrmm_opts(ctypes.Structure):
         ("noise_norm", ctypes.c_double), ("lam_fix", ctypes.c_double), ("lam_lo", ctypes.c_double),
         ("lam_hi", ctypes.c_double), ("c1", ctypes.c_double), ("beta", ctypes.c_double),
         ("alpha0", ctypes.c_double), ("mu_rel", ctypes.c_double), ("tol_u", ctypes.c_double),
-        ("tol_p", ctypes.c_double), ("temporal", ctypes.c_int32),
+        ("tol_p", ctypes.c_double), ("temporal", ctypes.c_int32), ("varpro", ctypes.c_int32),
     ]
 
 
@@ -115,6 +115,8 @@ def load_library(path: str | None = None):
     lib.ct_jacT_noalloc.restype = ctypes.c_int
     lib.nlrmm_varpro.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_double, P, ctypes.c_double, P, P, P]
     lib.nlrmm_varpro.restype = ctypes.c_int
+    lib.nlrmm_varpro_update.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_double, P, ctypes.c_double, P, P]
+    lib.nlrmm_varpro_update.restype = ctypes.c_int
     lib.nlrmm_default_opts.argtypes = [P]
     lib.nlrmm_default_opts.restype = None
     lib.nlrmm_gks_solve.argtypes = [P, P, P, P, P, P, P, P]
@@ -318,6 +320,17 @@ def nlrmm_varpro(h, b, theta, delta, V, k, lam, u_w, eps, fval, grad=None, u_out
                                        float(eps), _p(fval), _p(grad), _p(u_out)), "nlrmm_varpro")
 
 
+def nlrmm_varpro_update(h, b, theta_inout, delta, V, k, lam, u_w, eps, opts=None, **overrides):
+    """One VarPro parameter update (theta_inout updated in place); returns the
+    reduced objective before the first step and after each step."""
+    o = opts if opts is not None else nlrmm_default_opts(**overrides)
+    f_hist = (ctypes.c_double * (max(o.maxiter_p, 0) + 1))()
+    _check(load_library().nlrmm_varpro_update(h, _p(b), _p(theta_inout), _p(delta), _p(V), int(k), float(lam),
+                                              _p(u_w), float(eps), ctypes.byref(o), f_hist),
+           "nlrmm_varpro_update")
+    return list(f_hist)
+
+
 # --- tensor-level wrapper ---------------------------------------------------
 
 class CTOperator:
@@ -439,6 +452,18 @@ class CTOperator:
         nlrmm_varpro(self.h, b, self._ang(theta, "theta"), self._ang(delta, "delta"), V.contiguous(),
                      V.shape[0], lam, u_w, eps, fval, grad, u)
         return fval[0], grad, u
+
+    def varpro_update(self, b, theta, V, lam, u_w=None, eps=1e-3, delta=None, **opts):
+        """VarPro Gauss-Newton update of the angles on the basis V (k x n):
+        returns (new angles, reduced objective per step).  theta is not modified."""
+        self._chk(b, self.m, "b")
+        self._chk(V, self.n, "V")
+        if u_w is not None:
+            self._chk(u_w, self.n, "u_w")
+        th = self._ang(theta, "theta").clone()
+        f_hist = nlrmm_varpro_update(self.h, b, th, self._ang(delta, "delta"), V.contiguous(), V.shape[0], lam,
+                                     u_w, eps, **opts)
+        return th, f_hist
 
     def solve(self, b, theta0, delta=None, x_true=None, **opts):
         """NL-RMM-GKS: returns (x, theta, stats).  theta0 is not modified."""
