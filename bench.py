@@ -621,8 +621,13 @@ def main():
     frames = None
     streaming = None
     dynamic = None
+    varpro = None
     if not args.no_solver and world == 1:
         solver = solver_comparison(w, dev, args.solver_iters)
+        # the same solve with the VarPro parameter update (Alg. "UPDATE-PARAM-VarPro")
+        varpro = solver_comparison(w, dev, args.solver_iters, varpro=1)
+        varpro["note"] = ("NL-RMM-GKS with the VarPro Gauss-Newton update on the compressed basis; compare "
+                          "ms_per_outer_iter, final_rre and rel_angle_err with 'solver' (per-view AltMin update)")
         frames = batched_frames(dev, min(args.steps, 200), flush)
         streaming = streaming_c5(dev, args.stream_passes) if args.stream_passes > 0 else None
         wd = synth.make_workload("C4")
@@ -668,6 +673,7 @@ def main():
         "batched_frames": frames,
         "streaming": streaming,
         "dynamic_solver": dynamic,
+        "varpro_solver": varpro,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step(tuning) * args.steps,
         "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
