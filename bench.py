@@ -91,6 +91,10 @@ def parse():
     ap.add_argument("--solver-iters", type=int, default=30)
     ap.add_argument("--stream-passes", type=int, default=2,
                     help="passes of the streaming solve on the 2048^2 / 1440-view workload (0: skip)")
+    ap.add_argument("--solver-only", action="store_true",
+                    help="run only the FP32 NL-RMM-GKS solve of the workload (--solver-iters outer iterations) "
+                         "and print its timing: the command the solver's profiles are taken with")
+    ap.add_argument("--varpro", action="store_true", help="with --solver-only: the VarPro parameter update")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw,fstage,jstage,astage' "
                          "(the ct_set_tuning values) instead of autotuning")
@@ -272,6 +276,39 @@ def solver_comparison(w, dev, outer_iters, **extra):
                             stop_on_convergence=0)
         out["fp32_spatial_only_final_rre"] = st["rre"][-1]
     return out
+
+
+def solver_only(w, dev, outer_iters, tuning=None, **extra):
+    """The FP32 NL-RMM-GKS solve of solver_comparison alone (for profiling):
+    autotune (or the given launch shapes), one 2-iteration warm-up solve, then
+    the timed solve."""
+    import torch
+    from paper_2605_06336_gb300 import ct
+    u_true = torch.tensor(w.images.reshape(-1), dtype=torch.float64, device=dev)
+    th_true = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
+    op64 = ct.CTOperator(w.N, w.B, w.V, w.views_per_frame, max_batch=8, dtype=torch.float64)
+    b_true = op64.forward(u_true, th_true)
+    e = torch.tensor(w.noise_dir, dtype=torch.float64, device=dev)
+    e *= w.noise_level * b_true.norm() / e.norm()
+    b = (b_true + e).float()
+    nn = float(e.norm())
+    th0 = torch.tensor(w.theta_nominal, dtype=torch.float64, device=dev)
+    op = ct.CTOperator(w.N, w.B, w.V, w.views_per_frame, max_batch=8, dtype=torch.float32)
+    if tuning:
+        op.tuning = tuning
+    else:
+        op.autotune()
+    op.solve(b, th0, x_true=u_true.float(), noise_norm=nn, outer_iters=2, stop_on_convergence=0, **extra)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, _, st = op.solve(b, th0, x_true=u_true.float(), noise_norm=nn, outer_iters=outer_iters, stop_on_convergence=0,
+                        **extra)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"ms_per_outer_iter": ms / outer_iters, "enlarge_steps": sum(st["enlarge_steps"]),
+            "final_rre": st["rre"][-1], "outer_iters": outer_iters, "tuning": dict(zip(ct.TUNING_FIELDS, op.tuning))}
 
 
 def streaming_c5(dev, passes):
@@ -459,6 +496,11 @@ def main():
     ct.load_library()  # fails loudly if the CUDA library is missing
 
     w = synth.make_workload(WORKLOAD)
+    if args.solver_only:
+        tun = [int(x) for x in args.tuning.split(",")] if args.tuning else None
+        out = solver_only(w, dev, args.solver_iters, tun, varpro=int(args.varpro))
+        print(json.dumps({"solver_only": out}), flush=True)
+        return
     N, B, V, K = w.N, w.B, w.V, KBLOCK
     rng = np.random.default_rng(100 + rank)
     Xh = np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(K - 1, N * N))]).astype(np.float32)

@@ -183,7 +183,8 @@ template <typename T> struct Solver {
         SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
         SV_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kScalCount, h.stream));
         const size_t small_smem = sizeof(SmallShared);
-        SV_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+        SV_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(SolveShared)));
         SV_CUDA(cudaFuncSetAttribute(k_compress_basis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)small_smem));
         SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, sizeof(T) == 4 ? 8 : 4>,
@@ -205,7 +206,9 @@ template <typename T> struct Solver {
     int dots_into(const T *A, long long len, int k, const T *x, const T *x2, double *out, const int *stop)
     {
         k_dots<T><<<kRedBlocks, kThreads, 0, h.stream>>>(A, len, len, k, x, x2, part_dot, stop);
-        k_dots_reduce<<<1, kKMax + 2, 0, h.stream>>>(part_dot, kRedBlocks, k + (x2 ? 1 : 0), out, stop);
+        const int kk = k + (x2 ? 1 : 0);
+        k_dots_reduce<<<(kk + kDotsReduceWarps - 1) / kDotsReduceWarps, 32 * kDotsReduceWarps, 0, h.stream>>>(
+            part_dot, kRedBlocks, kk, out, stop);
         SV_CUDA(cudaGetLastError());
         return CT_OK;
     }
@@ -331,10 +334,10 @@ template <typename T> struct Solver {
         constexpr int TR = sizeof(T) == 4 ? 8 : 4;
         k_gram_psi<T, TR><<<gblk, kThreads, gram_smem(kc, o.temporal && h.F > 1), h.stream>>>(V, n, kc, w, h.N, h.F, o.temporal, part_gram,
                                                                       stop);
-        k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gblk, kc, GP, stop);
+        k_gram_reduce<<<gram_reduce_blocks(kc), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gblk, kc, GP, stop);
         // lambda and the reduced solution
         const double target = (o.tau * noise) * (o.tau * noise);
-        k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
+        k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
                                                                      o.lam_lo, o.lam_hi, o.lam_iters, y, scal, ctl);
         // u = V y ; res = (HV) y - b
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, kc, y, u, T(0), T(1), nullptr, T(0), stop);
@@ -450,7 +453,7 @@ template <typename T> struct Solver {
         SV_TRY(project(theta, 0, k, nullptr));
         SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_TRY(full_gram(k));
-        k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
+        k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
                                                                      1, y, vp_scal, vp_ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, vp_u, T(0), T(1), nullptr, T(0), nullptr);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);
@@ -475,7 +478,8 @@ template <typename T> struct Solver {
         constexpr int TR = sizeof(T) == 4 ? 8 : 4;
         k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k, o.temporal && h.F > 1), h.stream>>>(
             V, n, k, w, h.N, h.F, o.temporal, part_gram, nullptr);
-        k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gram_blocks, k, GP, nullptr);
+        k_gram_reduce<<<gram_reduce_blocks(k), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gram_blocks, k, GP,
+                                                                                        nullptr);
         SV_CUDA(cudaMemcpyAsync(th_n, theta_in, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
         double f_last = 0.0;
         for (int it = 0; it < o.maxiter_p; ++it) {
@@ -567,8 +571,9 @@ template <typename T> struct Solver {
         constexpr int TR = sizeof(T) == 4 ? 8 : 4;
         k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k, o.temporal && h.F > 1), h.stream>>>(V, n, k, w, h.N, h.F, o.temporal, part_gram,
                                                                             nullptr);
-        k_gram_reduce<<<4, kThreads, 0, h.stream>>>(part_gram, gram_blocks, k, GP, nullptr);
-        k_small_solve<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
+        k_gram_reduce<<<gram_reduce_blocks(k), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gram_blocks, k, GP,
+                                                                                        nullptr);
+        k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
                                                                      1, y, scal, ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, u, T(0), T(1), nullptr, T(0), nullptr);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);

@@ -10,6 +10,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cmath>
 
 #include "ct_device.cuh"
@@ -215,23 +217,34 @@ __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long 
     }
 }
 
-// G (ld kKMax, symmetric, k x k) = sum over nblk partials (fixed order).
-__global__ void k_gram_reduce(const double *__restrict__ part, int nblk, int k, double *__restrict__ G,
-                              const int *stop)
+// G (ld kKMax, symmetric, k x k) = sum over nblk partials: one warp per entry,
+// each lane sums the partials c = lane, lane + 32, ... and the warp adds the
+// lanes in a fixed tree (FP64 is narrow on this part: no long dependent chains).
+constexpr int kGramReduceWarps = 8;
+inline int gram_reduce_blocks(int k) { return (k * (k + 1) / 2 + kGramReduceWarps - 1) / kGramReduceWarps; }
+
+__global__ void __launch_bounds__(32 * kGramReduceWarps) k_gram_reduce(const double *__restrict__ part, int nblk,
+                                                                       int k, double *__restrict__ G,
+                                                                       const int *stop)
 {
     if (stopped(stop)) return;
     const int np = k * (k + 1) / 2;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < np; p += nw) {
         double s = 0.0;
-        for (int c = 0; c < nblk; ++c) s += part[(long long)c * kGramPairs + p];
-        int a = 0, rem = p;
-        while (rem >= k - a) {
-            rem -= k - a;
-            ++a;
+        for (int c = lane; c < nblk; c += 32) s += part[(long long)c * kGramPairs + p];
+        s = warp_sum(s);
+        if (lane == 0) {
+            int a = 0, rem = p;
+            while (rem >= k - a) {
+                rem -= k - a;
+                ++a;
+            }
+            const int b = a + rem;
+            G[a * kKMax + b] = s;
+            G[b * kKMax + a] = s;
         }
-        const int b = a + rem;
-        G[a * kKMax + b] = s;
-        G[b * kKMax + a] = s;
     }
 }
 
@@ -240,35 +253,76 @@ __global__ void k_gram_reduce(const double *__restrict__ part, int nblk, int k, 
 // with column stride lda); x2 (nullable) adds out[k] = x . x2 .
 // kRedBlocks CTAs each own a contiguous slice; partials reduced in order.
 // ---------------------------------------------------------------------------
+// Columns are taken 16 at a time.  Every thread sums its elements of the 16
+// products in FP64; the 256 per-thread sums of a column are then added
+// through shared memory: 16 threads per column sum 16 values each (strided)
+// and combine them in a 16-lane tree, far fewer FP64 instructions than a
+// shuffle tree per warp (the FP64 pipe of this part is narrow).  Fixed order
+// throughout.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dots(const T *__restrict__ A, long long len, long long lda, int k,
                                               const T *__restrict__ x, const T *__restrict__ x2,
                                               double *__restrict__ part, const int *stop)
 {
     if (stopped(stop)) return;
-    __shared__ double sh[33];
+    constexpr int G = 16;
+    __shared__ double sh[G][257];
     const long long per = (len + gridDim.x - 1) / gridDim.x;
     const long long lo = blockIdx.x * per, hi = min(len, lo + per);
     const int kk = k + (x2 ? 1 : 0);
-    for (int a = 0; a < kk; ++a) {
-        const T *col = (a < k) ? A + (long long)a * lda : x2;
-        double s = 0.0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += (double)(col[i] * x[i]);
-        s = block_sum(s, sh);
-        if (threadIdx.x == 0) part[(long long)blockIdx.x * (kKMax + 2) + a] = s;
+    for (int a0 = 0; a0 < kk; a0 += G) {
+        const int na = min(G, kk - a0);
+        const T *cols[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int a = min(a0 + q, kk - 1);
+            cols[q] = (a < k) ? A + (long long)a * lda : x2;
+        }
+        double s[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) s[q] = 0.0;
+        // each product is rounded to T and summed in FP64 (FP32 partial sums
+        // cost the FP32 solver its agreement with the FP64 reference)
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const T xi = x[i];
+#pragma unroll
+            for (int q = 0; q < G; ++q)
+                if (q < na) s[q] += (double)(cols[q][i] * xi);
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+            if (q < na) sh[q][threadIdx.x] = s[q];
+        __syncthreads();
+        {
+            const int q = threadIdx.x >> 4, seg = threadIdx.x & 15;
+            double t = 0.0;
+            if (q < na) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) t += sh[q][seg + 16 * e];  // conflict-free
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (seg == 0 && q < na) part[(long long)blockIdx.x * (kKMax + 2) + a0 + q] = t;
+        }
+        __syncthreads();
     }
 }
 
-// out[a] = scale * sum_c part[c][a] for a < kk (fixed order)
-__global__ void k_dots_reduce(const double *__restrict__ part, int nblk, int kk, double *__restrict__ out,
-                              const int *stop)
+// out[a] = sum_c part[c][a] for a < kk: one warp per output, lanes over the
+// partials, a fixed warp tree
+constexpr int kDotsReduceWarps = 8;
+__global__ void __launch_bounds__(32 * kDotsReduceWarps) k_dots_reduce(const double *__restrict__ part, int nblk,
+                                                                       int kk, double *__restrict__ out,
+                                                                       const int *stop)
 {
     if (stopped(stop)) return;
-    const int a = threadIdx.x;
+    const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (a >= kk) return;
     double s = 0.0;
-    for (int c = 0; c < nblk; ++c) s += part[(long long)c * (kKMax + 2) + a];
-    out[a] = s;
+    for (int c = lane; c < nblk; c += 32) s += part[(long long)c * (kKMax + 2) + a];
+    s = warp_sum(s);
+    if (lane == 0) out[a] = s;
 }
 
 // out[i] = beta*out[i] + sgn * sum_a A[a][i] * y[a]  (+ bias[i] * bsgn)
@@ -339,14 +393,18 @@ __global__ void k_norms3(const T *__restrict__ a, const T *__restrict__ b, long 
     }
 }
 
+// one warp: lanes over the partials, a fixed warp tree per output
 __global__ void k_norms3_reduce(const double *__restrict__ part, int nblk, double *__restrict__ out3,
                                 const int *stop)
 {
     if (stopped(stop)) return;
-    if (threadIdx.x >= 3) return;
-    double s = 0.0;
-    for (int c = 0; c < nblk; ++c) s += part[c * 3 + threadIdx.x];
-    out3[threadIdx.x] = s;
+    if (threadIdx.x >= 32) return;
+    for (int q = 0; q < 3; ++q) {
+        double s = 0.0;
+        for (int c = threadIdx.x; c < nblk; c += 32) s += part[c * 3 + q];
+        s = warp_sum(s);
+        if (threadIdx.x == 0) out3[q] = s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -543,13 +601,88 @@ struct SmallShared {
 // Reduced problem of one Enlarge step:
 //   G_H = (H V)^T (H V), c = (H V)^T b (both maintained incrementally),
 //   G_P = (P Psi V)^T (P Psi V).
-// With G_H = L L^T and L^{-1} G_P L^{-T} = U diag(sig) U^T the normal
-// equations (G_H + lambda G_P) y = c have y = L^{-T} U diag(1/(1 + lambda
-// sig)) U^T L^{-1} c, and the projected residual |H V y - b|^2 =
-// |b|^2 - sum_i chat_i^2 (1 - (lambda sig_i / (1 + lambda sig_i))^2),
-// chat = U^T L^{-1} c -- the same quantity as the QR form
-// |R_H y - Q_H^T b|^2 + |b|^2 - |Q_H^T b|^2 of the reduced problem.
-// lambda: fixed, or the discrepancy principle by bisection in log10(lambda).
+// For a given lambda the normal equations (G_H + lambda G_P) y = c are solved
+// by an L D L^T factorization, and the projected residual (the QR form
+// |R_H y - Q_H^T b|^2 + |b|^2 - |Q_H^T b|^2 of the reduced problem) is
+//   phi(lambda) = |H V y - b|^2 = |b|^2 - c.y - lambda y.G_P y,
+// increasing in lambda with d phi / d lambda = 2 lambda w.(G_H + lambda G_P)^{-1} w,
+// w = G_P y.  lambda: fixed, or the discrepancy principle phi = target solved
+// in t = log10(lambda) over [lam_lo, lam_hi] by Newton steps safeguarded by
+// bisection of the bracket (started from the previous lambda in scal[kLam]);
+// a target at or below phi(10^lam_lo) gives 10^lam_lo, at or above
+// phi(10^lam_hi) gives 10^lam_hi, as for plain bisection.  The root is found
+// to 1e-12 in t (lambda to ~2e-12 relative): the limit of plain bisection
+// up to the rounding of phi itself.  The matrix is factored as L D L^T.
+//
+// The whole solve runs in warp 0 (k <= 64, lanes over rows, warp barriers
+// only): FP64 is a narrow pipe on this part, so the kernel is arranged for
+// short dependent chains rather than many threads.
+struct SolveShared {
+    double GH[kKMax * kLd], GP[kKMax * kLd], L[kKMax * kLd];
+    double c[kKMax], v[kKMax], y[kKMax], w[kKMax], inv[kKMax];
+    int bad;
+};
+
+// LDL^T factorization of the lower triangle of L in place (one warp): the
+// strict lower triangle becomes the unit factor, inv[j] = 1 / D_j (no square
+// roots: one division per column on the serial path).  Pivots at or below
+// tiny * L_00 are clamped and flag *bad.
+__device__ void ldlt_warp(double *L, double *inv, int k, int *bad)
+{
+    const int lane = threadIdx.x & 31;
+    const double floor_ = 1e-300 + 1e-15 * fabs(L[0]);
+    for (int j = 0; j < k; ++j) {
+        if (lane == 0) {
+            double d = L[j * kLd + j];
+            if (!(d > floor_)) {
+                d = floor_;
+                *bad = 1;
+            }
+            inv[j] = 1.0 / d;
+        }
+        __syncwarp();
+        const double id = inv[j];
+        // trailing lower triangle: rows i > j, columns j < l <= i, from the
+        // unscaled column (A_ij A_lj / D_j)
+        const int m = k - j - 1;
+        int i = 0, l = lane;  // entry idx = i (i + 1) / 2 + l of the trailing block, 0 <= l <= i
+        while (l > i) {
+            l -= i + 1;
+            ++i;
+        }
+        for (int idx = lane; idx < m * (m + 1) / 2; idx += 32) {
+            const int ri = j + 1 + i, cl = j + 1 + l;
+            L[ri * kLd + cl] -= L[ri * kLd + j] * id * L[cl * kLd + j];
+            l += 32;
+            while (l > i) {
+                l -= i + 1;
+                ++i;
+            }
+        }
+        __syncwarp();
+        for (int r = j + 1 + lane; r < k; r += 32) L[r * kLd + j] *= id;  // unit factor column
+        __syncwarp();
+    }
+}
+
+// v := (L D L^T)^{-1} v (one warp, lanes over rows)
+__device__ void ldlt_solve_warp(const double *L, const double *inv, double *v, int k)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < k; ++j) {
+        const double zj = v[j];
+        for (int i = j + 1 + lane; i < k; i += 32) v[i] -= L[i * kLd + j] * zj;
+        __syncwarp();
+    }
+    for (int i = lane; i < k; i += 32) v[i] *= inv[i];
+    __syncwarp();
+    for (int j = k - 1; j >= 0; --j) {
+        const double yj = v[j];
+        for (int i = lane; i < j; i += 32) v[i] -= L[j * kLd + i] * yj;
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ GH, const double *__restrict__ cvec,
                                                      const double *__restrict__ GP, int k, double bnorm2,
                                                      double target, double lam_fix, double lam_lo, double lam_hi,
@@ -557,97 +690,98 @@ __global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ 
                                                      int *__restrict__ ctl)
 {
     if (ctl[kStop]) return;
+    if (threadIdx.x >= 32) return;  // warp 0 does the work
     extern __shared__ unsigned char smem_raw[];
-    SmallShared &S = *reinterpret_cast<SmallShared *>(smem_raw);
-    if (threadIdx.x == 0) S.bad = 0;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    SolveShared &S = *reinterpret_cast<SolveShared *>(smem_raw);
+    const int lane = threadIdx.x;
+    if (lane == 0) S.bad = 0;
+    for (int idx = lane; idx < k * k; idx += 32) {
         const int i = idx / k, j = idx % k;
-        S.A[i * kLd + j] = GH[i * kKMax + j];
-        S.B[i * kLd + j] = GP[i * kKMax + j];
+        S.GH[i * kLd + j] = GH[i * kKMax + j];
+        S.GP[i * kLd + j] = GP[i * kKMax + j];
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) S.vec[0][i] = cvec[i];
-    __syncthreads();
-    chol(S.A, k, &S.bad);                    // A = L (lower)
-    trsm_lower(S.A, S.B, k, k);              // B = L^{-1} G_P
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {  // U = B^T (scratch)
-        const int i = idx / k, j = idx % k;
-        S.U[i * kLd + j] = S.B[j * kLd + i];
-    }
-    __syncthreads();
-    trsm_lower(S.A, S.U, k, k);              // U = L^{-1} G_P L^{-T}
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {  // symmetrize into B
-        const int i = idx / k, j = idx % k;
-        S.B[i * kLd + j] = 0.5 * (S.U[i * kLd + j] + S.U[j * kLd + i]);
-    }
-    // chat = U^T L^{-1} c  (vec[1] = L^{-1} c)
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < k; ++i) {
-            double s = S.vec[0][i];
-            for (int l = 0; l < i; ++l) s -= S.A[i * kLd + l] * S.vec[1][l];
-            S.vec[1][i] = s / S.A[i * kLd + i];
+    for (int i = lane; i < k; i += 32) S.c[i] = cvec[i];
+    const double lam_prev = scal[kLam];
+    __syncwarp();
+    // phi(lambda) (and d phi / d t, t = log10 lambda, when want_d); leaves y in S.y
+    auto eval = [&](double lam, bool want_d, double &dphi_dt) -> double {
+        for (int idx = lane; idx < k * k; idx += 32) {
+            const int i = idx / k, j = idx % k;
+            if (j <= i) S.L[i * kLd + j] = S.GH[i * kLd + j] + lam * S.GP[i * kLd + j];
         }
-    }
-    __syncthreads();
-    jacobi_eig(S.B, S.U, k, S.cs, S.sn, S.pp, S.qq, S.sh);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        double s = 0.0;
-        for (int l = 0; l < k; ++l) s += S.U[l * kLd + i] * S.vec[1][l];
-        S.vec[2][i] = s;                          // chat
-        S.vec[3][i] = fmax(S.B[i * kLd + i], 0.0);  // sigma
-    }
-    __syncthreads();
-    double lam;
+        for (int i = lane; i < k; i += 32) S.y[i] = S.c[i];
+        __syncwarp();
+        ldlt_warp(S.L, S.inv, k, &S.bad);
+        ldlt_solve_warp(S.L, S.inv, S.y, k);
+        double cy = 0.0, yw = 0.0;
+        for (int i = lane; i < k; i += 32) {
+            double t = 0.0;
+            for (int l = 0; l < k; ++l) t += S.GP[i * kLd + l] * S.y[l];
+            S.w[i] = t;
+            S.v[i] = t;
+            cy += S.c[i] * S.y[i];
+            yw += S.y[i] * t;
+        }
+        cy = warp_sum(cy);
+        yw = warp_sum(yw);
+        __syncwarp();
+        dphi_dt = 0.0;
+        if (want_d) {
+            ldlt_solve_warp(S.L, S.inv, S.v, k);
+            double wz = 0.0;
+            for (int i = lane; i < k; i += 32) wz += S.w[i] * S.v[i];
+            wz = warp_sum(wz);
+            dphi_dt = 2.0 * lam * wz * lam * 2.302585092994045684;  // d/dt = lambda ln(10) d/dlambda
+        }
+        return bnorm2 - cy - lam * yw;
+    };
+    double lam, dd;
     if (lam_fix > 0.0) {
         lam = lam_fix;
+        eval(lam, false, dd);
     } else {
-        // phi(lambda) evaluated by warp 0
-        auto phi = [&](double l) {
-            double s = 0.0;
-            if (threadIdx.x < 32) {
-                for (int i = threadIdx.x; i < k; i += 32) {
-                    const double q = l * S.vec[3][i] / (1.0 + l * S.vec[3][i]);
-                    s += S.vec[2][i] * S.vec[2][i] * (1.0 - q * q);
-                }
-                s = warp_sum(s);
-            }
-            return bnorm2 - s;
-        };
+        // Newton in t on the bracket [lo, hi]; an end of the bracket that is
+        // still lam_lo (lam_hi) is evaluated only when a step would leave it,
+        // and ends the search when the target lies beyond it.  S.y always
+        // holds the solution at the last evaluated t, which is returned.
         double lo = lam_lo, hi = lam_hi;
-        if (threadIdx.x < 32) {
-            if (phi(pow(10.0, lo)) >= target) {
-                hi = lo;
-            } else if (phi(pow(10.0, hi)) <= target) {
-                lo = hi;
+        bool lo_seen = false, hi_seen = false;
+        double t = (lam_prev > 0.0) ? log10(lam_prev) : 0.5 * (lo + hi);
+        if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+        double te = t;  // last evaluated t
+        for (int it = 0; it < lam_iters + 2; ++it) {
+            double dft;
+            te = t;
+            const double f = eval(pow(10.0, t), true, dft) - target;
+            if (t == lam_lo && f >= 0.0) break;  // target at or below the smallest residual
+            if (t == lam_hi && f <= 0.0) break;  // target at or above the largest residual
+            if (f == 0.0) break;
+            if (f < 0.0) {
+                lo = t;
+                lo_seen = true;
             } else {
-                for (int it = 0; it < lam_iters; ++it) {
-                    const double mid = 0.5 * (lo + hi);
-                    if (phi(pow(10.0, mid)) < target) lo = mid;
-                    else hi = mid;
-                }
+                hi = t;
+                hi_seen = true;
             }
-            if (threadIdx.x == 0) S.sh[0] = (lo == hi) ? pow(10.0, lo) : pow(10.0, 0.5 * (lo + hi));
+            double tn = t - f / dft;
+            if (!(dft > 0.0) || !(tn > lo && tn < hi)) {
+                if (!(tn > lo) && !lo_seen) tn = lo;        // check the lower end first
+                else if (!(tn < hi) && !hi_seen) tn = hi;   // the upper end
+                else tn = 0.5 * (lo + hi);
+            }
+            // phi carries rounding errors of ~1e-13 relative, so the root is
+            // not defined more finely than this in t
+            const double tol = 1e-12 * fmax(1.0, fabs(t));
+            if (fabs(tn - t) <= tol || hi - lo <= tol) break;  // t is the root to tol
+            t = tn;
         }
-        __syncthreads();
-        lam = S.sh[0];
+        lam = pow(10.0, te);
     }
-    // y = L^{-T} U diag(t) chat
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        double s = 0.0;
-        for (int l = 0; l < k; ++l) s += S.U[i * kLd + l] * S.vec[2][l] / (1.0 + lam * S.vec[3][l]);
-        S.vec[0][i] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = k - 1; i >= 0; --i) {
-            double s = S.vec[0][i];
-            for (int l = i + 1; l < k; ++l) s -= S.A[l * kLd + i] * S.vec[1][l];
-            S.vec[1][i] = s / S.A[i * kLd + i];
-        }
+    for (int i = lane; i < k; i += 32) y[i] = S.y[i];
+    if (lane == 0) {
         scal[kLam] = lam;
         if (S.bad) ctl[kBreakdown] = 1;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = S.vec[1][i];
 }
 
 // Compress: right singular vectors of [R_H; sqrt(lambda) R_P] are the
