@@ -95,6 +95,11 @@ def parse():
                     help="run only the FP32 NL-RMM-GKS solve of the workload (--solver-iters outer iterations) "
                          "and print its timing: the command the solver's profiles are taken with")
     ap.add_argument("--varpro", action="store_true", help="with --solver-only: the VarPro parameter update")
+    ap.add_argument("--stream-only", action="store_true",
+                    help="run only the streaming solve on the 2048^2 / 1440-view workload (--stream-passes passes) "
+                         "and print its timing: the command the streaming profiles are taken with")
+    ap.add_argument("--stream-scale", type=float, default=1.0,
+                    help="with --stream-only: shrink the streaming workload (image side, bins, views)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes 'fkb,fsplit,fvw,akb,asplit,jsplit,jvw,fstage,jstage,astage' "
                          "(the ct_set_tuning values) instead of autotuning")
@@ -311,14 +316,15 @@ def solver_only(w, dev, outer_iters, tuning=None, **extra):
             "final_rre": st["rre"][-1], "outer_iters": outer_iters, "tuning": dict(zip(ct.TUNING_FIELDS, op.tuning))}
 
 
-def streaming_c5(dev, passes):
+def streaming_c5(dev, passes, scale=1.0):
     """Streaming NL-RMM-GKS (FP32 operators, FP64 small algebra) on the 2048^2 /
     1440-view workload in its 12 random chunks of 120 views: one handle per
     chunk, `passes` passes.  The data are H(theta_true) u_true from the FP64
-    GPU forward plus 0.5 % noise."""
+    GPU forward plus 0.5 % noise.  `scale` < 1 shrinks the same recipe (for
+    profiler captures of a smaller case)."""
     import torch
     from paper_2605_06336_gb300 import ct, synth
-    w = synth.make_workload("C5")
+    w = synth.make_workload("C5", scale=scale)
     N, B = w.N, w.B
     chunks = w.extra["chunks"]
     u64 = torch.tensor(w.images.reshape(-1), dtype=torch.float64, device=dev)
@@ -495,6 +501,9 @@ def main():
     from paper_2605_06336_gb300 import ct, synth
     ct.load_library()  # fails loudly if the CUDA library is missing
 
+    if args.stream_only:
+        print(json.dumps({"streaming": streaming_c5(dev, max(args.stream_passes, 1), args.stream_scale)}), flush=True)
+        return
     w = synth.make_workload(WORKLOAD)
     if args.solver_only:
         tun = [int(x) for x in args.tuning.split(",")] if args.tuning else None

@@ -140,7 +140,9 @@ template <typename T> struct Solver {
         m = (long long)h.V * h.B;
         ne = psi_edges(h.N, h.F, o.temporal);
         KC = o.k_max + 2;
-        const int tiles = ((h.N + 31) / 32) * ((h.N + (sizeof(T) == 4 ? 8 : 4) - 1) / (sizeof(T) == 4 ? 8 : 4)) * h.F;
+        // tiles of the Gram kernel: kRbRows x 32 pixels (FP32, register-blocked), 4 x 32 (FP64)
+        const int tile_rows = sizeof(T) == 4 ? kRbRows : 4;
+        const int tiles = ((h.N + 31) / 32) * ((h.N + tile_rows - 1) / tile_rows) * h.F;
         gram_blocks = std::min(tiles, 2 * h.num_sms);
         const long long m_all = std::max(m, m_cap);
         const int v_all = std::max(h.V, v_cap);
@@ -187,16 +189,37 @@ template <typename T> struct Solver {
                                      (int)sizeof(SolveShared)));
         SV_CUDA(cudaFuncSetAttribute(k_compress_basis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)small_smem));
-        SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, sizeof(T) == 4 ? 8 : 4>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem(kKMax, true)));
+        if constexpr (sizeof(T) == 4) {
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_rb_smem(kKMax, 3)));
+        } else {
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_smem(kKMax, true)));
+        }
         return CT_OK;
     }
 
     // k columns of the edges of one tile: 2 per pixel, 3 with the temporal edge (ANISO-TV)
     static size_t gram_smem(int k, bool temporal)
     {
-        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        return (size_t)k * ((temporal ? 3 : 2) * TR * 32 + 1) * sizeof(T);
+        return (size_t)k * ((temporal ? 3 : 2) * 4 * 32 + 1) * sizeof(T);
+    }
+
+    // GP = (P Psi V)^T (P Psi V) over V[:, :k] with the weights in w
+    int gram_psi(int k, const int *stop)
+    {
+        const bool tm = o.temporal && h.F > 1;
+        if constexpr (sizeof(T) == 4) {
+            k_gram_psi_rb<<<gram_blocks, kThreads, gram_rb_smem(k, tm ? 3 : 2), h.stream>>>(V, n, k, w, h.N, h.F,
+                                                                                       o.temporal, part_gram, stop);
+        } else {
+            k_gram_psi<T, 4><<<gram_blocks, kThreads, gram_smem(k, tm), h.stream>>>(V, n, k, w, h.N, h.F, o.temporal,
+                                                                                 part_gram, stop);
+        }
+        k_gram_reduce<<<gram_reduce_blocks(k), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gram_blocks, k, GP,
+                                                                                     stop);
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
     }
 
     T *col(T *base, long long len, int j) const { return base + (long long)j * len; }
@@ -327,14 +350,10 @@ template <typename T> struct Solver {
     int enlarge_step(const double *theta, int kc)
     {
         const int *stop = ctl + kStop;
-        const int gblk = gram_blocks;
         // P^2 from the previous iterate
         k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(uold, w, h.N, h.F, o.temporal, o.eps, stop);
         // G_P = (P Psi V)^T (P Psi V)
-        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        k_gram_psi<T, TR><<<gblk, kThreads, gram_smem(kc, o.temporal && h.F > 1), h.stream>>>(V, n, kc, w, h.N, h.F, o.temporal, part_gram,
-                                                                      stop);
-        k_gram_reduce<<<gram_reduce_blocks(kc), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gblk, kc, GP, stop);
+        SV_TRY(gram_psi(kc, stop));
         // lambda and the reduced solution
         const double target = (o.tau * noise) * (o.tau * noise);
         k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
@@ -475,11 +494,7 @@ template <typename T> struct Solver {
     {
         if (k < 1 || k > kVpMax) return CT_ERR_ARG;
         SV_TRY(varpro_setup());
-        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k, o.temporal && h.F > 1), h.stream>>>(
-            V, n, k, w, h.N, h.F, o.temporal, part_gram, nullptr);
-        k_gram_reduce<<<gram_reduce_blocks(k), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gram_blocks, k, GP,
-                                                                                        nullptr);
+        SV_TRY(gram_psi(k, nullptr));
         SV_CUDA(cudaMemcpyAsync(th_n, theta_in, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
         double f_last = 0.0;
         for (int it = 0; it < o.maxiter_p; ++it) {
@@ -568,11 +583,7 @@ template <typename T> struct Solver {
         } else {
             k_fill<T><<<grid_for(ne), kThreads, 0, h.stream>>>(w, ne, T(1));
         }
-        constexpr int TR = sizeof(T) == 4 ? 8 : 4;
-        k_gram_psi<T, TR><<<gram_blocks, kThreads, gram_smem(k, o.temporal && h.F > 1), h.stream>>>(V, n, k, w, h.N, h.F, o.temporal, part_gram,
-                                                                            nullptr);
-        k_gram_reduce<<<gram_reduce_blocks(k), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gram_blocks, k, GP,
-                                                                                        nullptr);
+        SV_TRY(gram_psi(k, nullptr));
         k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
                                                                      1, y, scal, ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, u, T(0), T(1), nullptr, T(0), nullptr);

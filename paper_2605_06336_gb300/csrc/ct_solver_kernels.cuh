@@ -217,6 +217,128 @@ __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long 
     }
 }
 
+// Register-blocked form for FP32 bases.  A tile is 4 x 32 pixels of one
+// frame; its edges (right, down, and with ANISO-TV the next frame) of all k
+// columns go to shared memory as rows E[e][0..KP) (KP = k rounded up to 32),
+// each 16-byte group of a row stored at group ^ (pixel & 7) so that the
+// float4 stores of 8 consecutive pixels fall in distinct bank groups.  The
+// k x k upper triangle is cut into 4 x 4 blocks; block pair (bi <= bj) and
+// edge phase ph go to one thread, which sums its edges e = ph, ph + phases, ...
+// with two float4 reads and 16 FMAs per edge.  Per tile the phases are added
+// in FP32 in shared memory and the sum goes to the owner's FP64 accumulators;
+// per-CTA FP64 partials as for k_gram_psi.
+constexpr int kRbRows = 4;                      // tile rows
+constexpr int kRbPix = kRbRows * 32;            // tile pixels
+inline size_t gram_rb_smem(int k, int epp)
+{
+    const int kp = 32 * ((k + 31) / 32);
+    return (size_t)epp * kRbPix * kp * sizeof(float) + 256 * 16 * sizeof(float);
+}
+
+__global__ void __launch_bounds__(256) k_gram_psi_rb(const float *__restrict__ V, long long n, int k,
+                                                     const float *__restrict__ w, int N, int F, int temporal,
+                                                     double *__restrict__ part, const int *stop)
+{
+    if (stopped(stop)) return;
+    extern __shared__ float4 rb_smem[];
+    const int EPP = (temporal && F > 1) ? 3 : 2;
+    const int KP = 32 * ((k + 31) / 32);
+    const int NE = EPP * kRbPix;
+    float *E = reinterpret_cast<float *>(rb_smem);  // [NE][KP], swizzled 16-byte groups
+    float *red = E + (size_t)NE * KP;               // [256][16]
+    const int kb = (k + 3) / 4;
+    const int P = kb * (kb + 1) / 2;
+    const int phases = max(1, min(8, 256 / P));
+    const int t = threadIdx.x;
+    const bool busy = t < P * phases;
+    const int p = t % P, ph = t / P;
+    int bi = 0, rem = p;
+    while (rem >= kb - bi) {
+        rem -= kb - bi;
+        ++bi;
+    }
+    const int bj = bi + rem;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    const int tiles_x = (N + 31) / 32, tiles_y = (N + kRbRows - 1) / kRbRows;
+    const int ntiles = tiles_x * tiles_y * F;
+    const long long nx = (long long)F * N * (N - 1);
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const int tile = tt % (tiles_x * tiles_y);
+        const int f = tt / (tiles_x * tiles_y);
+        const int i0 = (tile / tiles_x) * kRbRows, j0 = (tile % tiles_x) * 32;
+        const float *wx = w + (long long)f * N * (N - 1);
+        const float *wy = w + nx + (long long)f * (N - 1) * N;
+        const float *wt = w + 2 * nx + (long long)f * N * N;
+        __syncthreads();  // the previous tile is done with E and red
+        // edges: thread = (column group of 4, pixel); consecutive threads take consecutive pixels
+        for (int idx = t; idx < kb * kRbPix; idx += 256) {
+            const int g = idx / kRbPix, pix = idx % kRbPix;
+            const int i = i0 + pix / 32, j = j0 + pix % 32;
+            float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, et[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < N && j < N) {
+                const float sx = j < N - 1 ? sqrtf(wx[i * (N - 1) + j]) : 0.f;
+                const float sy = i < N - 1 ? sqrtf(wy[i * N + j]) : 0.f;
+                const float st = (EPP == 3 && f < F - 1) ? sqrtf(wt[(size_t)i * N + j]) : 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int a = 4 * g + c;
+                    if (a < k) {
+                        const float *va = V + (long long)a * n + (long long)f * N * N;
+                        const float v0 = va[(size_t)i * N + j];
+                        if (j < N - 1) ex[c] = (va[(size_t)i * N + j + 1] - v0) * sx;
+                        if (i < N - 1) ey[c] = (va[(size_t)(i + 1) * N + j] - v0) * sy;
+                        if (EPP == 3 && f < F - 1) et[c] = (va[(size_t)N * N + (size_t)i * N + j] - v0) * st;
+                    }
+                }
+            }
+            const int col = (4 * g) ^ ((pix & 7) << 2);
+            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix) * KP + col) = make_float4(ex[0], ex[1], ex[2], ex[3]);
+            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 1) * KP + col) =
+                make_float4(ey[0], ey[1], ey[2], ey[3]);
+            if (EPP == 3)
+                *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 2) * KP + col) =
+                    make_float4(et[0], et[1], et[2], et[3]);
+        }
+        __syncthreads();
+        if (busy) {
+            float s[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s[q] = 0.f;
+            for (int e = ph; e < NE; e += phases) {
+                const int sw = ((e / EPP) & 7) << 2;
+                const float4 A = *reinterpret_cast<const float4 *>(E + (size_t)e * KP + ((4 * bi) ^ sw));
+                const float4 Bv = *reinterpret_cast<const float4 *>(E + (size_t)e * KP + ((4 * bj) ^ sw));
+                const float av[4] = {A.x, A.y, A.z, A.w}, bv[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) s[4 * r + c] = fmaf(av[r], bv[c], s[4 * r + c]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+                *reinterpret_cast<float4 *>(red + (size_t)t * 16 + q) = make_float4(s[q], s[q + 1], s[q + 2], s[q + 3]);
+        }
+        __syncthreads();
+        if (t < P) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                float v = 0.f;
+                for (int r = 0; r < phases; ++r) v += red[(size_t)(r * P + t) * 16 + q];
+                acc[q] += (double)v;
+            }
+        }
+    }
+    if (t < P) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int a = 4 * bi + q / 4, b = 4 * bj + q % 4;
+            if (a <= b && b < k) part[(long long)blockIdx.x * kGramPairs + a * k - a * (a - 1) / 2 + (b - a)] = acc[q];
+        }
+    }
+}
+
 // G (ld kKMax, symmetric, k x k) = sum over nblk partials: one warp per entry,
 // each lane sums the partials c = lane, lane + 32, ... and the warp adds the
 // lanes in a fixed tree (FP64 is narrow on this part: no long dependent chains).
@@ -254,11 +376,13 @@ __global__ void __launch_bounds__(32 * kGramReduceWarps) k_gram_reduce(const dou
 // kRedBlocks CTAs each own a contiguous slice; partials reduced in order.
 // ---------------------------------------------------------------------------
 // Columns are taken 16 at a time.  Every thread sums its elements of the 16
-// products in FP64; the 256 per-thread sums of a column are then added
+// products: in FP64 for T = double; for T = float in FP32 over runs of 16
+// elements, each run then added in FP64 (the products are FP32 to begin with,
+// and the FP64 pipe of this part is narrow: at 2048^2 per-element FP64 adds
+// bound the kernel).  The 256 per-thread sums of a column are then added
 // through shared memory: 16 threads per column sum 16 values each (strided)
 // and combine them in a 16-lane tree, far fewer FP64 instructions than a
-// shuffle tree per warp (the FP64 pipe of this part is narrow).  Fixed order
-// throughout.
+// shuffle tree per warp.  Fixed order throughout.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dots(const T *__restrict__ A, long long len, long long lda, int k,
                                               const T *__restrict__ x, const T *__restrict__ x2,
@@ -281,13 +405,36 @@ __global__ void __launch_bounds__(256) k_dots(const T *__restrict__ A, long long
         double s[G];
 #pragma unroll
         for (int q = 0; q < G; ++q) s[q] = 0.0;
-        // each product is rounded to T and summed in FP64 (FP32 partial sums
-        // cost the FP32 solver its agreement with the FP64 reference)
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const T xi = x[i];
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 fused multiply-adds over runs of 16 of the thread's
+            // elements, each run added to the FP64 sum
+            float fr[G];
 #pragma unroll
-            for (int q = 0; q < G; ++q)
-                if (q < na) s[q] += (double)(cols[q][i] * xi);
+            for (int q = 0; q < G; ++q) fr[q] = 0.0f;
+            int run = 0;
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const float xi = x[i];
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    if (q < na) fr[q] = fmaf(cols[q][i], xi, fr[q]);
+                if (++run == 16) {
+#pragma unroll
+                    for (int q = 0; q < G; ++q) {
+                        s[q] += (double)fr[q];
+                        fr[q] = 0.0f;
+                    }
+                    run = 0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < G; ++q) s[q] += (double)fr[q];
+        } else {
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const T xi = x[i];
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    if (q < na) s[q] = fma(cols[q][i], xi, s[q]);
+            }
         }
 #pragma unroll
         for (int q = 0; q < G; ++q)
