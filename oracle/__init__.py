@@ -5,7 +5,8 @@ CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA path of ``paper_2605_06336_gb300`` and never imports it.
 
 ``ct_oracle.c`` holds the operator arithmetic (Joseph line integrals, a
-scatter-form transpose, the analytic angle/offset derivatives); this module
+scatter-form transpose, the analytic angle/offset derivatives, for the
+parallel beam and the fan beam); this module
 compiles it with gcc and wraps it with numpy.  ``nlrmm.py`` holds the solver
 (MM-GKS / RMM-GKS / NL-RMM-GKS, Sec. 3-4 and the supplementary algorithms).
 """
@@ -44,7 +45,12 @@ def _load():
         lib.orc_dsample.argtypes = [I, I, I, P, P, P, P, P, P]
         lib.orc_jac.argtypes = [I, I, I, P, P, P, P, P, P, P]
         lib.orc_jacT.argtypes = [I, I, I, P, P, P, P, P, P, P]
-        for f in (lib.orc_forward, lib.orc_adjoint, lib.orc_dsample, lib.orc_jac, lib.orc_jacT):
+        D = ctypes.c_double
+        lib.orc_fan_forward.argtypes = [I, I, I, P, D, P, P, P, P]
+        lib.orc_fan_adjoint.argtypes = [I, I, I, I, P, D, P, P, P, P]
+        lib.orc_fan_dsample.argtypes = [I, I, I, P, D, P, P, P, P, P]
+        for f in (lib.orc_forward, lib.orc_adjoint, lib.orc_dsample, lib.orc_jac, lib.orc_jacT,
+                  lib.orc_fan_forward, lib.orc_fan_adjoint, lib.orc_fan_dsample):
             f.restype = None
         _lib = lib
     return _lib
@@ -59,14 +65,17 @@ def _ptr(a):
 
 
 class Geometry:
-    """Parallel-beam geometry: N x N image, B bins, per-view frame index.
+    """Geometry: N x N image, B bins, per-view frame index.
 
     ``views_per_frame`` splits the flat view list into consecutive frames
     (block-diagonal operator of the dynamic problem); ``None`` = one frame.
+    ``fan_D``: parallel beam when None, else fan beam with the source at
+    distance fan_D (pixels) from the rotation centre (``ct_oracle.c``).
     """
 
-    def __init__(self, N: int, B: int, n_views: int, views_per_frame=None):
+    def __init__(self, N: int, B: int, n_views: int, views_per_frame=None, fan_D=None):
         self.N, self.B, self.V = int(N), int(B), int(n_views)
+        self.fan_D = None if fan_D is None else float(fan_D)
         if views_per_frame is None:
             self.F = 1
             self.fov = None
@@ -97,7 +106,10 @@ def forward(g: Geometry, theta, X, delta=None):
     for k in range(batch.shape[0]):
         xk = np.ascontiguousarray(batch[k])
         yk = np.empty(g.m)
-        lib.orc_forward(g.N, g.B, g.V, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(xk), _ptr(yk))
+        if g.fan_D is None:
+            lib.orc_forward(g.N, g.B, g.V, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(xk), _ptr(yk))
+        else:
+            lib.orc_fan_forward(g.N, g.B, g.V, _ptr(g.fov), g.fan_D, _ptr(th), _ptr(dl), _ptr(xk), _ptr(yk))
         out[k] = yk
     return out.reshape(X.shape[:-1] + (g.m,)) if X.ndim > 1 else out[0]
 
@@ -113,7 +125,10 @@ def adjoint(g: Geometry, theta, Y, delta=None):
     for k in range(batch.shape[0]):
         yk = np.ascontiguousarray(batch[k])
         xk = np.empty(g.n)
-        lib.orc_adjoint(g.N, g.B, g.V, g.F, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(yk), _ptr(xk))
+        if g.fan_D is None:
+            lib.orc_adjoint(g.N, g.B, g.V, g.F, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(yk), _ptr(xk))
+        else:
+            lib.orc_fan_adjoint(g.N, g.B, g.V, g.F, _ptr(g.fov), g.fan_D, _ptr(th), _ptr(dl), _ptr(yk), _ptr(xk))
         out[k] = xk
     return out.reshape(Y.shape[:-1] + (g.n,)) if Y.ndim > 1 else out[0]
 
@@ -126,7 +141,10 @@ def dsample(g: Geometry, theta, X, delta=None):
     dl = None if delta is None else _f64(delta)
     dt = np.empty(g.m)
     dd = np.empty(g.m)
-    lib.orc_dsample(g.N, g.B, g.V, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(X), _ptr(dt), _ptr(dd))
+    if g.fan_D is None:
+        lib.orc_dsample(g.N, g.B, g.V, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(X), _ptr(dt), _ptr(dd))
+    else:
+        lib.orc_fan_dsample(g.N, g.B, g.V, _ptr(g.fov), g.fan_D, _ptr(th), _ptr(dl), _ptr(X), _ptr(dt), _ptr(dd))
     return dt, dd
 
 
@@ -136,6 +154,12 @@ def jac(g: Geometry, theta, X, dtheta, delta=None, ddelta=None):
     X, th, dth = _f64(X), _f64(theta), _f64(dtheta)
     dl = None if delta is None else _f64(delta)
     ddl = None if ddelta is None else _f64(ddelta)
+    if g.fan_D is not None:  # per-sample derivatives times the per-view directions
+        dt, dd = dsample(g, theta, X, delta)
+        dy = (dt.reshape(g.V, g.B) * dth[:, None]).ravel()
+        if ddl is not None:
+            dy += (dd.reshape(g.V, g.B) * ddl[:, None]).ravel()
+        return dy
     dy = np.empty(g.m)
     lib.orc_jac(g.N, g.B, g.V, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(X), _ptr(dth), _ptr(ddl), _ptr(dy))
     return dy
@@ -146,6 +170,9 @@ def jacT(g: Geometry, theta, X, R, delta=None):
     lib = _load()
     X, th, R = _f64(X), _f64(theta), _f64(R)
     dl = None if delta is None else _f64(delta)
+    if g.fan_D is not None:  # per-view sums of the residual times the per-sample derivatives
+        dt, dd = dsample(g, theta, X, delta)
+        return (dt * R).reshape(g.V, g.B).sum(1), (dd * R).reshape(g.V, g.B).sum(1)
     gt = np.empty(g.V)
     gd = np.empty(g.V)
     lib.orc_jacT(g.N, g.B, g.V, _ptr(g.fov), _ptr(th), _ptr(dl), _ptr(X), _ptr(R), _ptr(gt), _ptr(gd))

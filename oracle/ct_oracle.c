@@ -239,3 +239,177 @@ void orc_jacT(int N, int B, int V, const int *fov, const double *theta,
             g_delta[v] = gd;
     }
 }
+
+/*
+ * Fan-beam variant (the paper's CT experiments are fan-beam, Sec. 6.2; its
+ * source and detector distances are not given).  Reading: point source at
+ * distance D from the rotation centre, flat detector rescaled to the line
+ * through the centre, so bin b keeps the parallel-beam centre s_b on that
+ * line.  With t = (-sin, cos) (the parallel-beam ray direction) and
+ * e = (cos, sin) (the detector axis), the source sits at S = -D t, bin b at
+ * P_b = s_b e, and ray (v,b) is the line through S and P_b, direction
+ * r = P_b - S = (s_b cos - D sin, s_b sin + D cos).  As D -> infinity it
+ * becomes the parallel-beam ray { x cos + y sin = s_b }.
+ *
+ * Joseph rule per ray: rows if |r_x| <= |r_y| (one sample per image row,
+ * x(y) = A + C y with C = r_x / r_y, A = P_x - P_y C), else columns
+ * (y(x) = A + C x with C = r_y / r_x, A = P_y - P_x C); weight sqrt(1 + C^2)
+ * (path length per row or column).  Interpolation, zero extension and the
+ * kink convention as for the parallel beam.
+ *
+ * Derivatives: the geometry rotates rigidly with theta, so dr/dtheta =
+ * (-r_y, r_x) and dP_b/dtheta = s_b (-sin, cos); with respect to delta,
+ * dr/ds_b = dP_b/ds_b = e.  Hence, for rows,
+ *   dC/dtheta = -(1 + C^2),  dA/dtheta = dP_x - C dP_y - P_y dC/dtheta,
+ *   dC/ds = (cos r_y - sin r_x) / r_y^2,  dA/ds = cos - C sin - P_y dC/ds,
+ * for columns
+ *   dC/dtheta = 1 + C^2,  dA/dtheta = dP_y - C dP_x - P_x dC/dtheta,
+ *   dC/ds = (sin r_x - cos r_y) / r_x^2,  dA/ds = sin - C cos - P_x dC/ds,
+ * and dw = C dC / w.
+ */
+static void fan_ray(const double *X, int N, int B, double D, double theta,
+                    double delta, int b, double *val, double *d_theta,
+                    double *d_delta)
+{
+    const double c = cos(theta), sn = sin(theta);
+    const double h = 0.5 * (N - 1);
+    const double s = (b - 0.5 * (B - 1)) + delta;
+    const double rx = s * c - D * sn, ry = s * sn + D * c;
+    const double px = s * c, py = s * sn;
+    const double dpx = -s * sn, dpy = s * c; /* dP_b/dtheta */
+    double sum = 0.0, st = 0.0, sd = 0.0;
+    double C, A, w, dC, dA, dw, dCs, dAs, dws;
+
+    if (fabs(rx) <= fabs(ry)) {
+        /* one sample per image row */
+        C = rx / ry;
+        A = px - py * C;
+        w = sqrt(1.0 + C * C);
+        dC = -(1.0 + C * C);
+        dA = dpx - C * dpy - py * dC;
+        dCs = (c * ry - sn * rx) / (ry * ry);
+        dAs = c - C * sn - py * dCs;
+        for (int i = 0; i < N; i++) {
+            const double y = h - i;
+            const double u = A + C * y + h;
+            const double u0 = floor(u);
+            const int j0 = (int)u0;
+            const double f = u - u0;
+            const double v0 = pixel(X, N, i, j0);
+            const double v1 = pixel(X, N, i, j0 + 1);
+            const double slope = v1 - v0;
+            sum += (1.0 - f) * v0 + f * v1;
+            st += slope * (dA + y * dC); /* du/dtheta */
+            sd += slope * (dAs + y * dCs); /* du/ds */
+        }
+    } else {
+        /* one sample per image column */
+        C = ry / rx;
+        A = py - px * C;
+        w = sqrt(1.0 + C * C);
+        dC = 1.0 + C * C;
+        dA = dpy - C * dpx - px * dC;
+        dCs = (sn * rx - c * ry) / (rx * rx);
+        dAs = sn - C * c - px * dCs;
+        for (int j = 0; j < N; j++) {
+            const double x = j - h;
+            const double t = h - (A + C * x);
+            const double t0 = floor(t);
+            const int i0 = (int)t0;
+            const double f = t - t0;
+            const double v0 = pixel(X, N, i0, j);
+            const double v1 = pixel(X, N, i0 + 1, j);
+            const double slope = v1 - v0;
+            sum += (1.0 - f) * v0 + f * v1;
+            st += slope * (-(dA + x * dC)); /* dt/dtheta */
+            sd += slope * (-(dAs + x * dCs)); /* dt/ds */
+        }
+    }
+    dw = C * dC / w;
+    dws = C * dCs / w;
+    *val = w * sum;
+    if (d_theta)
+        *d_theta = dw * sum + w * st;
+    if (d_delta)
+        *d_delta = dws * sum + w * sd;
+}
+
+/* Fan-beam Y[v*B + b] = (H(theta, delta) X)[v, b], source distance D. */
+void orc_fan_forward(int N, int B, int V, const int *fov, double D,
+                     const double *theta, const double *delta, const double *X,
+                     double *Y)
+{
+    for (int v = 0; v < V; v++) {
+        const double *Xv = frame_image(X, N, fov, v);
+        const double dl = delta ? delta[v] : 0.0;
+        for (int b = 0; b < B; b++)
+            fan_ray(Xv, N, B, D, theta[v], dl, b, &Y[(size_t)v * B + b], NULL,
+                    NULL);
+    }
+}
+
+/* Fan-beam X = H^T Y by scattering the interpolation weights of every ray. */
+void orc_fan_adjoint(int N, int B, int V, int n_frames, const int *fov,
+                     double D, const double *theta, const double *delta,
+                     const double *Y, double *X)
+{
+    memset(X, 0, sizeof(double) * (size_t)n_frames * N * N);
+    const double h = 0.5 * (N - 1);
+    for (int v = 0; v < V; v++) {
+        double *Xv = X + (size_t)(fov ? fov[v] : 0) * N * N;
+        const double c = cos(theta[v]), sn = sin(theta[v]);
+        const double dl = delta ? delta[v] : 0.0;
+        for (int b = 0; b < B; b++) {
+            const double yv = Y[(size_t)v * B + b];
+            const double s = (b - 0.5 * (B - 1)) + dl;
+            const double rx = s * c - D * sn, ry = s * sn + D * c;
+            const double px = s * c, py = s * sn;
+            if (fabs(rx) <= fabs(ry)) {
+                const double C = rx / ry, A = px - py * C;
+                const double w = sqrt(1.0 + C * C);
+                for (int i = 0; i < N; i++) {
+                    const double u = A + C * (h - i) + h;
+                    const double u0 = floor(u);
+                    const int j0 = (int)u0;
+                    const double f = u - u0;
+                    if (j0 >= 0 && j0 < N)
+                        Xv[(size_t)i * N + j0] += w * (1.0 - f) * yv;
+                    if (j0 + 1 >= 0 && j0 + 1 < N)
+                        Xv[(size_t)i * N + j0 + 1] += w * f * yv;
+                }
+            } else {
+                const double C = ry / rx, A = py - px * C;
+                const double w = sqrt(1.0 + C * C);
+                for (int j = 0; j < N; j++) {
+                    const double t = h - (A + C * (j - h));
+                    const double t0 = floor(t);
+                    const int i0 = (int)t0;
+                    const double f = t - t0;
+                    if (i0 >= 0 && i0 < N)
+                        Xv[(size_t)i0 * N + j] += w * (1.0 - f) * yv;
+                    if (i0 + 1 >= 0 && i0 + 1 < N)
+                        Xv[(size_t)(i0 + 1) * N + j] += w * f * yv;
+                }
+            }
+        }
+    }
+}
+
+/* Fan-beam per-sample derivatives (d/dtheta_v, d/ddelta_v of (HX)[v,b]). */
+void orc_fan_dsample(int N, int B, int V, const int *fov, double D,
+                     const double *theta, const double *delta, const double *X,
+                     double *Dth, double *Ddl)
+{
+    for (int v = 0; v < V; v++) {
+        const double *Xv = frame_image(X, N, fov, v);
+        const double dl = delta ? delta[v] : 0.0;
+        for (int b = 0; b < B; b++) {
+            double val, dt, dd;
+            fan_ray(Xv, N, B, D, theta[v], dl, b, &val, &dt, &dd);
+            if (Dth)
+                Dth[(size_t)v * B + b] = dt;
+            if (Ddl)
+                Ddl[(size_t)v * B + b] = dd;
+        }
+    }
+}
