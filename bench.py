@@ -463,6 +463,40 @@ def batched_frames(dev, steps, flush):
             "tuning": dict(zip(ct.TUNING_FIELDS, tuning)), "launch": "CUDA graph replay"}
 
 
+def fan_beam_step(dev, steps, flush):
+    """The headline step (H on an 8-image block, H^T on 8 sinograms, J dtheta,
+    J^T r) on the 256^2 / 180-view / 363-bin workload in fan-beam geometry
+    (source at 2N from the rotation centre), replayed from a CUDA graph; the
+    fan-beam kernels take only the images-per-lane shapes (kb) of the tuning."""
+    import torch
+    from paper_2605_06336_gb300 import ct, synth
+    w = synth.make_workload(WORKLOAD)
+    K = KBLOCK
+    D = 2.0 * w.N
+    op = ct.CTOperator(w.N, w.B, w.V, max_batch=K, dtype=torch.float32, source_distance=D)
+    rng = np.random.default_rng(6)
+    th = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
+    dth = torch.tensor(rng.standard_normal(w.V), dtype=torch.float64, device=dev)
+    X = torch.tensor(np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(K - 1, op.n))]),
+                     dtype=torch.float32, device=dev)
+    Ys = torch.tensor(rng.standard_normal((K, op.m)), dtype=torch.float32, device=dev)
+    Y, Xa = torch.empty_like(Ys), torch.empty_like(X)
+    dy = torch.empty(op.m, device=dev)
+    gt = torch.empty(w.V, dtype=torch.float64, device=dev)
+
+    def step():
+        ct.ct_forward(op.h, th, None, X, Y, K)
+        ct.ct_adjoint(op.h, th, None, Ys, Xa, K)
+        ct.ct_jac(op.h, th, None, X[0], dth, None, dy)
+        ct.ct_jacT(op.h, th, None, X[0], Ys[0], gt, None)
+
+    ms = graph_step_timing(op, step, steps, flush, None)
+    samples = w.V * w.B * (K + K + 1 + 1)
+    return {"workload": f"fan beam, source at {D:.0f} px: {w.N}x{w.N}, {w.V} views, {w.B} bins, Krylov block {K}",
+            "ms_per_step": ms, "value": samples / (ms * 1e-3) / 1e9, "unit": "GSamples/s",
+            "tuning": dict(zip(ct.TUNING_FIELDS, op.tuning)), "launch": "CUDA graph replay"}
+
+
 def cpu_baseline(w, seconds):
     import oracle
     g = oracle.Geometry(w.N, w.B, w.V)
@@ -670,6 +704,7 @@ def main():
     peaks, src = measured_peaks()
     solver = None
     frames = None
+    fan = None
     streaming = None
     dynamic = None
     varpro = None
@@ -680,6 +715,7 @@ def main():
         varpro["note"] = ("NL-RMM-GKS with the VarPro Gauss-Newton update on the compressed basis; compare "
                           "ms_per_outer_iter, final_rre and rel_angle_err with 'solver' (per-view AltMin update)")
         frames = batched_frames(dev, min(args.steps, 200), flush)
+        fan = fan_beam_step(dev, min(args.steps, 200), flush)
         streaming = streaming_c5(dev, args.stream_passes) if args.stream_passes > 0 else None
         wd = synth.make_workload("C4")
         dynamic = solver_comparison(wd, dev, wd.outer_iters, temporal=1)
@@ -722,6 +758,7 @@ def main():
         "cpu_baseline": cpu,
         "solver": solver,
         "batched_frames": frames,
+        "fan_beam": fan,
         "streaming": streaming,
         "dynamic_solver": dynamic,
         "varpro_solver": varpro,

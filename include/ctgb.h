@@ -66,6 +66,16 @@ typedef struct {
     int32_t max_batch;                /* largest batch any call will pass, >= 1 */
     int32_t use_offsets;              /* reserved: offsets are accepted whenever delta != NULL */
     int32_t precision;                /* 0 = float32 images/sinograms, 1 = float64 */
+    double source_distance;           /* 0: parallel beam.  > 0: fan beam (the geometry of the
+                                         paper's CT experiments, Sec. 6.2, whose distances it does not
+                                         give): point source at this distance (pixels) from the
+                                         rotation centre, flat detector rescaled to the line through
+                                         the centre, bin b centred at s_b = b - (B-1)/2 + delta_v on
+                                         it; ray (v,b) joins the source and s_b (cos, sin)(theta_v).
+                                         Must exceed 0.75 max(N, B).  Fan-beam handles run H, H^T,
+                                         J_theta, J_theta^T and the solvers; offsets delta are
+                                         accepted in H and H^T, their derivatives are not (ct_jac
+                                         with ddelta and ct_jacT with gdelta return CT_ERR_ARG). */
 } ct_geom;
 
 typedef struct ct_handle ct_handle;

@@ -4,6 +4,7 @@
 
 #include <cstdio>
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -46,6 +47,8 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_yp);
     cudaFree(h.d_partial);
     cudaFree(h.d_segpart);
+    cudaFree(h.d_rays);
+    h.d_rays = nullptr;
     h.d_views = nullptr;
     h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = nullptr;
     h.d_px = h.d_pt = h.d_yp = nullptr;
@@ -319,6 +322,12 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
     if (g->N < 2 || g->N > ctgb::kMaxN || g->B < 1 || g->n_views < 1 || g->n_frames < 1 || g->max_batch < 1 ||
         (g->precision != 0 && g->precision != 1))
         return CT_ERR_ARG;
+    // fan beam: the source must lie outside the disc that holds the image and
+    // the detector line (every ray then has a well-defined march axis)
+    if (!(g->source_distance == 0.0 ||
+          (g->source_distance > 0.0 && std::isfinite(g->source_distance) &&
+           g->source_distance > 0.75 * std::max((double)g->N, (double)g->B))))
+        return CT_ERR_ARG;
     std::vector<int> vpf;
     if (g->views_per_frame) {
         long long sum = 0;
@@ -346,6 +355,7 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
     h.nchunks = (h.B + ctgb::kChunk - 1) / ctgb::kChunk;
     h.Pp = h.N + 4;
     h.Pb = (h.B + 5) & ~1;  // B + 4 rounded up to even: sinogram pair rows start on 16-byte boundaries
+    h.fan_D = g->source_distance;
     int rc = CT_OK;
     do {
         cudaError_t e = cudaGetDevice(&h.device);
@@ -373,7 +383,9 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
                   cudaMalloc(&h.d_px, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_pt, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_yp, sino_pairs * pair_bytes) == cudaSuccess &&
-                  cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.V * h.nchunks) == cudaSuccess;
+                  cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.V * h.nchunks) == cudaSuccess &&
+                  (h.fan_D == 0.0 ||
+                   cudaMalloc(&h.d_rays, ctgb::fan_ray_bytes(h.precision) * (size_t)h.V * h.B) == cudaSuccess);
         if (!ok) {
             cudaGetLastError();
             rc = CT_ERR_OOM;
@@ -458,6 +470,7 @@ int ct_jac(ct_handle *H, const double *theta, const double *delta, const void *x
            const double *ddelta, void *dy)
 {
     if (!H || !theta || !x || !dtheta || !dy) return CT_ERR_ARG;
+    if (H->h.fan_D > 0.0 && ddelta) return CT_ERR_ARG;  // fan beam: angle derivatives only
     H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jac<double>(H->h, theta, delta, x, dtheta, ddelta, dy)
                           : do_jac<float>(H->h, theta, delta, x, dtheta, ddelta, dy);
@@ -467,6 +480,7 @@ int ct_jacT(ct_handle *H, const double *theta, const double *delta, const void *
             double *gdelta)
 {
     if (!H || !theta || !x || !r || !gtheta) return CT_ERR_ARG;
+    if (H->h.fan_D > 0.0 && gdelta) return CT_ERR_ARG;  // fan beam: angle derivatives only
     H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jacT<double>(H->h, theta, delta, x, r, gtheta, gdelta)
                           : do_jacT<float>(H->h, theta, delta, x, r, gtheta, gdelta);

@@ -1,0 +1,387 @@
+// Fan-beam form of the Joseph operator (sm_103a).
+//
+// Geometry (the fan-beam CT of Sec. 6.2; the paper gives no distances, so
+// they are a reading): a point source at distance D from the rotation
+// centre and a flat detector rescaled to the line through the centre, on
+// which bin b keeps the parallel-beam centre s_b = b - (B-1)/2 + delta_v.
+// With e = (cos, sin) and t = (-sin, cos), the source is S = -D t, bin b is
+// P_b = s_b e, and ray (v,b) has direction r = P_b - S = s_b e + D t.  As D
+// grows the rays become the parallel-beam rays.
+//
+// Every ray is marched like a parallel-beam ray, but with its own line: rows
+// when |r_x| <= |r_y| (x(y) = A + C y, C = r_x / r_y, A = P_x - P_y C),
+// columns otherwise (y(x) = A + C x, C = r_y / r_x, A = P_y - P_x C), weight
+// sqrt(1 + C^2).  In march coordinates q(r) = q_h + (r - h) qr with
+// q_h = h + A (rows) or h - A (columns), qr = -C, carried in the same 64-bit
+// fixed point as the parallel-beam lines.  The geometry turns rigidly with
+// theta (dr/dtheta = (-r_y, r_x), dP_b/dtheta = s_b t), so
+// dq/dtheta = g0 + r gr with gr = -dC/dtheta, g0 = +-dA/dtheta + h dC/dtheta,
+// and dw/dtheta = C dC/dtheta / w.
+//
+//   k_fan_rays   per-ray table (fixed-point line, weight, derivative
+//                constants, march range) from the view table
+//   k_ray_fan    one warp per 32 bins of one view: forward (KB images),
+//                JVP, VJP and Gauss-Newton terms, each lane on its own line
+//   k_adj_fan    exact transpose in gather form: a pixel takes, per view,
+//                the rays whose fixed-point sample at its row (row-marched
+//                rays) or column (column-marched rays) falls in its
+//                interpolation cell; the candidates come from the projective
+//                inverse of the pixel's neighbourhood and are then tested
+//                with the very values the forward uses, so the matrix
+//                entries are those of the forward.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "ct_device.cuh"
+#include "ct_internal.cuh"
+
+namespace ctgb {
+namespace {
+
+template <typename T> struct __align__(16) FanRay {
+    long long Qc, Qh;  // q(r) = (Qc + (2r - (N-1)) Qh) / 2^48
+    T w, dw, g0, gr;   // weight, d w / d theta, dq/dtheta = g0 + r gr
+    float rlo, rhi;    // march indices with -1 < q < N lie in [rlo, rhi] (two indices of margin)
+    int mode, pad;     // 0: rows of X, 1: rows of X^T (columns)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg, int V, int B, int N, double D,
+                                                  FanRay<T> *__restrict__ out, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const double h = 0.5 * (N - 1);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)V * B;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(idx / B), b = (int)(idx - (long long)v * B);
+        const ViewGeo &g = vg[v];
+        const double c = g.c, sn = g.s, s = g.sb0d + (double)b;
+        const double rx = s * c - D * sn, ry = s * sn + D * c;
+        const double px = s * c, py = s * sn, dpx = -s * sn, dpy = s * c;
+        double C, A, dC, dA, qh, g0;
+        int mode;
+        if (fabs(rx) <= fabs(ry)) {
+            mode = 0;
+            C = rx / ry;
+            A = px - py * C;
+            dC = -(1.0 + C * C);
+            dA = dpx - C * dpy - py * dC;
+            qh = h + A;
+            g0 = dA + h * dC;
+        } else {
+            mode = 1;
+            C = ry / rx;
+            A = py - px * C;
+            dC = 1.0 + C * C;
+            dA = dpy - C * dpx - px * dC;
+            qh = h - A;
+            g0 = -dA + h * dC;
+        }
+        const double qr = -C;
+        const double w = sqrt(1.0 + C * C);
+        FanRay<T> R;
+        R.Qc = __double2ll_rn(qh * kFixScale);
+        R.Qh = __double2ll_rn(qr * 0.5 * kFixScale);
+        R.w = (T)w;
+        R.dw = (T)(C * dC / w);
+        R.g0 = (T)g0;
+        R.gr = (T)(-dC);
+        R.mode = mode;
+        R.pad = 0;
+        if (fabs(qr) < 1e-12) {
+            const bool in = qh > -1.0 && qh < (double)N;
+            R.rlo = in ? 0.0f : (float)N;
+            R.rhi = in ? (float)(N - 1) : -1.0f;
+        } else {
+            const double ra = h + (-1.0 - qh) / qr, rb = h + ((double)N - qh) / qr;
+            R.rlo = (float)fmin(fmax(fmin(ra, rb) - 2.0, 0.0), (double)N);
+            R.rhi = (float)fmax(fmin(fmax(ra, rb) + 2.0, (double)(N - 1)), -1.0);
+        }
+        out[idx] = R;
+    }
+}
+
+// One warp = 32 consecutive bins of one view (and one batch group of KB
+// images for the forward); four warps per CTA take four work items.
+template <typename T, int MODE, int KB>
+__global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *__restrict__ rays)
+{
+    using P2 = pair_t<T>;
+    constexpr int NACC = (MODE == kFwd) ? KB : 2;
+    const int lane = threadIdx.x & 31;
+    const int N = a.N;
+    const long long total = (long long)a.ngroups * a.V * a.nchunks;
+    if (a.skip && *a.skip) return;
+    for (long long item = blockIdx.x * 4LL + (threadIdx.x >> 5); item < total; item += gridDim.x * 4LL) {
+        const int chunk = (int)(item % a.nchunks);
+        const long long t = item / a.nchunks;
+        const int v = (int)(t % a.V);
+        const int grp = (int)(t / a.V);
+        if (MODE == kGn && a.view_mask && a.view_mask[v] == 0) continue;  // warp-uniform
+        const int b = chunk * kChunk + lane;
+        const bool active = b < a.B;
+        const FanRay<T> R = rays[(size_t)v * a.B + (active ? b : a.B - 1)];
+        const int k0 = a.kbase + grp * KB;
+        int rlo = active ? (int)floorf(R.rlo) : N, rhi = active ? (int)ceilf(R.rhi) : -1;
+        rlo = __reduce_min_sync(0xffffffffu, rlo);
+        rhi = __reduce_max_sync(0xffffffffu, rhi);
+        T acc[NACC];
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) acc[k] = T(0);
+        const P2 *img = (R.mode ? a.PT : a.PX) + (size_t)a.vg[v].frame * N * a.Pp + (size_t)k0 * a.pimg_stride + 2;
+        const long long dQ = 2 * R.Qh;
+        long long Q = R.Qc + (long long)(2 * rlo - (N - 1)) * R.Qh;
+        constexpr int U = 4;
+        int r = rlo;
+        if constexpr (MODE == kFwd) {
+            for (; r + U - 1 <= rhi; r += U) {
+                P2 p[U][KB];
+                T f[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long Qu = Q + (long long)u * dQ;
+                    const int cell = min(max(cell_of(Qu), -2), N);
+                    f[u] = frac_of(Qu, T());
+                    const P2 *row = img + (size_t)(r + u) * a.Pp + cell;
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) p[u][k] = __ldg(row + (size_t)k * a.pimg_stride);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const T omf = T(1) - f[u];
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) acc[k] = fma(omf, p[u][k].x, fma(f[u], p[u][k].y, acc[k]));
+                }
+                Q += (long long)U * dQ;
+            }
+            for (; r <= rhi; ++r, Q += dQ) {
+                const int cell = min(max(cell_of(Q), -2), N);
+                const T fr = frac_of(Q, T());
+                const T omf = T(1) - fr;
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    const P2 q = __ldg(img + (size_t)r * a.Pp + (size_t)k * a.pimg_stride + cell);
+                    acc[k] = fma(omf, q.x, fma(fr, q.y, acc[k]));
+                }
+            }
+        } else {
+            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta
+            for (; r <= rhi; ++r, Q += dQ) {
+                const int cell = min(max(cell_of(Q), -2), N);
+                const T fr = frac_of(Q, T());
+                const P2 q = __ldg(img + (size_t)r * a.Pp + cell);
+                const T d = q.y - q.x;
+                acc[0] += fma(fr, d, q.x);
+                acc[1] = fma(d, fma((T)r, R.gr, R.g0), acc[1]);
+            }
+        }
+        if constexpr (MODE == kFwd) {
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < KB; ++k) a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = R.w * acc[k];
+            }
+        } else {
+            const T jt = fma(R.dw, acc[0], R.w * acc[1]);
+            if constexpr (MODE == kJvp) {
+                if (active) a.Y[(size_t)v * a.B + b] = (T)a.dtheta[v] * jt;
+            } else if constexpr (MODE == kVjp) {
+                double pt = active ? (double)(a.R[(size_t)v * a.B + b] * jt) : 0.0;
+                pt = warp_sum(pt);
+                if (lane == 0) {
+                    double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                    p[0] = pt;
+                    p[1] = 0.0;
+                }
+            } else {  // kGn
+                double pg = 0.0, pj = 0.0, pf = 0.0;
+                if (active) {
+                    const T rr = R.w * acc[0] - a.R[(size_t)v * a.B + b];
+                    if (a.res) a.res[(size_t)v * a.B + b] = rr;
+                    pg = (double)rr * (double)jt;
+                    pj = (double)jt * (double)jt;
+                    pf = (double)rr * (double)rr;
+                }
+                pg = warp_sum(pg);
+                pj = warp_sum(pj);
+                pf = warp_sum(pf);
+                if (lane == 0) {
+                    double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                    p[0] = pg;
+                    p[1] = pj;
+                    p[2] = pf;
+                }
+            }
+        }
+    }
+}
+
+// Detector coordinate of the point (x, y) for view (c, sn): the bin centre
+// s of the ray through it, s = (x c + y sn) / (1 + (y c - x sn) / D).
+__device__ __forceinline__ float fan_s(float x, float y, float c, float sn, float iD)
+{
+    return (x * c + y * sn) / (1.0f + (y * c - x * sn) * iD);
+}
+
+struct AdjFanArgs {
+    const ViewGeo *vg;
+    const int *fstart, *fcount;
+    int N, B, F, tps, Pb, kbase, ngroups;
+    float iD;
+    long long ysino_stride, img_stride;
+    const int *skip;
+};
+
+// One CTA = one 16 x 16 pixel tile of one frame and KB sinograms; a thread
+// owns one pixel and sums the views of its frame in order.
+template <typename T, int KB>
+__global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *__restrict__ rays,
+                                                 const pair_t<T> *__restrict__ YP, T *__restrict__ X)
+{
+    const int tx = threadIdx.x & (kTile - 1), ty = threadIdx.x / kTile;
+    const int N = a.N;
+    const int tiles = a.tps * a.tps;
+    const long long total = (long long)a.ngroups * a.F * tiles;
+    const float h = 0.5f * (float)(N - 1);
+    if (a.skip && *a.skip) return;
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int tile = (int)(item % tiles);
+        const long long t2 = item / tiles;
+        const int f = (int)(t2 % a.F);
+        const int grp = (int)(t2 / a.F);
+        const int i = (tile / a.tps) * kTile + ty, j = (tile % a.tps) * kTile + tx;
+        const int k0 = a.kbase + grp * KB;
+        if (i >= N || j >= N) continue;  // no barriers below
+        const float x = (float)j - h, y = h - (float)i;
+        const long long Qrow = (long long)(2 * i - (N - 1)), Qcol = (long long)(2 * j - (N - 1));
+        T acc[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) acc[k] = T(0);
+        const int vs = a.fstart[f], vc = a.fcount[f];
+        for (int v = vs; v < vs + vc; ++v) {
+            const ViewGeo &g = a.vg[v];
+            const float c = (float)g.c, sn = (float)g.s, sb0 = (float)g.sb0d;
+            const FanRay<T> *rv = rays + (size_t)v * a.B;
+            const pair_t<T> *yv = YP + (size_t)k0 * a.ysino_stride + (size_t)v * a.Pb + 2;
+            // rays marched along rows that sample row i inside (x - 1, x + 1), then
+            // rays marched along columns that sample column j inside (y - 1, y + 1)
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                const float s1 = pass == 0 ? fan_s(x - 1.0f, y, c, sn, a.iD) : fan_s(x, y - 1.0f, c, sn, a.iD);
+                const float s2 = pass == 0 ? fan_s(x + 1.0f, y, c, sn, a.iD) : fan_s(x, y + 1.0f, c, sn, a.iD);
+                const int blo = max(0, (int)floorf(fminf(s1, s2) - sb0) - 1);
+                const int bhi = min(a.B - 1, (int)ceilf(fmaxf(s1, s2) - sb0) + 1);
+                const long long Qr = pass == 0 ? Qrow : Qcol;
+                const int me = pass == 0 ? j : i;
+                for (int b = blo; b <= bhi; ++b) {
+                    const FanRay<T> R = rv[b];
+                    if (R.mode != pass) continue;
+                    const long long Q = R.Qc + Qr * R.Qh;
+                    const int cell = cell_of(Q);
+                    if (cell != me && cell != me - 1) continue;
+                    const T fr = frac_of(Q, T());
+                    const T wt = R.w * (cell == me ? T(1) - fr : fr);
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) acc[k] = fma(wt, yv[(size_t)k * a.ysino_stride + b].x, acc[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k) X[(size_t)(k0 + k) * a.img_stride + (size_t)f * N * N + (size_t)i * N + j] = acc[k];
+    }
+}
+
+template <typename T, int MODE, int KB> cudaError_t run_fan(const Handle &h, const RayArgs<T> &a)
+{
+    auto kern = k_ray_fan<T, MODE, KB>;
+    const long long warps = (long long)a.ngroups * a.V * a.nchunks;
+    const int grid = persistent_grid(kern, 128, 0, (warps + 3) / 4, h.num_sms);
+    kern<<<grid, 128, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays);
+    return cudaGetLastError();
+}
+
+template <typename T, int KB> cudaError_t run_adj_fan(const Handle &h, const AdjFanArgs &a, T *X)
+{
+    auto kern = k_adj_fan<T, KB>;
+    const long long items = (long long)a.ngroups * a.F * a.tps * a.tps;
+    const int grid = persistent_grid(kern, 256, 0, items, h.num_sms);
+    kern<<<grid, 256, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const pair_t<T> *)h.d_yp, X);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t fan_ray_bytes(int precision) { return precision ? sizeof(FanRay<double>) : sizeof(FanRay<float>); }
+
+cudaError_t launch_fan_rays(const Handle &h, const int *skip)
+{
+    const long long n = (long long)h.V * h.B;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4LL * h.num_sms));
+    if (h.precision)
+        k_fan_rays<double><<<grid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.N, h.fan_D,
+                                                       (FanRay<double> *)h.d_rays, skip);
+    else
+        k_fan_rays<float><<<grid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.N, h.fan_D, (FanRay<float> *)h.d_rays,
+                                                      skip);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb)
+{
+    switch (mode) {
+    case kFwd:
+        switch (kb) {
+        case 1: return run_fan<T, kFwd, 1>(h, a);
+        case 2: return run_fan<T, kFwd, 2>(h, a);
+        case 4: return run_fan<T, kFwd, 4>(h, a);
+        default: return run_fan<T, kFwd, 8>(h, a);
+        }
+    case kJvp: return run_fan<T, kJvp, 1>(h, a);
+    case kVjp: return run_fan<T, kVjp, 1>(h, a);
+    default: return run_fan<T, kGn, 1>(h, a);
+    }
+}
+
+template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, const int *skip)
+{
+    AdjFanArgs a{};
+    a.vg = h.d_views;
+    a.fstart = h.d_fstart;
+    a.fcount = h.d_fcount;
+    a.N = h.N;
+    a.B = h.B;
+    a.F = h.F;
+    a.tps = (h.N + kTile - 1) / kTile;
+    a.Pb = h.Pb;
+    a.iD = (float)(1.0 / h.fan_D);
+    a.ysino_stride = (long long)h.V * h.Pb;
+    a.img_stride = (long long)h.F * h.N * h.N;
+    a.skip = skip;
+    int k = 0;
+    for (int width : {8, 4, 2, 1}) {
+        if (width > kb) continue;
+        const int groups = (batch - k) / width;
+        if (groups == 0) continue;
+        a.kbase = k;
+        a.ngroups = groups;
+        cudaError_t e;
+        switch (width) {
+        case 1: e = run_adj_fan<T, 1>(h, a, X); break;
+        case 2: e = run_adj_fan<T, 2>(h, a, X); break;
+        case 4: e = run_adj_fan<T, 4>(h, a, X); break;
+        default: e = run_adj_fan<T, 8>(h, a, X); break;
+        }
+        if (e != cudaSuccess) return e;
+        k += groups * width;
+    }
+    return cudaSuccess;
+}
+
+template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int);
+template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int);
+template cudaError_t launch_fan_adjoint<float>(const Handle &, float *, int, int, const int *);
+template cudaError_t launch_fan_adjoint<double>(const Handle &, double *, int, int, const int *);
+
+}  // namespace ctgb

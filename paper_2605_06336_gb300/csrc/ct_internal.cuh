@@ -99,6 +99,8 @@ struct Handle {
                                   // (images): 3 * max_batch * max(V * B, F * N * N) floats, allocated
                                   // when a shape with several CTAs per ray or tile is set
     int nchunks = 0;              // ceil(B / kChunk)
+    double fan_D = 0.0;           // > 0: fan beam with the source at this distance (ct_fan.cu); 0: parallel
+    void *d_rays = nullptr;       // fan beam: per-ray table, V * B entries
     // Batch sizes whose forward (adjoint) inputs are still laid out in the
     // handle from the last ct_forward (ct_adjoint) call: ct_forward_repeat
     // (ct_adjoint_repeat) may rerun the projection kernel alone.  Any other
@@ -147,5 +149,13 @@ cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdel
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval,
                       int split, int vw, int stage, const int *view_mask = nullptr, const int *skip = nullptr);
+
+// Fan beam (ct_fan.cu).  launch_fan_rays rebuilds the per-ray table from the
+// view table; every launcher that brings the view table up to date runs it
+// on a fan-beam handle.  The transpose of a fan-beam handle reads the pair
+// sinograms like the parallel-beam one.
+size_t fan_ray_bytes(int precision);
+cudaError_t launch_fan_rays(const Handle &h, const int *skip);
+template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, const int *skip);
 
 }  // namespace ctgb

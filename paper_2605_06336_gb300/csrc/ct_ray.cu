@@ -482,6 +482,7 @@ cudaError_t run_ray_split(const Handle &h, const RayArgs<T> &a, int split)
 template <typename T, int MODE, bool OFFS, int KB>
 cudaError_t run_ray_any(const Handle &h, const RayArgs<T> &a, int split, int stage)
 {
+    if (h.fan_D > 0.0) return run_fan_ray<T>(h, a, MODE, KB);
     if constexpr (std::is_same<T, float>::value) {
         if (stage > 0 && band_shape_ok(MODE, KB, a.VW, stage)) return run_ray_band(h, a, MODE, OFFS, KB, stage);
     }
@@ -537,6 +538,11 @@ template <typename K> cudaError_t allow_prep_smem(K kernel)
 cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta, const int *skip)
 {
     k_view_prep<<<1, 1024, 0, h.stream>>>(view_prep_args(h, theta, delta), skip);
+    if (h.fan_D > 0.0 && theta) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_fan_rays(h, skip);
+    }
     return cudaGetLastError();
 }
 
@@ -550,6 +556,11 @@ cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *s
     dim3 grid((h.Pp + 31) / 32 + (p.on ? 1 : 0), (h.N + 31) / 32, std::max(1, std::min(nimg, 65535)));
     k_pairs_img<T><<<grid, 256, prep_smem(p), h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp,
                                                           nimg, p, skip);
+    if (h.fan_D > 0.0 && theta) {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_fan_rays(h, skip);
+    }
     return cudaGetLastError();
 }
 
@@ -572,6 +583,11 @@ cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int 
     const long long blocks = std::min<long long>((total + threads - 1) / threads, (long long)h.num_sms * 16);
     k_pairs_sino<T><<<(int)std::max<long long>(1, blocks) + (p.on ? 1 : 0), threads, prep_smem(p), h.stream>>>(
         Y, (pair_t<T> *)h.d_yp, h.B, h.Pb, total, p, skip);
+    if (h.fan_D > 0.0 && theta) {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_fan_rays(h, skip);
+    }
     return cudaGetLastError();
 }
 
@@ -583,7 +599,8 @@ cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, 
     a.skip = skip;
     a.VW = vw;
     // band-staged FP32 march with `split` CTAs per ray: segment partials go to Y and d_segpart
-    const bool band = std::is_same<T, float>::value && stage > 0 && band_shape_ok(kFwd, 1, vw, stage);
+    const bool band = std::is_same<T, float>::value && stage > 0 && band_shape_ok(kFwd, 1, vw, stage) &&
+                      !(h.fan_D > 0.0);
     if (band && split > 1) {
         if (!h.d_segpart || split > 4) return cudaErrorInvalidValue;
         a.segs = split;

@@ -48,6 +48,7 @@ class ct_geom(ctypes.Structure):
         ("max_batch", ctypes.c_int32),
         ("use_offsets", ctypes.c_int32),
         ("precision", ctypes.c_int32),
+        ("source_distance", ctypes.c_double),
     ]
 
 
@@ -150,7 +151,7 @@ def _stream_ptr(stream=None):
 
 # --- C-named entry points (argument marshalling only) ----------------------
 
-def ct_init(N, B, n_views, views_per_frame=None, max_batch=1, precision=0, stream=None):
+def ct_init(N, B, n_views, views_per_frame=None, max_batch=1, precision=0, stream=None, source_distance=0.0):
     lib = load_library()
     g = ct_geom()
     g.N, g.B, g.n_views = int(N), int(B), int(n_views)
@@ -163,6 +164,7 @@ def ct_init(N, B, n_views, views_per_frame=None, max_batch=1, precision=0, strea
         g.n_frames = 1
         g.views_per_frame = None
     g.max_batch, g.use_offsets, g.precision = int(max_batch), 1, int(precision)
+    g.source_distance = float(source_distance or 0.0)
     h = ctypes.c_void_p()
     _check(lib.ct_init(ctypes.byref(g), _stream_ptr(stream), ctypes.byref(h)), "ct_init")
     return h
@@ -340,7 +342,10 @@ class CTOperator:
     angles/offsets are float64 CUDA tensors of length V.
     """
 
-    def __init__(self, N, B, n_views, views_per_frame=None, max_batch=8, dtype=torch.float32, device="cuda"):
+    def __init__(self, N, B, n_views, views_per_frame=None, max_batch=8, dtype=torch.float32, device="cuda",
+                 source_distance=None):
+        """source_distance: None for the parallel beam, else the fan-beam source
+        distance from the rotation centre in pixels (see ct_geom)."""
         if dtype not in (torch.float32, torch.float64):
             raise ValueError("dtype must be float32 or float64")
         self.N, self.B, self.V = int(N), int(B), int(n_views)
@@ -349,8 +354,10 @@ class CTOperator:
         self.max_batch = int(max_batch)
         self.dtype = dtype
         self.device = torch.device(device)
+        self.source_distance = source_distance
         with torch.cuda.device(self.device):
-            self.h = ct_init(N, B, n_views, views_per_frame, max_batch, 1 if dtype == torch.float64 else 0)
+            self.h = ct_init(N, B, n_views, views_per_frame, max_batch, 1 if dtype == torch.float64 else 0,
+                             source_distance=source_distance or 0.0)
 
     @property
     def n(self):

@@ -45,4 +45,8 @@ def test_init_rejects_bad_geometry_without_touching_the_gpu():
     assert lib.ct_init(ctypes.byref(g), None, ctypes.byref(h)) == ct.CT_ERR_ARG
     g.N, g.precision = 16, 7
     assert lib.ct_init(ctypes.byref(g), None, ctypes.byref(h)) == ct.CT_ERR_ARG
+    g.precision = 0
+    for D in (-1.0, 5.0, float("inf"), float("nan")):  # fan source inside the image disc, or not finite
+        g.source_distance = D
+        assert lib.ct_init(ctypes.byref(g), None, ctypes.byref(h)) == ct.CT_ERR_ARG
     assert lib.ct_forward(None, None, None, None, None, 1) == ct.CT_ERR_ARG
