@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--stream-only", action="store_true",
                     help="run only the streaming solve on the 2048^2 / 1440-view workload (--stream-passes passes) "
                          "and print its timing: the command the streaming profiles are taken with")
+    ap.add_argument("--fan-only", action="store_true",
+                    help="run only the fan-beam operator step (--steps replays) and print its timing")
     ap.add_argument("--stream-scale", type=float, default=1.0,
                     help="with --stream-only: shrink the streaming workload (image side, bins, views)")
     ap.add_argument("--tuning", default=None,
@@ -535,6 +537,11 @@ def main():
     from paper_2605_06336_gb300 import ct, synth
     ct.load_library()  # fails loudly if the CUDA library is missing
 
+    if args.fan_only:
+        import torch
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"fan_beam": fan_beam_step(dev, max(args.steps, 1), flush)}), flush=True)
+        return
     if args.stream_only:
         print(json.dumps({"streaming": streaming_c5(dev, max(args.stream_passes, 1), args.stream_scale)}), flush=True)
         return

@@ -48,7 +48,9 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_partial);
     cudaFree(h.d_segpart);
     cudaFree(h.d_rays);
+    cudaFree(h.d_fanview);
     h.d_rays = nullptr;
+    h.d_fanview = nullptr;
     h.d_views = nullptr;
     h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = nullptr;
     h.d_px = h.d_pt = h.d_yp = nullptr;
@@ -385,7 +387,8 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
                   cudaMalloc(&h.d_yp, sino_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.V * h.nchunks) == cudaSuccess &&
                   (h.fan_D == 0.0 ||
-                   cudaMalloc(&h.d_rays, ctgb::fan_ray_bytes(h.precision) * (size_t)h.V * h.B) == cudaSuccess);
+                   (cudaMalloc(&h.d_rays, ctgb::fan_ray_bytes(h.precision) * (size_t)h.V * h.B) == cudaSuccess &&
+                    cudaMalloc(&h.d_fanview, ctgb::fan_view_bytes() * (size_t)h.V) == cudaSuccess));
         if (!ok) {
             cudaGetLastError();
             rc = CT_ERR_OOM;
@@ -399,6 +402,10 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
         if (e == cudaSuccess) e = cudaMemset(h.d_px, 0, img_pairs * pair_bytes);
         if (e == cudaSuccess) e = cudaMemset(h.d_pt, 0, img_pairs * pair_bytes);
         if (e == cudaSuccess) e = cudaMemset(h.d_yp, 0, sino_pairs * pair_bytes);
+        // fan beam: generation 0 marks every ray and view entry as not built (views start at 1)
+        if (e == cudaSuccess && h.d_rays)
+            e = cudaMemset(h.d_rays, 0, ctgb::fan_ray_bytes(h.precision) * (size_t)h.V * h.B);
+        if (e == cudaSuccess && h.d_fanview) e = cudaMemset(h.d_fanview, 0, ctgb::fan_view_bytes() * (size_t)h.V);
         if (e != cudaSuccess) {
             rc = cuda_fail(e);
             break;

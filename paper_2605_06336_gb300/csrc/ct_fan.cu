@@ -19,7 +19,10 @@
 // and dw/dtheta = C dC/dtheta / w.
 //
 //   k_fan_rays   per-ray table (fixed-point line, weight, derivative
-//                constants, march range) from the view table
+//                constants, march range) from the view table, for the views
+//                rebuilt since (generation stamps)
+//   k_fan_views  per-view record of the transpose (FP32 constants, bin
+//                ranges of row- and column-marched rays)
 //   k_ray_fan    one warp per 32 bins of one view: forward (KB images),
 //                JVP, VJP and Gauss-Newton terms, each lane on its own line
 //   k_adj_fan    exact transpose in gather form: a pixel takes, per view,
@@ -45,7 +48,17 @@ template <typename T> struct __align__(16) FanRay {
     long long Qc, Qh;  // q(r) = (Qc + (2r - (N-1)) Qh) / 2^48
     T w, dw, g0, gr;   // weight, d w / d theta, dq/dtheta = g0 + r gr
     float rlo, rhi;    // march indices with -1 < q < N lie in [rlo, rhi] (two indices of margin)
-    int mode, pad;     // 0: rows of X, 1: rows of X^T (columns)
+    int mode;          // 0: rows of X, 1: rows of X^T (columns)
+    int gen;           // generation of the view record the entry was built from (0: never)
+};
+
+// Per view: FP32 constants of the transpose's candidate search and the bin
+// ranges of the two march axes (the ray direction turns monotonically with
+// s_b over a fan narrower than 90 degrees, so the axis changes at most once:
+// bins [0, split) march along mode0, bins [split, B) along the other axis).
+struct __align__(16) FanView {
+    float c, sn, sb0, iD;
+    int mode0, split, gen, pad;
 };
 
 template <typename T>
@@ -58,6 +71,7 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
          idx += (long long)gridDim.x * blockDim.x) {
         const int v = (int)(idx / B), b = (int)(idx - (long long)v * B);
         const ViewGeo &g = vg[v];
+        if (out[idx].gen == g.gen) continue;  // built from this view record already
         const double c = g.c, sn = g.s, s = g.sb0d + (double)b;
         const double rx = s * c - D * sn, ry = s * sn + D * c;
         const double px = s * c, py = s * sn, dpx = -s * sn, dpy = s * c;
@@ -90,7 +104,7 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
         R.g0 = (T)g0;
         R.gr = (T)(-dC);
         R.mode = mode;
-        R.pad = 0;
+        R.gen = g.gen;
         if (fabs(qr) < 1e-12) {
             const bool in = qh > -1.0 && qh < (double)N;
             R.rlo = in ? 0.0f : (float)N;
@@ -101,6 +115,44 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
             R.rhi = (float)fmax(fmin(fmax(ra, rb) + 2.0, (double)(N - 1)), -1.0);
         }
         out[idx] = R;
+    }
+}
+
+// One warp per view: the per-view record of the transpose, rebuilt when the
+// view record changed (after k_fan_rays has rebuilt its rays).
+template <typename T>
+__global__ void __launch_bounds__(256) k_fan_views(const ViewGeo *__restrict__ vg, int V, int B, double D,
+                                                   const FanRay<T> *__restrict__ rays, FanView *__restrict__ out,
+                                                   const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= V) return;  // warp-uniform
+    const ViewGeo &g = vg[v];
+    if (out[v].gen == g.gen) return;
+    const FanRay<T> *rv = rays + (size_t)v * B;
+    const int mode0 = rv[0].mode;
+    int split = B;
+    for (int base = 0; base < B; base += 32) {
+        const int b = base + lane;
+        const unsigned other = __ballot_sync(0xffffffffu, b < B && rv[b].mode != mode0);
+        if (other) {
+            split = base + __ffs(other) - 1;
+            break;
+        }
+    }
+    if (lane == 0) {
+        FanView f;
+        f.c = (float)g.c;
+        f.sn = (float)g.s;
+        f.sb0 = (float)g.sb0d;
+        f.iD = (float)(1.0 / D);
+        f.mode0 = mode0;
+        f.split = split;
+        f.gen = g.gen;
+        f.pad = 0;
+        out[v] = f;
     }
 }
 
@@ -219,17 +271,16 @@ __global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *
 }
 
 // Detector coordinate of the point (x, y) for view (c, sn): the bin centre
-// s of the ray through it, s = (x c + y sn) / (1 + (y c - x sn) / D).
+// s of the ray through it, s = (x c + y sn) / (1 + (y c - x sn) / D).  Fast
+// division: the candidate range keeps a margin of one bin.
 __device__ __forceinline__ float fan_s(float x, float y, float c, float sn, float iD)
 {
-    return (x * c + y * sn) / (1.0f + (y * c - x * sn) * iD);
+    return __fdividef(x * c + y * sn, 1.0f + (y * c - x * sn) * iD);
 }
 
 struct AdjFanArgs {
-    const ViewGeo *vg;
     const int *fstart, *fcount;
     int N, B, F, tps, Pb, kbase, ngroups;
-    float iD;
     long long ysino_stride, img_stride;
     const int *skip;
 };
@@ -238,6 +289,7 @@ struct AdjFanArgs {
 // owns one pixel and sums the views of its frame in order.
 template <typename T, int KB>
 __global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *__restrict__ rays,
+                                                 const FanView *__restrict__ views,
                                                  const pair_t<T> *__restrict__ YP, T *__restrict__ X)
 {
     const int tx = threadIdx.x & (kTile - 1), ty = threadIdx.x / kTile;
@@ -261,28 +313,28 @@ __global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *
         for (int k = 0; k < KB; ++k) acc[k] = T(0);
         const int vs = a.fstart[f], vc = a.fcount[f];
         for (int v = vs; v < vs + vc; ++v) {
-            const ViewGeo &g = a.vg[v];
-            const float c = (float)g.c, sn = (float)g.s, sb0 = (float)g.sb0d;
+            const FanView fv = views[v];
             const FanRay<T> *rv = rays + (size_t)v * a.B;
             const pair_t<T> *yv = YP + (size_t)k0 * a.ysino_stride + (size_t)v * a.Pb + 2;
             // rays marched along rows that sample row i inside (x - 1, x + 1), then
             // rays marched along columns that sample column j inside (y - 1, y + 1)
-#pragma unroll 1
+#pragma unroll
             for (int pass = 0; pass < 2; ++pass) {
-                const float s1 = pass == 0 ? fan_s(x - 1.0f, y, c, sn, a.iD) : fan_s(x, y - 1.0f, c, sn, a.iD);
-                const float s2 = pass == 0 ? fan_s(x + 1.0f, y, c, sn, a.iD) : fan_s(x, y + 1.0f, c, sn, a.iD);
-                const int blo = max(0, (int)floorf(fminf(s1, s2) - sb0) - 1);
-                const int bhi = min(a.B - 1, (int)ceilf(fmaxf(s1, s2) - sb0) + 1);
+                const int mlo = fv.mode0 == pass ? 0 : fv.split;
+                const int mhi = fv.mode0 == pass ? fv.split : a.B;  // bins [mlo, mhi) march along this axis
+                if (mlo >= mhi) continue;
+                const float s1 = pass == 0 ? fan_s(x - 1.0f, y, fv.c, fv.sn, fv.iD) : fan_s(x, y - 1.0f, fv.c, fv.sn, fv.iD);
+                const float s2 = pass == 0 ? fan_s(x + 1.0f, y, fv.c, fv.sn, fv.iD) : fan_s(x, y + 1.0f, fv.c, fv.sn, fv.iD);
+                const int blo = max(mlo, (int)floorf(fminf(s1, s2) - fv.sb0) - 1);
+                const int bhi = min(mhi - 1, (int)ceilf(fmaxf(s1, s2) - fv.sb0) + 1);
                 const long long Qr = pass == 0 ? Qrow : Qcol;
                 const int me = pass == 0 ? j : i;
                 for (int b = blo; b <= bhi; ++b) {
-                    const FanRay<T> R = rv[b];
-                    if (R.mode != pass) continue;
-                    const long long Q = R.Qc + Qr * R.Qh;
+                    const long long Q = rv[b].Qc + Qr * rv[b].Qh;
                     const int cell = cell_of(Q);
                     if (cell != me && cell != me - 1) continue;
                     const T fr = frac_of(Q, T());
-                    const T wt = R.w * (cell == me ? T(1) - fr : fr);
+                    const T wt = rv[b].w * (cell == me ? T(1) - fr : fr);
 #pragma unroll
                     for (int k = 0; k < KB; ++k) acc[k] = fma(wt, yv[(size_t)k * a.ysino_stride + b].x, acc[k]);
                 }
@@ -307,24 +359,33 @@ template <typename T, int KB> cudaError_t run_adj_fan(const Handle &h, const Adj
     auto kern = k_adj_fan<T, KB>;
     const long long items = (long long)a.ngroups * a.F * a.tps * a.tps;
     const int grid = persistent_grid(kern, 256, 0, items, h.num_sms);
-    kern<<<grid, 256, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const pair_t<T> *)h.d_yp, X);
+    kern<<<grid, 256, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const FanView *)h.d_fanview,
+                                     (const pair_t<T> *)h.d_yp, X);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t fan_ray_bytes(int precision) { return precision ? sizeof(FanRay<double>) : sizeof(FanRay<float>); }
+size_t fan_view_bytes() { return sizeof(FanView); }
 
 cudaError_t launch_fan_rays(const Handle &h, const int *skip)
 {
     const long long n = (long long)h.V * h.B;
     const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4LL * h.num_sms));
-    if (h.precision)
+    const int vgrid = (h.V + 7) / 8;
+    if (h.precision) {
         k_fan_rays<double><<<grid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.N, h.fan_D,
                                                        (FanRay<double> *)h.d_rays, skip);
-    else
+        k_fan_views<double><<<vgrid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.fan_D,
+                                                         (const FanRay<double> *)h.d_rays, (FanView *)h.d_fanview,
+                                                         skip);
+    } else {
         k_fan_rays<float><<<grid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.N, h.fan_D, (FanRay<float> *)h.d_rays,
                                                       skip);
+        k_fan_views<float><<<vgrid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.fan_D, (const FanRay<float> *)h.d_rays,
+                                                        (FanView *)h.d_fanview, skip);
+    }
     return cudaGetLastError();
 }
 
@@ -347,7 +408,6 @@ template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> 
 template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, const int *skip)
 {
     AdjFanArgs a{};
-    a.vg = h.d_views;
     a.fstart = h.d_fstart;
     a.fcount = h.d_fcount;
     a.N = h.N;
@@ -355,7 +415,6 @@ template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int 
     a.F = h.F;
     a.tps = (h.N + kTile - 1) / kTile;
     a.Pb = h.Pb;
-    a.iD = (float)(1.0 / h.fan_D);
     a.ysino_stride = (long long)h.V * h.Pb;
     a.img_stride = (long long)h.F * h.N * h.N;
     a.skip = skip;

@@ -60,6 +60,7 @@ struct __align__(16) ViewGeo {
     int frame;
     int flags;
     int n0;                // integer part of the bin-centre offset -(B-1)/2 + delta
+    int gen;               // incremented at every rebuild (tables derived per view compare it)
 };
 
 // Launch shapes.  kb: images (or sinograms) per lane; split: warps sharing
@@ -101,6 +102,7 @@ struct Handle {
     int nchunks = 0;              // ceil(B / kChunk)
     double fan_D = 0.0;           // > 0: fan beam with the source at this distance (ct_fan.cu); 0: parallel
     void *d_rays = nullptr;       // fan beam: per-ray table, V * B entries
+    void *d_fanview = nullptr;    // fan beam: per-view FP32 constants and march-axis bin ranges
     // Batch sizes whose forward (adjoint) inputs are still laid out in the
     // handle from the last ct_forward (ct_adjoint) call: ct_forward_repeat
     // (ct_adjoint_repeat) may rerun the projection kernel alone.  Any other
@@ -155,6 +157,7 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
 // on a fan-beam handle.  The transpose of a fan-beam handle reads the pair
 // sinograms like the parallel-beam one.
 size_t fan_ray_bytes(int precision);
+size_t fan_view_bytes();
 cudaError_t launch_fan_rays(const Handle &h, const int *skip);
 template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, const int *skip);
 

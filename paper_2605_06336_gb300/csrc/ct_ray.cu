@@ -108,6 +108,7 @@ __device__ bool view_setup_one(int v, const double *__restrict__ theta, const do
     g.th = th_in;
     g.dl = dl_in;
     g.frame = fov ? fov[v] : 0;
+    g.gen = gp->gen + 1;
     *gp = g;
     return true;
 }
