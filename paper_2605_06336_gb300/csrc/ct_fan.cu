@@ -23,8 +23,9 @@
 //                rebuilt since (generation stamps)
 //   k_fan_views  per-view record of the transpose (FP32 constants, bin
 //                ranges of row- and column-marched rays)
-//   k_ray_fan    one warp per 32 bins of one view: forward (KB images),
-//                JVP, VJP and Gauss-Newton terms, each lane on its own line
+//   k_ray_fan    SPLIT warps (row segments) per 32 bins of one view: forward
+//                (KB images), JVP, VJP and Gauss-Newton terms, each lane on
+//                its own line
 //   k_adj_fan    exact transpose in gather form: a pixel takes, per view,
 //                the rays whose fixed-point sample at its row (row-marched
 //                rays) or column (column-marched rays) falls in its
@@ -156,23 +157,27 @@ __global__ void __launch_bounds__(256) k_fan_views(const ViewGeo *__restrict__ v
     }
 }
 
-// One warp = 32 consecutive bins of one view (and one batch group of KB
-// images for the forward); four warps per CTA take four work items.
-template <typename T, int MODE, int KB>
-__global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *__restrict__ rays)
+// One CTA = SPLIT warps on one work item: 32 consecutive bins of one view
+// (and one batch group of KB images for the forward).  The warps march
+// consecutive segments of the warp-union row range; their sums are added in
+// segment order in shared memory and warp 0 writes the result.
+template <typename T, int MODE, int KB, int SPLIT>
+__global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanRay<T> *__restrict__ rays)
 {
     using P2 = pair_t<T>;
     constexpr int NACC = (MODE == kFwd) ? KB : 2;
+    __shared__ T red[SPLIT > 1 ? SPLIT : 1][NACC][32];
     const int lane = threadIdx.x & 31;
+    const int seg = threadIdx.x >> 5;
     const int N = a.N;
     const long long total = (long long)a.ngroups * a.V * a.nchunks;
     if (a.skip && *a.skip) return;
-    for (long long item = blockIdx.x * 4LL + (threadIdx.x >> 5); item < total; item += gridDim.x * 4LL) {
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {  // CTA-uniform
         const int chunk = (int)(item % a.nchunks);
         const long long t = item / a.nchunks;
         const int v = (int)(t % a.V);
         const int grp = (int)(t / a.V);
-        if (MODE == kGn && a.view_mask && a.view_mask[v] == 0) continue;  // warp-uniform
+        if (MODE == kGn && a.view_mask && a.view_mask[v] == 0) continue;  // CTA-uniform
         const int b = chunk * kChunk + lane;
         const bool active = b < a.B;
         const FanRay<T> R = rays[(size_t)v * a.B + (active ? b : a.B - 1)];
@@ -180,16 +185,18 @@ __global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *
         int rlo = active ? (int)floorf(R.rlo) : N, rhi = active ? (int)ceilf(R.rhi) : -1;
         rlo = __reduce_min_sync(0xffffffffu, rlo);
         rhi = __reduce_max_sync(0xffffffffu, rhi);
+        const int per = rhi >= rlo ? (rhi - rlo + SPLIT) / SPLIT : 0;
+        const int r0 = rlo + seg * per, r1 = min(rhi, r0 + per - 1);
         T acc[NACC];
 #pragma unroll
         for (int k = 0; k < NACC; ++k) acc[k] = T(0);
         const P2 *img = (R.mode ? a.PT : a.PX) + (size_t)a.vg[v].frame * N * a.Pp + (size_t)k0 * a.pimg_stride + 2;
         const long long dQ = 2 * R.Qh;
-        long long Q = R.Qc + (long long)(2 * rlo - (N - 1)) * R.Qh;
+        long long Q = R.Qc + (long long)(2 * r0 - (N - 1)) * R.Qh;
         constexpr int U = 4;
-        int r = rlo;
+        int r = r0;
         if constexpr (MODE == kFwd) {
-            for (; r + U - 1 <= rhi; r += U) {
+            for (; r + U - 1 <= r1; r += U) {
                 P2 p[U][KB];
                 T f[U];
 #pragma unroll
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *
                 }
                 Q += (long long)U * dQ;
             }
-            for (; r <= rhi; ++r, Q += dQ) {
+            for (; r <= r1; ++r, Q += dQ) {
                 const int cell = min(max(cell_of(Q), -2), N);
                 const T fr = frac_of(Q, T());
                 const T omf = T(1) - fr;
@@ -220,8 +227,27 @@ __global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *
                 }
             }
         } else {
-            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta
-            for (; r <= rhi; ++r, Q += dQ) {
+            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta;
+            // rows in blocks of U whose loads are all issued first
+            for (; r + U - 1 <= r1; r += U) {
+                P2 p[U];
+                T f[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long Qu = Q + (long long)u * dQ;
+                    const int cell = min(max(cell_of(Qu), -2), N);
+                    f[u] = frac_of(Qu, T());
+                    p[u] = __ldg(img + (size_t)(r + u) * a.Pp + cell);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const T d = p[u].y - p[u].x;
+                    acc[0] += fma(f[u], d, p[u].x);
+                    acc[1] = fma(d, fma((T)(r + u), R.gr, R.g0), acc[1]);
+                }
+                Q += (long long)U * dQ;
+            }
+            for (; r <= r1; ++r, Q += dQ) {
                 const int cell = min(max(cell_of(Q), -2), N);
                 const T fr = frac_of(Q, T());
                 const P2 q = __ldg(img + (size_t)r * a.Pp + cell);
@@ -230,49 +256,67 @@ __global__ void __launch_bounds__(128) k_ray_fan(RayArgs<T> a, const FanRay<T> *
                 acc[1] = fma(d, fma((T)r, R.gr, R.g0), acc[1]);
             }
         }
-        if constexpr (MODE == kFwd) {
-            if (active) {
+        if constexpr (SPLIT > 1) {
 #pragma unroll
-                for (int k = 0; k < KB; ++k) a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = R.w * acc[k];
-            }
-        } else {
-            const T jt = fma(R.dw, acc[0], R.w * acc[1]);
-            if constexpr (MODE == kJvp) {
-                if (active) a.Y[(size_t)v * a.B + b] = (T)a.dtheta[v] * jt;
-            } else if constexpr (MODE == kVjp) {
-                double pt = active ? (double)(a.R[(size_t)v * a.B + b] * jt) : 0.0;
-                pt = warp_sum(pt);
-                if (lane == 0) {
-                    double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
-                    p[0] = pt;
-                    p[1] = 0.0;
-                }
-            } else {  // kGn
-                double pg = 0.0, pj = 0.0, pf = 0.0;
-                if (active) {
-                    const T rr = R.w * acc[0] - a.R[(size_t)v * a.B + b];
-                    if (a.res) a.res[(size_t)v * a.B + b] = rr;
-                    pg = (double)rr * (double)jt;
-                    pj = (double)jt * (double)jt;
-                    pf = (double)rr * (double)rr;
-                }
-                pg = warp_sum(pg);
-                pj = warp_sum(pj);
-                pf = warp_sum(pf);
-                if (lane == 0) {
-                    double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
-                    p[0] = pg;
-                    p[1] = pj;
-                    p[2] = pf;
+            for (int k = 0; k < NACC; ++k) red[seg][k][lane] = acc[k];
+            __syncthreads();
+            if (seg == 0) {
+#pragma unroll
+                for (int k = 0; k < NACC; ++k) {
+                    T sum = red[0][k][lane];
+#pragma unroll
+                    for (int q = 1; q < SPLIT; ++q) sum += red[q][k][lane];
+                    acc[k] = sum;
                 }
             }
         }
+        if (seg == 0) {
+            if constexpr (MODE == kFwd) {
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < KB; ++k)
+                        a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = R.w * acc[k];
+                }
+            } else {
+                const T jt = fma(R.dw, acc[0], R.w * acc[1]);
+                if constexpr (MODE == kJvp) {
+                    if (active) a.Y[(size_t)v * a.B + b] = (T)a.dtheta[v] * jt;
+                } else if constexpr (MODE == kVjp) {
+                    double pt = active ? (double)(a.R[(size_t)v * a.B + b] * jt) : 0.0;
+                    pt = warp_sum(pt);
+                    if (lane == 0) {
+                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                        p[0] = pt;
+                        p[1] = 0.0;
+                    }
+                } else {  // kGn
+                    double pg = 0.0, pj = 0.0, pf = 0.0;
+                    if (active) {
+                        const T rr = R.w * acc[0] - a.R[(size_t)v * a.B + b];
+                        if (a.res) a.res[(size_t)v * a.B + b] = rr;
+                        pg = (double)rr * (double)jt;
+                        pj = (double)jt * (double)jt;
+                        pf = (double)rr * (double)rr;
+                    }
+                    pg = warp_sum(pg);
+                    pj = warp_sum(pj);
+                    pf = warp_sum(pf);
+                    if (lane == 0) {
+                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                        p[0] = pg;
+                        p[1] = pj;
+                        p[2] = pf;
+                    }
+                }
+            }
+        }
+        if constexpr (SPLIT > 1) __syncthreads();  // red[] is reused by the next item
     }
 }
 
 // Detector coordinate of the point (x, y) for view (c, sn): the bin centre
 // s of the ray through it, s = (x c + y sn) / (1 + (y c - x sn) / D).  Fast
-// division: the candidate range keeps a margin of one bin.
+// division: the candidate range keeps a margin of 0.05 bins.
 __device__ __forceinline__ float fan_s(float x, float y, float c, float sn, float iD)
 {
     return __fdividef(x * c + y * sn, 1.0f + (y * c - x * sn) * iD);
@@ -325,8 +369,9 @@ __global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *
                 if (mlo >= mhi) continue;
                 const float s1 = pass == 0 ? fan_s(x - 1.0f, y, fv.c, fv.sn, fv.iD) : fan_s(x, y - 1.0f, fv.c, fv.sn, fv.iD);
                 const float s2 = pass == 0 ? fan_s(x + 1.0f, y, fv.c, fv.sn, fv.iD) : fan_s(x, y + 1.0f, fv.c, fv.sn, fv.iD);
-                const int blo = max(mlo, (int)floorf(fminf(s1, s2) - fv.sb0) - 1);
-                const int bhi = min(mhi - 1, (int)ceilf(fmaxf(s1, s2) - fv.sb0) + 1);
+                // margin 0.05 bins: the FP32 detector coordinates are off by < 0.01 bins for N <= 4096
+                const int blo = max(mlo, (int)floorf(fminf(s1, s2) - fv.sb0 - 0.05f));
+                const int bhi = min(mhi - 1, (int)ceilf(fmaxf(s1, s2) - fv.sb0 + 0.05f));
                 const long long Qr = pass == 0 ? Qrow : Qcol;
                 const int me = pass == 0 ? j : i;
                 for (int b = blo; b <= bhi; ++b) {
@@ -345,13 +390,22 @@ __global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *
     }
 }
 
-template <typename T, int MODE, int KB> cudaError_t run_fan(const Handle &h, const RayArgs<T> &a)
+template <typename T, int MODE, int KB, int SPLIT> cudaError_t run_fan(const Handle &h, const RayArgs<T> &a)
 {
-    auto kern = k_ray_fan<T, MODE, KB>;
-    const long long warps = (long long)a.ngroups * a.V * a.nchunks;
-    const int grid = persistent_grid(kern, 128, 0, (warps + 3) / 4, h.num_sms);
-    kern<<<grid, 128, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays);
+    auto kern = k_ray_fan<T, MODE, KB, SPLIT>;
+    const long long items = (long long)a.ngroups * a.V * a.nchunks;
+    const int grid = persistent_grid(kern, 32 * SPLIT, 0, items, h.num_sms);
+    kern<<<grid, 32 * SPLIT, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays);
     return cudaGetLastError();
+}
+
+template <typename T, int MODE, int KB> cudaError_t run_fan_split(const Handle &h, const RayArgs<T> &a, int split)
+{
+    switch (split) {
+    case 1: return run_fan<T, MODE, KB, 1>(h, a);
+    case 2: return run_fan<T, MODE, KB, 2>(h, a);
+    default: return run_fan<T, MODE, KB, 4>(h, a);
+    }
 }
 
 template <typename T, int KB> cudaError_t run_adj_fan(const Handle &h, const AdjFanArgs &a, T *X)
@@ -389,19 +443,20 @@ cudaError_t launch_fan_rays(const Handle &h, const int *skip)
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb)
+// split: warps per work item (row segments), 1, 2 or 4 (larger values take 4)
+template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb, int split)
 {
     switch (mode) {
     case kFwd:
         switch (kb) {
-        case 1: return run_fan<T, kFwd, 1>(h, a);
-        case 2: return run_fan<T, kFwd, 2>(h, a);
-        case 4: return run_fan<T, kFwd, 4>(h, a);
-        default: return run_fan<T, kFwd, 8>(h, a);
+        case 1: return run_fan_split<T, kFwd, 1>(h, a, split);
+        case 2: return run_fan_split<T, kFwd, 2>(h, a, split);
+        case 4: return run_fan_split<T, kFwd, 4>(h, a, split);
+        default: return run_fan_split<T, kFwd, 8>(h, a, split);
         }
-    case kJvp: return run_fan<T, kJvp, 1>(h, a);
-    case kVjp: return run_fan<T, kVjp, 1>(h, a);
-    default: return run_fan<T, kGn, 1>(h, a);
+    case kJvp: return run_fan_split<T, kJvp, 1>(h, a, split);
+    case kVjp: return run_fan_split<T, kVjp, 1>(h, a, split);
+    default: return run_fan_split<T, kGn, 1>(h, a, split);
     }
 }
 
@@ -438,8 +493,8 @@ template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int 
     return cudaSuccess;
 }
 
-template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int);
-template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int);
+template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int, int);
+template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int, int);
 template cudaError_t launch_fan_adjoint<float>(const Handle &, float *, int, int, const int *);
 template cudaError_t launch_fan_adjoint<double>(const Handle &, double *, int, int, const int *);
 
