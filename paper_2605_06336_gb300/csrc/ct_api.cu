@@ -130,6 +130,12 @@ void default_tuning(ctgb::Handle &h)
     h.tune.der_split = rays >= 32LL * h.num_sms ? 2 : 4;
     h.tune.fwd_vw = 2;
     h.tune.der_vw = 2;
+    if (h.fan_D > 0.0) {
+        // fan-beam transpose: one candidate search per pixel and view serves
+        // every sinogram of a thread; two view groups per pixel keep the warps up
+        h.tune.adj_kb = kb;
+        h.tune.adj_split = 2;
+    }
 }
 
 // Time one configuration: median over `reps` launches issued back to back

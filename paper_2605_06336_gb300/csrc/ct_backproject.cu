@@ -182,7 +182,7 @@ cudaError_t run_adj_split(const Handle &h, const AdjArgs<T> &a, int split)
 template <typename T>
 cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, int stage, const int *skip)
 {
-    if (h.fan_D > 0.0) return launch_fan_adjoint<T>(h, X, batch, kb, skip);
+    if (h.fan_D > 0.0) return launch_fan_adjoint<T>(h, X, batch, kb, split, skip);
     if constexpr (std::is_same<T, float>::value) {
         if (stage > 0 && adj_band_ok(h, stage, split)) return launch_adjoint_band(h, X, batch, kb, split, stage, skip);
     }

@@ -329,34 +329,38 @@ struct AdjFanArgs {
     const int *skip;
 };
 
-// One CTA = one 16 x 16 pixel tile of one frame and KB sinograms; a thread
-// owns one pixel and sums the views of its frame in order.
-template <typename T, int KB>
-__global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *__restrict__ rays,
-                                                 const FanView *__restrict__ views,
-                                                 const pair_t<T> *__restrict__ YP, T *__restrict__ X)
+// One CTA = one 16 x 16 pixel tile of one frame and KB sinograms, SPLIT
+// thread groups of 256: group g of a pixel sums the views vs + g, vs + g +
+// SPLIT, ... of its frame in order; the groups' sums are added in group
+// order in shared memory.
+template <typename T, int KB, int SPLIT>
+__global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const FanRay<T> *__restrict__ rays,
+                                                         const FanView *__restrict__ views,
+                                                         const pair_t<T> *__restrict__ YP, T *__restrict__ X)
 {
-    const int tx = threadIdx.x & (kTile - 1), ty = threadIdx.x / kTile;
+    __shared__ T red[SPLIT > 1 ? SPLIT - 1 : 1][KB][256];
+    const int pix = threadIdx.x & 255, grp_v = threadIdx.x >> 8;
+    const int tx = pix & (kTile - 1), ty = pix / kTile;
     const int N = a.N;
     const int tiles = a.tps * a.tps;
     const long long total = (long long)a.ngroups * a.F * tiles;
     const float h = 0.5f * (float)(N - 1);
     if (a.skip && *a.skip) return;
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {  // CTA-uniform
         const int tile = (int)(item % tiles);
         const long long t2 = item / tiles;
         const int f = (int)(t2 % a.F);
         const int grp = (int)(t2 / a.F);
         const int i = (tile / a.tps) * kTile + ty, j = (tile % a.tps) * kTile + tx;
         const int k0 = a.kbase + grp * KB;
-        if (i >= N || j >= N) continue;  // no barriers below
+        const bool inside = i < N && j < N;
         const float x = (float)j - h, y = h - (float)i;
         const long long Qrow = (long long)(2 * i - (N - 1)), Qcol = (long long)(2 * j - (N - 1));
         T acc[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) acc[k] = T(0);
         const int vs = a.fstart[f], vc = a.fcount[f];
-        for (int v = vs; v < vs + vc; ++v) {
+        for (int v = vs + grp_v; inside && v < vs + vc; v += SPLIT) {
             const FanView fv = views[v];
             const FanRay<T> *rv = rays + (size_t)v * a.B;
             const pair_t<T> *yv = YP + (size_t)k0 * a.ysino_stride + (size_t)v * a.Pb + 2;
@@ -385,8 +389,25 @@ __global__ void __launch_bounds__(256) k_adj_fan(AdjFanArgs a, const FanRay<T> *
                 }
             }
         }
+        if constexpr (SPLIT > 1) {
+            if (grp_v > 0) {
 #pragma unroll
-        for (int k = 0; k < KB; ++k) X[(size_t)(k0 + k) * a.img_stride + (size_t)f * N * N + (size_t)i * N + j] = acc[k];
+                for (int k = 0; k < KB; ++k) red[grp_v - 1][k][pix] = acc[k];
+            }
+            __syncthreads();
+            if (grp_v == 0) {
+#pragma unroll
+                for (int k = 0; k < KB; ++k)
+#pragma unroll
+                    for (int q = 0; q < SPLIT - 1; ++q) acc[k] += red[q][k][pix];
+            }
+        }
+        if (grp_v == 0 && inside) {
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                X[(size_t)(k0 + k) * a.img_stride + (size_t)f * N * N + (size_t)i * N + j] = acc[k];
+        }
+        if constexpr (SPLIT > 1) __syncthreads();  // red[] is reused by the next item
     }
 }
 
@@ -408,14 +429,20 @@ template <typename T, int MODE, int KB> cudaError_t run_fan_split(const Handle &
     }
 }
 
-template <typename T, int KB> cudaError_t run_adj_fan(const Handle &h, const AdjFanArgs &a, T *X)
+template <typename T, int KB, int SPLIT> cudaError_t run_adj_fan(const Handle &h, const AdjFanArgs &a, T *X)
 {
-    auto kern = k_adj_fan<T, KB>;
+    auto kern = k_adj_fan<T, KB, SPLIT>;
     const long long items = (long long)a.ngroups * a.F * a.tps * a.tps;
-    const int grid = persistent_grid(kern, 256, 0, items, h.num_sms);
-    kern<<<grid, 256, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const FanView *)h.d_fanview,
-                                     (const pair_t<T> *)h.d_yp, X);
+    const int grid = persistent_grid(kern, 256 * SPLIT, 0, items, h.num_sms);
+    kern<<<grid, 256 * SPLIT, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const FanView *)h.d_fanview,
+                                             (const pair_t<T> *)h.d_yp, X);
     return cudaGetLastError();
+}
+
+template <typename T, int KB> cudaError_t run_adj_fan_split(const Handle &h, const AdjFanArgs &a, T *X, int split)
+{
+    return split >= 4 ? run_adj_fan<T, KB, 4>(h, a, X)
+                      : (split >= 2 ? run_adj_fan<T, KB, 2>(h, a, X) : run_adj_fan<T, KB, 1>(h, a, X));
 }
 
 }  // namespace
@@ -460,7 +487,10 @@ template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> 
     }
 }
 
-template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, const int *skip)
+// kb: sinograms per thread (the candidate search of a pixel and view is
+// shared by them); split: thread groups per pixel (view subsets).
+template <typename T>
+cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip)
 {
     AdjFanArgs a{};
     a.fstart = h.d_fstart;
@@ -482,10 +512,10 @@ template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int 
         a.ngroups = groups;
         cudaError_t e;
         switch (width) {
-        case 1: e = run_adj_fan<T, 1>(h, a, X); break;
-        case 2: e = run_adj_fan<T, 2>(h, a, X); break;
-        case 4: e = run_adj_fan<T, 4>(h, a, X); break;
-        default: e = run_adj_fan<T, 8>(h, a, X); break;
+        case 1: e = run_adj_fan_split<T, 1>(h, a, X, split); break;
+        case 2: e = run_adj_fan_split<T, 2>(h, a, X, split); break;
+        case 4: e = run_adj_fan_split<T, 4>(h, a, X, split); break;
+        default: e = run_adj_fan_split<T, 8>(h, a, X, split); break;
         }
         if (e != cudaSuccess) return e;
         k += groups * width;
@@ -495,7 +525,7 @@ template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int 
 
 template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int, int);
 template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int, int);
-template cudaError_t launch_fan_adjoint<float>(const Handle &, float *, int, int, const int *);
-template cudaError_t launch_fan_adjoint<double>(const Handle &, double *, int, int, const int *);
+template cudaError_t launch_fan_adjoint<float>(const Handle &, float *, int, int, int, const int *);
+template cudaError_t launch_fan_adjoint<double>(const Handle &, double *, int, int, int, const int *);
 
 }  // namespace ctgb

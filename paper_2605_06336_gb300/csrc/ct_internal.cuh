@@ -159,6 +159,7 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
 size_t fan_ray_bytes(int precision);
 size_t fan_view_bytes();
 cudaError_t launch_fan_rays(const Handle &h, const int *skip);
-template <typename T> cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, const int *skip);
+template <typename T>
+cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip);
 
 }  // namespace ctgb
