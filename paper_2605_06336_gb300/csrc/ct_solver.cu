@@ -192,6 +192,8 @@ template <typename T> struct Solver {
         if constexpr (sizeof(T) == 4) {
             SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gram_rb_smem(kKMax, 3)));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGramPipeSmemMax));
         } else {
             SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gram_smem(kKMax, true)));
@@ -210,8 +212,13 @@ template <typename T> struct Solver {
     {
         const bool tm = o.temporal && h.F > 1;
         if constexpr (sizeof(T) == 4) {
-            k_gram_psi_rb<<<gram_blocks, kThreads, gram_rb_smem(k, tm ? 3 : 2), h.stream>>>(V, n, k, w, h.N, h.F,
-                                                                                       o.temporal, part_gram, stop);
+            const size_t pipe = gram_pipe_smem(k, tm ? 3 : 2);
+            if (pipe <= kGramPipeSmemMax)  // both raw buffers fit next to the edge block
+                k_gram_psi_pipe<<<gram_blocks, kThreads, pipe, h.stream>>>(V, n, k, w, h.N, h.F, o.temporal,
+                                                                            part_gram, stop);
+            else
+                k_gram_psi_rb<<<gram_blocks, kThreads, gram_rb_smem(k, tm ? 3 : 2), h.stream>>>(
+                    V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
         } else {
             k_gram_psi<T, 4><<<gram_blocks, kThreads, gram_smem(k, tm), h.stream>>>(V, n, k, w, h.N, h.F, o.temporal,
                                                                                  part_gram, stop);
@@ -228,10 +235,11 @@ template <typename T> struct Solver {
     // out[0..k) = A[:, 0..k)^T x  (+ out[k] = x2 . x when x2 != null)
     int dots_into(const T *A, long long len, int k, const T *x, const T *x2, double *out, const int *stop)
     {
-        k_dots<T><<<kRedBlocks, kThreads, 0, h.stream>>>(A, len, len, k, x, x2, part_dot, stop);
+        const int nblk = red_blocks(len);
+        k_dots<T><<<nblk, kThreads, 0, h.stream>>>(A, len, len, k, x, x2, part_dot, stop);
         const int kk = k + (x2 ? 1 : 0);
         k_dots_reduce<<<(kk + kDotsReduceWarps - 1) / kDotsReduceWarps, 32 * kDotsReduceWarps, 0, h.stream>>>(
-            part_dot, kRedBlocks, kk, out, stop);
+            part_dot, nblk, kk, out, stop);
         SV_CUDA(cudaGetLastError());
         return CT_OK;
     }
@@ -239,8 +247,9 @@ template <typename T> struct Solver {
     // norms3 of (a, b): {|a|^2, |a-b|^2, |b|^2}
     int norms3(const T *a, const T *bb, long long len, double *out, const int *stop)
     {
-        k_norms3<T><<<kRedBlocks, kThreads, 0, h.stream>>>(a, bb, len, part_n, stop);
-        k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, out, stop);
+        const int nblk = red_blocks(len);
+        k_norms3<T><<<nblk, kThreads, 0, h.stream>>>(a, bb, len, part_n, stop);
+        k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, nblk, out, stop);
         SV_CUDA(cudaGetLastError());
         return CT_OK;
     }
@@ -647,8 +656,8 @@ template <typename T> struct Solver {
         const int k_used = kc + steps_out - 1;
         SV_TRY(compress(k_used, kc));
         SV_TRY(param_update(kc));
-        k_norms3<double><<<kRedBlocks, kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
-        k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, norms, nullptr);
+        k_norms3<double><<<red_blocks(h.V), kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
+        k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, red_blocks(h.V), norms, nullptr);
         double dth3[3], lam_now[1];
         SV_TRY(read_doubles(norms, 3, dth3));
         SV_TRY(read_doubles(scal + kLam, 1, lam_now));
@@ -832,8 +841,8 @@ template <typename T> struct Solver {
                 scale(col(V, n, kc), n, 1.0 / std::sqrt(dr[0]));
                 kc += 1;
             }
-            k_norms3<double><<<kRedBlocks, kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
-            k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, kRedBlocks, norms, nullptr);
+            k_norms3<double><<<red_blocks(h.V), kThreads, 0, h.stream>>>(th_n, th_k, h.V, part_n, nullptr);
+            k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, red_blocks(h.V), norms, nullptr);
             double dth3[3];
             SV_TRY(read_doubles(norms, 3, dth3));
             double rre = -1.0;

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <type_traits>
+#include <algorithm>
 
 #include <cmath>
 
@@ -20,7 +21,14 @@ namespace ctgb {
 namespace solver {
 
 constexpr int kKMax = 64;       // largest basis the FP64 small algebra handles
-constexpr int kRedBlocks = 128;  // fixed partial-sum grid of the tall-skinny reductions
+constexpr int kRedBlocks = 608;  // largest partial-sum grid of the tall-skinny reductions (4 CTAs per SM of a GB300)
+// Partial-sum grid for vectors of length len: 128 CTAs up to half a million
+// elements, growing to kRedBlocks for the long image vectors (a fixed function
+// of the length, so the summation order is fixed too).
+inline int red_blocks(long long len)
+{
+    return (int)std::min<long long>(kRedBlocks, std::max<long long>(128, len / 4096));
+}
 
 // control words (int) and scalars (double) living on the device
 enum Ctl { kStop = 0, kStopNext, kSteps, kActive, kBreakdown, kCtlCount };
@@ -330,6 +338,188 @@ __global__ void __launch_bounds__(256) k_gram_psi_rb(const float *__restrict__ V
             }
         }
     }
+    if (t < P) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int a = 4 * bi + q / 4, b = 4 * bj + q % 4;
+            if (a <= b && b < k) part[(long long)blockIdx.x * kGramPairs + a * k - a * (a - 1) / 2 + (b - a)] = acc[q];
+        }
+    }
+}
+
+// Pipelined form of k_gram_psi_rb: the raw values a tile needs (rows
+// i0 .. i0 + 4 and columns j0 .. j0 + 32 of every basis column, the next
+// frame's rows with ANISO-TV, and the tile's weights) are copied to shared
+// memory with cp.async, the next tile's while the current tile builds its
+// edges and runs its products, so the tile loads no longer stall the CTA.
+// Same edges, blocks, phases and summation order as k_gram_psi_rb: the
+// results are bit-identical.
+constexpr int kRawRows = kRbRows + 1, kRawCols = 33;  // rows and columns of a tile's raw block
+constexpr size_t kGramPipeSmemMax = 200 * 1024;        // dynamic shared memory of the pipelined form
+inline int gram_raw_floats(int k, int epp)
+{
+    return k * (kRawRows * kRawCols + (epp == 3 ? kRbRows * 32 : 0)) + 3 * kRbPix;
+}
+inline size_t gram_pipe_smem(int k, int epp)
+{
+    return gram_rb_smem(k, epp) + 2 * (size_t)gram_raw_floats(k, epp) * sizeof(float);
+}
+
+__device__ __forceinline__ void cp_async4_zfill(float *smem, const float *gmem, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int bytes = valid ? 4 : 0;  // 0: the destination is zero-filled, the source is not read
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(256) k_gram_psi_pipe(const float *__restrict__ V, long long n, int k,
+                                                       const float *__restrict__ w, int N, int F, int temporal,
+                                                       double *__restrict__ part, const int *stop)
+{
+    if (stopped(stop)) return;
+    extern __shared__ float4 rb_smem[];
+    const int EPP = (temporal && F > 1) ? 3 : 2;
+    const int KP = 32 * ((k + 31) / 32);
+    const int NE = EPP * kRbPix;
+    float *E = reinterpret_cast<float *>(rb_smem);  // [NE][KP], swizzled 16-byte groups
+    float *red = E + (size_t)NE * KP;               // [256][16]
+    float *raw0 = red + 256 * 16;                   // two raw buffers
+    const int RAWC = k * kRawRows * kRawCols;        // per buffer: [k][5][33], then [k][4][32] (next frame), then weights
+    const int RAWT = EPP == 3 ? k * kRbRows * 32 : 0;
+    const int RAW = RAWC + RAWT + 3 * kRbPix;
+    const int kb = (k + 3) / 4;
+    const int P = kb * (kb + 1) / 2;
+    const int phases = max(1, min(8, 256 / P));
+    const int t = threadIdx.x;
+    const bool busy = t < P * phases;
+    const int p = t % P, ph = t / P;
+    int bi = 0, rem = p;
+    while (rem >= kb - bi) {
+        rem -= kb - bi;
+        ++bi;
+    }
+    const int bj = bi + rem;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    const int tiles_x = (N + 31) / 32, tiles_y = (N + kRbRows - 1) / kRbRows;
+    const int ntiles = tiles_x * tiles_y * F;
+    const long long nx = (long long)F * N * (N - 1);
+
+    // copies of tile tt into raw buffer dst
+    auto issue = [&](int tt, float *dst) {
+        const int tile = tt % (tiles_x * tiles_y);
+        const int f = tt / (tiles_x * tiles_y);
+        const int i0 = (tile / tiles_x) * kRbRows, j0 = (tile % tiles_x) * 32;
+        for (int idx = t; idx < RAWC; idx += 256) {
+            const int a = idx / (kRawRows * kRawCols), r = (idx / kRawCols) % kRawRows, c = idx % kRawCols;
+            const int gi = i0 + r, gj = j0 + c;
+            const bool ok = gi < N && gj < N;
+            const float *col = V + (long long)a * n + (long long)f * N * N;
+            cp_async4_zfill(dst + idx, ok ? col + (size_t)gi * N + gj : col, ok);
+        }
+        for (int idx = t; idx < RAWT; idx += 256) {  // the next frame's pixels of the tile
+            const int a = idx / (kRbRows * 32), r = (idx / 32) % kRbRows, c = idx % 32;
+            const int gi = i0 + r, gj = j0 + c;
+            const bool ok = f < F - 1 && gi < N && gj < N;
+            const float *col = V + (long long)a * n + (long long)(f + 1 < F ? f + 1 : f) * N * N;
+            cp_async4_zfill(dst + RAWC + idx, ok ? col + (size_t)gi * N + gj : col, ok);
+        }
+        for (int idx = t; idx < 3 * kRbPix; idx += 256) {  // weights of the right, down, next-frame edges
+            const int e = idx / kRbPix, pix = idx % kRbPix;
+            const int gi = i0 + pix / 32, gj = j0 + pix % 32;
+            bool ok;
+            long long off;
+            if (e == 0) {
+                ok = gi < N && gj < N - 1;
+                off = (long long)f * N * (N - 1) + (long long)gi * (N - 1) + gj;
+            } else if (e == 1) {
+                ok = gi < N - 1 && gj < N;
+                off = nx + (long long)f * (N - 1) * N + (long long)gi * N + gj;
+            } else {
+                ok = EPP == 3 && f < F - 1 && gi < N && gj < N;
+                off = 2 * nx + (long long)f * N * N + (long long)gi * N + gj;
+            }
+            cp_async4_zfill(dst + RAWC + RAWT + idx, ok ? w + off : w, ok);
+        }
+    };
+
+    int buf = 0;
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, raw0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const int nxt = tt + gridDim.x;
+        if (nxt < ntiles) issue(nxt, raw0 + (size_t)(buf ^ 1) * RAW);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // tile tt has landed
+        __syncthreads();  // ... for every thread; the previous tile is done with E and red
+        const float *rw = raw0 + (size_t)buf * RAW;
+        const float *rwt = rw + RAWC, *rww = rw + RAWC + RAWT;
+        const int tile = tt % (tiles_x * tiles_y);
+        const int f = tt / (tiles_x * tiles_y);
+        const int i0 = (tile / tiles_x) * kRbRows, j0 = (tile % tiles_x) * 32;
+        for (int idx = t; idx < kb * kRbPix; idx += 256) {
+            const int g = idx / kRbPix, pix = idx % kRbPix;
+            const int li = pix / 32, lj = pix % 32;
+            const int i = i0 + li, j = j0 + lj;
+            float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, et[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < N && j < N) {
+                const float sx = j < N - 1 ? sqrtf(rww[pix]) : 0.f;
+                const float sy = i < N - 1 ? sqrtf(rww[kRbPix + pix]) : 0.f;
+                const float st = (EPP == 3 && f < F - 1) ? sqrtf(rww[2 * kRbPix + pix]) : 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int a = 4 * g + c;
+                    if (a < k) {
+                        const float *ra = rw + (size_t)a * kRawRows * kRawCols;
+                        const float v0 = ra[li * kRawCols + lj];
+                        if (j < N - 1) ex[c] = (ra[li * kRawCols + lj + 1] - v0) * sx;
+                        if (i < N - 1) ey[c] = (ra[(li + 1) * kRawCols + lj] - v0) * sy;
+                        if (EPP == 3 && f < F - 1) et[c] = (rwt[(size_t)a * kRbRows * 32 + li * 32 + lj] - v0) * st;
+                    }
+                }
+            }
+            const int col = (4 * g) ^ ((pix & 7) << 2);
+            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix) * KP + col) = make_float4(ex[0], ex[1], ex[2], ex[3]);
+            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 1) * KP + col) =
+                make_float4(ey[0], ey[1], ey[2], ey[3]);
+            if (EPP == 3)
+                *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 2) * KP + col) =
+                    make_float4(et[0], et[1], et[2], et[3]);
+        }
+        __syncthreads();
+        if (busy) {
+            float sacc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) sacc[q] = 0.f;
+#pragma unroll 4
+            for (int e = ph; e < NE; e += phases) {
+                const int sw = ((e / EPP) & 7) << 2;
+                const float4 A = *reinterpret_cast<const float4 *>(E + (size_t)e * KP + ((4 * bi) ^ sw));
+                const float4 Bv = *reinterpret_cast<const float4 *>(E + (size_t)e * KP + ((4 * bj) ^ sw));
+                const float av[4] = {A.x, A.y, A.z, A.w}, bv[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) sacc[4 * r + c] = fmaf(av[r], bv[c], sacc[4 * r + c]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+                *reinterpret_cast<float4 *>(red + (size_t)t * 16 + q) =
+                    make_float4(sacc[q], sacc[q + 1], sacc[q + 2], sacc[q + 3]);
+        }
+        __syncthreads();
+        if (t < P) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                float v = 0.f;
+                for (int r = 0; r < phases; ++r) v += red[(size_t)(r * P + t) * 16 + q];
+                acc[q] += (double)v;
+            }
+        }
+        buf ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (t < P) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
