@@ -95,6 +95,8 @@ def parse():
                     help="run only the FP32 NL-RMM-GKS solve of the workload (--solver-iters outer iterations) "
                          "and print its timing: the command the solver's profiles are taken with")
     ap.add_argument("--varpro", action="store_true", help="with --solver-only: the VarPro parameter update")
+    ap.add_argument("--solver-workload", default=WORKLOAD, choices=["C1", "C2", "C3", "C4"],
+                    help="with --solver-only: the workload (C4: the 16-frame dynamic problem, with ANISO-TV)")
     ap.add_argument("--stream-only", action="store_true",
                     help="run only the streaming solve on the 2048^2 / 1440-view workload (--stream-passes passes) "
                          "and print its timing: the command the streaming profiles are taken with")
@@ -548,7 +550,11 @@ def main():
     w = synth.make_workload(WORKLOAD)
     if args.solver_only:
         tun = [int(x) for x in args.tuning.split(",")] if args.tuning else None
-        out = solver_only(w, dev, args.solver_iters, tun, varpro=int(args.varpro))
+        ws = synth.make_workload(args.solver_workload)
+        extra = {"varpro": int(args.varpro)}
+        if ws.F > 1:
+            extra["temporal"] = 1
+        out = solver_only(ws, dev, args.solver_iters, tun, **extra)
         print(json.dumps({"solver_only": out}), flush=True)
         return
     N, B, V, K = w.N, w.B, w.V, KBLOCK

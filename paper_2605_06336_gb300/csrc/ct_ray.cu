@@ -131,8 +131,8 @@ struct ViewPrep {
 };
 
 // The view-table step, run by one whole CTA; key: shared memory for
-// min(V, kOrderMaxV) doubles.
-__device__ void view_prep_block(const ViewPrep &p, double *key)
+// min(V, kOrderMaxV) 64-bit keys.
+__device__ void view_prep_block(const ViewPrep &p, unsigned long long *key)
 {
     __shared__ int s_changed;
     if (threadIdx.x == 0) s_changed = 0;
@@ -147,14 +147,19 @@ __device__ void view_prep_block(const ViewPrep &p, double *key)
         for (int i = threadIdx.x; i < p.V; i += blockDim.x) p.order[i] = i;
         return;
     }
+    // One unsigned 64-bit key per view orders by (frame, axis, slope): the
+    // fixed-point slope |Qh| < 2^47 is offset into 48 bits, the axis and the
+    // frame sit above it.  The rank of a view counts the keys below it (ties by
+    // index); integer compares, as the FP64 pipe of this part is narrow.
     for (int i = threadIdx.x; i < p.V; i += blockDim.x)
-        key[i] = p.vg[i].frame * 8.0 + p.vg[i].mode * 4.0 + 1.0 + (double)p.vg[i].Qh * (2.0 / kFixScale);
+        key[i] = ((unsigned long long)p.vg[i].frame << 49) | ((unsigned long long)p.vg[i].mode << 48) |
+                 (unsigned long long)(p.vg[i].Qh + (1LL << 47));
     __syncthreads();
     for (int i = threadIdx.x; i < p.V; i += blockDim.x) {
-        const double ki = key[i];
+        const unsigned long long ki = key[i];
         int rank = 0;
         for (int j = 0; j < p.V; ++j) {
-            const double kj = key[j];
+            const unsigned long long kj = key[j];
             rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
         }
         p.order[rank] = i;
@@ -163,7 +168,7 @@ __device__ void view_prep_block(const ViewPrep &p, double *key)
 
 __global__ void __launch_bounds__(1024) k_view_prep(ViewPrep p, const int *__restrict__ skip)
 {
-    __shared__ double key[kOrderMaxV];
+    __shared__ unsigned long long key[kOrderMaxV];
     if (skip && *skip) return;
     view_prep_block(p, key);
 }
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair
                                                    pair_t<T> *__restrict__ PT, int N, int Pp, int nimg, ViewPrep p,
                                                    const int *__restrict__ skip)
 {
-    extern __shared__ double prep_key[];
+    extern __shared__ unsigned long long prep_key[];
     if (skip && *skip) return;
     if (p.on && blockIdx.x == gridDim.x - 1) {
         if (blockIdx.y == 0 && blockIdx.z == 0) view_prep_block(p, prep_key);
@@ -229,7 +234,7 @@ template <typename T>
 __global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP, int B, int Pb, long long total,
                              ViewPrep p, const int *__restrict__ skip)
 {
-    extern __shared__ double prep_key[];
+    extern __shared__ unsigned long long prep_key[];
     if (skip && *skip) return;
     const int nblk = gridDim.x - (p.on ? 1 : 0);
     if (p.on && blockIdx.x == nblk) {
@@ -521,7 +526,7 @@ ViewPrep view_prep_args(const Handle &h, const double *theta, const double *delt
     return p;
 }
 
-size_t prep_smem(const ViewPrep &p) { return p.on ? sizeof(double) * std::min(p.V, kOrderMaxV) : 0; }
+size_t prep_smem(const ViewPrep &p) { return p.on ? sizeof(unsigned long long) * std::min(p.V, kOrderMaxV) : 0; }
 
 // The layout kernels may carry the view-table step in up to 32 KB of dynamic shared memory.
 template <typename K> cudaError_t allow_prep_smem(K kernel)
@@ -529,7 +534,7 @@ template <typename K> cudaError_t allow_prep_smem(K kernel)
     static bool done = false;  // per kernel; the attribute is idempotent, so a race is harmless
     if (done) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * kOrderMaxV));
+                                         (int)(sizeof(unsigned long long) * kOrderMaxV));
     if (e == cudaSuccess) done = true;
     return e;
 }
