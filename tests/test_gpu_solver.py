@@ -142,3 +142,19 @@ def test_fp32_aniso_tv_solver_reaches_the_oracle_reconstruction_error(ct):
     x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
                          outer_iters=6, stop_on_convergence=0, temporal=1)
     assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
+
+
+def test_fp32_aniso_tv_large_basis_uses_the_unpipelined_gram(ct):
+    """ANISO-TV with a basis above 40 columns: the weighted Gram of Psi V no
+    longer fits the two staging buffers of the pipelined kernel and runs in
+    the register-blocked form without staging.  One outer iteration of 40
+    Enlarge steps (k = 6 .. 45) against the oracle."""
+    g, vpf, th_nom, th_true, u_true, b, nn = _moving_sequence(N=24, vpf=(6, 7, 6, 7), seed=43)
+    kw = dict(k_min=5, k_max=45, outer_iters=1, tol1=0.0, stop_on_convergence=False, temporal=True)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, nlrmm.Options(noise_norm=nn, **kw)).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float32)
+    x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
+                         k_min=5, k_max=45, outer_iters=1, tol1=0.0, stop_on_convergence=0, temporal=1)
+    assert st["enlarge_steps"] == h_o.enlarge_steps == [40]
+    assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
+    assert abs(st["lambda"][-1] - h_o.lam[-1]) <= 1e-3 * h_o.lam[-1], (st["lambda"][-1], h_o.lam[-1])
