@@ -110,6 +110,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, world, device):
+    """The job's time for a timed region: the slowest replica's (all_reduce MAX)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ms, world):
+    """Whole-job throughput in G units/s: the units of every replica over the job's time."""
+    return world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -612,12 +628,9 @@ def main():
     per_op = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)])
     step_ms = per_op.sum(axis=1)
     total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     samples_per_step = V * B * (K + K + 1 + 1)
-    value_eager = world * samples_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    value_eager = job_rate(samples_per_step * args.steps, total_ms, world)
     # the same step replayed from a CUDA graph (what the solver and a serving loop run)
     if world > 1:
         dist.barrier()
@@ -625,11 +638,8 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    if world > 1:
-        t = torch.tensor([graph_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        graph_ms = float(t.item())
-    value = world * samples_per_step / (graph_ms * 1e-3) / 1e9
+    graph_ms = max_over_ranks(graph_ms, world, dev)
+    value = job_rate(samples_per_step, graph_ms, world)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     Xp = torch.tensor(Xh).pin_memory()
@@ -666,11 +676,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = world * samples_per_step * args.steps / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_val = job_rate(samples_per_step * args.steps, e2e_ms, world)
 
     if rank != 0:
         if world > 1:
