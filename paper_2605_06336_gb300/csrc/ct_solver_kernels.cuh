@@ -947,9 +947,9 @@ struct SmallShared {
 // in t = log10(lambda) over [lam_lo, lam_hi] by Newton steps safeguarded by
 // bisection of the bracket (started from the previous lambda in scal[kLam]);
 // a target at or below phi(10^lam_lo) gives 10^lam_lo, at or above
-// phi(10^lam_hi) gives 10^lam_hi, as for plain bisection.  The root is found
-// to 1e-12 in t (lambda to ~2e-12 relative): the limit of plain bisection
-// up to the rounding of phi itself.  The matrix is factored as L D L^T.
+// phi(10^lam_hi) gives 10^lam_hi, as for plain bisection.  The search stops
+// when |phi - target| <= 1e-10 target or the step falls below 1e-12 in t
+// (lambda within ~2e-10 of the root).  The matrix is factored as L D L^T.
 //
 // The whole solve runs in warp 0 (k <= 64, lanes over rows, warp barriers
 // only): FP64 is a narrow pipe on this part, so the kernel is arranged for
@@ -1092,7 +1092,10 @@ __global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ 
             const double f = eval(pow(10.0, t), true, dft) - target;
             if (t == lam_lo && f >= 0.0) break;  // target at or below the smallest residual
             if (t == lam_hi && f <= 0.0) break;  // target at or above the largest residual
-            if (f == 0.0) break;
+            // phi carries rounding errors near 1e-12 of the target here; once it
+            // is this close, further steps only chase that noise (lambda is then
+            // within ~2e-10 of the root)
+            if (fabs(f) <= 1e-10 * target) break;
             if (f < 0.0) {
                 lo = t;
                 lo_seen = true;
