@@ -49,8 +49,10 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_segpart);
     cudaFree(h.d_rays);
     cudaFree(h.d_fanview);
+    cudaFree(h.d_yi);
     h.d_rays = nullptr;
     h.d_fanview = nullptr;
+    h.d_yi = nullptr;
     h.d_views = nullptr;
     h.d_fov = h.d_fstart = h.d_fcount = h.d_flag = h.d_order = nullptr;
     h.d_px = h.d_pt = h.d_yp = nullptr;
@@ -394,7 +396,9 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
                   cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.V * h.nchunks) == cudaSuccess &&
                   (h.fan_D == 0.0 ||
                    (cudaMalloc(&h.d_rays, ctgb::fan_ray_bytes(h.precision) * (size_t)h.V * h.B) == cudaSuccess &&
-                    cudaMalloc(&h.d_fanview, ctgb::fan_view_bytes() * (size_t)h.V) == cudaSuccess));
+                    cudaMalloc(&h.d_fanview, ctgb::fan_view_bytes() * (size_t)h.V) == cudaSuccess &&
+                    cudaMalloc(&h.d_yi, elem_size(h) * 8 * (size_t)((h.max_batch + 7) / 8) * h.V * h.B) ==
+                        cudaSuccess));
         if (!ok) {
             cudaGetLastError();
             rc = CT_ERR_OOM;

@@ -26,6 +26,7 @@
 //   k_ray_fan    SPLIT warps (row segments) per 32 bins of one view: forward
 //                (KB images), JVP, VJP and Gauss-Newton terms, each lane on
 //                its own line
+//   k_fan_sino   sinograms interleaved in blocks of 8 for the transpose
 //   k_adj_fan    exact transpose in gather form: a pixel takes, per view,
 //                the rays whose fixed-point sample at its row (row-marched
 //                rays) or column (column-marched rays) falls in its
@@ -322,12 +323,53 @@ __device__ __forceinline__ float fan_s(float x, float y, float c, float sn, floa
     return __fdividef(x * c + y * sn, 1.0f + (y * c - x * sn) * iD);
 }
 
+// YI[k / 8][v][b][k % 8] = Y[k][v][b] for k < nsino
+template <typename T>
+__global__ void k_fan_sino(const T *__restrict__ Y, T *__restrict__ YI, long long m, int nsino,
+                           const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const long long total = (long long)nsino * m;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / m);
+        const long long e = idx - (long long)k * m;
+        YI[((long long)(k >> 3) * m + e) * 8 + (k & 7)] = Y[idx];
+    }
+}
+
 struct AdjFanArgs {
     const int *fstart, *fcount;
     int N, B, F, tps, Pb, kbase, ngroups;
     long long ysino_stride, img_stride;
     const int *skip;
 };
+
+// The KB values of one bin in the interleaved layout (16-byte loads where the
+// group is 16-byte aligned: FP32 groups of 4 or 8, FP64 groups of 2 or more).
+template <typename T, int KB> __device__ __forceinline__ void load_bin(const T *p, T (&out)[KB])
+{
+    if constexpr (std::is_same<T, float>::value && KB % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < KB / 4; ++q) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            out[4 * q] = v.x;
+            out[4 * q + 1] = v.y;
+            out[4 * q + 2] = v.z;
+            out[4 * q + 3] = v.w;
+        }
+    } else if constexpr (std::is_same<T, double>::value && KB % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < KB / 2; ++q) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + q);
+            out[2 * q] = v.x;
+            out[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KB; ++k) out[k] = __ldg(p + k);
+    }
+}
 
 // One CTA = one 16 x 16 pixel tile of one frame and KB sinograms, SPLIT
 // thread groups of 256: group g of a pixel sums the views vs + g, vs + g +
@@ -336,7 +378,7 @@ struct AdjFanArgs {
 template <typename T, int KB, int SPLIT>
 __global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const FanRay<T> *__restrict__ rays,
                                                          const FanView *__restrict__ views,
-                                                         const pair_t<T> *__restrict__ YP, T *__restrict__ X)
+                                                         const T *__restrict__ YI, T *__restrict__ X)
 {
     __shared__ T red[SPLIT > 1 ? SPLIT - 1 : 1][KB][256];
     const int pix = threadIdx.x & 255, grp_v = threadIdx.x >> 8;
@@ -363,7 +405,9 @@ __global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const Fan
         for (int v = vs + grp_v; inside && v < vs + vc; v += SPLIT) {
             const FanView fv = views[v];
             const FanRay<T> *rv = rays + (size_t)v * a.B;
-            const pair_t<T> *yv = YP + (size_t)k0 * a.ysino_stride + (size_t)v * a.Pb + 2;
+            // the KB sinograms of this group at bin b: KB consecutive values (KB divides 8, and a
+            // group starts at a multiple of its width)
+            const T *yv = YI + ((size_t)(k0 >> 3) * a.ysino_stride + (size_t)v * a.B) * 8 + (k0 & 7);
             // rays marched along rows that sample row i inside (x - 1, x + 1), then
             // rays marched along columns that sample column j inside (y - 1, y + 1)
 #pragma unroll
@@ -384,8 +428,10 @@ __global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const Fan
                     if (cell != me && cell != me - 1) continue;
                     const T fr = frac_of(Q, T());
                     const T wt = rv[b].w * (cell == me ? T(1) - fr : fr);
+                    T yk[KB];
+                    load_bin<T, KB>(yv + (size_t)b * 8, yk);
 #pragma unroll
-                    for (int k = 0; k < KB; ++k) acc[k] = fma(wt, yv[(size_t)k * a.ysino_stride + b].x, acc[k]);
+                    for (int k = 0; k < KB; ++k) acc[k] = fma(wt, yk[k], acc[k]);
                 }
             }
         }
@@ -435,7 +481,7 @@ template <typename T, int KB, int SPLIT> cudaError_t run_adj_fan(const Handle &h
     const long long items = (long long)a.ngroups * a.F * a.tps * a.tps;
     const int grid = persistent_grid(kern, 256 * SPLIT, 0, items, h.num_sms);
     kern<<<grid, 256 * SPLIT, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const FanView *)h.d_fanview,
-                                             (const pair_t<T> *)h.d_yp, X);
+                                             (const T *)h.d_yi, X);
     return cudaGetLastError();
 }
 
@@ -500,7 +546,7 @@ cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, int spl
     a.F = h.F;
     a.tps = (h.N + kTile - 1) / kTile;
     a.Pb = h.Pb;
-    a.ysino_stride = (long long)h.V * h.Pb;
+    a.ysino_stride = (long long)h.V * h.B;  // per block of 8 interleaved sinograms, in bins
     a.img_stride = (long long)h.F * h.N * h.N;
     a.skip = skip;
     int k = 0;
@@ -523,6 +569,17 @@ cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, int spl
     return cudaSuccess;
 }
 
+template <typename T> cudaError_t launch_fan_sino(const Handle &h, const T *Y, int nsino, const int *skip)
+{
+    const long long m = (long long)h.V * h.B;
+    const long long total = (long long)nsino * m;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8LL * h.num_sms));
+    k_fan_sino<T><<<grid, 256, 0, h.stream>>>(Y, (T *)h.d_yi, m, nsino, skip);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fan_sino<float>(const Handle &, const float *, int, const int *);
+template cudaError_t launch_fan_sino<double>(const Handle &, const double *, int, const int *);
 template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int, int);
 template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int, int);
 template cudaError_t launch_fan_adjoint<float>(const Handle &, float *, int, int, int, const int *);

@@ -103,6 +103,7 @@ struct Handle {
     double fan_D = 0.0;           // > 0: fan beam with the source at this distance (ct_fan.cu); 0: parallel
     void *d_rays = nullptr;       // fan beam: per-ray table, V * B entries
     void *d_fanview = nullptr;    // fan beam: per-view FP32 constants and march-axis bin ranges
+    void *d_yi = nullptr;         // fan beam: sinograms interleaved in blocks of 8, [k / 8][V][B][k % 8]
     // Batch sizes whose forward (adjoint) inputs are still laid out in the
     // handle from the last ct_forward (ct_adjoint) call: ct_forward_repeat
     // (ct_adjoint_repeat) may rerun the projection kernel alone.  Any other
@@ -158,6 +159,9 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
 // sinograms like the parallel-beam one.
 size_t fan_ray_bytes(int precision);
 size_t fan_view_bytes();
+// YI[k / 8][v][b][k % 8] = Y[k][v][b]: the 8 sinograms of a block at one bin
+// are contiguous for the fan-beam transpose (ct_fan.cu).
+template <typename T> cudaError_t launch_fan_sino(const Handle &h, const T *Y, int nsino, const int *skip);
 cudaError_t launch_fan_rays(const Handle &h, const int *skip);
 template <typename T>
 cudaError_t launch_fan_adjoint(const Handle &h, T *X, int batch, int kb, int split, const int *skip);

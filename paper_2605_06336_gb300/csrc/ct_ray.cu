@@ -587,13 +587,17 @@ cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int 
     const long long total = (long long)nsino * h.V * h.Pb;
     const int threads = 256;
     const long long blocks = std::min<long long>((total + threads - 1) / threads, (long long)h.num_sms * 16);
+    if (h.fan_D > 0.0) {
+        // fan beam: the transpose reads the interleaved layout instead; the view-table
+        // step (when the angles come with the call) runs on its own
+        if (p.on) {
+            e = launch_view_setup(h, theta, delta, skip);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_fan_sino<T>(h, Y, nsino, skip);
+    }
     k_pairs_sino<T><<<(int)std::max<long long>(1, blocks) + (p.on ? 1 : 0), threads, prep_smem(p), h.stream>>>(
         Y, (pair_t<T> *)h.d_yp, h.B, h.Pb, total, p, skip);
-    if (h.fan_D > 0.0 && theta) {
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        return launch_fan_rays(h, skip);
-    }
     return cudaGetLastError();
 }
 
