@@ -828,20 +828,6 @@ __device__ void chol(double *A, int k, int *bad)
     __syncthreads();
 }
 
-// X := L^{-1} X for ncol columns of X (one thread per column)
-__device__ void trsm_lower(const double *L, double *X, int k, int ncol)
-{
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-        for (int i = 0; i < k; ++i) {
-            double s = X[i * kLd + c];
-            for (int l = 0; l < i; ++l) s -= L[i * kLd + l] * X[l * kLd + c];
-            X[i * kLd + c] = s / L[i * kLd + i];
-        }
-    }
-    __syncthreads();
-}
-
 // Cyclic Jacobi eigen-decomposition of the symmetric k x k matrix A
 // (overwritten; its diagonal ends as the eigenvalues), eigenvectors in the
 // columns of U.  Parallel round-robin ordering of the (p, q) rotations.
@@ -924,15 +910,14 @@ __device__ void jacobi_eig(double *A, double *U, int k, double *cs, double *sn, 
     __syncthreads();
 }
 
+// Shared memory of k_compress_basis (matrix, eigenvectors, rotation tables).
 struct SmallShared {
     double A[kKMax * kLd];
-    double B[kKMax * kLd];
     double U[kKMax * kLd];
-    double vec[4][kKMax + 1];
+    double vec[1][kKMax + 1];
     double cs[kKMax / 2 + 1], sn[kKMax / 2 + 1];
     int pp[kKMax / 2 + 1], qq[kKMax / 2 + 1];
     double sh[40];
-    int bad;
 };
 
 // Reduced problem of one Enlarge step:
