@@ -185,3 +185,29 @@ def test_fp64_fan_solver_follows_the_oracle_iterates():
     assert rel(host(x), u_o) <= 1e-7
     assert np.max(np.abs(host(th) - th_o)) <= 1e-8
     assert np.linalg.norm(th_o - th_true) < np.linalg.norm(th_nom - th_true)
+
+
+def test_fp64_fan_varpro_solver_follows_the_oracle_iterates():
+    from paper_2605_06336_gb300 import ct
+    rng = np.random.default_rng(23)
+    N, V = 32, 40
+    B, D = synth.n_bins(N), 64.0
+    g = oracle.Geometry(N, B, V, fan_D=D)
+    th_nom = np.sort(synth.random_angles(V, rng))
+    th_true = th_nom + rng.normal(0, math.radians(0.5), V)
+    u_true = synth.rasterize(N, synth.random_ellipses(N, 4, rng)).ravel()
+    b_true = oracle.forward(g, th_true, u_true)
+    e = rng.standard_normal(g.m)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    b, nn = b_true + e, float(np.linalg.norm(e))
+    kw = dict(k_min=5, k_max=15, outer_iters=3, tol1=0.0)
+    o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, varpro=True, **kw)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(N, B, V, max_batch=8, dtype=torch.float64, source_distance=D)
+    x, th, st = op.solve(dev(b), dev(th_nom), x_true=dev(u_true), noise_norm=nn, stop_on_convergence=0, varpro=1,
+                         **kw)
+    assert st["enlarge_steps"] == h_o.enlarge_steps
+    np.testing.assert_allclose(st["lambda"], h_o.lam, rtol=1e-6)
+    np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-6)
+    assert rel(host(x), u_o) <= 1e-6
+    assert np.max(np.abs(host(th) - th_o)) <= 1e-7

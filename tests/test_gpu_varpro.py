@@ -190,3 +190,64 @@ def test_varpro_update_argument_errors():
         with pytest.raises(ct.CTError) as e:
             op.varpro_update(b, th, V, lam)
         assert e.value.code == ct.CT_ERR_ARG
+
+
+def _moving(N=24, vpf=(6, 7, 6, 7), seed=51):
+    rng = np.random.default_rng(seed)
+    ells = synth.random_ellipses(N, 3, rng)
+    u_true = np.stack([synth.rasterize(N, ells, shift=(0.5 * f, 0.0)) for f in range(len(vpf))]).ravel()
+    g = oracle.Geometry(N, synth.n_bins(N), sum(vpf), views_per_frame=list(vpf))
+    th_nom = np.sort(synth.random_angles(g.V, rng))
+    th_true = th_nom + rng.normal(0, math.radians(0.5), g.V)
+    b_true = oracle.forward(g, th_true, u_true)
+    e = rng.standard_normal(g.m)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    return g, list(vpf), th_nom, u_true, b_true + e, float(np.linalg.norm(e))
+
+
+def _follows(st, h_o, x, u_o, th, th_o):
+    # Gauss-Newton quotients amplify the rounding differences of the two FP64 paths
+    assert st["enlarge_steps"] == h_o.enlarge_steps
+    np.testing.assert_allclose(st["lambda"], h_o.lam, rtol=1e-6)
+    np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-6)
+    assert _rel(x, u_o) <= 1e-6
+    assert np.max(np.abs(th - th_o)) <= 1e-7
+
+
+def test_fp64_varpro_with_aniso_tv_follows_the_oracle_iterates():
+    from paper_2605_06336_gb300 import ct
+    g, vpf, th_nom, u_true, b, nn = _moving()
+    kw = dict(k_min=5, k_max=15, outer_iters=3, tol1=0.0)
+    o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, temporal=True, varpro=True, **kw)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float64)
+    dv = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    x, th, st = op.solve(dv(b), dv(th_nom), x_true=dv(u_true), noise_norm=nn, stop_on_convergence=0, temporal=1,
+                         varpro=1, **kw)
+    _follows(st, h_o, x.cpu().numpy(), u_o, th.cpu().numpy(), th_o)
+
+
+def test_fp64_varpro_streaming_follows_the_oracle_iterates():
+    from paper_2605_06336_gb300 import ct
+    rng = np.random.default_rng(52)
+    N, V, nblocks = 32, 36, 3
+    B = synth.n_bins(N)
+    g = oracle.Geometry(N, B, V)
+    th_nom = np.sort(synth.random_angles(V, rng))
+    th_true = th_nom + rng.normal(0, math.radians(0.5), V)
+    u_true = synth.rasterize(N, synth.random_ellipses(N, 4, rng)).ravel()
+    b_true = oracle.forward(g, th_true, u_true).reshape(V, B)
+    e = rng.standard_normal(b_true.shape)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    idx = [np.sort(ix) for ix in np.array_split(rng.permutation(V), nblocks)]
+    kw = dict(k_min=5, k_max=15, tol1=0.0)
+    orc = [nlrmm.NLRMMGKS(oracle.Geometry(N, B, len(ix)), (b_true[ix] + e[ix]).ravel(),
+                          nlrmm.Options(noise_norm=float(np.linalg.norm(e[ix])), stop_on_convergence=False,
+                                        varpro=True, **kw)) for ix in idx]
+    u_o, th_o, h_o = nlrmm.stream_solve(orc, [th_nom[ix] for ix in idx], passes=2, u_true=u_true)
+    dv = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    ops = [ct.CTOperator(N, B, len(ix), max_batch=8, dtype=torch.float64) for ix in idx]
+    x, th, st = ct.stream_solve(ops, [dv((b_true[ix] + e[ix]).ravel()) for ix in idx], [dv(th_nom[ix]) for ix in idx],
+                                [float(np.linalg.norm(e[ix])) for ix in idx], x_true=dv(u_true), outer_iters=2,
+                                stop_on_convergence=0, varpro=1, **kw)
+    _follows(st, h_o, x.cpu().numpy(), u_o, np.concatenate([t.cpu().numpy() for t in th]), np.concatenate(th_o))

@@ -278,6 +278,33 @@ def test_varpro_sensitivity_jacobians_match_central_differences():
     assert errs[1e-6][1] < max(errs[1e-4][1] / 20, 1e-7), errs
 
 
+def test_varpro_jacobians_with_temporal_differences_match_central_differences():
+    """The same pin with ANISO-TV (frame-to-frame differences in Psi) on 3 frames."""
+    rng = np.random.default_rng(13)
+    N, vpf = 14, [5, 4, 5]
+    g = oracle.Geometry(N, synth.n_bins(N), sum(vpf), vpf)
+    th = np.sort(synth.random_angles(g.V, rng))
+    u = np.stack([synth.rasterize(N, synth.random_ellipses(N, 2, rng)) for _ in vpf]).ravel()
+    b = oracle.forward(g, th, u) + 0.01 * rng.standard_normal(g.m)
+    Vb, _ = np.linalg.qr(rng.standard_normal((g.n, 5)))
+    ne = nlrmm.psi(g, u, True).size
+    w = rng.uniform(0.5, 2.0, ne)
+    lam = 0.3
+    Jr, Js, r, s_, f, uu = nlrmm.varpro_jacobians(g, b, th, Vb, lam, w, None, True)
+    errs = {}
+    for h in (1e-4, 1e-6):
+        er = nr = 0.0
+        for _ in range(4):
+            d = rng.standard_normal(g.V)
+            up = nlrmm.varpro_objective(g, b, th + h * d, Vb, lam, w, None, True)[2]
+            um = nlrmm.varpro_objective(g, b, th - h * d, Vb, lam, w, None, True)[2]
+            sp_, sm = np.sqrt(w) * nlrmm.psi(g, up, True), np.sqrt(w) * nlrmm.psi(g, um, True)
+            er += np.linalg.norm((sp_ - sm) / (2 * h) - Js @ d)
+            nr += np.linalg.norm(Js @ d)
+        errs[h] = er / nr
+    assert errs[1e-6] < max(errs[1e-4] / 20, 1e-7), errs
+
+
 def test_varpro_gauss_newton_gradient_is_the_envelope_gradient():
     g, th, _, b, Vb, w, _ = _varpro_case(N=16, V=10, k=5, seed=21)
     lam = 0.5
