@@ -72,7 +72,7 @@ typedef struct {
                                          rotation centre, flat detector rescaled to the line through
                                          the centre, bin b centred at s_b = b - (B-1)/2 + delta_v on
                                          it; ray (v,b) joins the source and s_b (cos, sin)(theta_v).
-                                         Must exceed 0.75 max(N, B).  Fan-beam handles run H, H^T,
+                                         Must exceed 0.75 max(N, B) + 2.  Fan-beam handles run H, H^T,
                                          J_theta, J_theta^T and the solvers; offsets delta are
                                          accepted in H and H^T, their derivatives are not (ct_jac
                                          with ddelta and ct_jacT with gdelta return CT_ERR_ARG). */

@@ -333,10 +333,13 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
         (g->precision != 0 && g->precision != 1))
         return CT_ERR_ARG;
     // fan beam: the source must lie outside the disc that holds the image and
-    // the detector line (every ray then has a well-defined march axis)
+    // the detector line, with two pixels to spare: the fan is then narrower than
+    // 90 degrees (one change of march axis per view at most) and the projective
+    // map of the transpose's candidate search stays positive on every pixel and
+    // its one-pixel neighbourhood (image depth at most N / sqrt(2) + sqrt(2))
     if (!(g->source_distance == 0.0 ||
           (g->source_distance > 0.0 && std::isfinite(g->source_distance) &&
-           g->source_distance > 0.75 * std::max((double)g->N, (double)g->B))))
+           g->source_distance > 0.75 * std::max((double)g->N, (double)g->B) + 2.0)))
         return CT_ERR_ARG;
     std::vector<int> vpf;
     if (g->views_per_frame) {
