@@ -119,6 +119,12 @@ struct Handle {
 // *skip != 0 the kernel returns at once.
 cudaError_t launch_view_setup(const Handle &h, const double *theta, const double *delta,
                               const int *skip = nullptr);
+// The same step with the per-view constants spread over many CTAs (for large
+// view counts) and the view order rebuilt by one more CTA when a view
+// changed; *changed (device, zero on entry) is the flag between the two and
+// is zero again afterwards.
+cudaError_t launch_view_setup_wide(const Handle &h, const double *theta, const double *delta, int *changed,
+                                   const int *skip = nullptr);
 
 // Layout kernels.  With theta non-null the same launch also runs the view-table
 // step of the call (what launch_view_setup does), in one extra CTA.

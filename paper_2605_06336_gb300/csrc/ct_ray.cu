@@ -130,6 +130,8 @@ struct ViewPrep {
     int *order;  // nullable: constants only
 };
 
+__device__ void build_order(const ViewPrep &p, unsigned long long *key);
+
 // The view-table step, run by one whole CTA; key: shared memory for
 // min(V, kOrderMaxV) 64-bit keys.
 __device__ void view_prep_block(const ViewPrep &p, unsigned long long *key)
@@ -143,6 +145,12 @@ __device__ void view_prep_block(const ViewPrep &p, unsigned long long *key)
     if (mine) s_changed = 1;  // every writer stores the same value
     __syncthreads();
     if (!p.order || !s_changed) return;
+    build_order(p, key);
+}
+
+// The view order of a CTA from the current view records (see view_prep_block).
+__device__ void build_order(const ViewPrep &p, unsigned long long *key)
+{
     if (p.V > kOrderMaxV) {
         for (int i = threadIdx.x; i < p.V; i += blockDim.x) p.order[i] = i;
         return;
@@ -171,6 +179,29 @@ __global__ void __launch_bounds__(1024) k_view_prep(ViewPrep p, const int *__res
     __shared__ unsigned long long key[kOrderMaxV];
     if (skip && *skip) return;
     view_prep_block(p, key);
+}
+
+// The same step spread over many CTAs: the per-view constants in parallel
+// (*changed = 1 when a view was rebuilt), then k_view_order in one CTA.
+__global__ void k_view_setup_many(ViewPrep p, int *changed, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    int mine = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < p.V; v += gridDim.x * blockDim.x)
+        mine |= view_setup_one(v, p.theta, p.delta, p.fov, p.N, p.B, p.vg, p.flag);
+    if (mine) *changed = 1;  // every writer stores the same value
+}
+
+__global__ void __launch_bounds__(1024) k_view_order(ViewPrep p, int *changed, const int *__restrict__ skip)
+{
+    __shared__ unsigned long long key[kOrderMaxV];
+    if (skip && *skip) return;
+    const int ch = *changed;
+    __syncthreads();  // every thread has read the flag before it is cleared below
+    if (!ch || !p.order) return;
+    build_order(p, key);
+    __syncthreads();
+    if (threadIdx.x == 0) *changed = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -550,6 +581,19 @@ cudaError_t launch_view_setup(const Handle &h, const double *theta, const double
         return launch_fan_rays(h, skip);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_view_setup_wide(const Handle &h, const double *theta, const double *delta, int *changed,
+                                   const int *skip)
+{
+    const ViewPrep p = view_prep_args(h, theta, delta);
+    const int grid = std::max(1, std::min((h.V + 127) / 128, 4 * h.num_sms));
+    k_view_setup_many<<<grid, 128, 0, h.stream>>>(p, changed, skip);
+    k_view_order<<<1, 1024, 0, h.stream>>>(p, changed, skip);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (h.fan_D > 0.0) return launch_fan_rays(h, skip);
+    return cudaSuccess;
 }
 
 template <typename T>

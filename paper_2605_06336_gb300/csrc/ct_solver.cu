@@ -439,7 +439,7 @@ template <typename T> struct Solver {
             k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
                                                      ctl);
             for (int hv = 0; hv <= o.max_halvings; ++hv) {
-                SV_CUDA(launch_view_setup(h, th_t, delta));
+                SV_CUDA(launch_view_setup_wide(h, th_t, delta, ctl + kViewChanged));
                 SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw,
                                      h.tune.der_stage, active));
                 k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, th_n, h.V, o.c1, o.beta, alpha, th_t, active, ctl,

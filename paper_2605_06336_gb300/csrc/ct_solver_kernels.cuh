@@ -31,7 +31,7 @@ inline int red_blocks(long long len)
 }
 
 // control words (int) and scalars (double) living on the device
-enum Ctl { kStop = 0, kStopNext, kSteps, kActive, kBreakdown, kCtlCount };
+enum Ctl { kStop = 0, kStopNext, kSteps, kActive, kBreakdown, kViewChanged, kCtlCount };
 enum Scal { kLam = 0, kRnorm2, kDu2, kU2, kJreg, kBnorm2, kTmp0, kTmp1, kScalCount };
 
 __device__ __forceinline__ bool stopped(const int *stop) { return stop && *stop; }
