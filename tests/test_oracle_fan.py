@@ -9,6 +9,8 @@ centres s_b on it); ray (v, b) runs from the source through s_b e(theta_v).
 * as D grows the fan operator and its derivatives tend to the parallel-beam
   ones (the limit the reading is built on);
 * convergence to the analytic line integrals of ellipses along the fan rays;
+* convergence of the angle and offset derivatives to the derivatives of the
+  closed-form line integrals of Gaussian blobs along the fan rays;
 * central finite differences for d/dtheta and d/ddelta;
 * adjoint identity and J / J^T duality with frames and offsets.
 """
@@ -105,6 +107,59 @@ def test_fan_converges_to_analytic_line_integrals_of_ellipses():
     for e0, e1 in zip(errs, errs[1:]):
         assert e1 < 0.8 * e0, errs
     assert errs[-1] < 2e-2, errs
+
+
+def _fan_gaussian_integrals(blobs, theta, delta, B, D):
+    """Closed-form integrals of isotropic Gaussians along the fan rays: a blob
+    contributes rho sqrt(2 pi) sigma exp(-t^2 / (2 sigma^2)), t its signed
+    distance from the ray through S = D (sin, -cos) and P_b = s_b (cos, sin)."""
+    s = np.arange(B) - (B - 1) / 2 + delta[:, None]
+    c, sn = np.cos(theta)[:, None], np.sin(theta)[:, None]
+    rx, ry = s * c - D * sn, s * sn + D * c
+    nr = np.hypot(rx, ry)
+    nx, ny = ry / nr, -rx / nr
+    p = nx * s * c + ny * s * sn
+    R = np.zeros(s.shape)
+    for cx, cy, sg, rho in blobs:
+        t = p - (nx * cx + ny * cy)
+        R += rho * math.sqrt(2 * math.pi) * sg * np.exp(-t * t / (2 * sg * sg))
+    return R
+
+
+def test_fan_derivatives_converge_to_those_of_gaussian_line_integrals():
+    rng = np.random.default_rng(8)
+    V = 24
+    theta = synth.random_angles(V, rng)
+    delta = rng.normal(0, 0.5, V)
+    base = []
+    for _ in range(5):   # blobs at least 5 sigma inside the image
+        r, a = 0.2 * math.sqrt(rng.uniform()), rng.uniform(0, 2 * math.pi)
+        base.append((r * math.cos(a), r * math.sin(a), rng.uniform(0.03, 0.06), rng.uniform(0.2, 1.0)))
+    errs = []
+    for N in (32, 64, 128, 256):
+        D = 2.0 * N
+        blobs = [(cx * N, cy * N, sg * N, rho) for (cx, cy, sg, rho) in base]
+        x = np.arange(N) - (N - 1) / 2
+        y = (N - 1) / 2 - np.arange(N)
+        X = sum(rho * np.exp(-((x[None, :] - cx) ** 2 + (y[:, None] - cy) ** 2) / (2 * sg * sg))
+                for cx, cy, sg, rho in blobs).ravel()
+        B = synth.n_bins(N)
+        g = oracle.Geometry(N, B, V, fan_D=D)
+        R = _fan_gaussian_integrals(blobs, theta, delta, B, D)
+        # derivatives of the closed form by central differences of the closed
+        # form itself (smooth: error ~1e-10, far below the discretization error)
+        h = 1e-6
+        R_th = (_fan_gaussian_integrals(blobs, theta + h, delta, B, D)
+                - _fan_gaussian_integrals(blobs, theta - h, delta, B, D)) / (2 * h)
+        R_s = (_fan_gaussian_integrals(blobs, theta, delta + h, B, D)
+               - _fan_gaussian_integrals(blobs, theta, delta - h, B, D)) / (2 * h)
+        Y = oracle.forward(g, theta, X, delta)
+        dt, dd = oracle.dsample(g, theta, X, delta)
+        errs.append([np.linalg.norm(a - r.ravel()) / np.linalg.norm(r) for a, r in ((Y, R), (dt, R_th), (dd, R_s))])
+    errs = np.array(errs)
+    assert np.all(errs[1:, 0] < 0.35 * errs[:-1, 0]), errs
+    assert np.all(errs[1:, 1:] < 0.6 * errs[:-1, 1:]), errs
+    assert errs[-1, 0] < 1e-3 and np.all(errs[-1, 1:] < 1.5e-2), errs
 
 
 @pytest.mark.parametrize("which", ["theta", "delta", "both"])

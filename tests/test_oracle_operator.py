@@ -4,6 +4,10 @@
 * closed forms at theta = 0 and theta = pi/2 (half-pixel column / row sums),
   the detector-offset shift, and the single-pixel hat;
 * convergence to the analytic Radon transform of ellipses as N grows;
+* convergence of the angle and offset derivatives to the closed-form
+  derivatives of the Radon transform of Gaussian blobs (smooth, so the
+  derivative converges in norm, unlike that of an ellipse's chord, whose edge
+  singularity is not square-integrable);
 * central finite differences for d/dtheta and d/ddelta (including the
   global-shift direction of the paper's CT experiments, J * 1);
 * closed-form angle / offset derivatives at theta = 0.
@@ -123,6 +127,67 @@ def test_converges_to_analytic_radon_of_ellipses():
     for e0, e1 in zip(errs, errs[1:]):
         assert e1 < 0.8 * e0, errs
     assert errs[-1] < 2e-2, errs
+
+
+def gaussian_blobs(rng, count=5):
+    """Isotropic Gaussians (cx, cy, sigma, rho) in units of the image side, placed so
+    that every blob is at least 5 sigma inside the image (truncation below 1e-5)."""
+    out = []
+    for _ in range(count):
+        r, a = 0.2 * math.sqrt(rng.uniform()), rng.uniform(0, 2 * math.pi)
+        out.append((r * math.cos(a), r * math.sin(a), rng.uniform(0.03, 0.06), rng.uniform(0.2, 1.0)))
+    return out
+
+
+def gaussian_image(N, blobs):
+    """Samples of sum rho exp(-|p - c|^2 / (2 sigma^2)) at the pixel centres."""
+    x = np.arange(N) - (N - 1) / 2
+    y = (N - 1) / 2 - np.arange(N)
+    X = np.zeros((N, N))
+    for cx, cy, sg, rho in blobs:
+        X += rho * np.exp(-((x[None, :] - cx) ** 2 + (y[:, None] - cy) ** 2) / (2 * sg * sg))
+    return X
+
+
+def _radon_gaussians(blobs, theta, s):
+    """Radon transform of the blobs on the lines x cos + y sin = s and its
+    derivatives in theta (s fixed) and in s: each blob projects to
+    rho sqrt(2 pi) sigma exp(-t^2 / (2 sigma^2)), t = s - c . (cos, sin), and
+    dt/dtheta = cx sin - cy cos."""
+    c, sn = np.cos(theta)[:, None], np.sin(theta)[:, None]
+    R = np.zeros(np.broadcast_shapes(c.shape, s.shape))
+    dR_dth, dR_ds = np.zeros_like(R), np.zeros_like(R)
+    for cx, cy, sg, rho in blobs:
+        t = s - (cx * c + cy * sn)
+        gv = rho * math.sqrt(2 * math.pi) * sg * np.exp(-t * t / (2 * sg * sg))
+        R += gv
+        dR_ds += -t / (sg * sg) * gv
+        dR_dth += -t / (sg * sg) * (cx * sn - cy * c) * gv
+    return R, dR_dth, dR_ds
+
+
+def test_derivatives_converge_to_those_of_the_analytic_radon_of_gaussians():
+    rng = np.random.default_rng(8)
+    V = 24
+    theta = synth.random_angles(V, rng)
+    delta = rng.normal(0, 0.5, V)
+    base = gaussian_blobs(rng)
+    errs = []
+    for N in (32, 64, 128, 256):
+        blobs = [(cx * N, cy * N, sg * N, rho) for (cx, cy, sg, rho) in base]
+        X = gaussian_image(N, blobs).ravel()
+        B = synth.n_bins(N)
+        g = _geom(N, V, B)
+        R, R_th, R_s = _radon_gaussians(blobs, theta, np.arange(B) - (B - 1) / 2 + delta[:, None])
+        Y = oracle.forward(g, theta, X, delta)
+        dt, dd = oracle.dsample(g, theta, X, delta)
+        errs.append([np.linalg.norm(a - r.ravel()) / np.linalg.norm(r) for a, r in ((Y, R), (dt, R_th), (dd, R_s))])
+    errs = np.array(errs)
+    # linear interpolation of a smooth image: O(N^-2) for the projection; the
+    # derivatives use the cell slopes, whose O(1/N) errors partly cancel over a ray
+    assert np.all(errs[1:, 0] < 0.35 * errs[:-1, 0]), errs
+    assert np.all(errs[1:, 1:] < 0.6 * errs[:-1, 1:]), errs
+    assert errs[-1, 0] < 1e-3 and np.all(errs[-1, 1:] < 1.5e-2), errs
 
 
 def _fd_setup(kind, N=32, V=12, seed=5):
