@@ -5,6 +5,10 @@
 * with fixed lambda and fixed weights the generalized Krylov iteration reaches
   the dense normal-equation solution once V spans the image space;
 * fixed-lambda Enlarge steps never increase J_{eps,lambda} (Lemma on image descent);
+* with the angles held (Alg. "NL-RMM-GKS" reduced to Alg. "RMM-GKS"), fixed lambda and
+  fixed weights, the restarted outer loop (Enlarge, Compress, residual append) never
+  increases J and converges to the dense normal-equation solution, even with a basis
+  far smaller than the image space;
 * after Compress u lies in span(V) and V has orthonormal columns;
 * the discrepancy-principle lambda hits the target residual;
 * the per-view Gauss-Newton / Armijo update reaches the brute-force minimizer of a
@@ -126,6 +130,29 @@ def test_fixed_lambda_enlarge_steps_decrease_the_objective():
         J.append(nlrmm.objective(g, th, None, u, b, lam, eps))
     assert all(J[i + 1] <= J[i] * (1 + 1e-12) for i in range(len(J) - 1)), J
     assert J[-1] < 0.5 * J[0]
+
+
+@pytest.mark.parametrize("k_min,k_max,iters,tol", [(3, 8, 30, 1e-10), (4, 12, 15, 1e-11)])
+def test_restarted_outer_loop_converges_to_the_dense_solution(k_min, k_max, iters, tol):
+    g, th, _, _, b, _ = small_problem(N=10, V=10)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 2.0, 2 * g.N * (g.N - 1))
+    lam = 0.3
+    A = oracle.dense_matrix(g, th)
+    E = np.eye(g.n)
+    PsiM = np.stack([nlrmm.psi(g, E[:, j]) for j in range(g.n)], 1)
+    u_ref = np.linalg.solve(A.T @ A + lam * PsiM.T @ (w[:, None] * PsiM), A.T @ b)
+
+    def J(u):
+        return 0.5 * np.sum((A @ u - b) ** 2) + 0.5 * lam * np.sum(w * (PsiM @ u) ** 2)
+
+    opts = nlrmm.Options(k_min=k_min, k_max=k_max, tol1=0.0, lam_fix=lam, fixed_weights=w,
+                         update_theta=False, stop_on_convergence=False, outer_iters=iters)
+    Js = []
+    u, theta, _ = nlrmm.NLRMMGKS(g, b, opts).solve(th, callback=lambda it, u, *_: Js.append(J(u)))
+    assert np.array_equal(theta, th)
+    assert all(Js[i + 1] <= Js[i] * (1 + 1e-12) for i in range(len(Js) - 1)), Js
+    assert np.linalg.norm(u - u_ref) <= tol * np.linalg.norm(u_ref)
 
 
 def test_compress_keeps_u_in_the_span_and_orthonormality():
