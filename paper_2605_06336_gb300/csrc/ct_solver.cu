@@ -365,7 +365,7 @@ template <typename T> struct Solver {
         SV_TRY(gram_psi(kc, stop));
         // lambda and the reduced solution
         const double target = (o.tau * noise) * (o.tau * noise);
-        k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
+        k_small_solve<<<1, kSolveThreads, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
                                                                      o.lam_lo, o.lam_hi, o.lam_iters, y, scal, ctl);
         // u = V y ; res = (HV) y - b
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, kc, y, u, T(0), T(1), nullptr, T(0), stop);
@@ -481,7 +481,7 @@ template <typename T> struct Solver {
         SV_TRY(project(theta, 0, k, nullptr));
         SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_TRY(full_gram(k));
-        k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
+        k_small_solve<<<1, kSolveThreads, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
                                                                      1, y, vp_scal, vp_ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, vp_u, T(0), T(1), nullptr, T(0), nullptr);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);
@@ -593,7 +593,7 @@ template <typename T> struct Solver {
             k_fill<T><<<grid_for(ne), kThreads, 0, h.stream>>>(w, ne, T(1));
         }
         SV_TRY(gram_psi(k, nullptr));
-        k_small_solve<<<1, 32, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
+        k_small_solve<<<1, kSolveThreads, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
                                                                      1, y, scal, ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, u, T(0), T(1), nullptr, T(0), nullptr);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);

@@ -936,59 +936,95 @@ struct SmallShared {
 // when |phi - target| <= 1e-10 target or the step falls below 1e-12 in t
 // (lambda within ~2e-10 of the root).  The matrix is factored as L D L^T.
 //
-// The whole solve runs in warp 0 (k <= 64, lanes over rows, warp barriers
-// only): FP64 is a narrow pipe on this part, so the kernel is arranged for
-// short dependent chains rather than many threads.
+// FP64 on this part issues one warp instruction per 64 cycles per SM
+// sub-partition, whatever the number of active lanes, so the solve is laid
+// out for short FP64 chains and spread over the four sub-partitions: one CTA
+// of four warps.  In the factorization thread 0 carries the pivot chain (it
+// updates the next pivot and takes its reciprocal while warps 1-3 update the
+// rest of the trailing block and the right-hand side); the substitutions and
+// the small reductions run in warp 0.
+constexpr int kSolveThreads = 128;
+
 struct SolveShared {
     double GH[kKMax * kLd], GP[kKMax * kLd], L[kKMax * kLd];
-    double c[kKMax], v[kKMax], y[kKMax], w[kKMax], inv[kKMax];
+    double c[kKMax], v[kKMax], y[kKMax], inv[kKMax];
+    double fd[2];  // phi(lambda) and d phi / d t of the last evaluation
     int bad;
 };
 
-// LDL^T factorization of the lower triangle of L in place (one warp): the
-// strict lower triangle becomes the unit factor, inv[j] = 1 / D_j (no square
-// roots: one division per column on the serial path).  Pivots at or below
-// tiny * L_00 are clamped and flag *bad.
-__device__ void ldlt_warp(double *L, double *inv, int k, int *bad)
+// L D L^T factorization of the lower triangle of L in place (all threads of a
+// kSolveThreads CTA), with the forward substitution z = L^{-1} rhs done along
+// the way (rhs overwritten).  The strict lower triangle becomes the unit
+// factor and inv[j] = 1 / D_j.  Column j updates the trailing entries
+// L[i][l] -= L[i][j] L[l][j] / D_j from the unscaled column; thread 0 updates
+// the next pivot first and takes its reciprocal, warps 1-3 the other entries
+// and rhs[i] -= (L[i][j] / D_j) rhs[j]; the columns are scaled at the end.
+// Pivots at or below tiny * L_00 are clamped and flag *bad.
+__device__ void ldlt_fwd(double *L, double *inv, double *rhs, int k, int *bad)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int kWorkers = kSolveThreads - 32;
+    const int tid = threadIdx.x;
     const double floor_ = 1e-300 + 1e-15 * fabs(L[0]);
+    if (tid == 0) {
+        double d = L[0];
+        if (!(d > floor_)) {
+            d = floor_;
+            *bad = 1;
+        }
+        inv[0] = 1.0 / d;
+    }
+    __syncthreads();
     for (int j = 0; j < k; ++j) {
-        if (lane == 0) {
-            double d = L[j * kLd + j];
-            if (!(d > floor_)) {
-                d = floor_;
-                *bad = 1;
-            }
-            inv[j] = 1.0 / d;
-        }
-        __syncwarp();
         const double id = inv[j];
-        // trailing lower triangle: rows i > j, columns j < l <= i, from the
-        // unscaled column (A_ij A_lj / D_j)
         const int m = k - j - 1;
-        int i = 0, l = lane;  // entry idx = i (i + 1) / 2 + l of the trailing block, 0 <= l <= i
-        while (l > i) {
-            l -= i + 1;
-            ++i;
-        }
-        for (int idx = lane; idx < m * (m + 1) / 2; idx += 32) {
-            const int ri = j + 1 + i, cl = j + 1 + l;
-            L[ri * kLd + cl] -= L[ri * kLd + j] * id * L[cl * kLd + j];
-            l += 32;
+        if (tid == 0) {
+            if (m > 0) {
+                const int p = (j + 1) * kLd + j + 1, q = (j + 1) * kLd + j;
+                L[p] -= L[q] * id * L[q];
+                double d = L[p];
+                if (!(d > floor_)) {
+                    d = floor_;
+                    *bad = 1;
+                }
+                inv[j + 1] = 1.0 / d;
+            }
+        } else if (tid >= 32) {
+            // entry e of the trailing triangle (row i, column l <= i, e = i (i + 1) / 2 + l),
+            // e = 1 .. m (m + 1) / 2 - 1 (e = 0 is the next pivot); e beyond the triangle
+            // (row i = m) is the right-hand-side entry of row j + 1 + l
+            const int e0 = tid - 31;
+            int i = 0, l = e0;
             while (l > i) {
                 l -= i + 1;
                 ++i;
             }
+            const double zj = rhs[j];
+            for (int e = e0; e < m * (m + 1) / 2 + m; e += kWorkers) {
+                if (i < m) {
+                    const int ri = j + 1 + i, cl = j + 1 + l;
+                    L[ri * kLd + cl] -= L[ri * kLd + j] * id * L[cl * kLd + j];
+                } else {
+                    const int r = j + 1 + l;
+                    rhs[r] -= L[r * kLd + j] * id * zj;
+                }
+                l += kWorkers;
+                while (l > i && i < m) {
+                    l -= i + 1;
+                    ++i;
+                }
+            }
         }
-        __syncwarp();
-        for (int r = j + 1 + lane; r < k; r += 32) L[r * kLd + j] *= id;  // unit factor column
-        __syncwarp();
+        __syncthreads();
     }
+    for (int e = tid; e < k * k; e += kSolveThreads) {  // unit factor
+        const int r = e / k, c = e % k;
+        if (c < r) L[r * kLd + c] *= inv[c];
+    }
+    __syncthreads();
 }
 
-// v := (L D L^T)^{-1} v (one warp, lanes over rows)
-__device__ void ldlt_solve_warp(const double *L, const double *inv, double *v, int k)
+// v := L^{-1} v for the unit factor (warp 0, lanes over rows)
+__device__ void fwd_subst_warp(const double *L, double *v, int k)
 {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < k; ++j) {
@@ -996,6 +1032,12 @@ __device__ void ldlt_solve_warp(const double *L, const double *inv, double *v, i
         for (int i = j + 1 + lane; i < k; i += 32) v[i] -= L[i * kLd + j] * zj;
         __syncwarp();
     }
+}
+
+// v := L^{-T} D^{-1} v (warp 0): the second half of an L D L^T solve
+__device__ void back_subst_warp(const double *L, const double *inv, double *v, int k)
+{
+    const int lane = threadIdx.x & 31;
     for (int i = lane; i < k; i += 32) v[i] *= inv[i];
     __syncwarp();
     for (int j = k - 1; j >= 0; --j) {
@@ -1005,58 +1047,73 @@ __device__ void ldlt_solve_warp(const double *L, const double *inv, double *v, i
     }
 }
 
-__global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ GH, const double *__restrict__ cvec,
-                                                     const double *__restrict__ GP, int k, double bnorm2,
-                                                     double target, double lam_fix, double lam_lo, double lam_hi,
-                                                     int lam_iters, double *__restrict__ y, double *__restrict__ scal,
-                                                     int *__restrict__ ctl)
+__global__ void __launch_bounds__(kSolveThreads) k_small_solve(const double *__restrict__ GH,
+                                                               const double *__restrict__ cvec,
+                                                               const double *__restrict__ GP, int k, double bnorm2,
+                                                               double target, double lam_fix, double lam_lo,
+                                                               double lam_hi, int lam_iters, double *__restrict__ y,
+                                                               double *__restrict__ scal, int *__restrict__ ctl)
 {
     if (ctl[kStop]) return;
-    if (threadIdx.x >= 32) return;  // warp 0 does the work
     extern __shared__ unsigned char smem_raw[];
     SolveShared &S = *reinterpret_cast<SolveShared *>(smem_raw);
-    const int lane = threadIdx.x;
-    if (lane == 0) S.bad = 0;
-    for (int idx = lane; idx < k * k; idx += 32) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) S.bad = 0;
+    for (int idx = tid; idx < k * k; idx += kSolveThreads) {
         const int i = idx / k, j = idx % k;
         S.GH[i * kLd + j] = GH[i * kKMax + j];
         S.GP[i * kLd + j] = GP[i * kKMax + j];
     }
-    for (int i = lane; i < k; i += 32) S.c[i] = cvec[i];
+    for (int i = tid; i < k; i += kSolveThreads) S.c[i] = cvec[i];
     const double lam_prev = scal[kLam];
-    __syncwarp();
-    // phi(lambda) (and d phi / d t, t = log10 lambda, when want_d); leaves y in S.y
+    __syncthreads();
+    // phi(lambda) (and d phi / d t, t = log10 lambda, when want_d); leaves y in
+    // S.y.  Called by every thread with the same arguments; returns the same
+    // value in every thread.
     auto eval = [&](double lam, bool want_d, double &dphi_dt) -> double {
-        for (int idx = lane; idx < k * k; idx += 32) {
+        for (int idx = tid; idx < k * k; idx += kSolveThreads) {
             const int i = idx / k, j = idx % k;
             if (j <= i) S.L[i * kLd + j] = S.GH[i * kLd + j] + lam * S.GP[i * kLd + j];
         }
-        for (int i = lane; i < k; i += 32) S.y[i] = S.c[i];
-        __syncwarp();
-        ldlt_warp(S.L, S.inv, k, &S.bad);
-        ldlt_solve_warp(S.L, S.inv, S.y, k);
-        double cy = 0.0, yw = 0.0;
-        for (int i = lane; i < k; i += 32) {
-            double t = 0.0;
-            for (int l = 0; l < k; ++l) t += S.GP[i * kLd + l] * S.y[l];
-            S.w[i] = t;
-            S.v[i] = t;
-            cy += S.c[i] * S.y[i];
-            yw += S.y[i] * t;
+        for (int i = tid; i < k; i += kSolveThreads) S.y[i] = S.c[i];
+        __syncthreads();
+        ldlt_fwd(S.L, S.inv, S.y, k, &S.bad);
+        if (tid < 32) {
+            back_subst_warp(S.L, S.inv, S.y, k);
+            double cy = 0.0, yw = 0.0;
+            for (int i = lane; i < k; i += 32) {
+                double t = 0.0;
+                for (int l = 0; l < k; ++l) t += S.GP[i * kLd + l] * S.y[l];
+                S.v[i] = t;
+                cy += S.c[i] * S.y[i];
+                yw += S.y[i] * t;
+            }
+            cy = warp_sum(cy);
+            yw = warp_sum(yw);
+            __syncwarp();
+            double d = 0.0;
+            if (want_d) {
+                // w.(L D L^T)^{-1} w = sum_i (L^{-1} w)_i^2 / D_i, w = G_P y
+                fwd_subst_warp(S.L, S.v, k);
+                double wz = 0.0;
+                for (int i = lane; i < k; i += 32) wz += S.v[i] * S.v[i] * S.inv[i];
+                wz = warp_sum(wz);
+                d = 2.0 * lam * wz * lam * 2.302585092994045684;  // d/dt = lambda ln(10) d/dlambda
+            }
+            if (lane == 0) {
+                S.fd[0] = bnorm2 - cy - lam * yw;
+                S.fd[1] = d;
+            }
         }
-        cy = warp_sum(cy);
-        yw = warp_sum(yw);
-        __syncwarp();
-        dphi_dt = 0.0;
-        if (want_d) {
-            ldlt_solve_warp(S.L, S.inv, S.v, k);
-            double wz = 0.0;
-            for (int i = lane; i < k; i += 32) wz += S.w[i] * S.v[i];
-            wz = warp_sum(wz);
-            dphi_dt = 2.0 * lam * wz * lam * 2.302585092994045684;  // d/dt = lambda ln(10) d/dlambda
-        }
-        return bnorm2 - cy - lam * yw;
+        __syncthreads();
+        const double f = S.fd[0];
+        dphi_dt = S.fd[1];
+        __syncthreads();  // S.fd is rewritten by the next evaluation
+        return f;
     };
+    // 10^t (exp of t ln 10: the search only needs a smooth monotone map, and
+    // the lambda returned is the one the last evaluation used)
+    auto p10 = [](double t) { return exp(t * 2.302585092994045684); };
     double lam, dd;
     if (lam_fix > 0.0) {
         lam = lam_fix;
@@ -1066,6 +1123,7 @@ __global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ 
         // still lam_lo (lam_hi) is evaluated only when a step would leave it,
         // and ends the search when the target lies beyond it.  S.y always
         // holds the solution at the last evaluated t, which is returned.
+        // Every thread runs this control flow on the same values.
         double lo = lam_lo, hi = lam_hi;
         bool lo_seen = false, hi_seen = false;
         double t = (lam_prev > 0.0) ? log10(lam_prev) : 0.5 * (lo + hi);
@@ -1074,7 +1132,7 @@ __global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ 
         for (int it = 0; it < lam_iters + 2; ++it) {
             double dft;
             te = t;
-            const double f = eval(pow(10.0, t), true, dft) - target;
+            const double f = eval(p10(t), true, dft) - target;
             if (t == lam_lo && f >= 0.0) break;  // target at or below the smallest residual
             if (t == lam_hi && f <= 0.0) break;  // target at or above the largest residual
             // phi carries rounding errors near 1e-12 of the target here; once it
@@ -1100,10 +1158,10 @@ __global__ void __launch_bounds__(256) k_small_solve(const double *__restrict__ 
             if (fabs(tn - t) <= tol || hi - lo <= tol) break;  // t is the root to tol
             t = tn;
         }
-        lam = pow(10.0, te);
+        lam = p10(te);
     }
-    for (int i = lane; i < k; i += 32) y[i] = S.y[i];
-    if (lane == 0) {
+    for (int i = tid; i < k; i += kSolveThreads) y[i] = S.y[i];
+    if (tid == 0) {
         scal[kLam] = lam;
         if (S.bad) ctl[kBreakdown] = 1;
     }
