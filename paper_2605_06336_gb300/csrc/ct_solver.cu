@@ -438,14 +438,23 @@ template <typename T> struct Solver {
             SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
             k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
                                                      ctl);
+            // Trial rounds run predicated on ctl[kArmijoDone] (set by k_armijo when no
+            // view searches any more); the host reads the flag after rounds 1, 3, 7, 15
+            // and the last only, so a search that needs many halvings costs few round
+            // trips and one that ends early enqueues few idle rounds.
+            const int *done = ctl + kArmijoDone;
+            int next_check = 1;
             for (int hv = 0; hv <= o.max_halvings; ++hv) {
-                SV_CUDA(launch_view_setup_wide(h, th_t, delta, ctl + kViewChanged));
+                SV_CUDA(launch_view_setup_wide(h, th_t, delta, ctl + kViewChanged, done));
                 SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw,
-                                     h.tune.der_stage, active));
+                                     h.tune.der_stage, active, done));
                 k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, th_n, h.V, o.c1, o.beta, alpha, th_t, active, ctl,
                                                    hv == o.max_halvings ? 1 : 0);
-                SV_TRY(sync_ctl());
-                if (h_ctl[kActive] == 0) break;
+                if (hv + 1 == next_check || hv == o.max_halvings) {
+                    SV_TRY(sync_ctl());
+                    if (h_ctl[kArmijoDone]) break;
+                    next_check = 2 * next_check + 1;
+                }
             }
             SV_CUDA(cudaMemcpyAsync(th_n, th_t, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
         }

@@ -31,7 +31,7 @@ inline int red_blocks(long long len)
 }
 
 // control words (int) and scalars (double) living on the device
-enum Ctl { kStop = 0, kStopNext, kSteps, kActive, kBreakdown, kViewChanged, kCtlCount };
+enum Ctl { kStop = 0, kStopNext, kSteps, kActive, kBreakdown, kViewChanged, kArmijoDone, kCtlCount };
 enum Scal { kLam = 0, kRnorm2, kDu2, kU2, kJreg, kBnorm2, kTmp0, kTmp1, kScalCount };
 
 __device__ __forceinline__ bool stopped(const int *stop) { return stop && *stop; }
@@ -1259,16 +1259,22 @@ __global__ void k_gn_direction(const double *__restrict__ g, const double *__res
         theta_trial[v] = theta[v] + alpha0 * dv;
         active[v] = 1;
     }
-    if (threadIdx.x == 0) ctl[kActive] = V;
+    if (threadIdx.x == 0) {
+        ctl[kActive] = V;
+        ctl[kArmijoDone] = V == 0;
+    }
 }
 
 // Armijo test for the views still searching; shrinks alpha of the failures.
+// ctl[kArmijoDone] becomes 1 once no view searches; the trial kernels of the
+// later rounds (and this kernel) then return at once.
 __global__ void k_armijo(const double *__restrict__ f0, const double *__restrict__ ft, const double *__restrict__ g,
                          const double *__restrict__ d, const double *__restrict__ theta, int V, double c1, double beta,
                          double *__restrict__ alpha, double *__restrict__ theta_trial, int *__restrict__ active,
                          int *__restrict__ ctl, int last)
 {
     __shared__ int cnt[32];
+    if (ctl[kArmijoDone]) return;
     int mine = 0;
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
         if (!active[v]) continue;
@@ -1291,6 +1297,7 @@ __global__ void k_armijo(const double *__restrict__ f0, const double *__restrict
         int t = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += cnt[i];
         ctl[kActive] = t;
+        ctl[kArmijoDone] = t == 0;
     }
 }
 
