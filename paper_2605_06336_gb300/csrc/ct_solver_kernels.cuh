@@ -133,18 +133,6 @@ __global__ void k_add_reg(T *__restrict__ r, const T *__restrict__ u, const T *_
     }
 }
 
-// J_reg partial: sum_e sqrt(z_e^2 + eps^2) is 1/w_e; summed per block
-template <typename T>
-__global__ void k_reg_value(const T *__restrict__ w, long long ne, double *__restrict__ part)
-{
-    __shared__ double sh[33];
-    double s = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
-        s += 1.0 / (double)w[e];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
 // ---------------------------------------------------------------------------
 // weighted Gram of Psi V:  G[a][b] = sum_e w_e (Psi v_a)_e (Psi v_b)_e,
 // a <= b < k.  A fixed grid of CTAs walks the tiles (TR x 32 pixels of one
