@@ -8,7 +8,8 @@
 * with the angles held (Alg. "NL-RMM-GKS" reduced to Alg. "RMM-GKS"), fixed lambda and
   fixed weights, the restarted outer loop (Enlarge, Compress, residual append) never
   increases J and converges to the dense normal-equation solution, even with a basis
-  far smaller than the image space;
+  far smaller than the image space; the same holds for the dynamic form, whose Psi
+  adds the frame-to-frame differences (ANISO-TV), on frames with uneven view counts;
 * after Compress u lies in span(V) and V has orthonormal columns;
 * the discrepancy-principle lambda hits the target residual;
 * the per-view Gauss-Newton / Armijo update reaches the brute-force minimizer of a
@@ -153,6 +154,31 @@ def test_restarted_outer_loop_converges_to_the_dense_solution(k_min, k_max, iter
     assert np.array_equal(theta, th)
     assert all(Js[i + 1] <= Js[i] * (1 + 1e-12) for i in range(len(Js) - 1)), Js
     assert np.linalg.norm(u - u_ref) <= tol * np.linalg.norm(u_ref)
+
+
+@pytest.mark.parametrize("k_min,k_max,iters", [(3, 8, 40), (4, 12, 20)])
+def test_restarted_dynamic_loop_converges_to_the_space_time_dense_solution(k_min, k_max, iters):
+    rng = np.random.default_rng(5)
+    N, vpf = 6, [4, 5, 3]
+    g = oracle.Geometry(N, synth.n_bins(N), sum(vpf), views_per_frame=vpf)
+    th = np.sort(rng.uniform(0, math.pi, g.V))
+    b = oracle.forward(g, th, rng.uniform(size=g.n)) + 0.01 * rng.standard_normal(g.m)
+    w = rng.uniform(0.5, 2.0, nlrmm.psi(g, np.zeros(g.n), temporal=True).size)
+    lam = 0.3
+    A = oracle.dense_matrix(g, th)
+    E = np.eye(g.n)
+    D1 = np.stack([nlrmm.psi(g, E[:, j], temporal=True) for j in range(g.n)], 1)   # pinned by the Kronecker test
+    u_ref = np.linalg.solve(A.T @ A + lam * D1.T @ (w[:, None] * D1), A.T @ b)
+
+    def J(u):
+        return 0.5 * np.sum((A @ u - b) ** 2) + 0.5 * lam * np.sum(w * (D1 @ u) ** 2)
+
+    opts = nlrmm.Options(k_min=k_min, k_max=k_max, tol1=0.0, lam_fix=lam, fixed_weights=w, update_theta=False,
+                         stop_on_convergence=False, outer_iters=iters, temporal=True)
+    Js = []
+    u, _, _ = nlrmm.NLRMMGKS(g, b, opts).solve(th, callback=lambda it, u, *_: Js.append(J(u)))
+    assert all(Js[i + 1] <= Js[i] * (1 + 1e-12) for i in range(len(Js) - 1)), Js
+    assert np.linalg.norm(u - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
 
 
 def test_compress_keeps_u_in_the_span_and_orthonormality():
