@@ -234,7 +234,9 @@ typedef struct {
     int32_t outer_iters;    /* outer iteration limit */
     int32_t maxiter_p;      /* Gauss-Newton iterations per outer iteration (default 3) */
     int32_t max_halvings;   /* Armijo backtracking halvings (default 20) */
-    int32_t lam_iters;      /* bisection steps of the discrepancy principle (default 60) */
+    int32_t lam_iters;      /* step limit of the discrepancy-principle search for lambda (default 60;
+                               the device runs safeguarded Newton steps in log10 lambda, at most
+                               lam_iters + 2 evaluations, stopping at |phi - target| <= 1e-10 target) */
     int32_t update_theta;   /* 0: angles fixed (the solve is RMM-GKS) */
     int32_t stop_on_convergence; /* stop when du < tol_u and dtheta < tol_p */
     double eps;             /* smoothing of the l1 term, P = diag((z^2 + eps^2)^(-1/4)) (default 1e-3) */
@@ -256,7 +258,7 @@ typedef struct {
 typedef struct {
     int32_t outer_done;     /* outer iterations run */
     int32_t converged;      /* stopping rule met */
-    int32_t breakdown;      /* a Cholesky pivot was clamped or a residual vanished */
+    int32_t breakdown;      /* a pivot of the reduced problem's L D L^T was clamped or a residual vanished */
     int32_t enlarge_steps[NLRMM_MAX_HIST];
     double lambda[NLRMM_MAX_HIST];   /* lambda of the last Enlarge step */
     double du[NLRMM_MAX_HIST];       /* |u_{k+1} - u_k| / |u_k| */
