@@ -284,7 +284,10 @@ def solver_comparison(w, dev, outer_iters, **extra):
         torch.cuda.synchronize()
         total_ms = e0.elapsed_time(e1)
         ang = float((th - th_true).norm() / th_true.norm())
+        it_ms = np.asarray(st["ms"], dtype=float)   # host wall time of each outer iteration
+        spread = [float(np.percentile(it_ms, q)) for q in (10, 50, 90)] if it_ms.size else None
         out[name] = {"total_ms": total_ms, "ms_per_outer_iter": total_ms / outer_iters,
+                     "outer_iter_ms_p10_p50_p90": spread,
                      "final_rre": st["rre"][-1], "rel_angle_err": ang,
                      "max_abs_angle_err_deg": float((th - th_true).abs().max()) * 180 / math.pi,
                      "enlarge_steps": sum(st["enlarge_steps"])}
