@@ -2,6 +2,8 @@
 
 * Psi is the stacked Kronecker finite-difference operator and Psi^T its transpose;
 * the MM majorant touches J at u_k and lies above it (properties (i), (iii), Sec. 3.1);
+* the Golub-Kahan start basis spans the Krylov space K_k(H^T H, H^T b), starts along
+  H^T b, is orthonormal, and V^T H^T H V is tridiagonal (the Lanczos relation);
 * with fixed lambda and fixed weights the generalized Krylov iteration reaches
   the dense normal-equation solution once V spans the image space;
 * fixed-lambda Enlarge steps never increase J_{eps,lambda} (Lemma on image descent);
@@ -97,6 +99,24 @@ def test_majorant_touches_and_majorizes():
     for _ in range(20):
         u = uk + rng.standard_normal(g.n) * rng.uniform(0.01, 2)
         assert nlrmm.majorant(g, th, None, u, uk, b, lam, eps) >= nlrmm.objective(g, th, None, u, b, lam, eps) - 1e-9
+
+
+def test_golub_kahan_basis_spans_the_krylov_space():
+    g, th, _, _, b, nn = small_problem(N=12, V=10)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(noise_norm=nn))
+    A = oracle.dense_matrix(g, th)
+    for k in (2, 3, 4, 5):
+        V = s.gkb(th, k)
+        K = [A.T @ b]
+        for _ in range(k - 1):
+            K.append(A.T @ (A @ K[-1]))
+        Q, _ = np.linalg.qr(np.stack(K, 1))
+        assert np.linalg.norm(V @ V.T - Q @ Q.T) <= 1e-9
+        assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-13
+        v0 = A.T @ b
+        assert abs(abs(V[:, 0] @ v0) - np.linalg.norm(v0)) <= 1e-12 * np.linalg.norm(v0)
+        T = (A @ V).T @ (A @ V)
+        assert np.abs(np.triu(T, 2)).max() <= 1e-12 * np.abs(T).max()
 
 
 def test_full_krylov_space_gives_the_dense_solution():
