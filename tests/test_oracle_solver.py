@@ -12,7 +12,9 @@
   increases J and converges to the dense normal-equation solution, even with a basis
   far smaller than the image space; the same holds for the dynamic form, whose Psi
   adds the frame-to-frame differences (ANISO-TV), on frames with uneven view counts;
-* after Compress u lies in span(V) and V has orthonormal columns;
+* after Compress u lies in span(V) and V has orthonormal columns; the retained
+  directions are the dominant eigenvectors of V^T (H^T H + lambda Psi^T P^2 Psi) V formed
+  from the dense matrices (the leading right singular vectors of [R_H; sqrt(lambda) R_Psi]);
 * the discrepancy-principle lambda hits the target residual;
 * the per-view Gauss-Newton / Armijo update reaches the brute-force minimizer of a
   single view's misfit;
@@ -214,6 +216,31 @@ def test_compress_keeps_u_in_the_span_and_orthonormality():
     assert Vk.shape[1] == opts.k_min
     assert np.abs(Vk.T @ Vk - np.eye(Vk.shape[1])).max() < 1e-12
     assert np.linalg.norm(u - Vk @ (Vk.T @ u)) <= 1e-12 * np.linalg.norm(u)
+
+
+def test_compress_keeps_the_dominant_directions():
+    g, th, _, _, b, nn = small_problem(N=12, V=10, seed=5)
+    rng = np.random.default_rng(9)
+    w = rng.uniform(0.5, 2.0, 2 * g.N * (g.N - 1))
+    lam = 0.2
+    opts = nlrmm.Options(k_min=4, k_max=14, tol1=0.0, lam_fix=lam, fixed_weights=w)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    V = s.gkb(th, opts.k_min)
+    HV = np.stack([s.H(th, V[:, j]) for j in range(V.shape[1])], 1)
+    u, lam_used, Vg, _, RH, RP, used, _ = s.enlarge(th, V, HV, np.zeros(g.n), 10)
+    assert lam_used == lam
+    Vk = s.compress(Vg, RH, RP, used, lam, u)
+    A = oracle.dense_matrix(g, th)
+    E = np.eye(g.n)
+    PsiM = np.stack([nlrmm.psi(g, E[:, j]) for j in range(g.n)], 1)
+    Vu = Vg[:, :used]
+    M = Vu.T @ (A.T @ A + lam * PsiM.T @ (w[:, None] * PsiM)) @ Vu
+    ev, Q = np.linalg.eigh(M)
+    keep = opts.k_min - 1
+    assert ev[-keep] - ev[-keep - 1] > 1e-6 * ev[-1]          # the kept block is separated
+    top = Vu @ Q[:, -keep:]
+    got = Vk[:, :keep]
+    assert np.linalg.norm(top @ top.T - got @ got.T) <= 1e-8
 
 
 def test_discrepancy_principle_hits_the_target():
