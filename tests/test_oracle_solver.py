@@ -15,7 +15,8 @@
 * after Compress u lies in span(V) and V has orthonormal columns; the retained
   directions are the dominant eigenvectors of V^T (H^T H + lambda Psi^T P^2 Psi) V formed
   from the dense matrices (the leading right singular vectors of [R_H; sqrt(lambda) R_Psi]);
-* the discrepancy-principle lambda hits the target residual;
+* the discrepancy-principle lambda hits the target residual; targets out of reach give
+  the ends of the bracket, and the projected residual increases with lambda;
 * the per-view Gauss-Newton / Armijo update reaches the brute-force minimizer of a
   single view's misfit;
 * a small alternating solve reduces both the image and the angle error;
@@ -261,6 +262,26 @@ def test_discrepancy_principle_hits_the_target():
     # the same residual computed in the full space
     r = HV @ y - b
     assert abs(r @ r - phi) <= 1e-9 * target
+
+
+def test_discrepancy_targets_out_of_reach_give_the_bracket_ends():
+    """The reading for targets no lambda in [10^-10, 10^10] reaches: a target at or below
+    the smallest projected residual gives 10^-10, one at or above the largest 10^10;
+    phi is increasing in lambda in between."""
+    g, th, _, _, b, nn = small_problem(N=16, V=12, seed=6, noise=0.05)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(noise_norm=nn))
+    V = s.gkb(th, 8)
+    HV = np.stack([s.H(th, V[:, j]) for j in range(V.shape[1])], 1)
+    QH, RH = np.linalg.qr(HV)
+    _, RP = np.linalg.qr(np.stack([nlrmm.psi(g, V[:, j]) for j in range(V.shape[1])], 1))
+    QHb = QH.T @ b
+    phis = [s.projected_residual2(RH, RP, QHb, 10.0 ** t)[0] for t in np.linspace(-10, 10, 41)]
+    assert all(p1 >= p0 * (1 - 1e-12) for p0, p1 in zip(phis, phis[1:]))
+    lo_phi, hi_phi = phis[0], phis[-1]
+    s.o.noise_norm = 0.5 * np.sqrt(lo_phi) / s.o.tau         # target below every reachable residual
+    assert s.choose_lambda(RH, RP, QHb) == 1e-10
+    s.o.noise_norm = 2.0 * np.sqrt(hi_phi) / s.o.tau         # target above every reachable residual
+    assert s.choose_lambda(RH, RP, QHb) == 1e10
 
 
 def test_gauss_newton_reaches_the_single_view_minimizer():
