@@ -2,6 +2,9 @@
 
 * Psi is the stacked Kronecker finite-difference operator and Psi^T its transpose;
 * the MM majorant touches J at u_k and lies above it (properties (i), (iii), Sec. 3.1);
+* the orthogonalization of new basis vectors (two classical Gram-Schmidt passes) leaves
+  a vector orthogonal to V to rounding even when it lies almost in span(V), where one
+  pass fails;
 * the Golub-Kahan start basis spans the Krylov space K_k(H^T H, H^T b), starts along
   H^T b, is orthonormal, and V^T H^T H V is tridiagonal (the Lanczos relation);
 * with fixed lambda and fixed weights the generalized Krylov iteration reaches
@@ -102,6 +105,17 @@ def test_majorant_touches_and_majorizes():
     for _ in range(20):
         u = uk + rng.standard_normal(g.n) * rng.uniform(0.01, 2)
         assert nlrmm.majorant(g, th, None, u, uk, b, lam, eps) >= nlrmm.objective(g, th, None, u, b, lam, eps) - 1e-9
+
+
+def test_reorthogonalization_survives_vectors_almost_in_the_span():
+    rng = np.random.default_rng(3)
+    V, _ = np.linalg.qr(rng.standard_normal((2000, 12)))
+    for eps in (1e-6, 1e-9, 1e-12):
+        r = V @ rng.standard_normal(12) + eps * rng.standard_normal(2000)
+        q = nlrmm.cgs2(V, r)
+        assert np.abs(V.T @ q).max() <= 1e-15 * np.linalg.norm(q)
+        # what is removed lies in span(V): q is r minus its projection
+        np.testing.assert_allclose(q, r - V @ (V.T @ r), atol=1e-13 * np.linalg.norm(r))
 
 
 def test_golub_kahan_basis_spans_the_krylov_space():
