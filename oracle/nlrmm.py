@@ -42,6 +42,14 @@ Readings where the paper is silent (also listed in the design notes):
     backtracking (c1 = 1e-4, beta = 1/2, alpha_bar = 1, at most 20 halvings,
     no step if none is accepted) is applied to each view's own data term;
     3 Gauss-Newton iterations per outer iteration;
+  * Armijo in finite precision (the paper's descent lemmas assume exact
+    arithmetic): before each trial, a search whose predicted decrease
+    c1 * alpha * |g^T d| is below armijo_eps * f (f the misfit being tested,
+    armijo_eps the unit roundoff of the precision the misfit is computed in:
+    2^-53 for FP64, 2^-24 for FP32 residuals) ends with no acceptable step;
+    per view in UPDATE-PARAM, on the whole reduced objective in the VarPro
+    update.  Such a test compares two misfits that differ by less than their
+    own rounding, so its outcome carries no information;
   * VarPro (Options.varpro): the basis is the compressed V^(k+1)_kmin of the
     primary solve, lambda_hat = lambda^(k), B_hat = P Psi V with P^2 the MM
     weights of u^(k+1); the Gauss-Newton matrix is damped by mu = 1e-8 times
@@ -145,6 +153,7 @@ class Options:
     beta: float = 0.5
     alpha0: float = 1.0
     max_halvings: int = 20
+    armijo_eps: float = 2.0 ** -53            # unit roundoff of the misfit's precision (noise floor of Armijo)
     mu_rel: float = 1e-8
     outer_iters: int = 20
     tol_u: float = 1e-3
@@ -293,8 +302,16 @@ class NLRMMGKS:
             d = -grad / (jn2 + mu)
             alpha = np.full(theta.shape, o.alpha0)
             active = np.ones(theta.shape, bool)
+            trials = np.zeros(theta.shape, int)
             for _h in range(o.max_halvings + 1):
+                # noise floor: the predicted decrease is below the rounding of f_v
+                low = active & (o.c1 * alpha * np.abs(grad * d) < o.armijo_eps * f0)
+                alpha[low] = 0.0
+                active &= ~low
+                if not active.any():
+                    break
                 ft = self.view_f(theta + alpha * d, u)
+                trials += active
                 ok = ft <= f0 + o.c1 * alpha * grad * d
                 active &= ~ok
                 if not active.any():
@@ -302,6 +319,7 @@ class NLRMMGKS:
                 alpha[active] *= o.beta
             alpha[active] = 0.0  # no acceptable step for these views
             theta = theta + alpha * d
+            self.last_trials = trials
         return theta
 
     # -- Alg. "UPDATE-PARAM-VarPro" (Sec. 4.2) ----------------------------------
@@ -320,8 +338,12 @@ class NLRMMGKS:
             gd = float(grad @ d)
             alpha = o.alpha0
             accepted = False
+            self.last_trials = 0
             for _h in range(o.max_halvings + 1):
+                if o.c1 * alpha * abs(gd) < o.armijo_eps * f0:
+                    break  # noise floor: the predicted decrease is below the rounding of f
                 ft = varpro_objective(g, self.b, theta + alpha * d, V, lam, w, self.delta, o.temporal)[0]
+                self.last_trials += 1
                 if ft <= f0 + o.c1 * alpha * gd:
                     accepted = True
                     break

@@ -585,3 +585,75 @@ def test_aniso_tv_helps_a_slowly_moving_sequence():
         u, _, hist = nlrmm.NLRMMGKS(g, b_true + e, o).solve(th, u_true=u_true)
         rre[tm] = hist.rre[-1]
     assert rre[True] < rre[False], rre
+
+
+def _view_minimizers(s, th0, u, halfwidth):
+    """Per-view golden-section minimizers of the separable view misfits f_v(theta_v)."""
+    V = th0.size
+    lo, hi = th0 - halfwidth, th0 + halfwidth
+    gr = (math.sqrt(5) - 1) / 2
+    for _ in range(70):
+        a, c = hi - gr * (hi - lo), lo + gr * (hi - lo)
+        fa, fc = s.view_f(a, u), s.view_f(c, u)
+        left = fa < fc
+        hi = np.where(left, c, hi)
+        lo = np.where(left, lo, a)
+    return 0.5 * (lo + hi)
+
+
+def test_armijo_noise_floor_ends_rounding_decided_searches():
+    # noisy data: at a view's own minimizer its predicted decrease c1 |g d| is far
+    # below the rounding of f_v, so any Armijo decision there is rounding noise
+    g, th_nom, th_true, u_true, b, _ = small_problem(N=20, V=16, seed=21, sigma_deg=1.0)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1))
+    th_star = _view_minimizers(s, th_true, u_true, math.radians(3.0))
+    near = np.arange(16) < 8                  # views 0..7 at their minimizer, 8..15 half a degree off
+    th0 = np.where(near, th_star, th_star + math.radians(0.5))
+    grad, jn2, f0 = s.view_terms(th0, u_true)
+    d = -grad / (jn2 + 1e-8 * jn2.max())
+    u32 = 2.0 ** -24
+    pred = 1e-4 * np.abs(grad * d) / f0
+    assert np.all(pred[near] < u32) and np.all(pred[~near] > 1e3 * u32)
+
+    s_off = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1, armijo_eps=0.0))
+    th_off = s_off.update_param(th0, u_true)
+    trials_off = s_off.last_trials
+    s_on = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1, armijo_eps=u32))
+    th_on = s_on.update_param(th0, u_true)
+    trials_on = s_on.last_trials
+    # without the floor the searches at the minimizers run (rounding decides them);
+    # with it they end before the first trial and the angles stay
+    assert trials_off[near].sum() > 8
+    assert np.all(trials_on[near] == 0)
+    assert np.array_equal(th_on[near], th0[near])
+    # views with a real decrease take exactly the steps they take without the floor
+    assert np.array_equal(th_on[~near], th_off[~near])
+    assert np.array_equal(trials_on[~near], trials_off[~near])
+    f_on = s.view_f(th_on, u_true)
+    assert np.all(f_on[~near] < f0[~near])
+    # the floor at FP64 rounding still ends the searches at the minimizers
+    s64 = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1))
+    s64.update_param(th0, u_true)
+    assert np.all(s64.last_trials[near] <= trials_off[near])
+
+
+def test_armijo_noise_floor_stops_after_the_halving_that_crosses_it():
+    # one view, a search that fails at alpha = 1 (a step far too long for this
+    # c1): the floor at armijo_eps = c1 |g d| / (f0 * 2^(k + 1/2)) permits trials
+    # at alpha = 1, 1/2, ..., 2^-k and none after
+    g, th_nom, th_true, u_true, b, _ = small_problem(N=20, V=1, seed=22, sigma_deg=1.0)
+    opts = nlrmm.Options(maxiter_p=1, alpha0=64.0, armijo_eps=0.0)
+    s = nlrmm.NLRMMGKS(g, b, opts)
+    th0 = th_true + math.radians(0.4)
+    s.update_param(th0, u_true)
+    t_free = int(s.last_trials[0])
+    assert t_free >= 5                           # alpha0 = 64 overshoots: several halvings needed
+    grad, jn2, f0 = s.view_terms(th0, u_true)
+    d = -grad / (jn2 + 1e-8 * jn2.max())
+    for k in range(t_free - 1):
+        opts_k = nlrmm.Options(maxiter_p=1, alpha0=64.0,
+                               armijo_eps=1e-4 * 64.0 * abs(grad[0] * d[0]) / (f0[0] * 2.0 ** (k + 0.5)))
+        s_k = nlrmm.NLRMMGKS(g, b, opts_k)
+        th_k = s_k.update_param(th0, u_true)
+        assert int(s_k.last_trials[0]) == k + 1
+        assert th_k[0] == th0[0]                 # no trial accepted before the floor: no step
