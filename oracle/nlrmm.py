@@ -43,13 +43,16 @@ Readings where the paper is silent (also listed in the design notes):
     no step if none is accepted) is applied to each view's own data term;
     3 Gauss-Newton iterations per outer iteration;
   * Armijo in finite precision (the paper's descent lemmas assume exact
-    arithmetic): before each trial, a search whose predicted decrease
-    c1 * alpha * |g^T d| is below armijo_eps * f (f the misfit being tested,
-    armijo_eps the unit roundoff of the precision the misfit is computed in:
-    2^-53 for FP64, 2^-24 for FP32 residuals) ends with no acceptable step;
-    per view in UPDATE-PARAM, on the whole reduced objective in the VarPro
-    update.  Such a test compares two misfits that differ by less than their
-    own rounding, so its outcome carries no information;
+    arithmetic): before each trial, a search whose first-order change of the
+    misfit, alpha * |g^T d|, is below armijo_eps * rho ends with no acceptable
+    step.  rho = sum_b |r_b| (|(H u)_b| + |b_b|) over the residuals r = H u - b
+    the misfit f = 1/2 |r|^2 is formed from bounds the rounding error of
+    evaluating f (each r_b is off by at most a unit roundoff of |H u| + |b|),
+    and armijo_eps is the unit roundoff of the precision f is computed in:
+    2^-53 for FP64, 2^-24 to follow FP32 residuals.  Per view in UPDATE-PARAM
+    (r of that view), on the data residual of the reduced objective in the
+    VarPro update.  Such a test compares two misfits that differ by less than
+    their own rounding, so its outcome carries no information;
   * VarPro (Options.varpro): the basis is the compressed V^(k+1)_kmin of the
     primary solve, lambda_hat = lambda^(k), B_hat = P Psi V with P^2 the MM
     weights of u^(k+1); the Gauss-Newton matrix is damped by mu = 1e-8 times
@@ -153,7 +156,7 @@ class Options:
     beta: float = 0.5
     alpha0: float = 1.0
     max_halvings: int = 20
-    armijo_eps: float = 2.0 ** -53            # unit roundoff of the misfit's precision (noise floor of Armijo)
+    armijo_eps: float = 2.0 ** -53            # unit roundoff of the misfit's precision (Armijo noise floor)
     mu_rel: float = 1e-8
     outer_iters: int = 20
     tol_u: float = 1e-3
@@ -282,11 +285,16 @@ class NLRMMGKS:
 
     # -- Alg. "UPDATE-PARAM" (per view) ---------------------------------------
     def view_terms(self, theta, u):
+        """Per view: gradient g_v, |J_v|^2, misfit f_v and the rounding scale
+        rho_v = sum_b |r_b| (|(H u)_b| + |b_b|) of f_v."""
         g = self.g
-        r = (self.H(theta, u) - self.b).reshape(g.V, g.B)
+        Hu = self.H(theta, u).reshape(g.V, g.B)
+        bv = self.b.reshape(g.V, g.B)
+        r = Hu - bv
         dt, _ = dsample(g, theta, u, self.delta)
         dt = dt.reshape(g.V, g.B)
-        return (r * dt).sum(1), (dt * dt).sum(1), 0.5 * (r * r).sum(1)
+        rho = (np.abs(r) * (np.abs(Hu) + np.abs(bv))).sum(1)
+        return (r * dt).sum(1), (dt * dt).sum(1), 0.5 * (r * r).sum(1), rho
 
     def view_f(self, theta, u):
         g = self.g
@@ -297,15 +305,15 @@ class NLRMMGKS:
         o = self.o
         theta = theta.copy()
         for _ in range(o.maxiter_p):
-            grad, jn2, f0 = self.view_terms(theta, u)
+            grad, jn2, f0, rho = self.view_terms(theta, u)
             mu = o.mu_rel * max(float(jn2.max()), 1e-300)
             d = -grad / (jn2 + mu)
             alpha = np.full(theta.shape, o.alpha0)
             active = np.ones(theta.shape, bool)
             trials = np.zeros(theta.shape, int)
             for _h in range(o.max_halvings + 1):
-                # noise floor: the predicted decrease is below the rounding of f_v
-                low = active & (o.c1 * alpha * np.abs(grad * d) < o.armijo_eps * f0)
+                # noise floor: the first-order change of f_v is below its rounding
+                low = active & (alpha * np.abs(grad * d) < o.armijo_eps * rho)
                 alpha[low] = 0.0
                 active &= ~low
                 if not active.any():
@@ -330,6 +338,7 @@ class NLRMMGKS:
         theta = np.array(theta, float)
         for _ in range(o.maxiter_p):
             Jr, Js, r, s, f0, u = varpro_jacobians(g, self.b, theta, V, lam, w, self.delta, o.temporal)
+            rho = float(np.sum(np.abs(r) * (np.abs(r + self.b) + np.abs(self.b))))
             # gradient of J_{eps,lambda}(u_hat, theta) in theta: only the data term depends on theta
             grad, _ = jacT(g, theta, u, r, self.delta)
             A = Jr.T @ Jr + lam * (Js.T @ Js)
@@ -340,8 +349,8 @@ class NLRMMGKS:
             accepted = False
             self.last_trials = 0
             for _h in range(o.max_halvings + 1):
-                if o.c1 * alpha * abs(gd) < o.armijo_eps * f0:
-                    break  # noise floor: the predicted decrease is below the rounding of f
+                if alpha * abs(gd) < o.armijo_eps * rho:
+                    break  # noise floor: the first-order change of f is below its rounding
                 ft = varpro_objective(g, self.b, theta + alpha * d, V, lam, w, self.delta, o.temporal)[0]
                 self.last_trials += 1
                 if ft <= f0 + o.c1 * alpha * gd:

@@ -278,3 +278,31 @@ def test_frames_are_block_diagonal():
         Yf = oracle.forward(gf, theta[start:start + nv], x[f * N * N:(f + 1) * N * N])
         np.testing.assert_array_equal(Y[start * g.B:(start + nv) * g.B], Yf)
         start += nv
+
+
+def test_joseph_axis_ties_go_to_rows_at_the_fp64_diagonals():
+    """The axis rule (rows iff |cos| >= |sin|, decided on theta mod pi against
+    the doubles nearest pi/4 and 3pi/4): at those doubles the view is
+    row-marched.  The Joseph sums are continuous across the diagonal, their
+    angle derivative is not (row- and column-marched interpolation slopes
+    differ), so the derivative there equals the one a picoradian inside the
+    row-marched side and not the one inside the column-marched side; the same
+    one half-turn on and for negative angles."""
+    N = 16
+    B = synth.n_bins(N)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(size=N * N)
+    q1, q3 = math.pi / 4, 3 * math.pi / 4
+    eps = 1e-12
+    # (diagonal angle, a row-marched neighbour, a column-marched neighbour)
+    cases = [(q1, q1 - eps, q1 + eps), (q3, q3 + eps, q3 - eps), (q1 + math.pi, q1 + math.pi - eps, q1 + math.pi + eps),
+             (-q1, -q1 + eps, -q1 - eps), (q3 - math.pi, q3 - math.pi + eps, q3 - math.pi - eps)]
+    g = oracle.Geometry(N, B, 1)
+    dl = np.array([0.1234])  # moves the samples off the interpolation kinks that an exact 45 degree view meets
+    for t, t_rows, t_cols in cases:
+        assert abs(math.cos(t_rows)) > abs(math.sin(t_rows)) and abs(math.cos(t_cols)) < abs(math.sin(t_cols))
+        y, y_rows, y_cols = (oracle.forward(g, np.array([a]), x, dl) for a in (t, t_rows, t_cols))
+        assert np.max(np.abs(y_rows - y_cols)) <= 1e-9 * np.max(np.abs(y))   # H is continuous there
+        d, d_rows, d_cols = (oracle.dsample(g, np.array([a]), x, dl)[0] for a in (t, t_rows, t_cols))
+        assert np.max(np.abs(d - d_rows)) <= 1e-6 * np.max(np.abs(d)), t
+        assert np.max(np.abs(d - d_cols)) > 1e-2 * np.max(np.abs(d)), t

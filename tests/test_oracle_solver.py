@@ -609,11 +609,12 @@ def test_armijo_noise_floor_ends_rounding_decided_searches():
     th_star = _view_minimizers(s, th_true, u_true, math.radians(3.0))
     near = np.arange(16) < 8                  # views 0..7 at their minimizer, 8..15 half a degree off
     th0 = np.where(near, th_star, th_star + math.radians(0.5))
-    grad, jn2, f0 = s.view_terms(th0, u_true)
+    grad, jn2, f0, rho = s.view_terms(th0, u_true)
     d = -grad / (jn2 + 1e-8 * jn2.max())
     u32 = 2.0 ** -24
-    pred = 1e-4 * np.abs(grad * d) / f0
+    pred = np.abs(grad * d) / rho
     assert np.all(pred[near] < u32) and np.all(pred[~near] > 1e3 * u32)
+    assert np.all(rho >= 2 * f0)   # |H u| + |b| >= |r| term by term
 
     s_off = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1, armijo_eps=0.0))
     th_off = s_off.update_param(th0, u_true)
@@ -638,9 +639,9 @@ def test_armijo_noise_floor_ends_rounding_decided_searches():
 
 
 def test_armijo_noise_floor_stops_after_the_halving_that_crosses_it():
-    # one view, a search that fails at alpha = 1 (a step far too long for this
-    # c1): the floor at armijo_eps = c1 |g d| / (f0 * 2^(k + 1/2)) permits trials
-    # at alpha = 1, 1/2, ..., 2^-k and none after
+    # one view, a search that fails at alpha0 = 64 (a step far too long): the
+    # floor at armijo_eps = alpha0 |g d| / (rho * 2^(k + 1/2)) permits trials at
+    # alpha = alpha0, alpha0 / 2, ..., alpha0 2^-k and none after
     g, th_nom, th_true, u_true, b, _ = small_problem(N=20, V=1, seed=22, sigma_deg=1.0)
     opts = nlrmm.Options(maxiter_p=1, alpha0=64.0, armijo_eps=0.0)
     s = nlrmm.NLRMMGKS(g, b, opts)
@@ -648,12 +649,29 @@ def test_armijo_noise_floor_stops_after_the_halving_that_crosses_it():
     s.update_param(th0, u_true)
     t_free = int(s.last_trials[0])
     assert t_free >= 5                           # alpha0 = 64 overshoots: several halvings needed
-    grad, jn2, f0 = s.view_terms(th0, u_true)
+    grad, jn2, f0, rho = s.view_terms(th0, u_true)
     d = -grad / (jn2 + 1e-8 * jn2.max())
     for k in range(t_free - 1):
         opts_k = nlrmm.Options(maxiter_p=1, alpha0=64.0,
-                               armijo_eps=1e-4 * 64.0 * abs(grad[0] * d[0]) / (f0[0] * 2.0 ** (k + 0.5)))
+                               armijo_eps=64.0 * abs(grad[0] * d[0]) / (rho[0] * 2.0 ** (k + 0.5)))
         s_k = nlrmm.NLRMMGKS(g, b, opts_k)
         th_k = s_k.update_param(th0, u_true)
         assert int(s_k.last_trials[0]) == k + 1
         assert th_k[0] == th0[0]                 # no trial accepted before the floor: no step
+
+
+def test_rounding_scale_bounds_the_float32_misfit_error():
+    # rho_v = sum_b |r_b| (|(Hu)_b| + |b_b|) bounds, to first order, the error of
+    # evaluating f_v = 1/2 |r_v|^2 from float32 residuals: each r_b = fl(fl(Hu) - fl(b))
+    # is off by at most u (|Hu| + |b| + |r|) <= 2u (|Hu| + |b|), so |f32 - f| <= 2 u rho
+    g, th_nom, th_true, u_true, b, _ = small_problem(N=24, V=20, seed=23, sigma_deg=1.0)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options())
+    _, _, f, rho = s.view_terms(th_nom, u_true)
+    Hu = oracle.forward(g, th_nom, u_true).reshape(g.V, g.B)
+    r32 = (Hu.astype(np.float32) - b.reshape(g.V, g.B).astype(np.float32)).astype(np.float64)
+    f32 = 0.5 * (r32 * r32).sum(1)
+    u32 = 2.0 ** -24
+    ratio = np.abs(f32 - f) / (u32 * rho)
+    assert np.all(ratio <= 2.0 + 1e-6), ratio.max()
+    assert ratio.max() > 1e-3          # and rho is not a vacuous bound
+    assert np.all(rho >= 2 * f)
