@@ -17,7 +17,10 @@
  *   Joseph  |cos| >= |sin|: one linear interpolation per image row at
  *           x = (s_b - y_i sin)/cos, weight 1/|cos|; otherwise one per
  *           column at y = (s_b - x_j cos)/sin, weight 1/|sin|; pixels outside
- *           the image are zero.
+ *           the image are zero.  The axis is decided on theta itself: rows
+ *           iff fmod(theta, pi) (+ pi when negative) <= pi/4 or >= 3pi/4,
+ *           with the doubles nearest pi, pi/4, 3pi/4 (exact operations, so
+ *           the decision does not depend on the last bit of a sine).
  *
  * Frames (block-diagonal operator of the dynamic problem, Sec. 7): the flat
  * view list is split into consecutive frames, views_per_frame[f] views for
@@ -166,6 +169,42 @@ int ct_gn_terms(ct_handle *h, const double *theta, const double *delta,
                 double *jnorm2, double *fval);
 
 /*
+ * Batched Jacobian products: `batch` images x_k (1 <= batch <= max_batch)
+ * sharing the angles and offsets, one ray-march launch for the whole batch
+ * (the block V of basis vectors of Sec. 3.2 whose sensitivities H_{p_i} V_c
+ * enter the VarPro Gauss-Newton system of Sec. 4.2, Alg.
+ * "UPDATE-PARAM-VarPro"; the batched backward of the autograd projection).
+ * Each image's result equals the single-image call's (ct_jac, ct_jacT,
+ * ct_gn_terms) on that image, up to the summation order within a ray.
+ *
+ * ct_jac_batch: dY[k][v,b] = dtheta_k[v] d(H x_k)[v,b]/dtheta_v
+ *                           (+ ddelta_k[v] d(H x_k)[v,b]/ddelta_v)
+ *   X [batch][n_frames][N][N]; dY [batch][n_views][B];
+ *   dtheta, ddelta (nullable): [n_views] shared by every image, or
+ *   [batch][n_views] with flags & CT_BATCH_PER_IMAGE_DIRECTION.
+ * ct_jacT_batch: gtheta[k][v] = sum_b R_k[v,b] d(H x_k)[v,b]/dtheta_v (and gdelta)
+ *   R [batch][n_views][B], or one [n_views][B] shared by every image with
+ *   flags & CT_BATCH_SHARED_R; gtheta, gdelta (nullable) [batch][n_views], or
+ *   with flags & CT_BATCH_SUM one [n_views] vector: the sum over the images,
+ *   added in image order after each image's fixed-order sum over bins (the
+ *   gradient of sum_k <R_k, H(theta) x_k> with respect to theta).
+ * ct_gn_terms_batch: the four ct_gn_terms outputs for each image, against
+ *   data bdata [batch][n_views][B]: res [batch][n_views][B] (nullable),
+ *   grad, jnorm2, fval (nullable) [batch][n_views].
+ * Fan-beam handles: angle derivatives only (ddelta / gdelta give CT_ERR_ARG).
+ * CT_ERR_ARG for batch out of range, null required pointers or unknown flags.
+ */
+#define CT_BATCH_PER_IMAGE_DIRECTION 1
+#define CT_BATCH_SHARED_R 2
+#define CT_BATCH_SUM 4
+int ct_jac_batch(ct_handle *h, const double *theta, const double *delta, const void *X, const double *dtheta,
+                 const double *ddelta, void *dY, int batch, int flags);
+int ct_jacT_batch(ct_handle *h, const double *theta, const double *delta, const void *X, const void *R,
+                  double *gtheta, double *gdelta, int batch, int flags);
+int ct_gn_terms_batch(ct_handle *h, const double *theta, const double *delta, const void *X, const void *bdata,
+                      void *res, double *grad, double *jnorm2, double *fval, int batch);
+
+/*
  * Rebind the handle to another stream (for example a stream being captured
  * into a CUDA graph).  Later calls launch on it.
  */
@@ -176,7 +215,8 @@ int ct_set_stream(ct_handle *h, void *cuda_stream);
  * its stream: images per lane (1, 2, 4, 8), warps per ray (1, 2, 4, 8) and
  * neighbouring views per CTA (1, 2, 4, 8) for the forward projection at
  * max_batch, images per thread and view groups per pixel tile (1, 2, 4) for
- * the transpose, warps per ray and views per CTA for the Jacobian kernels,
+ * the transpose, warps per ray and views per CTA for the Jacobian kernels
+ * (and, for max_batch > 1, images per lane of the batched ones),
  * and (FP32 handles) the staged forms: the forward and Jacobian kernels
  * with 4 or 8 views per CTA, 4 or 8 rows per shared-memory block and 1, 2
  * or 4 CTAs per ray, the transpose with 8 or 16 views per block and 1, 2 or
@@ -192,7 +232,8 @@ int ct_autotune(ct_handle *h);
  *   [2] forward views per CTA, [3] transpose images per thread,
  *   [4] transpose view groups per pixel tile, [5] Jacobian warps per ray,
  *   [6] Jacobian views per CTA, [7] forward staging, [8] Jacobian staging,
- *   [9] transpose staging.
+ *   [9] transpose staging, [10] images per lane of the batched Jacobian
+ *   products (1, 2 or 4; the staged and fan-beam forms take 1).
  * [0]..[6] are powers of two, at most 8 (view groups at most 4), warps per
  * ray x views per CTA at most 16 (unstaged kernels).  Forward / Jacobian
  * staging is 0 (gathers through L1) or 4 / 8 (rows per shared-memory block of
@@ -206,7 +247,7 @@ int ct_autotune(ct_handle *h);
  * that fails).  The Jacobian kernels ignore [5] when staged.  CT_ERR_ARG for
  * any other value.
  */
-#define CT_TUNING_COUNT 10
+#define CT_TUNING_COUNT 11
 int ct_get_tuning(ct_handle *h, int32_t *out);
 int ct_set_tuning(ct_handle *h, const int32_t *in);
 
@@ -253,6 +294,19 @@ typedef struct {
     int32_t varpro;         /* 1: parameter update by Alg. "UPDATE-PARAM-VarPro" (Sec. 4.2) on the
                                compressed basis (see nlrmm_varpro_update) instead of the per-view
                                AltMin update; default 0 */
+    double armijo_eps;      /* noise floor of the Armijo searches: a search whose first-order change
+                               alpha |g d| of the misfit f = 1/2 |r|^2 is below armijo_eps * rho, with
+                               rho = sum_b |r_b| (|(H u)_b| + |b_b|) the rounding scale of f (one view's
+                               residual in the AltMin update, the data residual of the reduced
+                               objective in the VarPro update), ends before that trial with no
+                               acceptable step: its test would compare two misfits closer than their
+                               rounding (the paper's descent lemmas assume exact arithmetic).  < 0
+                               (default): the unit roundoff of the handle's precision, 2^-24 (float32
+                               residuals) or 2^-53; 0: no floor */
+    int32_t plain;          /* 1: the unpackaged form, for comparison: no CUDA graphs, every projection
+                               of the basis one column per launch (no Krylov-block batching), the
+                               Armijo flag read after every trial round; same iterates.  Default 0 */
+    int32_t reserved0;      /* must be 0 */
 } nlrmm_opts;
 
 typedef struct {
@@ -401,8 +455,10 @@ int nlrmm_varpro_update(ct_handle *h, const void *b, double *theta_inout, const 
  * make that first call before any stream capture.  All calls share the one
  * array: calls that may overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  No cudaMalloc,
- * cudaFree or allocating library routine is called.  Returns CT_OK,
- * CT_ERR_ARG or CT_ERR_CUDA; asynchronous, like ct_jacT.
+ * cudaFree or allocating library routine is called.  A view whose angle or
+ * offset is not finite gets NaN in gtheta (and gdelta): there is no status
+ * call here (ct_jacT reports the same input through ct_status).  Returns
+ * CT_OK, CT_ERR_ARG or CT_ERR_CUDA; asynchronous, like ct_jacT.
  */
 int ct_jacT_noalloc(int32_t N, int32_t B, int32_t n_views, const double *theta, const double *delta,
                     const float *x, const float *r, double *gtheta, double *gdelta, void *cuda_stream);

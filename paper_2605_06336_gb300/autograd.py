@@ -3,9 +3,9 @@
 ``CTProject.apply(x, theta, delta, op)`` returns H(theta, delta) x through
 ``ct_forward``; its backward returns
     dL/dx     = H^T g                (ct_adjoint, the gather transpose)
-    dL/dtheta = J_theta(x)^T g       (ct_jacT)
-    dL/ddelta = J_delta(x)^T g       (ct_jacT)
-for the incoming gradient g.  Those are the gradient components
+    dL/dtheta = sum_k J_theta(x_k)^T g_k   (ct_jacT_batch, summed over the batch in the kernel)
+    dL/ddelta = sum_k J_delta(x_k)^T g_k   (ct_jacT_batch)
+for the incoming gradient g (one image or a batch of images x_k).  Those are the gradient components
 [grad_p J]_i = (H_{p_i} u)^T (H u - b) of the appendix lemma on the
 Lipschitz gradient when the loss is 1/2 |H u - b|^2.  Everything runs in the
 library's kernels; nothing is differentiated by torch itself.
@@ -37,17 +37,13 @@ class CTProject(torch.autograd.Function):
         if ctx.needs_input_grad[0]:
             gx = op.adjoint(gy, theta, d)
         if ctx.needs_input_grad[1] or (ctx.has_delta and ctx.needs_input_grad[2]):
-            xs = x.reshape(-1, op.n)
-            gs = gy.reshape(-1, op.m)
-            gth = torch.zeros(op.V, dtype=torch.float64, device=x.device)
-            gdl = torch.zeros(op.V, dtype=torch.float64, device=x.device) if ctx.has_delta else None
-            for k in range(xs.shape[0]):  # one Jacobian per image of the batch
-                if ctx.has_delta:
-                    gt, gd = op.jacT(xs[k].contiguous(), theta, gs[k].contiguous(), d, want_delta=True)
-                    gdl += gd
-                else:
-                    gt = op.jacT(xs[k].contiguous(), theta, gs[k].contiguous(), None)
-                gth += gt
+            # one launch over the whole batch; the kernel adds the images' gradients in order
+            xs = x.reshape(-1, op.n).contiguous()
+            gs = gy.reshape(-1, op.m).contiguous()
+            if ctx.has_delta:
+                gth, gdl = op.jacT_batch(xs, theta, gs, d, want_delta=True, sum_images=True)
+            else:
+                gth, gdl = op.jacT_batch(xs, theta, gs, sum_images=True), None
             if not ctx.needs_input_grad[1]:
                 gth = None
             if not (ctx.has_delta and ctx.needs_input_grad[2]):

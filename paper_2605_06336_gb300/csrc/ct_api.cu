@@ -95,6 +95,38 @@ int do_jacT(ctgb::Handle &h, const double *theta, const double *delta, const voi
 }
 
 template <typename T>
+int do_jac_batch(ctgb::Handle &h, const double *theta, const double *delta, const void *X, const double *dtheta,
+                 const double *ddelta, void *dY, int batch, int flags)
+{
+    const long long dstride = (flags & CT_BATCH_PER_IMAGE_DIRECTION) ? h.V : 0;
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dY, h.tune.der_split, h.tune.der_vw, h.tune.der_stage, batch,
+                                h.tune.der_kb, dstride));
+    return CT_OK;
+}
+
+template <typename T>
+int do_jacT_batch(ctgb::Handle &h, const double *theta, const double *delta, const void *X, const void *R,
+                  double *gtheta, double *gdelta, int batch, int flags)
+{
+    const long long rstride = (flags & CT_BATCH_SHARED_R) ? 0 : (long long)h.V * h.B;
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)R, gtheta, gdelta, h.tune.der_split, h.tune.der_vw, h.tune.der_stage,
+                                batch, h.tune.der_kb, rstride, (flags & CT_BATCH_SUM) ? 1 : 0));
+    return CT_OK;
+}
+
+template <typename T>
+int do_gn_batch(ctgb::Handle &h, const double *theta, const double *delta, const void *X, const void *bdata,
+                void *res, double *grad, double *jnorm2, double *fval, int batch)
+{
+    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw,
+                               h.tune.der_stage, nullptr, nullptr, batch, h.tune.der_kb));
+    return CT_OK;
+}
+
+template <typename T>
 int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
           double *grad, double *jnorm2, double *fval)
 {
@@ -132,6 +164,7 @@ void default_tuning(ctgb::Handle &h)
     h.tune.der_split = rays >= 32LL * h.num_sms ? 2 : 4;
     h.tune.fwd_vw = 2;
     h.tune.der_vw = 2;
+    h.tune.der_kb = std::min(kb, 4);
     if (h.fan_D > 0.0) {
         // fan-beam transpose: one candidate search per pixel and view serves
         // every sinogram of a thread; two view groups per pixel keep the warps up
@@ -304,6 +337,22 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
                 }
             }
         }
+        // images per lane of the batched derivative modes, on the whole batch at
+        // the chosen split / views per CTA (per image: the single-image time above)
+        if (K > 1) {
+            best = 1e30f;
+            for (int kb : {1, 2, 4}) {
+                if (kb > K) continue;
+                const float ms = time_config(h.stream, [&] {
+                    ctgb::launch_pairs_img<T>(h, X, K * h.F);
+                    ctgb::launch_jvp<T>(h, d_g, nullptr, (T *)d_out, t.der_split, t.der_vw, t.der_stage, K, kb);
+                });
+                if (ms < best) {
+                    best = ms;
+                    t.der_kb = kb;
+                }
+            }
+        }
         e = cudaStreamSynchronize(h.stream);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -396,7 +445,8 @@ int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
                   cudaMalloc(&h.d_px, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_pt, img_pairs * pair_bytes) == cudaSuccess &&
                   cudaMalloc(&h.d_yp, sino_pairs * pair_bytes) == cudaSuccess &&
-                  cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.V * h.nchunks) == cudaSuccess &&
+                  cudaMalloc(&h.d_partial, sizeof(double) * 4 * (size_t)h.max_batch * h.V * h.nchunks) ==
+                      cudaSuccess &&
                   (h.fan_D == 0.0 ||
                    (cudaMalloc(&h.d_rays, ctgb::fan_ray_bytes(h.precision) * (size_t)h.V * h.B) == cudaSuccess &&
                     cudaMalloc(&h.d_fanview, ctgb::fan_view_bytes() * (size_t)h.V) == cudaSuccess &&
@@ -515,6 +565,39 @@ int ct_gn_terms(ct_handle *H, const double *theta, const double *delta, const vo
                           : do_gn<float>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval);
 }
 
+int ct_jac_batch(ct_handle *H, const double *theta, const double *delta, const void *X, const double *dtheta,
+                 const double *ddelta, void *dY, int batch, int flags)
+{
+    if (!H || !theta || !X || !dtheta || !dY || batch < 1 || batch > H->h.max_batch ||
+        (flags & ~CT_BATCH_PER_IMAGE_DIRECTION))
+        return CT_ERR_ARG;
+    if (H->h.fan_D > 0.0 && ddelta) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
+    return H->h.precision ? do_jac_batch<double>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags)
+                          : do_jac_batch<float>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags);
+}
+
+int ct_jacT_batch(ct_handle *H, const double *theta, const double *delta, const void *X, const void *R,
+                  double *gtheta, double *gdelta, int batch, int flags)
+{
+    if (!H || !theta || !X || !R || !gtheta || batch < 1 || batch > H->h.max_batch ||
+        (flags & ~(CT_BATCH_SHARED_R | CT_BATCH_SUM)))
+        return CT_ERR_ARG;
+    if (H->h.fan_D > 0.0 && gdelta) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
+    return H->h.precision ? do_jacT_batch<double>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags)
+                          : do_jacT_batch<float>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags);
+}
+
+int ct_gn_terms_batch(ct_handle *H, const double *theta, const double *delta, const void *X, const void *bdata,
+                      void *res, double *grad, double *jnorm2, double *fval, int batch)
+{
+    if (!H || !theta || !X || !bdata || !grad || !jnorm2 || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
+    H->h.fwd_ready = H->h.adj_ready = 0;
+    return H->h.precision ? do_gn_batch<double>(H->h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch)
+                          : do_gn_batch<float>(H->h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch);
+}
+
 int ct_set_stream(ct_handle *H, void *cuda_stream)
 {
     if (!H) return CT_ERR_ARG;
@@ -533,8 +616,9 @@ int ct_get_tuning(ct_handle *H, int32_t *out)
 {
     if (!H || !out) return CT_ERR_ARG;
     const ctgb::Tuning &t = H->h.tune;
-    const int32_t v[CT_TUNING_COUNT] = {t.fwd_kb, t.fwd_split, t.fwd_vw,    t.adj_kb,    t.adj_split,
-                                        t.der_split, t.der_vw, t.fwd_stage, t.der_stage, t.adj_stage};
+    const int32_t v[CT_TUNING_COUNT] = {t.fwd_kb,    t.fwd_split, t.fwd_vw,    t.adj_kb,
+                                        t.adj_split, t.der_split, t.der_vw,    t.fwd_stage,
+                                        t.der_stage, t.adj_stage, t.der_kb};
     for (int i = 0; i < CT_TUNING_COUNT; ++i) out[i] = v[i];
     return CT_OK;
 }
@@ -547,7 +631,7 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
     if (!pow2(in[0], 8) || !pow2(in[1], 8) || !pow2(in[2], 8) || !pow2(in[3], 8) || !pow2(in[4], 4) ||
         !pow2(in[5], 8) || !pow2(in[6], 8) || (in[7] == 0 && in[1] * in[2] > 16) ||
         (in[8] == 0 && in[5] * in[6] > 16) || !stage_ok(in[7], in[2]) || !stage_ok(in[8], in[6]) ||
-        (in[7] > 0 && in[1] > 4) || (in[9] != 0 && in[9] != 8 && in[9] != 16))
+        (in[7] > 0 && in[1] > 4) || (in[9] != 0 && in[9] != 8 && in[9] != 16) || !pow2(in[10], 4))
         return CT_ERR_ARG;
     if ((in[7] > 0 && in[1] > 1) || (in[9] > 0 && in[4] > 1)) {
         const int rc = ensure_seg_partials(H->h);
@@ -564,6 +648,7 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
     t.fwd_stage = in[7];
     t.der_stage = in[8];
     t.adj_stage = in[9];
+    t.der_kb = in[10];
     return CT_OK;
 }
 

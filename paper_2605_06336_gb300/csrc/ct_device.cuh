@@ -106,9 +106,12 @@ template <typename T> struct RayArgs {
     T *Y;                   // FWD: [batch][V*B]; JVP: dY
     long long sino_stride;
     const double *dtheta, *ddelta;
+    long long dir_stride;   // JVP: doubles between the directions of consecutive images (0: one for all)
     const T *R;             // VJP: r; GN: data b
     T *res;                 // GN: residual (nullable)
-    double *partial;        // VJP / GN
+    long long r_stride;     // VJP / GN: elements between the R of consecutive images (0: one for all)
+    double *partial;        // VJP / GN: [image][view][chunk][4]
+    long long part_stride;  // doubles between the partials of consecutive images (V * nchunks * 4)
     const int *view_mask;   // GN: views with mask 0 are skipped (nullable)
     const int *skip;        // whole launch is a no-op when *skip != 0 (nullable)
     const int *order;       // view order (nullable: identity)
@@ -146,7 +149,7 @@ __device__ __forceinline__ void warp_rows(const ViewGeo &g, int b, bool active, 
 // per-(view, chunk) partial sums reduced over the warp in a fixed order.
 template <typename T, int MODE, bool OFFS, int KB>
 __device__ __forceinline__ void ray_epilogue(const RayArgs<T> &a, const ViewGeo &g, int v, int b, bool active, int k0,
-                                             int chunk, int lane, const T (&acc)[(MODE == kFwd) ? KB : 3])
+                                             int chunk, int lane, const T (&acc)[(MODE == kFwd) ? KB : 3 * KB])
 {
     const T wv = GeoT<T>::w(g);
     if constexpr (MODE == kFwd) {
@@ -156,45 +159,57 @@ __device__ __forceinline__ void ray_epilogue(const RayArgs<T> &a, const ViewGeo 
                 a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = wv * acc[k];
         }
     } else {
-        const T jt = fma(GeoT<T>::dw(g), acc[0], wv * acc[1]);
-        const T jd = wv * GeoT<T>::qb(g) * acc[2];
-        if constexpr (MODE == kJvp) {
-            if (active) {
-                T out = (T)a.dtheta[v] * jt;
-                if (OFFS) out = fma((T)a.ddelta[v], jd, out);
-                a.Y[(size_t)v * a.B + b] = out;
-            }
-        } else if constexpr (MODE == kVjp) {
-            double pt = 0.0, pd = 0.0;
-            if (active) {
-                const T r = a.R[(size_t)v * a.B + b];
-                pt = (double)(r * jt);
-                if (OFFS) pd = (double)(r * jd);
-            }
-            pt = warp_sum(pt);
-            if (OFFS) pd = warp_sum(pd);
-            if (lane == 0) {
-                double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
-                p[0] = pt;
-                p[1] = pd;
-            }
-        } else {  // kGn
-            double pg = 0.0, pj = 0.0, pf = 0.0;
-            if (active) {
-                const T rr = wv * acc[0] - a.R[(size_t)v * a.B + b];
-                if (a.res) a.res[(size_t)v * a.B + b] = rr;
-                pg = (double)rr * (double)jt;
-                pj = (double)jt * (double)jt;
-                pf = (double)rr * (double)rr;
-            }
-            pg = warp_sum(pg);
-            pj = warp_sum(pj);
-            pf = warp_sum(pf);
-            if (lane == 0) {
-                double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
-                p[0] = pg;
-                p[1] = pj;
-                p[2] = pf;
+        // image k of the group: acc[3k] interpolated sum, acc[3k+1] slope x dq/dtheta, acc[3k+2] slopes
+        const size_t vb = (size_t)v * a.B + b;
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            const size_t img = (size_t)(k0 + k);
+            const T jt = fma(GeoT<T>::dw(g), acc[3 * k], wv * acc[3 * k + 1]);
+            const T jd = wv * GeoT<T>::qb(g) * acc[3 * k + 2];
+            if constexpr (MODE == kJvp) {
+                if (active) {
+                    T out = (T)a.dtheta[img * a.dir_stride + v] * jt;
+                    if (OFFS) out = fma((T)a.ddelta[img * a.dir_stride + v], jd, out);
+                    a.Y[img * a.sino_stride + vb] = out;
+                }
+            } else if constexpr (MODE == kVjp) {
+                double pt = 0.0, pd = 0.0;
+                if (active) {
+                    const T r = a.R[img * a.r_stride + vb];
+                    pt = (double)(r * jt);
+                    if (OFFS) pd = (double)(r * jd);
+                }
+                pt = warp_sum(pt);
+                if (OFFS) pd = warp_sum(pd);
+                if (lane == 0) {
+                    double *p = a.partial + img * a.part_stride + ((size_t)v * a.nchunks + chunk) * 4;
+                    p[0] = pt;
+                    p[1] = pd;
+                }
+            } else {  // kGn
+                // pr: the rounding scale |r| (|H x| + |b|) of the misfit (Armijo noise floor)
+                double pg = 0.0, pj = 0.0, pf = 0.0, pr = 0.0;
+                if (active) {
+                    const T hx = wv * acc[3 * k];
+                    const T bb = a.R[img * a.r_stride + vb];
+                    const T rr = hx - bb;
+                    if (a.res) a.res[img * a.sino_stride + vb] = rr;
+                    pg = (double)rr * (double)jt;
+                    pj = (double)jt * (double)jt;
+                    pf = (double)rr * (double)rr;
+                    pr = fabs((double)rr) * (fabs((double)hx) + fabs((double)bb));
+                }
+                pg = warp_sum(pg);
+                pj = warp_sum(pj);
+                pf = warp_sum(pf);
+                pr = warp_sum(pr);
+                if (lane == 0) {
+                    double *p = a.partial + img * a.part_stride + ((size_t)v * a.nchunks + chunk) * 4;
+                    p[0] = pg;
+                    p[1] = pj;
+                    p[2] = pf;
+                    p[3] = pr;
+                }
             }
         }
     }

@@ -279,34 +279,41 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanR
                         a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = R.w * acc[k];
                 }
             } else {
+                // one image per lane in the derivative modes: image k0 of the batch
+                const size_t img = (size_t)k0, vb = (size_t)v * a.B + b;
                 const T jt = fma(R.dw, acc[0], R.w * acc[1]);
                 if constexpr (MODE == kJvp) {
-                    if (active) a.Y[(size_t)v * a.B + b] = (T)a.dtheta[v] * jt;
+                    if (active) a.Y[img * a.sino_stride + vb] = (T)a.dtheta[img * a.dir_stride + v] * jt;
                 } else if constexpr (MODE == kVjp) {
-                    double pt = active ? (double)(a.R[(size_t)v * a.B + b] * jt) : 0.0;
+                    double pt = active ? (double)(a.R[img * a.r_stride + vb] * jt) : 0.0;
                     pt = warp_sum(pt);
                     if (lane == 0) {
-                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                        double *p = a.partial + img * a.part_stride + ((size_t)v * a.nchunks + chunk) * 4;
                         p[0] = pt;
                         p[1] = 0.0;
                     }
                 } else {  // kGn
-                    double pg = 0.0, pj = 0.0, pf = 0.0;
+                    double pg = 0.0, pj = 0.0, pf = 0.0, pr = 0.0;
                     if (active) {
-                        const T rr = R.w * acc[0] - a.R[(size_t)v * a.B + b];
-                        if (a.res) a.res[(size_t)v * a.B + b] = rr;
+                        const T hx = R.w * acc[0];
+                        const T bb = a.R[img * a.r_stride + vb];
+                        const T rr = hx - bb;
+                        if (a.res) a.res[img * a.sino_stride + vb] = rr;
                         pg = (double)rr * (double)jt;
                         pj = (double)jt * (double)jt;
                         pf = (double)rr * (double)rr;
+                        pr = fabs((double)rr) * (fabs((double)hx) + fabs((double)bb));
                     }
                     pg = warp_sum(pg);
                     pj = warp_sum(pj);
                     pf = warp_sum(pf);
+                    pr = warp_sum(pr);
                     if (lane == 0) {
-                        double *p = a.partial + ((size_t)v * a.nchunks + chunk) * 4;
+                        double *p = a.partial + img * a.part_stride + ((size_t)v * a.nchunks + chunk) * 4;
                         p[0] = pg;
                         p[1] = pj;
                         p[2] = pf;
+                        p[3] = pr;
                     }
                 }
             }

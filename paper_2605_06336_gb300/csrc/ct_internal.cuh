@@ -75,7 +75,8 @@ struct __align__(16) ViewGeo {
 struct Tuning {
     int fwd_kb = 8, fwd_split = 2, fwd_vw = 1;  // forward projection of a batch
     int adj_kb = 8, adj_split = 2;              // transpose of a batch
-    int der_split = 4, der_vw = 1;              // JVP / VJP / Gauss-Newton terms (one image)
+    int der_split = 4, der_vw = 1;              // JVP / VJP / Gauss-Newton terms
+    int der_kb = 1;                             // images per lane of the batched derivative modes
     int fwd_stage = 0, der_stage = 0;
     int adj_stage = 0;  // 0: gather through L1; 8 or 16: views per shared-memory block of the
                         // staged FP32 transpose, whose adj_split is then CTAs per tile
@@ -95,7 +96,7 @@ struct Handle {
     void *d_px = nullptr;     // pair images, rows of X:   (max_batch + 1) * F * N * Pp pairs
     void *d_pt = nullptr;     // pair images, rows of X^T: (max_batch + 1) * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
-    double *d_partial = nullptr;  // per (view, chunk) reduction partials, 4 per item
+    double *d_partial = nullptr;  // per (image, view, chunk) reduction partials, 4 per item, max_batch images
     void *d_segpart = nullptr;    // segment partials of the staged forward (sinograms) and transpose
                                   // (images): 3 * max_batch * max(V * B, F * N * N) floats, allocated
                                   // when a shape with several CTAs per ray or tile is set
@@ -150,14 +151,24 @@ cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, 
 // Staged FP32 transpose (ct_adj_band.cu); adj_band_ok tells whether a shape can run on this handle.
 bool adj_band_ok(const Handle &h, int stage, int segs);
 cudaError_t launch_adjoint_band(const Handle &h, float *X, int batch, int kb, int segs, int stage, const int *skip);
+// Derivative modes on `batch` images laid out in the pair buffers (kb images
+// per lane: 1, 2 or 4), one launch of the ray kernel plus (VJP, GN) the
+// per-view reduction.  JVP: image k uses dtheta + k * dir_stride (0: one
+// direction for all) and writes dY + k * V * B.  VJP: image k reads
+// R + k * r_stride (0: one r for all) and writes gtheta + k * V, or with sum
+// one [V] vector summing the images in order.  GN: image k reads
+// bdata + k * V * B and writes [k][V] outputs; rscale (nullable) receives
+// sum_b |r_b| (|(H x)_b| + |b_b|) per view, the rounding scale of the misfit.
 template <typename T>
 cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw,
-                       int stage);
+                       int stage, int batch = 1, int kb = 1, long long dir_stride = 0);
 template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw, int stage);
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw, int stage,
+                       int batch = 1, int kb = 1, long long r_stride = 0, int sum = 0);
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval,
-                      int split, int vw, int stage, const int *view_mask = nullptr, const int *skip = nullptr);
+                      int split, int vw, int stage, const int *view_mask = nullptr, const int *skip = nullptr,
+                      int batch = 1, int kb = 1, double *rscale = nullptr);
 
 // Fan beam (ct_fan.cu).  launch_fan_rays rebuilds the per-ray table from the
 // view table; every launcher that brings the view table up to date runs it

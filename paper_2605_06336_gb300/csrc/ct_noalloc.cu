@@ -64,6 +64,19 @@ cudaError_t scratch_base(void **out)
     return cudaSuccess;
 }
 
+// Views whose angle or offset is not finite: their outputs become NaN, so that
+// the caller sees the bad input in the result (this entry point has no status
+// call; the kernels compute such a view at angle 0 and offset 0).
+__global__ void k_mark_nonfinite(const double *__restrict__ theta, const double *__restrict__ delta, int V,
+                                 double *__restrict__ gtheta, double *__restrict__ gdelta)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        if (isfinite(theta[v]) && (!delta || isfinite(delta[v]))) continue;
+        gtheta[v] = __longlong_as_double(0x7ff8000000000000LL);
+        if (gdelta) gdelta[v] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+}
+
 }  // namespace
 
 extern "C" int ct_jacT_noalloc(int32_t N, int32_t B, int32_t n_views, const double *theta, const double *delta,
@@ -83,7 +96,7 @@ extern "C" int ct_jacT_noalloc(int32_t N, int32_t B, int32_t n_views, const doub
     h.max_batch = 1;
     h.precision = 0;
     h.Pp = N + 4;
-    h.Pb = B + 4;
+    h.Pb = (B + 5) & ~1;  // even pair pitch, as ct_init sets it
     h.stream = (cudaStream_t)cuda_stream;
     h.d_views = reinterpret_cast<ctgb::ViewGeo *>(s + kOffViews);
     h.d_fov = nullptr;  // one frame
@@ -105,5 +118,7 @@ extern "C" int ct_jacT_noalloc(int32_t N, int32_t B, int32_t n_views, const doub
     if (ctgb::launch_view_setup(h, theta, delta) != cudaSuccess) return CT_ERR_CUDA;
     if (ctgb::launch_pairs_img<float>(h, x, 1) != cudaSuccess) return CT_ERR_CUDA;
     if (ctgb::launch_vjp<float>(h, r, gtheta, gdelta, h.tune.der_split, 1, 0) != cudaSuccess) return CT_ERR_CUDA;
+    k_mark_nonfinite<<<(n_views + 255) / 256, 256, 0, h.stream>>>(theta, delta, n_views, gtheta, gdelta);
+    if (cudaGetLastError() != cudaSuccess) return CT_ERR_CUDA;
     return CT_OK;
 }

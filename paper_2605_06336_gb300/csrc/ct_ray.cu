@@ -31,6 +31,20 @@ namespace {
 // ---------------------------------------------------------------------------
 // per-view setup
 // ---------------------------------------------------------------------------
+// Joseph axis: one sample per image row iff |cos theta| >= |sin theta|, i.e.
+// iff theta mod pi lies in [0, pi/4] or [3pi/4, pi).  The test runs on theta
+// itself with exact operations (fmod is exact, one rounded addition for a
+// negative angle) against the doubles nearest pi, pi/4 and 3pi/4: it differs
+// from the exact rule only within ~3e-16 rad of a diagonal, where comparing
+// |cos| with |sin| would depend on the last bit of the sine and cosine.
+__device__ __forceinline__ bool march_rows(double theta)
+{
+    const double pi = 3.14159265358979323846, q1 = 0.78539816339744830962, q3 = 2.35619449019234492885;
+    double t = fmod(theta, pi);
+    if (t < 0.0) t = __dadd_rn(t, pi);
+    return t <= q1 || t >= q3;
+}
+
 // Rebuilds the constants of view v when its (theta, delta) changed since the
 // last call; returns whether it did.
 __device__ bool view_setup_one(int v, const double *__restrict__ theta, const double *__restrict__ delta,
@@ -57,7 +71,7 @@ __device__ bool view_setup_one(int v, const double *__restrict__ theta, const do
     const double sb0 = -0.5 * (B - 1) + dl;
     ViewGeo g;
     double q0, qb, qr;
-    if (fabs(c) >= fabs(s)) {  // one sample per image row
+    if (march_rows(th)) {  // one sample per image row
         const double ic = 1.0 / c;
         const double ic2 = ic * ic;
         g.mode = 0;
@@ -298,7 +312,7 @@ template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
 __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
 {
     using P2 = pair_t<T>;
-    constexpr int NACC = (MODE == kFwd) ? KB : 3;
+    constexpr int NACC = (MODE == kFwd) ? KB : 3 * KB;
     extern __shared__ unsigned char ray_smem[];
     T *red = reinterpret_cast<T *>(ray_smem);  // [VW][SPLIT][NACC][32], only when SPLIT > 1
     const int lane = threadIdx.x & 31;
@@ -338,7 +352,7 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
                             (size_t)r0 * a.Pp + 2;
             // Rows are processed in blocks of U: all loads of a block are issued
             // before any of them is used, so U*KB gathers are in flight per warp.
-            constexpr int U = (MODE == kFwd) ? (KB >= 4 ? 4 : 8) : 8;
+            constexpr int U = KB >= 4 ? 4 : 8;
             const int pp = a.Pp;
             if constexpr (MODE == kFwd) {
                 int r = r0;
@@ -374,28 +388,35 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
                     }
                 }
             } else {
-                // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta,
-                // acc[2] = sum of slopes (offset derivative)
+                // per image k of the group: acc[3k] = sum of interpolated values,
+                // acc[3k+1] = sum slope * dq/dtheta, acc[3k+2] = sum of slopes
+                // (offset derivative); the line, cell and fraction serve all KB images
                 const T g0 = fma(GeoT<T>::sb(g, b), GeoT<T>::gs(g), GeoT<T>::gh(g, N));
                 const T gr = GeoT<T>::gr(g);
                 T rf = (T)r0;
                 int r = r0;
                 for (; r + U - 1 <= r1; r += U) {
-                    P2 p[U];
+                    P2 p[U][KB];
                     T f[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const long long Qu = Q + (long long)u * dQ;
                         const int cell = min(max(cell_of(Qu), -2), N);
                         f[u] = frac_of(Qu, T());
-                        p[u] = __ldg(img + (size_t)u * pp + cell);
+                        const P2 *row = img + (size_t)u * pp + cell;
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) p[u][k] = __ldg(row + (size_t)k * a.pimg_stride);
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const T d = p[u].y - p[u].x;
-                        acc[0] += fma(f[u], d, p[u].x);
-                        acc[1] = fma(d, fma(rf + T(u), gr, g0), acc[1]);
-                        if (OFFS) acc[2] += d;
+                        const T dq = fma(rf + T(u), gr, g0);
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) {
+                            const T d = p[u][k].y - p[u][k].x;
+                            acc[3 * k] += fma(f[u], d, p[u][k].x);
+                            acc[3 * k + 1] = fma(d, dq, acc[3 * k + 1]);
+                            if (OFFS) acc[3 * k + 2] += d;
+                        }
                     }
                     img += (size_t)U * pp;
                     Q += (long long)U * dQ;
@@ -404,11 +425,15 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
                 for (; r <= r1; ++r, img += pp, Q += dQ, rf += T(1)) {
                     const int cell = min(max(cell_of(Q), -2), N);
                     const T fr = frac_of(Q, T());
-                    const P2 q = __ldg(img + cell);
-                    const T d = q.y - q.x;
-                    acc[0] += fma(fr, d, q.x);
-                    acc[1] = fma(d, fma(rf, gr, g0), acc[1]);
-                    if (OFFS) acc[2] += d;
+                    const T dq = fma(rf, gr, g0);
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) {
+                        const P2 q = __ldg(img + (size_t)k * a.pimg_stride + cell);
+                        const T d = q.y - q.x;
+                        acc[3 * k] += fma(fr, d, q.x);
+                        acc[3 * k + 1] = fma(d, dq, acc[3 * k + 1]);
+                        if (OFFS) acc[3 * k + 2] += d;
+                    }
                 }
             }
         }
@@ -433,36 +458,53 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
     }
 }
 
-// out_q[v] = scale_q * sum_c partial[v][c][q], summed in chunk order.  One
-// warp per view: the lanes load 32 chunks at a time in one round trip, and
-// the sums run over them in chunk order through shuffles.
-__global__ void k_finalize(const double *__restrict__ partial, int V, int nchunks, double *out0, double *out1,
-                           double *out2, double scale2, const int *__restrict__ view_mask,
-                           const int *__restrict__ skip)
+// out_q[k][v] = scale_q * sum_c partial[k][v][c][q], summed in chunk order,
+// for each of nimg images (partials part_stride doubles apart); with sum, one
+// output per view summing the images in order (each image's chunks in order).
+// One warp per output: the lanes load 32 chunks at a time in one round trip,
+// and the sums run over them in chunk order through shuffles.
+__global__ void k_finalize(const double *__restrict__ partial, int V, int nchunks, int nimg, long long part_stride,
+                           int sum, double *out0, double *out1, double *out2, double scale2, double *out3,
+                           const int *__restrict__ view_mask, const int *__restrict__ skip)
 {
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (v >= V || (skip && *skip) || (view_mask && view_mask[v] == 0)) return;  // warp-uniform
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    const double *p = partial + (size_t)v * nchunks * 4;
-    for (int base = 0; base < nchunks; base += 32) {
-        double q0 = 0.0, q1 = 0.0, q2 = 0.0;
-        if (base + lane < nchunks) {
-            q0 = p[4 * (base + lane) + 0];
-            q1 = p[4 * (base + lane) + 1];
-            q2 = p[4 * (base + lane) + 2];
+    const int nout = sum ? 1 : nimg;
+    if (w >= V * nout || (skip && *skip)) return;  // warp-uniform
+    const int v = w % V, kout = w / V;
+    if (view_mask && view_mask[v] == 0) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // sums over the images, each image's sum added in order
+    const int klo = sum ? 0 : kout, khi = sum ? nimg : kout + 1;
+    for (int k = klo; k < khi; ++k) {
+        const double *p = partial + (size_t)k * part_stride + (size_t)v * nchunks * 4;
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;  // this image, chunks in order
+        for (int base = 0; base < nchunks; base += 32) {
+            double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+            if (base + lane < nchunks) {
+                q0 = p[4 * (base + lane) + 0];
+                q1 = p[4 * (base + lane) + 1];
+                q2 = p[4 * (base + lane) + 2];
+                if (out3) q3 = p[4 * (base + lane) + 3];
+            }
+            const int n = min(32, nchunks - base);
+            for (int c = 0; c < n; ++c) {
+                t0 += __shfl_sync(0xffffffffu, q0, c);
+                t1 += __shfl_sync(0xffffffffu, q1, c);
+                t2 += __shfl_sync(0xffffffffu, q2, c);
+                if (out3) t3 += __shfl_sync(0xffffffffu, q3, c);
+            }
         }
-        const int n = min(32, nchunks - base);
-        for (int k = 0; k < n; ++k) {
-            s0 += __shfl_sync(0xffffffffu, q0, k);
-            s1 += __shfl_sync(0xffffffffu, q1, k);
-            s2 += __shfl_sync(0xffffffffu, q2, k);
-        }
+        s0 += t0;
+        s1 += t1;
+        s2 += t2;
+        s3 += t3;
     }
     if (lane == 0) {
-        if (out0) out0[v] = s0;
-        if (out1) out1[v] = s1;
-        if (out2) out2[v] = scale2 * s2;
+        const size_t o = (size_t)kout * V + v;
+        if (out0) out0[o] = s0;
+        if (out1) out1[o] = s1;
+        if (out2) out2[o] = scale2 * s2;
+        if (out3) out3[o] = s3;
     }
 }
 
@@ -494,7 +536,7 @@ template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
 cudaError_t run_ray(const Handle &h, const RayArgs<T> &a)
 {
     auto kern = k_ray<T, MODE, OFFS, KB, SPLIT>;
-    constexpr int NACC = (MODE == kFwd) ? KB : 3;
+    constexpr int NACC = (MODE == kFwd) ? KB : 3 * KB;
     const int threads = 32 * SPLIT * a.VW;
     const size_t smem = SPLIT > 1 ? (size_t)a.VW * SPLIT * NACC * 32 * sizeof(T) : 0;
     const long long items = (long long)a.ngroups * ((a.V + a.VW - 1) / a.VW) * a.nchunks;
@@ -678,48 +720,85 @@ cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, 
     return cudaSuccess;
 }
 
+// The derivative modes over `batch` images sharing the view table: groups of
+// up to kb (1, 2 or 4) images per lane; the fan-beam and band-staged forms
+// take one image per lane (their launches still cover the whole batch).
+template <typename T, int MODE, bool OFFS>
+cudaError_t der_groups(const Handle &h, RayArgs<T> a, int batch, int kb, int split, int stage)
+{
+    bool one = h.fan_D > 0.0;
+    if constexpr (std::is_same<T, float>::value) one = one || (stage > 0 && band_shape_ok(MODE, 1, a.VW, stage));
+    int k = 0;
+    for (int width : {4, 2, 1}) {
+        if (width > kb || (one && width > 1)) continue;
+        const int groups = (batch - k) / width;
+        if (groups == 0) continue;
+        a.kbase = k;
+        a.ngroups = groups;
+        cudaError_t e;
+        switch (width) {
+        case 4: e = run_ray_any<T, MODE, OFFS, 4>(h, a, split, stage); break;
+        case 2: e = run_ray_any<T, MODE, OFFS, 2>(h, a, split, stage); break;
+        default: e = run_ray_any<T, MODE, OFFS, 1>(h, a, split, stage); break;
+        }
+        if (e != cudaSuccess) return e;
+        k += groups * width;
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_jvp(const Handle &h, const double *dtheta, const double *ddelta, T *dY, int split, int vw,
-                       int stage)
+                       int stage, int batch, int kb, long long dir_stride)
 {
     RayArgs<T> a = base_args<T>(h);
     a.VW = vw;
     a.Y = dY;
     a.dtheta = dtheta;
     a.ddelta = ddelta;
-    return ddelta ? run_ray_any<T, kJvp, true, 1>(h, a, split, stage) : run_ray_any<T, kJvp, false, 1>(h, a, split, stage);
+    a.dir_stride = dir_stride;
+    return ddelta ? der_groups<T, kJvp, true>(h, a, batch, kb, split, stage)
+                  : der_groups<T, kJvp, false>(h, a, batch, kb, split, stage);
 }
 
 template <typename T>
-cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw, int stage)
+cudaError_t launch_vjp(const Handle &h, const T *R, double *gtheta, double *gdelta, int split, int vw, int stage,
+                       int batch, int kb, long long r_stride, int sum)
 {
     RayArgs<T> a = base_args<T>(h);
     a.VW = vw;
     a.R = R;
+    a.r_stride = r_stride;
     a.partial = h.d_partial;
-    cudaError_t e = gdelta ? run_ray_any<T, kVjp, true, 1>(h, a, split, stage)
-                           : run_ray_any<T, kVjp, false, 1>(h, a, split, stage);
+    a.part_stride = 4LL * h.V * h.nchunks;
+    cudaError_t e = gdelta ? der_groups<T, kVjp, true>(h, a, batch, kb, split, stage)
+                           : der_groups<T, kVjp, false>(h, a, batch, kb, split, stage);
     if (e != cudaSuccess) return e;
-    k_finalize<<<(h.V + 7) / 8, 256, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, gtheta, gdelta, nullptr, 1.0,
-                                                        nullptr, nullptr);
+    const long long outs = (long long)h.V * (sum ? 1 : batch);
+    k_finalize<<<(int)((outs + 7) / 8), 256, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, batch, a.part_stride,
+                                                            sum, gtheta, gdelta, nullptr, 1.0, nullptr, nullptr,
+                                                            nullptr);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, double *jnorm2, double *fval, int split,
-                      int vw, int stage, const int *view_mask, const int *skip)
+                      int vw, int stage, const int *view_mask, const int *skip, int batch, int kb, double *rscale)
 {
     RayArgs<T> a = base_args<T>(h);
     a.VW = vw;
     a.R = bdata;
+    a.r_stride = (long long)h.V * h.B;
     a.res = res;
     a.partial = h.d_partial;
+    a.part_stride = 4LL * h.V * h.nchunks;
     a.view_mask = view_mask;
     a.skip = skip;
-    cudaError_t e = run_ray_any<T, kGn, false, 1>(h, a, split, stage);
+    cudaError_t e = der_groups<T, kGn, false>(h, a, batch, kb, split, stage);
     if (e != cudaSuccess) return e;
-    k_finalize<<<(h.V + 7) / 8, 256, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, grad, jnorm2, fval, 0.5,
-                                                        view_mask, skip);
+    const long long outs = (long long)h.V * batch;
+    k_finalize<<<(int)((outs + 7) / 8), 256, 0, h.stream>>>(h.d_partial, h.V, h.nchunks, batch, a.part_stride, 0,
+                                                            grad, jnorm2, fval, 0.5, rscale, view_mask, skip);
     return cudaGetLastError();
 }
 
@@ -731,10 +810,12 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
     template cudaError_t launch_prep_forward<T>(const Handle &, const T *, int, const int *, const double *, \
                                                 const double *);                                           \
     template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, int, const int *);     \
-    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int, int); \
-    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int, int);      \
+    template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int, int, int, \
+                                       int, long long);                                                   \
+    template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int, int, int, int, \
+                                       long long, int);                                                   \
     template cudaError_t launch_gn<T>(const Handle &, const T *, T *, double *, double *, double *, int,    \
-                                      int, int, const int *, const int *);
+                                      int, int, const int *, const int *, int, int, double *);
 
 CTGB_RAY_INSTANTIATE(float)
 CTGB_RAY_INSTANTIATE(double)

@@ -81,12 +81,12 @@ template <typename T> struct Solver {
            *part_gram = nullptr, *part_dot = nullptr, *part_n = nullptr, *norms = nullptr, *norms2 = nullptr,
            *scal = nullptr;
     double *th_k = nullptr, *th_n = nullptr, *th_t = nullptr, *d = nullptr, *alpha = nullptr, *g = nullptr,
-           *j2 = nullptr, *f0 = nullptr, *ft = nullptr, *scratch_v = nullptr;
+           *j2 = nullptr, *f0 = nullptr, *ft = nullptr, *rho = nullptr, *scratch_v = nullptr;
     int *ctl = nullptr, *active = nullptr;
     // VarPro Gauss-Newton work (allocated on first use)
     T *vp_a = nullptr, *vp_u = nullptr;
     double *vp_E = nullptr, *vp_G = nullptr, *vp_Y = nullptr, *vp_idel = nullptr, *vp_ones = nullptr,
-           *vp_scal = nullptr;
+           *vp_scal = nullptr, *vp_rho = nullptr;
     int *vp_ctl = nullptr;
     int *h_ctl = nullptr;       // pinned mirror of ctl
     double *h_scal = nullptr;   // pinned mirror of small results
@@ -94,8 +94,10 @@ template <typename T> struct Solver {
     int *d_stop = nullptr;      // its device address
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::vector<cudaGraphExec_t> step_graph;  // one captured Enlarge step per basis size
-    bool use_graphs = true;
+    bool use_graphs = true;  // off in the plain form
     double noise = 0.0;      // noise norm of the discrepancy principle for the bound data
+    // unit roundoff of the Armijo noise floor: the option, or that of the misfit's precision
+    double armijo_u() const { return o.armijo_eps >= 0.0 ? o.armijo_eps : (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53); }
     long long m_cap = 0;     // streaming: capacities over all blocks (0: this handle's)
     int v_cap = 0;
 
@@ -103,6 +105,7 @@ template <typename T> struct Solver {
         : h(h_), o(o_), b(b_), delta(delta_), noise(o_.noise_norm)
     {
         h.stream = s_;
+        if (o.plain) use_graphs = false;
     }
 
     ~Solver()
@@ -166,7 +169,8 @@ template <typename T> struct Solver {
         SV_TRY(alloc(norms, 3));
         SV_TRY(alloc(norms2, 3));
         SV_TRY(alloc(scal, kScalCount));
-        for (double **p : {&th_k, &th_n, &th_t, &d, &alpha, &g, &j2, &f0, &ft, &scratch_v}) SV_TRY(alloc(*p, v_all));
+        for (double **p : {&th_k, &th_n, &th_t, &d, &alpha, &g, &j2, &f0, &ft, &rho, &scratch_v})
+            SV_TRY(alloc(*p, v_all));
         SV_TRY(alloc(ctl, kCtlCount));
         SV_TRY(alloc(active, v_all));
         if (cudaMallocHost(&h_ctl, sizeof(int) * kCtlCount) != cudaSuccess ||
@@ -267,12 +271,15 @@ template <typename T> struct Solver {
         return CT_OK;
     }
 
-    // HV[:, j0:j0+cnt) = H(theta) V[:, j0:j0+cnt), in chunks of max_batch columns
+    // columns per projection launch: the Krylov block (max_batch), or one in the plain form
+    int block() const { return o.plain ? 1 : h.max_batch; }
+
+    // HV[:, j0:j0+cnt) = H(theta) V[:, j0:j0+cnt), in chunks of block() columns
     int project(const double *theta, int j0, int cnt, const int *stop)
     {
         if (cnt <= 0) SV_CUDA(launch_view_setup(h, theta, delta, stop));
-        for (int j = j0; j < j0 + cnt; j += h.max_batch) {
-            const int nb = std::min(h.max_batch, j0 + cnt - j);
+        for (int j = j0; j < j0 + cnt; j += block()) {
+            const int nb = std::min(block(), j0 + cnt - j);
             // the first layout launch also brings the view table up to date
             SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop, j == j0 ? theta : nullptr, delta));
             SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
@@ -435,9 +442,10 @@ template <typename T> struct Solver {
         SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
         for (int it = 0; it < o.maxiter_p; ++it) {
             SV_CUDA(launch_pairs_img<T>(h, uimg, h.F, nullptr, th_n, delta));
-            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
-            k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, h.V, o.mu_rel, o.alpha0, th_n, d, alpha, th_t, active,
-                                                     ctl);
+            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw, h.tune.der_stage,
+                                 nullptr, nullptr, 1, 1, rho));
+            k_gn_direction<<<1, 1024, 0, h.stream>>>(g, j2, rho, h.V, o.mu_rel, o.alpha0, armijo_u(), th_n, d, alpha,
+                                                     th_t, active, ctl);
             // Trial rounds run predicated on ctl[kArmijoDone] (set by k_armijo when no
             // view searches any more); the host reads the flag after rounds 1, 3, 7, 15
             // and the last only, so a search that needs many halvings costs few round
@@ -448,9 +456,9 @@ template <typename T> struct Solver {
                 SV_CUDA(launch_view_setup_wide(h, th_t, delta, ctl + kViewChanged, done));
                 SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw,
                                      h.tune.der_stage, active, done));
-                k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, th_n, h.V, o.c1, o.beta, alpha, th_t, active, ctl,
-                                                   hv == o.max_halvings ? 1 : 0);
-                if (hv + 1 == next_check || hv == o.max_halvings) {
+                k_armijo<<<1, 1024, 0, h.stream>>>(f0, ft, g, d, rho, th_n, h.V, o.c1, o.beta, armijo_u(), alpha,
+                                                   th_t, active, ctl, hv == o.max_halvings ? 1 : 0);
+                if (hv + 1 == next_check || hv == o.max_halvings || o.plain) {
                     SV_TRY(sync_ctl());
                     if (h_ctl[kArmijoDone]) break;
                     next_check = 2 * next_check + 1;
@@ -474,6 +482,7 @@ template <typename T> struct Solver {
         SV_TRY(alloc(vp_idel, v_all));
         SV_TRY(alloc(vp_ones, v_all));
         SV_TRY(alloc(vp_scal, kScalCount));
+        SV_TRY(alloc(vp_rho, 3));
         SV_TRY(alloc(vp_ctl, kCtlCount));
         k_fill<double><<<grid_for(v_all), kThreads, 0, h.stream>>>(vp_ones, v_all, 1.0);
         SV_CUDA(cudaMemsetAsync(vp_ctl, 0, sizeof(int) * kCtlCount, h.stream));
@@ -517,21 +526,30 @@ template <typename T> struct Solver {
         double f_last = 0.0;
         for (int it = 0; it < o.maxiter_p; ++it) {
             SV_TRY(varpro_eval(th_n, k, lam, vp_scal + kTmp0));
+            {  // rounding scale of f's data term at theta (Armijo noise floor)
+                const int nblk = red_blocks(m);
+                k_round_scale<T><<<nblk, kThreads, 0, h.stream>>>(res, b, m, part_n);
+                k_norms3_reduce<<<1, 32, 0, h.stream>>>(part_n, nblk, vp_rho, nullptr);
+            }
             SV_CUDA(launch_pairs_img<T>(h, vp_u, h.F, nullptr, th_n, delta));
             SV_CUDA(launch_jvp<T>(h, vp_ones, nullptr, vp_a, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
             k_view_dots<T><<<std::min(h.V, 8 * h.num_sms), 128, 0, h.stream>>>(HV, m, k, vp_a, res, h.V, h.B, vp_E,
                                                                                j2, g);
-            for (int c = 0; c < k; ++c) {
-                SV_CUDA(launch_pairs_img<T>(h, col(V, n, c), h.F, nullptr, nullptr, delta));
+            // G[c][j] = (H_j V_c)^T r: the basis columns in batches of max_batch, one
+            // batched VJP against the shared residual per batch
+            for (int c = 0; c < k; c += block()) {
+                const int nb = std::min(block(), k - c);
+                SV_CUDA(launch_pairs_img<T>(h, col(V, n, c), nb * h.F, nullptr, nullptr, delta));
                 SV_CUDA(launch_vjp<T>(h, res, vp_G + (size_t)c * h.V, nullptr, h.tune.der_split, h.tune.der_vw,
-                                      h.tune.der_stage));
+                                      h.tune.der_stage, nb, h.tune.der_kb, 0, 0));
             }
             k_varpro_direction<<<1, 1024, sizeof(VpShared), h.stream>>>(GH, GP, lam, vp_E, vp_G, j2, g, k, h.V,
                                                                         o.mu_rel, vp_Y, vp_idel, d, vp_scal + kTmp1,
                                                                         ctl);
             SV_CUDA(cudaGetLastError());
-            double fg[2];
+            double fg[2], rho0;
             SV_TRY(read_doubles(vp_scal + kTmp0, 2, fg));
+            SV_TRY(read_doubles(vp_rho, 1, &rho0));
             const double f0 = fg[0], gd = fg[1];
             if (it == 0 && f_hist) f_hist[0] = f0;
             f_last = f0;
@@ -539,6 +557,7 @@ template <typename T> struct Solver {
             double alpha = o.alpha0;
             if (gd < 0.0) {
                 for (int hv = 0; hv <= o.max_halvings; ++hv) {
+                    if (alpha * std::fabs(gd) < armijo_u() * rho0) break;  // noise floor: no step
                     k_theta_step<<<grid_for(h.V), kThreads, 0, h.stream>>>(th_n, d, alpha, h.V, th_t);
                     SV_TRY(varpro_eval(th_t, k, lam, vp_scal + kRnorm2));
                     double ft;
@@ -923,6 +942,7 @@ void nlrmm_default_opts(nlrmm_opts *o)
     o->mu_rel = 1e-8;
     o->tol_u = 1e-3;
     o->tol_p = 1e-4;
+    o->armijo_eps = -1.0;
 }
 
 int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const double *delta, void *x_out,
@@ -934,6 +954,7 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
         return CT_ERR_ARG;
+    if ((o.plain != 0 && o.plain != 1) || o.reserved0 != 0) return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
     h.fwd_ready = h.adj_ready = 0;
     // The solve runs on a private stream ordered after the work already queued
@@ -972,6 +993,7 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !noise_norms))
         return CT_ERR_ARG;
+    if ((o.plain != 0 && o.plain != 1) || o.reserved0 != 0) return CT_ERR_ARG;
     std::vector<const ctgb::Handle *> hs(nblocks);
     for (int j = 0; j < nblocks; ++j) {
         if (!blocks[j] || !b[j] || !theta_inout[j]) return CT_ERR_ARG;
@@ -1075,6 +1097,9 @@ int nlrmm_varpro_update(ct_handle *H, const void *b, double *theta_inout, const 
         o.alpha0 = opts->alpha0;
         o.mu_rel = opts->mu_rel;
         o.temporal = opts->temporal;
+        o.armijo_eps = opts->armijo_eps;
+        if (opts->plain != 0 && opts->plain != 1) return CT_ERR_ARG;
+        o.plain = opts->plain;
     }
     ctgb::Handle &h = H->h;
     h.fwd_ready = h.adj_ready = 0;

@@ -1200,6 +1200,26 @@ __global__ void __launch_bounds__(256) k_compress_basis(const double *__restrict
     }
 }
 
+// Rounding scale sum |r| (|r + b| + |b|) of a misfit 1/2 |r|^2 formed from
+// r = A - b (A = r + b); per-block partials in slot 0 of 3 (k_norms3_reduce).
+template <typename T>
+__global__ void k_round_scale(const T *__restrict__ r, const T *__restrict__ b, long long len,
+                              double *__restrict__ part)
+{
+    __shared__ double sh[33];
+    double s0 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+        const double x = (double)r[i], y = (double)b[i];
+        s0 += fabs(x) * (fabs((double)(r[i] + b[i])) + fabs(y));
+    }
+    s0 = block_sum(s0, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 3 + 0] = s0;
+        part[blockIdx.x * 3 + 1] = 0.0;
+        part[blockIdx.x * 3 + 2] = 0.0;
+    }
+}
+
 // VarPro reduced objective f = 1/2 |res|^2 + lambda/2 y^T G_P y (one thread).
 __global__ void k_varpro_value(const double *__restrict__ norms3_res, const double *__restrict__ GP,
                                const double *__restrict__ y, int k, double lam, double *__restrict__ fval)
@@ -1221,11 +1241,17 @@ template <typename T> __global__ void k_fill(T *__restrict__ x, long long len, T
 // ---------------------------------------------------------------------------
 // mu = mu_rel * max_v |J_v|^2; d_v = -g_v / (|J_v|^2 + mu); alpha = alpha0;
 // theta_trial = theta + alpha d; every view active.
-__global__ void k_gn_direction(const double *__restrict__ g, const double *__restrict__ j2, int V, double mu_rel,
-                               double alpha0, const double *__restrict__ theta, double *__restrict__ d,
-                               double *__restrict__ alpha, double *__restrict__ theta_trial, int *__restrict__ active,
-                               int *__restrict__ ctl)
+// Per-view damped Gauss-Newton direction d_v = -g_v / (|J_v|^2 + mu) and the
+// first Armijo trial alpha0.  A view whose first-order change alpha0 |g_v d_v|
+// is below u rho_v (rho_v the rounding scale of its misfit, u the unit
+// roundoff of the misfit's precision) ends its search here with no step (the
+// noise floor); ctl[kActive] counts the views that search.
+__global__ void k_gn_direction(const double *__restrict__ g, const double *__restrict__ j2,
+                               const double *__restrict__ rho, int V, double mu_rel, double alpha0, double unit,
+                               const double *__restrict__ theta, double *__restrict__ d, double *__restrict__ alpha,
+                               double *__restrict__ theta_trial, int *__restrict__ active, int *__restrict__ ctl)
 {
+    __shared__ int cnt[32];
     __shared__ double sh[40];
     double mx = 0.0;
     for (int v = threadIdx.x; v < V; v += blockDim.x) mx = fmax(mx, j2[v]);
@@ -1240,24 +1266,35 @@ __global__ void k_gn_direction(const double *__restrict__ g, const double *__res
     }
     __syncthreads();
     const double mu = mu_rel * fmax(sh[32], 1e-300);
+    int mine = 0;
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
         const double dv = -g[v] / (j2[v] + mu);
         d[v] = dv;
-        alpha[v] = alpha0;
-        theta_trial[v] = theta[v] + alpha0 * dv;
-        active[v] = 1;
+        const bool on = !(alpha0 * fabs(g[v] * dv) < unit * rho[v]);
+        alpha[v] = on ? alpha0 : 0.0;
+        theta_trial[v] = on ? theta[v] + alpha0 * dv : theta[v];
+        active[v] = on ? 1 : 0;
+        mine += on ? 1 : 0;
     }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = mine;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        ctl[kActive] = V;
-        ctl[kArmijoDone] = V == 0;
+        int t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += cnt[i];
+        ctl[kActive] = t;
+        ctl[kArmijoDone] = t == 0;
     }
 }
 
 // Armijo test for the views still searching; shrinks alpha of the failures.
-// ctl[kArmijoDone] becomes 1 once no view searches; the trial kernels of the
-// later rounds (and this kernel) then return at once.
+// A failure whose next first-order change alpha |g_v d_v| falls below u rho_v
+// (the noise floor) ends its search with no step, as does a failure in the
+// last round.  ctl[kArmijoDone] becomes 1 once no view searches; the trial
+// kernels of the later rounds (and this kernel) then return at once.
 __global__ void k_armijo(const double *__restrict__ f0, const double *__restrict__ ft, const double *__restrict__ g,
-                         const double *__restrict__ d, const double *__restrict__ theta, int V, double c1, double beta,
+                         const double *__restrict__ d, const double *__restrict__ rho,
+                         const double *__restrict__ theta, int V, double c1, double beta, double unit,
                          double *__restrict__ alpha, double *__restrict__ theta_trial, int *__restrict__ active,
                          int *__restrict__ ctl, int last)
 {
@@ -1269,6 +1306,10 @@ __global__ void k_armijo(const double *__restrict__ f0, const double *__restrict
         if (ft[v] <= f0[v] + c1 * alpha[v] * g[v] * d[v]) {
             active[v] = 0;
         } else if (last) {  // no acceptable step: keep the old angle
+            active[v] = 0;
+            alpha[v] = 0.0;
+            theta_trial[v] = theta[v];
+        } else if ((alpha[v] * beta) * fabs(g[v] * d[v]) < unit * rho[v]) {  // noise floor: no step
             active[v] = 0;
             alpha[v] = 0.0;
             theta_trial[v] = theta[v];

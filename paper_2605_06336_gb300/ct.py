@@ -65,6 +65,7 @@ class nlrmm_opts(ctypes.Structure):
         ("lam_hi", ctypes.c_double), ("c1", ctypes.c_double), ("beta", ctypes.c_double),
         ("alpha0", ctypes.c_double), ("mu_rel", ctypes.c_double), ("tol_u", ctypes.c_double),
         ("tol_p", ctypes.c_double), ("temporal", ctypes.c_int32), ("varpro", ctypes.c_int32),
+        ("armijo_eps", ctypes.c_double), ("plain", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -107,6 +108,9 @@ def load_library(path: str | None = None):
     lib.ct_jac.argtypes = [P, P, P, P, P, P, P]
     lib.ct_jacT.argtypes = [P, P, P, P, P, P, P]
     lib.ct_gn_terms.argtypes = [P, P, P, P, P, P, P, P, P]
+    lib.ct_jac_batch.argtypes = [P, P, P, P, P, P, P, I, I]
+    lib.ct_jacT_batch.argtypes = [P, P, P, P, P, P, P, I, I]
+    lib.ct_gn_terms_batch.argtypes = [P, P, P, P, P, P, P, P, P, I]
     lib.ct_status.argtypes = [P]
     lib.ct_set_stream.argtypes = [P, P]
     lib.ct_autotune.argtypes = [P]
@@ -129,7 +133,8 @@ def load_library(path: str | None = None):
     lib.ct_last_cuda_error.argtypes = []
     lib.ct_last_cuda_error.restype = ctypes.c_char_p
     for f in ("ct_init", "ct_forward", "ct_adjoint", "ct_forward_repeat", "ct_adjoint_repeat", "ct_jac", "ct_jacT",
-              "ct_gn_terms", "ct_status", "ct_set_stream", "ct_autotune", "ct_get_tuning", "ct_set_tuning"):
+              "ct_gn_terms", "ct_jac_batch", "ct_jacT_batch", "ct_gn_terms_batch", "ct_status", "ct_set_stream",
+              "ct_autotune", "ct_get_tuning", "ct_set_tuning"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -210,6 +215,24 @@ def ct_gn_terms(h, theta, delta, x, bdata, res, grad, jnorm2, fval):
                                       _p(fval)), "ct_gn_terms")
 
 
+CT_BATCH_PER_IMAGE_DIRECTION, CT_BATCH_SHARED_R, CT_BATCH_SUM = 1, 2, 4
+
+
+def ct_jac_batch(h, theta, delta, X, dtheta, ddelta, dY, batch, flags=0):
+    _check(load_library().ct_jac_batch(h, _p(theta), _p(delta), _p(X), _p(dtheta), _p(ddelta), _p(dY), int(batch),
+                                       int(flags)), "ct_jac_batch")
+
+
+def ct_jacT_batch(h, theta, delta, X, R, gtheta, gdelta, batch, flags=0):
+    _check(load_library().ct_jacT_batch(h, _p(theta), _p(delta), _p(X), _p(R), _p(gtheta), _p(gdelta), int(batch),
+                                        int(flags)), "ct_jacT_batch")
+
+
+def ct_gn_terms_batch(h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch):
+    _check(load_library().ct_gn_terms_batch(h, _p(theta), _p(delta), _p(X), _p(bdata), _p(res), _p(grad),
+                                            _p(jnorm2), _p(fval), int(batch)), "ct_gn_terms_batch")
+
+
 def ct_status(h):
     return load_library().ct_status(h)
 
@@ -224,7 +247,7 @@ def ct_autotune(h):
 
 TUNING_FIELDS = ("fwd_images_per_lane", "fwd_warps_per_ray", "fwd_views_per_cta", "adj_images_per_thread",
                  "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta", "fwd_staging", "jac_staging",
-                 "adj_staging")
+                 "adj_staging", "jac_images_per_lane")
 
 
 def ct_get_tuning(h):
@@ -243,12 +266,46 @@ def ct_set_tuning(h, values):
 NOALLOC_MAX_N, NOALLOC_MAX_VIEWS, NOALLOC_MAX_BINS = 256, 512, 1024
 
 
+def _noalloc_args(specs):
+    """Check the tensor arguments of ct_jacT_noalloc (the C entry point reads and
+    writes through raw pointers with the sizes it is given): specs are
+    (name, tensor or None, dtype, element count, required).  Types, counts and
+    strides of every argument are checked before any device."""
+    import torch
+    for name, t, dtype, numel, required in specs:
+        if t is None:
+            if required:
+                raise ValueError(f"ct_jacT_noalloc: {name} is required")
+            continue
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"ct_jacT_noalloc: {name} must be a torch tensor")
+        if t.dtype != dtype:
+            raise ValueError(f"ct_jacT_noalloc: {name} must be {dtype}, got {t.dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"ct_jacT_noalloc: {name} must have {numel} elements, got {t.numel()}")
+        if not t.is_contiguous():
+            raise ValueError(f"ct_jacT_noalloc: {name} must be contiguous")
+    for name, t, _, _, _ in specs:
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"ct_jacT_noalloc: {name} must be a CUDA tensor")
+
+
 def ct_jacT_noalloc(N, B, n_views, theta, delta, x, r, gtheta, gdelta, stream=None):
     """ct_jacT without a handle or any device allocation (for callers that cannot
-    allocate); the workspace is a static device array, so sizes are capped."""
+    allocate); the workspace is a static device array, so sizes are capped.
+    theta, delta (or None), gtheta, gdelta (or None): float64 [n_views]; x:
+    float32 [N*N]; r: float32 [n_views*B]; all contiguous CUDA tensors."""
+    import torch
+    N, B, n_views = int(N), int(B), int(n_views)
+    if N < 2 or B < 1 or n_views < 1:
+        raise ValueError(f"ct_jacT_noalloc: N={N}, B={B}, views={n_views} below the minimum 2/1/1")
     if N > NOALLOC_MAX_N or B > NOALLOC_MAX_BINS or n_views > NOALLOC_MAX_VIEWS:
         raise ValueError(f"ct_jacT_noalloc: N={N}, B={B}, views={n_views} exceed the limits "
                          f"{NOALLOC_MAX_N}/{NOALLOC_MAX_BINS}/{NOALLOC_MAX_VIEWS} of its static workspace")
+    _noalloc_args([("theta", theta, torch.float64, n_views, True), ("delta", delta, torch.float64, n_views, False),
+                   ("x", x, torch.float32, N * N, True), ("r", r, torch.float32, n_views * B, True),
+                   ("gtheta", gtheta, torch.float64, n_views, True),
+                   ("gdelta", gdelta, torch.float64, n_views, False)])
     _check(load_library().ct_jacT_noalloc(int(N), int(B), int(n_views), _p(theta), _p(delta), _p(x), _p(r),
                                           _p(gtheta), _p(gdelta), _stream_ptr(stream)), "ct_jacT_noalloc")
 
@@ -418,6 +475,54 @@ class CTOperator:
         gd = torch.empty(self.V, dtype=torch.float64, device=x.device) if want_delta else None
         ct_jacT(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, r, gt, gd)
         return (gt, gd) if want_delta else gt
+
+    def _batch(self, X, last, name):
+        self._chk(X, last, name)
+        K = 1 if X.dim() == 1 else X.shape[0]
+        if K > self.max_batch:
+            raise ValueError(f"{name}: batch {K} above max_batch {self.max_batch}")
+        return K
+
+    def jac_batch(self, X, theta, dtheta, delta=None, ddelta=None, out=None):
+        """dY[k] = J(x_k) dtheta (+ J_delta(x_k) ddelta) for the K images of X in one
+        launch; dtheta / ddelta are [V] (shared) or [K, V] (one per image)."""
+        K = self._batch(X, self.n, "X")
+        per = dtheta.dim() == 2
+        for nm, d in (("dtheta", dtheta), ("ddelta", ddelta)):
+            if d is not None and not (d.is_cuda and d.dtype == torch.float64 and d.is_contiguous() and
+                                      d.numel() == (K * self.V if per else self.V)):
+                raise ValueError(f"{nm}: expected contiguous float64 CUDA tensor of {K if per else 1} x {self.V}")
+        dY = out if out is not None else torch.empty(X.shape[:-1] + (self.m,), dtype=self.dtype, device=X.device)
+        ct_jac_batch(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), X, dtheta, ddelta, dY, K,
+                     CT_BATCH_PER_IMAGE_DIRECTION if per else 0)
+        return dY
+
+    def jacT_batch(self, X, theta, R, delta=None, want_delta=False, sum_images=False):
+        """g[k] = J(x_k)^T R_k for the K images of X in one launch; R is [K, m] or
+        one [m] sinogram shared by every image.  sum_images: one [V] gradient,
+        the images added in order."""
+        K = self._batch(X, self.n, "X")
+        self._chk(R, self.m, "R")
+        shared = R.dim() == 1
+        if not shared and R.shape[0] != K:
+            raise ValueError(f"R: {R.shape[0]} sinograms for {K} images")
+        shape = (self.V,) if sum_images else (K, self.V)
+        gt = torch.empty(shape, dtype=torch.float64, device=X.device)
+        gd = torch.empty(shape, dtype=torch.float64, device=X.device) if want_delta else None
+        flags = (CT_BATCH_SHARED_R if shared else 0) | (CT_BATCH_SUM if sum_images else 0)
+        ct_jacT_batch(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), X, R, gt, gd, K, flags)
+        return (gt, gd) if want_delta else gt
+
+    def gn_terms_batch(self, X, theta, bdata, delta=None, want_residual=False):
+        """ct_gn_terms for each of the K images of X against the K data sinograms bdata."""
+        K = self._batch(X, self.n, "X")
+        self._chk(bdata, self.m, "bdata")
+        if (1 if bdata.dim() == 1 else bdata.shape[0]) != K:
+            raise ValueError("bdata: one data sinogram per image expected")
+        res = torch.empty((K, self.m), dtype=self.dtype, device=X.device) if want_residual else None
+        g, j2, f = (torch.empty((K, self.V), dtype=torch.float64, device=X.device) for _ in range(3))
+        ct_gn_terms_batch(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), X, bdata, res, g, j2, f, K)
+        return g, j2, f, res
 
     def gn_terms(self, x, theta, bdata, delta=None, want_residual=False):
         self._chk(x, self.n, "x")

@@ -50,3 +50,43 @@ def test_init_rejects_bad_geometry_without_touching_the_gpu():
         g.source_distance = D
         assert lib.ct_init(ctypes.byref(g), None, ctypes.byref(h)) == ct.CT_ERR_ARG
     assert lib.ct_forward(None, None, None, None, None, 1) == ct.CT_ERR_ARG
+
+
+def test_noalloc_binding_rejects_bad_arguments_before_any_call():
+    """ct_jacT_noalloc writes through raw pointers with the sizes it is given:
+    the binding refuses wrong sizes, dtypes, element counts, strides and CPU
+    tensors before calling it (dtype / count / stride checks come before the
+    device check, so each is reached here with CPU tensors)."""
+    torch = pytest.importorskip("torch")
+    from paper_2605_06336_gb300 import ct
+    N, B, V = 16, 23, 6
+    f64, f32 = torch.float64, torch.float32
+    good = dict(theta=torch.zeros(V, dtype=f64), delta=torch.zeros(V, dtype=f64), x=torch.zeros(N * N, dtype=f32),
+                r=torch.zeros(V * B, dtype=f32), gtheta=torch.zeros(V, dtype=f64), gdelta=torch.zeros(V, dtype=f64))
+
+    def call(N=N, B=B, V=V, **over):
+        a = dict(good, **over)
+        ct.ct_jacT_noalloc(N, B, V, a["theta"], a["delta"], a["x"], a["r"], a["gtheta"], a["gdelta"])
+
+    for sizes in (dict(N=1), dict(B=0), dict(V=0), dict(N=ct.NOALLOC_MAX_N + 1), dict(B=ct.NOALLOC_MAX_BINS + 1),
+                  dict(V=ct.NOALLOC_MAX_VIEWS + 1)):
+        with pytest.raises(ValueError):
+            call(**sizes)
+    bad = {
+        "theta": [None, torch.zeros(V, dtype=f32), torch.zeros(V + 1, dtype=f64), torch.zeros(2 * V, dtype=f64)[::2]],
+        "delta": [torch.zeros(V, dtype=f32), torch.zeros(V - 1, dtype=f64)],
+        "x": [None, torch.zeros(N * N, dtype=f64), torch.zeros(N * N, dtype=torch.float16), torch.zeros(N * N - 1, dtype=f32),
+              torch.zeros(N, 2 * N, dtype=f32)[:, ::2]],
+        "r": [None, torch.zeros(V * B, dtype=f64), torch.zeros(V * B + 1, dtype=f32)],
+        "gtheta": [None, torch.zeros(V, dtype=f32), torch.zeros(V - 1, dtype=f64)],
+        "gdelta": [torch.zeros(V, dtype=f32), torch.zeros(V + 1, dtype=f64)],
+    }
+    for name, values in bad.items():
+        for v in values:
+            with pytest.raises(ValueError, match=f"noalloc: {name} "):
+                call(**{name: v})
+    # everything well formed but on the host: refused as not CUDA
+    with pytest.raises(ValueError, match="CUDA"):
+        call()
+    with pytest.raises(ValueError, match="CUDA"):
+        call(delta=None, gdelta=None)

@@ -86,8 +86,8 @@ def test_band_matches_gather_bit_for_bit(case):
 
     for vw, rb, segs in SHAPES:
         # L1-gather reference: the same row segments per ray (as warps of one CTA), whole rays for J
-        ref = run([kb, segs, 1, 1, 1, 1, 1, 0, 0, 0])
-        got = run([kb, segs, vw, 1, 1, 1, vw, rb, rb, 0])
+        ref = run([kb, segs, 1, 1, 1, 1, 1, 0, 0, 0, 1])
+        got = run([kb, segs, vw, 1, 1, 1, vw, rb, rb, 0, 1])
         for name, a, b in zip(("forward", "jvp", "vjp_theta", "vjp_delta", "gn_grad", "gn_j2", "gn_f", "gn_res"),
                               got, ref):
             assert torch.equal(a, b), (name, vw, rb, segs, float((a.double() - b.double()).abs().max()))
@@ -104,7 +104,7 @@ def test_band_forward_full_batch_matches_oracle():
     rng = np.random.default_rng(3)
     X = np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(K - 1, w.N * w.N))])
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=K, dtype=torch.float32)
-    op.tuning = [8, 2, 8, 8, 2, 1, 8, 4, 4, 0]
+    op.tuning = [8, 2, 8, 8, 2, 1, 8, 4, 4, 0, 1]
     y = host(op.forward(dev(X, torch.float32), dev(w.theta_true)))
     g = oracle.Geometry(w.N, w.B, w.V)
     assert rel(y, oracle.forward(g, w.theta_true, X)) <= 1e-5
@@ -129,9 +129,9 @@ def test_staged_transpose_matches_gather_bit_for_bit(case):
     th, dl, Yg = dev(theta), dev(delta), dev(Y, torch.float32)
     for akb in sorted({1, 2, 4, 8} & set(range(1, K + 1))):
         for vb, segs in ADJ_SHAPES:
-            op.tuning = [1, 1, 1, akb, segs, 1, 1, 0, 0, 0]
+            op.tuning = [1, 1, 1, akb, segs, 1, 1, 0, 0, 0, 1]
             ref = op.adjoint(Yg, th, dl).clone()
-            op.tuning = [1, 1, 1, akb, segs, 1, 1, 0, 0, vb]
+            op.tuning = [1, 1, 1, akb, segs, 1, 1, 0, 0, vb, 1]
             got = op.adjoint(Yg, th, dl).clone()
             assert torch.equal(got, ref), (akb, vb, segs, float((got - ref).abs().max()))
     g_o = oracle.Geometry(N, B, V, vpf)

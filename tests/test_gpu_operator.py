@@ -3,6 +3,11 @@
 Tolerances (normwise relative, ||gpu - oracle|| / ||oracle||):
   * float32 operators: 1e-5 for H, H^T, J and J^T;
   * float64 operators: 1e-12.
+The same bounds hold element by element, so that an error confined to a few
+samples (one flipped interpolation cell) is not averaged away: per view for
+sinograms, max_b |gpu - oracle| / max_b |oracle|; per image row for images;
+per view for J^T, |gpu - oracle| / sum_b |r_vb| |dH x/dtheta_v|_b (the
+magnitude of the terms the view's sum cancels).
 Angles are kept away from |cos| = |sin| (the Joseph axis switch), where the
 two sides could break the tie differently in the last bit.  For the angle
 derivative the view at "pi/2" is pi/2 + 1e-7: at pi/2 itself cos() is 6e-17,
@@ -29,6 +34,25 @@ def rel(a, b):
     b = np.asarray(b, dtype=np.float64)
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def rows_rel(a, b, ncols):
+    """max over rows of max|a - b| / max|b| in that row (rows of ncols entries;
+    rows of b that are all zero are compared against 1)."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1, ncols)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, ncols)
+    if a.size == 0:
+        return 0.0
+    scale = np.abs(b).max(1)
+    scale[scale == 0] = 1.0
+    return float((np.abs(a - b).max(1) / scale).max())
+
+
+def view_sum_rel(gv, go, r, dt, V, B):
+    """per-view error of a sum over bins, against the magnitude of its terms"""
+    mag = (np.abs(np.asarray(r).reshape(V, B)) * np.abs(np.asarray(dt).reshape(V, B))).sum(1)
+    mag[mag == 0] = 1.0
+    return float((np.abs(np.asarray(gv) - np.asarray(go)) / mag).max()) if V else 0.0
 
 
 @pytest.fixture(scope="module")
@@ -85,6 +109,8 @@ def test_forward_adjoint_parity(ct, case, dtype):
     Xo = oracle.adjoint(g, theta, Y, delta)
     assert rel(host(Yg), Yo) <= TOL[dtype]
     assert rel(host(Xg), Xo) <= TOL[dtype]
+    assert rows_rel(host(Yg), Yo, B) <= TOL[dtype]
+    assert rows_rel(host(Xg), Xo, N) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
@@ -108,6 +134,47 @@ def test_jacobian_parity(ct, case, dtype):
     assert rel(host(dy), dyo) <= TOL[dtype]
     assert rel(host(gt), gto) <= TOL[dtype]
     assert rel(host(gd), gdo) <= TOL[dtype]
+    dt, dd = oracle.dsample(g, theta, x, delta)
+    assert rows_rel(host(dy), dyo, B) <= TOL[dtype]
+    assert view_sum_rel(host(gt), gto, r, dt, V, B) <= TOL[dtype]
+    assert view_sum_rel(host(gd), gdo, r, dd, V, B) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_views_exactly_on_the_diagonals(ct, dtype):
+    """Views at the FP64 values of pi/4, 3pi/4 (and those plus pi, minus pi),
+    where |cos| and |sin| differ by about one unit in the last place.  The
+    axis is decided on theta itself (theta mod pi against the doubles nearest
+    pi/4 and 3pi/4, ties to rows), the same on both sides, which matters for J
+    and J^T: the Joseph sums are continuous across the diagonal, their angle
+    derivative is not.  A detector offset keeps the samples off the
+    interpolation kinks that an exact 45 degree view meets, where the one-sided
+    slope would depend on the last bit of tan(theta)."""
+    N, B = 40, 57
+    rng = np.random.default_rng(77)
+    theta = np.array([math.pi / 4, 3 * math.pi / 4, math.pi / 4 + math.pi, 3 * math.pi / 4 - math.pi,
+                      0.3, 2.0])
+    V = theta.size
+    g = oracle.Geometry(N, B, V)
+    x = rng.uniform(size=N * N)
+    r = rng.standard_normal(V * B)
+    dth = rng.standard_normal(V)
+    delta = np.full(V, 0.1234)
+    op = ct.CTOperator(N, B, V, max_batch=1, dtype=dtype)
+    th, dl = dev(theta), dev(delta)
+    y = op.forward(dev(x, dtype), th, dl)
+    xa = op.adjoint(dev(r, dtype), th, dl)
+    dy = op.jac(dev(x, dtype), th, dev(dth), dl)
+    gt = op.jacT(dev(x, dtype), th, dev(r, dtype), dl)
+    torch.cuda.synchronize()
+    yo, xo = oracle.forward(g, theta, x, delta), oracle.adjoint(g, theta, r, delta)
+    dyo = oracle.jac(g, theta, x, dth, delta)
+    gto, _ = oracle.jacT(g, theta, x, r, delta)
+    dt, _ = oracle.dsample(g, theta, x, delta)
+    assert rows_rel(host(y), yo, B) <= TOL[dtype]
+    assert rows_rel(host(xa), xo, N) <= TOL[dtype]
+    assert rows_rel(host(dy), dyo, B) <= TOL[dtype]
+    assert view_sum_rel(host(gt), gto, r, dt, V, B) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
@@ -129,6 +196,10 @@ def test_gauss_newton_terms(ct, dtype):
     assert rel(host(gr), (R * dt).sum(1)) <= TOL[dtype]
     assert rel(host(j2), (dt * dt).sum(1)) <= TOL[dtype]
     assert rel(host(f), 0.5 * (R * R).sum(1)) <= TOL[dtype]
+    assert rows_rel(host(res), r_o, B) <= TOL[dtype]
+    assert view_sum_rel(host(gr), (R * dt).sum(1), R, dt, V, B) <= TOL[dtype]
+    assert float(np.max(np.abs(host(j2) / (dt * dt).sum(1) - 1))) <= TOL[dtype]
+    assert float(np.max(np.abs(host(f) / (0.5 * (R * R).sum(1)) - 1))) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
@@ -199,10 +270,10 @@ def test_large_image_sampled_views(ct):
     assert rel(host(op.adjoint(dev(y, torch.float32), th)), oracle.adjoint(g, theta, y)) <= 1e-5
 
 
-@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1, 1, 1, 0, 0, 0], [2, 4, 2, 2, 2, 2, 4, 0, 0, 8],
-                                    [8, 8, 2, 8, 4, 8, 2, 0, 0, 16], [4, 2, 8, 1, 4, 4, 4, 0, 4, 0],
-                                    [8, 1, 8, 8, 2, 1, 8, 8, 8, 16], [4, 1, 4, 2, 2, 1, 4, 4, 8, 8],
-                                    [2, 2, 8, 4, 1, 2, 8, 8, 4, 16], [8, 1, 4, 1, 1, 1, 8, 4, 0, 8]])
+@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 1], [2, 4, 2, 2, 2, 2, 4, 0, 0, 8, 2],
+                                    [8, 8, 2, 8, 4, 8, 2, 0, 0, 16, 4], [4, 2, 8, 1, 4, 4, 4, 0, 4, 0, 1],
+                                    [8, 1, 8, 8, 2, 1, 8, 8, 8, 16, 2], [4, 1, 4, 2, 2, 1, 4, 4, 8, 8, 4],
+                                    [2, 2, 8, 4, 1, 2, 8, 8, 4, 16, 1], [8, 1, 4, 1, 1, 1, 8, 4, 0, 8, 4]])
 def test_results_do_not_depend_on_launch_shapes(ct, tuning):
     N, B, vpf = 40, 59, [7, 13]
     V = sum(vpf)
@@ -223,14 +294,20 @@ def test_results_do_not_depend_on_launch_shapes(ct, tuning):
                oracle.jac(g, theta, X[0], dth, delta)) <= 1e-5
     gt = host(op.jacT(dev(X[0], torch.float32), th, dev(Y[0], torch.float32), dl))
     assert rel(gt, oracle.jacT(g, theta, X[0], Y[0], delta)[0]) <= 1e-5
+    # the batched Jacobian products at this shape's images per lane (11 = 4 + 4 + 2 + 1)
+    dY = host(op.jac_batch(dev(X, torch.float32), th, dev(dth), dl))
+    gb = host(op.jacT_batch(dev(X, torch.float32), th, dev(Y, torch.float32), dl))
+    for k in (0, 5, 10):
+        assert rel(dY[k], oracle.jac(g, theta, X[k], dth, delta)) <= 1e-5
+        assert rel(gb[k], oracle.jacT(g, theta, X[k], Y[k], delta)[0]) <= 1e-5
 
 
 def test_autotune_picks_valid_shapes(ct):
     w = synth.make_workload("C2")
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
     t = op.autotune()
-    assert len(t) == 10 and all(x in (1, 2, 4, 8) for x in t[:7]) and t[7] in (0, 4, 8) and t[8] in (0, 4, 8)
-    assert t[9] in (0, 8, 16)
+    assert len(t) == 11 and all(x in (1, 2, 4, 8) for x in t[:7]) and t[7] in (0, 4, 8) and t[8] in (0, 4, 8)
+    assert t[9] in (0, 8, 16) and t[10] in (1, 2, 4)
     th = dev(w.theta_true)
     x = w.images.reshape(1, -1)
     g = oracle.Geometry(w.N, w.B, w.V)

@@ -4,7 +4,8 @@
   iterates (tolerances below), with the Enlarge early stop disabled so both sides
   take the same number of steps;
 * FP32 operators + FP64 small algebra: the final relative reconstruction error
-  matches the oracle's within 1e-3 (relative) on the 64^2 / 90-view workload;
+  matches the oracle's within 1e-3 (relative) on the 64^2 / 90-view workload
+  (the oracle applies the Armijo noise floor of an FP32 misfit, as the GPU does);
 * fixed angles reduce the solve to RMM-GKS (angles returned unchanged).
 """
 import math
@@ -68,7 +69,7 @@ def test_fp32_solver_reaches_the_oracle_reconstruction_error(ct):
     e = w.noise_dir * (w.noise_level * np.linalg.norm(b_true) / np.linalg.norm(w.noise_dir))
     b = b_true + e
     nn = float(np.linalg.norm(e))
-    o = nlrmm.Options(noise_norm=nn, outer_iters=w.outer_iters, stop_on_convergence=False)
+    o = nlrmm.Options(noise_norm=nn, outer_iters=w.outer_iters, stop_on_convergence=False, armijo_eps=2.0 ** -24)
     u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(w.theta_nominal, u_true=u_true, theta_true=w.theta_true)
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
     x, th, st = op.solve(dev(b, torch.float32), dev(w.theta_nominal), x_true=dev(u_true, torch.float32),
@@ -136,7 +137,7 @@ def test_fp64_aniso_tv_solver_follows_the_oracle_iterates(ct):
 
 def test_fp32_aniso_tv_solver_reaches_the_oracle_reconstruction_error(ct):
     g, vpf, th_nom, th_true, u_true, b, nn = _moving_sequence(N=48, vpf=(12, 13, 12, 13, 12, 13), seed=42)
-    o = nlrmm.Options(noise_norm=nn, outer_iters=6, stop_on_convergence=False, temporal=True)
+    o = nlrmm.Options(noise_norm=nn, outer_iters=6, stop_on_convergence=False, temporal=True, armijo_eps=2.0 ** -24)
     u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
     op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float32)
     x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
@@ -150,7 +151,8 @@ def test_fp32_aniso_tv_large_basis_uses_the_unpipelined_gram(ct):
     the register-blocked form without staging.  One outer iteration of 40
     Enlarge steps (k = 6 .. 45) against the oracle."""
     g, vpf, th_nom, th_true, u_true, b, nn = _moving_sequence(N=24, vpf=(6, 7, 6, 7), seed=43)
-    kw = dict(k_min=5, k_max=45, outer_iters=1, tol1=0.0, stop_on_convergence=False, temporal=True)
+    kw = dict(k_min=5, k_max=45, outer_iters=1, tol1=0.0, stop_on_convergence=False, temporal=True,
+              armijo_eps=2.0 ** -24)
     u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, nlrmm.Options(noise_norm=nn, **kw)).solve(th_nom, u_true=u_true)
     op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float32)
     x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
@@ -158,3 +160,20 @@ def test_fp32_aniso_tv_large_basis_uses_the_unpipelined_gram(ct):
     assert st["enlarge_steps"] == h_o.enlarge_steps == [40]
     assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
     assert abs(st["lambda"][-1] - h_o.lam[-1]) <= 1e-3 * h_o.lam[-1], (st["lambda"][-1], h_o.lam[-1])
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_plain_form_takes_the_same_iterates(ct, dtype):
+    """opts.plain (no CUDA graphs, one basis column per projection launch, the
+    Armijo flag read every round) changes how the work is launched, not what
+    is computed: the per-ray sums run in the same order whatever the number of
+    images per launch, so the iterates are bit-identical."""
+    g, th_nom, th_true, u_true, b, nn = problem(32, 40, seed=5)
+    op = ct.CTOperator(g.N, g.B, g.V, max_batch=8, dtype=dtype)
+    kw = dict(noise_norm=nn, k_min=5, k_max=15, outer_iters=3, stop_on_convergence=0)
+    x1, th1, st1 = op.solve(dev(b, dtype), dev(th_nom), x_true=dev(u_true, dtype), **kw)
+    x2, th2, st2 = op.solve(dev(b, dtype), dev(th_nom), x_true=dev(u_true, dtype), plain=1, **kw)
+    assert torch.equal(x1, x2) and torch.equal(th1, th2)
+    assert st1["lambda"] == st2["lambda"] and st1["enlarge_steps"] == st2["enlarge_steps"]
+    with pytest.raises(ct.CTError):
+        op.solve(dev(b, dtype), dev(th_nom), plain=2, **kw)

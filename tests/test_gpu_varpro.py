@@ -56,7 +56,11 @@ def test_varpro_value_and_gradient_match_the_oracle(dtype, tol):
     assert abs(float(f) - f_o) <= tol * abs(f_o)
     rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)
     assert rel(u.double().cpu().numpy(), u_o) <= tol
-    assert rel(grad.cpu().numpy(), gt_o) <= tol * 10
+    # the gradient sums residual x derivative over bins with little cancellation
+    # (sum |r||J| / |sum r J| is about 1.4 here), and rounding V, b and the
+    # weights to float32 moves the oracle's gradient by 3e-7: no looser bound
+    # than for f and u is justified
+    assert rel(grad.cpu().numpy(), gt_o) <= tol
 
 
 def test_autograd_varpro_recomputes_and_matches():
@@ -84,7 +88,8 @@ def test_varpro_update_matches_the_oracle(dtype, steps):
     w, g, b, V, u_w = _problem()
     lam, eps = 0.3, 1e-2
     wts = nlrmm.mm_weights(nlrmm.psi(g, u_w), eps)
-    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=steps), delta=w.delta_true)
+    unit = 2.0 ** -53 if dtype == torch.float64 else 2.0 ** -24   # Armijo noise floor of the misfit's precision
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=steps, armijo_eps=unit), delta=w.delta_true)
     th_o = s.update_param_varpro(w.theta_nominal, V, lam, wts)
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=4, dtype=dtype)
     dv = lambda a, t=dtype: torch.tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
@@ -169,7 +174,8 @@ def test_fp32_varpro_solver_reaches_the_oracle_reconstruction_error():
     b = b_true + e
     nn = float(np.linalg.norm(e))
     iters = min(w.outer_iters, 6)
-    o = nlrmm.Options(noise_norm=nn, outer_iters=iters, stop_on_convergence=False, varpro=True)
+    o = nlrmm.Options(noise_norm=nn, outer_iters=iters, stop_on_convergence=False, varpro=True,
+                      armijo_eps=2.0 ** -24)
     u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(w.theta_nominal, u_true=u_true, theta_true=w.theta_true)
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
     dv = lambda a, t=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
