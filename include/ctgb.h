@@ -271,7 +271,8 @@ int ct_measure_peaks(double *l2_read_gbs, double *smem_read_gbs);
 
 typedef struct {
     int32_t k_min;          /* compressed basis size (Sec. 6 default 5); 2 <= k_min <= 32 */
-    int32_t k_max;          /* enlarged basis size (default 25); k_min < k_max <= 62 */
+    int32_t k_max;          /* enlarged basis size (default 25); k_min < k_max <= 120 (bases above 62
+                               columns keep the FP64 small algebra in a device work area) */
     int32_t outer_iters;    /* outer iteration limit */
     int32_t maxiter_p;      /* Gauss-Newton iterations per outer iteration (default 3) */
     int32_t max_halvings;   /* Armijo backtracking halvings (default 20) */
@@ -396,7 +397,7 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
  * reduced solve and one transposed-Jacobian pass; nothing of the inner solve
  * is kept between calls.
  *   b [n_views][B]; theta, delta [n_views] device double (delta nullable);
- *   V [k][n_frames][N][N] device, k <= 62 columns; u_w [n_frames][N][N] or NULL;
+ *   V [k][n_frames][N][N] device, k <= 120 columns; u_w [n_frames][N][N] or NULL;
  *   fval: one device double; grad [n_views] device double or NULL;
  *   u_out [n_frames][N][N] device or NULL.
  * Allocates and frees its workspace; synchronises.  CT_OK, CT_ERR_ARG,

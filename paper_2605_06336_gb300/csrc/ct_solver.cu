@@ -5,7 +5,7 @@
 // (supplementary Sec. S1.2), "UPDATE-PARAM" (Sec. 4.1.2) or, with
 // opts.varpro, "UPDATE-PARAM-VarPro" (Sec. 4.2).  Operators are the
 // ct kernels of this library in the handle's precision; every small matrix
-// (k <= 64) is FP64 on the device.
+// (k <= 122) is FP64 on the device.
 //
 // Differences from the printed form, none of which changes the iterates in
 // exact arithmetic:
@@ -87,6 +87,7 @@ template <typename T> struct Solver {
     T *vp_a = nullptr, *vp_u = nullptr;
     double *vp_E = nullptr, *vp_G = nullptr, *vp_Y = nullptr, *vp_idel = nullptr, *vp_ones = nullptr,
            *vp_scal = nullptr, *vp_rho = nullptr;
+    double *small_work = nullptr;  // device work area of the FP64 small algebra above kKSmem columns
     int *vp_ctl = nullptr;
     int *h_ctl = nullptr;       // pinned mirror of ctl
     double *h_scal = nullptr;   // pinned mirror of small results
@@ -188,27 +189,54 @@ template <typename T> struct Solver {
         SV_CUDA(cudaMemsetAsync(GP, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * kCtlCount, h.stream));
         SV_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * kScalCount, h.stream));
-        const size_t small_smem = sizeof(SmallShared);
-        SV_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(SolveShared)));
-        SV_CUDA(cudaFuncSetAttribute(k_compress_basis, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)small_smem));
+        SV_CUDA(cudaFuncSetAttribute(k_small_solve<kKSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(SolveShared<kKSmem>)));
+        SV_CUDA(cudaFuncSetAttribute(k_compress_basis<kKSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(SmallShared<kKSmem>)));
+        if (KC > kKSmem) SV_TRY(alloc(small_work, kSmallWorkBytes / sizeof(double) + 1));
         if constexpr (sizeof(T) == 4) {
-            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gram_rb_smem(kKMax, 3)));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_rb_smem(kKLimit, 3, 256)));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_rb_smem(kKLimit, 3, 512)));
             SV_CUDA(cudaFuncSetAttribute(k_gram_psi_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kGramPipeSmemMax));
         } else {
-            SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gram_smem(kKMax, true)));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, 4, gram_slots(kKSmem)>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_smem(kKSmem, true, 4)));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi<T, 1, gram_slots(kKLimit)>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gram_smem(kKLimit, true, 1)));
         }
         return CT_OK;
     }
 
-    // k columns of the edges of one tile: 2 per pixel, 3 with the temporal edge (ANISO-TV)
-    static size_t gram_smem(int k, bool temporal)
+    // FP64 small algebra: shared-memory form up to kKSmem columns, device workspace above
+    void small_solve(int k, double target, double lam_fix, double lam_lo, double lam_hi, int lam_iters, double *yout,
+                     double *scal_out, int *ctl_out)
     {
-        return (size_t)k * ((temporal ? 3 : 2) * 4 * 32 + 1) * sizeof(T);
+        if (k <= kKSmem)
+            k_small_solve<kKSmem><<<1, kSolveThreads, sizeof(SolveShared<kKSmem>), h.stream>>>(
+                GH, cvec, GP, k, bnorm2, target, lam_fix, lam_lo, lam_hi, lam_iters, yout, scal_out, ctl_out, nullptr);
+        else
+            k_small_solve<kKMax><<<1, kSolveThreads, 0, h.stream>>>(GH, cvec, GP, k, bnorm2, target, lam_fix, lam_lo,
+                                                                     lam_hi, lam_iters, yout, scal_out, ctl_out,
+                                                                     small_work);
+    }
+    void compress_basis(int k, int keep)
+    {
+        if (k <= kKSmem)
+            k_compress_basis<kKSmem><<<1, 256, sizeof(SmallShared<kKSmem>), h.stream>>>(GH, GP, k, scal, keep, W,
+                                                                                       nullptr);
+        else
+            k_compress_basis<kKMax><<<1, 256, 0, h.stream>>>(GH, GP, k, scal, keep, W, small_work);
+    }
+
+    // k columns of the edges of one tile of TR x 32 pixels: 2 per pixel, 3 with the temporal edge (ANISO-TV)
+    static size_t gram_smem(int k, bool temporal, int tr)
+    {
+        return (size_t)k * ((temporal ? 3 : 2) * tr * 32 + 1) * sizeof(T);
     }
 
     // GP = (P Psi V)^T (P Psi V) over V[:, :k] with the weights in w
@@ -217,15 +245,23 @@ template <typename T> struct Solver {
         const bool tm = o.temporal && h.F > 1;
         if constexpr (sizeof(T) == 4) {
             const size_t pipe = gram_pipe_smem(k, tm ? 3 : 2);
-            if (pipe <= kGramPipeSmemMax)  // both raw buffers fit next to the edge block
+            const int nt = gram_rb_threads(k);
+            if (pipe <= kGramPipeSmemMax && nt == 256)  // both raw buffers fit next to the edge block
                 k_gram_psi_pipe<<<gram_blocks, kThreads, pipe, h.stream>>>(V, n, k, w, h.N, h.F, o.temporal,
                                                                             part_gram, stop);
+            else if (nt == 256)
+                k_gram_psi_rb<256><<<gram_blocks, 256, gram_rb_smem(k, tm ? 3 : 2, 256), h.stream>>>(
+                    V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
             else
-                k_gram_psi_rb<<<gram_blocks, kThreads, gram_rb_smem(k, tm ? 3 : 2), h.stream>>>(
+                k_gram_psi_rb<512><<<gram_blocks, 512, gram_rb_smem(k, tm ? 3 : 2, 512), h.stream>>>(
                     V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
         } else {
-            k_gram_psi<T, 4><<<gram_blocks, kThreads, gram_smem(k, tm), h.stream>>>(V, n, k, w, h.N, h.F, o.temporal,
-                                                                                 part_gram, stop);
+            if (k <= kKSmem)
+                k_gram_psi<T, 4, gram_slots(kKSmem)><<<gram_blocks, kThreads, gram_smem(k, tm, 4), h.stream>>>(
+                    V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
+            else
+                k_gram_psi<T, 1, gram_slots(kKLimit)><<<gram_blocks, kThreads, gram_smem(k, tm, 1), h.stream>>>(
+                    V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
         }
         k_gram_reduce<<<gram_reduce_blocks(k), 32 * kGramReduceWarps, 0, h.stream>>>(part_gram, gram_blocks, k, GP,
                                                                                      stop);
@@ -372,8 +408,7 @@ template <typename T> struct Solver {
         SV_TRY(gram_psi(kc, stop));
         // lambda and the reduced solution
         const double target = (o.tau * noise) * (o.tau * noise);
-        k_small_solve<<<1, kSolveThreads, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, kc, bnorm2, target, o.lam_fix,
-                                                                     o.lam_lo, o.lam_hi, o.lam_iters, y, scal, ctl);
+        small_solve(kc, target, o.lam_fix, o.lam_lo, o.lam_hi, o.lam_iters, y, scal, ctl);
         // u = V y ; res = (HV) y - b
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, kc, y, u, T(0), T(1), nullptr, T(0), stop);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, kc, y, res, T(0), T(1), b, T(-1), stop);
@@ -499,8 +534,7 @@ template <typename T> struct Solver {
         SV_TRY(project(theta, 0, k, nullptr));
         SV_CUDA(cudaMemsetAsync(GH, 0, sizeof(double) * kKMax * kKMax, h.stream));
         SV_TRY(full_gram(k));
-        k_small_solve<<<1, kSolveThreads, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
-                                                                     1, y, vp_scal, vp_ctl);
+        small_solve(k, 1.0, lam, 0.0, 0.0, 1, y, vp_scal, vp_ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, vp_u, T(0), T(1), nullptr, T(0), nullptr);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);
         SV_TRY(norms3(res, nullptr, m, norms, nullptr));
@@ -621,8 +655,7 @@ template <typename T> struct Solver {
             k_fill<T><<<grid_for(ne), kThreads, 0, h.stream>>>(w, ne, T(1));
         }
         SV_TRY(gram_psi(k, nullptr));
-        k_small_solve<<<1, kSolveThreads, sizeof(SolveShared), h.stream>>>(GH, cvec, GP, k, bnorm2, 1.0, lam, 0.0, 0.0,
-                                                                     1, y, scal, ctl);
+        small_solve(k, 1.0, lam, 0.0, 0.0, 1, y, scal, ctl);
         k_gemv<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k, y, u, T(0), T(1), nullptr, T(0), nullptr);
         k_gemv<T><<<grid_for(m), kThreads, 0, h.stream>>>(HV, m, m, k, y, res, T(0), T(1), b, T(-1), nullptr);
         SV_TRY(norms3(res, nullptr, m, norms, nullptr));
@@ -701,7 +734,7 @@ template <typename T> struct Solver {
     int compress(int k_used, int &kc)
     {
         const int keep = std::min(o.k_min - 1, k_used);
-        k_compress_basis<<<1, kThreads, sizeof(SmallShared), h.stream>>>(GH, GP, k_used, scal, keep, W);
+        compress_basis(k_used, keep);
         for (int c0 = 0; c0 < keep; c0 += 16)  // 16 output columns per pass over V
             k_gemm_small<T><<<grid_for(n), kThreads, 0, h.stream>>>(V, n, n, k_used, W + c0,
                                                                     std::min(16, keep - c0), col(Vtmp, n, c0), n);
@@ -950,7 +983,7 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
 {
     if (!H || !b || !theta_inout || !x_out || !opts) return CT_ERR_ARG;
     const nlrmm_opts &o = *opts;
-    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min > 32 ||
+    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKLimit || o.k_min > 32 ||
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
         return CT_ERR_ARG;
@@ -989,7 +1022,7 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
 {
     if (!blocks || nblocks < 1 || !b || !theta_inout || !x_out || !opts) return CT_ERR_ARG;
     const nlrmm_opts &o = *opts;
-    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKMax || o.k_min > 32 ||
+    if (o.k_min < 2 || o.k_max <= o.k_min || o.k_max + 2 > ctgb::solver::kKLimit || o.k_min > 32 ||
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !noise_norms))
         return CT_ERR_ARG;
@@ -1043,7 +1076,7 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
 int nlrmm_varpro(ct_handle *H, const void *b, const double *theta, const double *delta, const void *V, int k,
                  double lam, const void *u_w, double eps, double *fval, double *grad, void *u_out)
 {
-    if (!H || !b || !theta || !V || !fval || k < 1 || k + 2 > ctgb::solver::kKMax || !(lam > 0.0) ||
+    if (!H || !b || !theta || !V || !fval || k < 1 || k + 2 > ctgb::solver::kKLimit || !(lam > 0.0) ||
         (u_w && !(eps > 0.0)))
         return CT_ERR_ARG;
     ctgb::Handle &h = H->h;

@@ -20,7 +20,9 @@
 namespace ctgb {
 namespace solver {
 
-constexpr int kKMax = 64;       // largest basis the FP64 small algebra handles
+constexpr int kKMax = 128;      // leading dimension of the k x k FP64 matrices in device memory
+constexpr int kKSmem = 64;      // bases of up to this many columns keep the FP64 small algebra in shared memory
+constexpr int kKLimit = 122;    // largest basis (columns): the register-blocked Gram's 4 x 4 block pairs fit 512 threads
 constexpr int kRedBlocks = 608;  // largest partial-sum grid of the tall-skinny reductions (4 CTAs per SM of a GB300)
 // Partial-sum grid for vectors of length len: 128 CTAs up to half a million
 // elements, growing to kRedBlocks for the long image vectors (a fixed function
@@ -143,9 +145,10 @@ __global__ void k_add_reg(T *__restrict__ r, const T *__restrict__ u, const T *_
 // k_gram_reduce sums them in order.
 // ---------------------------------------------------------------------------
 constexpr int kGramPairs = kKMax * (kKMax + 1) / 2;
-constexpr int kGramSlots = (kGramPairs + 255) / 256;
+// register slots per thread of k_gram_psi: (pairs of a basis of kc columns) / 256
+constexpr int gram_slots(int kc) { return (kc * (kc + 1) / 2 + 255) / 256; }
 
-template <typename T, int TR>
+template <typename T, int TR, int kGramSlots>
 __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long long n, int k,
                                                   const T *__restrict__ w, int N, int F, int temporal,
                                                   double *__restrict__ part, const int *stop)
@@ -223,17 +226,26 @@ __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long 
 // with two float4 reads and 16 FMAs per edge.  Per tile the phases are added
 // in FP32 in shared memory and the sum goes to the owner's FP64 accumulators;
 // per-CTA FP64 partials as for k_gram_psi.
+// NT threads (256, or 512 for bases above 88 columns, whose 4 x 4 block pairs
+// outnumber 256 threads) each own one block pair.
 constexpr int kRbRows = 4;                      // tile rows
 constexpr int kRbPix = kRbRows * 32;            // tile pixels
-inline size_t gram_rb_smem(int k, int epp)
+inline size_t gram_rb_smem(int k, int epp, int nt = 256)
 {
     const int kp = 32 * ((k + 31) / 32);
-    return (size_t)epp * kRbPix * kp * sizeof(float) + 256 * 16 * sizeof(float);
+    return (size_t)epp * kRbPix * kp * sizeof(float) + (size_t)nt * 16 * sizeof(float);
+}
+// threads of the register-blocked Gram for k columns (one 4 x 4 block pair each)
+inline int gram_rb_threads(int k)
+{
+    const int kb = (k + 3) / 4;
+    return kb * (kb + 1) / 2 <= 256 ? 256 : 512;
 }
 
-__global__ void __launch_bounds__(256) k_gram_psi_rb(const float *__restrict__ V, long long n, int k,
-                                                     const float *__restrict__ w, int N, int F, int temporal,
-                                                     double *__restrict__ part, const int *stop)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_gram_psi_rb(const float *__restrict__ V, long long n, int k,
+                                                    const float *__restrict__ w, int N, int F, int temporal,
+                                                    double *__restrict__ part, const int *stop)
 {
     if (stopped(stop)) return;
     extern __shared__ float4 rb_smem[];
@@ -241,10 +253,10 @@ __global__ void __launch_bounds__(256) k_gram_psi_rb(const float *__restrict__ V
     const int KP = 32 * ((k + 31) / 32);
     const int NE = EPP * kRbPix;
     float *E = reinterpret_cast<float *>(rb_smem);  // [NE][KP], swizzled 16-byte groups
-    float *red = E + (size_t)NE * KP;               // [256][16]
+    float *red = E + (size_t)NE * KP;               // [NT][16]
     const int kb = (k + 3) / 4;
     const int P = kb * (kb + 1) / 2;
-    const int phases = max(1, min(8, 256 / P));
+    const int phases = max(1, min(8, NT / P));
     const int t = threadIdx.x;
     const bool busy = t < P * phases;
     const int p = t % P, ph = t / P;
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(256) k_gram_psi_rb(const float *__restrict__ V
         const float *wt = w + 2 * nx + (long long)f * N * N;
         __syncthreads();  // the previous tile is done with E and red
         // edges: thread = (column group of 4, pixel); consecutive threads take consecutive pixels
-        for (int idx = t; idx < kb * kRbPix; idx += 256) {
+        for (int idx = t; idx < kb * kRbPix; idx += NT) {
             const int g = idx / kRbPix, pix = idx % kRbPix;
             const int i = i0 + pix / 32, j = j0 + pix % 32;
             float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, et[4] = {0.f, 0.f, 0.f, 0.f};
@@ -784,12 +796,14 @@ __global__ void k_step_commit(int *__restrict__ ctl, volatile int *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 small algebra in one CTA (k <= kKMax).  Matrices in shared memory with
-// leading dimension kKMax + 1.
+// FP64 small algebra in one CTA.  Its matrices have leading dimension KM + 1
+// (KM = kKSmem: in shared memory, for bases of up to kKSmem columns;
+// KM = kKMax: in a device workspace the solver allocates, for larger bases --
+// __syncthreads orders a block's global accesses as it orders its shared ones).
 // ---------------------------------------------------------------------------
-constexpr int kLd = kKMax + 1;
 
 // Cholesky A = L L^T in place (lower triangle); pivots clamped at tiny*A00.
+template <int kLd>
 __device__ void chol(double *A, int k, int *bad)
 {
     for (int j = 0; j < k; ++j) {
@@ -819,6 +833,7 @@ __device__ void chol(double *A, int k, int *bad)
 // Cyclic Jacobi eigen-decomposition of the symmetric k x k matrix A
 // (overwritten; its diagonal ends as the eigenvalues), eigenvectors in the
 // columns of U.  Parallel round-robin ordering of the (p, q) rotations.
+template <int kLd>
 __device__ void jacobi_eig(double *A, double *U, int k, double *cs, double *sn, int *pp, int *qq, double *sh)
 {
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
@@ -898,13 +913,14 @@ __device__ void jacobi_eig(double *A, double *U, int k, double *cs, double *sn, 
     __syncthreads();
 }
 
-// Shared memory of k_compress_basis (matrix, eigenvectors, rotation tables).
-struct SmallShared {
-    double A[kKMax * kLd];
-    double U[kKMax * kLd];
-    double vec[1][kKMax + 1];
-    double cs[kKMax / 2 + 1], sn[kKMax / 2 + 1];
-    int pp[kKMax / 2 + 1], qq[kKMax / 2 + 1];
+// Work area of k_compress_basis (matrix, eigenvectors, rotation tables).
+template <int KM> struct SmallShared {
+    static constexpr int kLd = KM + 1;
+    double A[KM * kLd];
+    double U[KM * kLd];
+    double vec[1][KM + 1];
+    double cs[KM / 2 + 1], sn[KM / 2 + 1];
+    int pp[KM / 2 + 1], qq[KM / 2 + 1];
     double sh[40];
 };
 
@@ -933,12 +949,16 @@ struct SmallShared {
 // the small reductions run in warp 0.
 constexpr int kSolveThreads = 128;
 
-struct SolveShared {
-    double GH[kKMax * kLd], GP[kKMax * kLd], L[kKMax * kLd];
-    double c[kKMax], v[kKMax], y[kKMax], inv[kKMax];
+template <int KM> struct SolveShared {
+    static constexpr int kLd = KM + 1;
+    double GH[KM * kLd], GP[KM * kLd], L[KM * kLd];
+    double c[KM], v[KM], y[KM], inv[KM];
     double fd[2];  // phi(lambda) and d phi / d t of the last evaluation
     int bad;
 };
+// bytes of device workspace the large-basis forms of k_small_solve and k_compress_basis need
+constexpr size_t kSmallWorkBytes = sizeof(SolveShared<kKMax>) > sizeof(SmallShared<kKMax>)
+                                       ? sizeof(SolveShared<kKMax>) : sizeof(SmallShared<kKMax>);
 
 // L D L^T factorization of the lower triangle of L in place (all threads of a
 // kSolveThreads CTA), with the forward substitution z = L^{-1} rhs done along
@@ -948,6 +968,7 @@ struct SolveShared {
 // the next pivot first and takes its reciprocal, warps 1-3 the other entries
 // and rhs[i] -= (L[i][j] / D_j) rhs[j]; the columns are scaled at the end.
 // Pivots at or below tiny * L_00 are clamped and flag *bad.
+template <int kLd>
 __device__ void ldlt_fwd(double *L, double *inv, double *rhs, int k, int *bad)
 {
     constexpr int kWorkers = kSolveThreads - 32;
@@ -1012,6 +1033,7 @@ __device__ void ldlt_fwd(double *L, double *inv, double *rhs, int k, int *bad)
 }
 
 // v := L^{-1} v for the unit factor (warp 0, lanes over rows)
+template <int kLd>
 __device__ void fwd_subst_warp(const double *L, double *v, int k)
 {
     const int lane = threadIdx.x & 31;
@@ -1023,6 +1045,7 @@ __device__ void fwd_subst_warp(const double *L, double *v, int k)
 }
 
 // v := L^{-T} D^{-1} v (warp 0): the second half of an L D L^T solve
+template <int kLd>
 __device__ void back_subst_warp(const double *L, const double *inv, double *v, int k)
 {
     const int lane = threadIdx.x & 31;
@@ -1035,16 +1058,25 @@ __device__ void back_subst_warp(const double *L, const double *inv, double *v, i
     }
 }
 
+// KM = kKSmem: the work area in dynamic shared memory; KM = kKMax: in `work`
+// (device, kSmallWorkBytes).  The threads of the block exchange values through
+// the work area (pivots, phi(lambda), the convergence tests that steer every
+// thread's control flow), so `work` must not be restrict-qualified: that would
+// let the compiler assume no other thread writes it and keep stale copies,
+// after which threads could take different branches around a barrier.
+template <int KM>
 __global__ void __launch_bounds__(kSolveThreads) k_small_solve(const double *__restrict__ GH,
                                                                const double *__restrict__ cvec,
                                                                const double *__restrict__ GP, int k, double bnorm2,
                                                                double target, double lam_fix, double lam_lo,
                                                                double lam_hi, int lam_iters, double *__restrict__ y,
-                                                               double *__restrict__ scal, int *__restrict__ ctl)
+                                                               double *__restrict__ scal, int *__restrict__ ctl,
+                                                               double *work)
 {
     if (ctl[kStop]) return;
     extern __shared__ unsigned char smem_raw[];
-    SolveShared &S = *reinterpret_cast<SolveShared *>(smem_raw);
+    constexpr int kLd = SolveShared<KM>::kLd;
+    SolveShared<KM> &S = *reinterpret_cast<SolveShared<KM> *>(KM > kKSmem ? (unsigned char *)work : smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) S.bad = 0;
     for (int idx = tid; idx < k * k; idx += kSolveThreads) {
@@ -1065,9 +1097,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_small_solve(const double *__r
         }
         for (int i = tid; i < k; i += kSolveThreads) S.y[i] = S.c[i];
         __syncthreads();
-        ldlt_fwd(S.L, S.inv, S.y, k, &S.bad);
+        ldlt_fwd<kLd>(S.L, S.inv, S.y, k, &S.bad);
         if (tid < 32) {
-            back_subst_warp(S.L, S.inv, S.y, k);
+            back_subst_warp<kLd>(S.L, S.inv, S.y, k);
             double cy = 0.0, yw = 0.0;
             for (int i = lane; i < k; i += 32) {
                 double t = 0.0;
@@ -1082,7 +1114,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_small_solve(const double *__r
             double d = 0.0;
             if (want_d) {
                 // w.(L D L^T)^{-1} w = sum_i (L^{-1} w)_i^2 / D_i, w = G_P y
-                fwd_subst_warp(S.L, S.v, k);
+                fwd_subst_warp<kLd>(S.L, S.v, k);
                 double wz = 0.0;
                 for (int i = lane; i < k; i += 32) wz += S.v[i] * S.v[i] * S.inv[i];
                 wz = warp_sum(wz);
@@ -1159,19 +1191,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_small_solve(const double *__r
 // eigenvectors of G_H + lambda G_P; W (row-major, ld kKMax) receives the
 // keep = k_min - 1 of largest eigenvalue, ordered by decreasing eigenvalue
 // (ties by index), each signed so its largest-magnitude entry is positive.
+template <int KM>
 __global__ void __launch_bounds__(256) k_compress_basis(const double *__restrict__ GH, const double *__restrict__ GP,
                                                         int k, const double *__restrict__ scal, int keep,
-                                                        double *__restrict__ W)
+                                                        double *__restrict__ W, double *work)
 {
     extern __shared__ unsigned char smem_raw[];
-    SmallShared &S = *reinterpret_cast<SmallShared *>(smem_raw);
+    constexpr int kLd = SmallShared<KM>::kLd;
+    SmallShared<KM> &S = *reinterpret_cast<SmallShared<KM> *>(KM > kKSmem ? (unsigned char *)work : smem_raw);
     const double lam = scal[kLam];
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
         const int i = idx / k, j = idx % k;
         S.A[i * kLd + j] = GH[i * kKMax + j] + lam * GP[i * kKMax + j];
     }
     __syncthreads();
-    jacobi_eig(S.A, S.U, k, S.cs, S.sn, S.pp, S.qq, S.sh);
+    jacobi_eig<kLd>(S.A, S.U, k, S.cs, S.sn, S.pp, S.qq, S.sh);
     if (threadIdx.x == 0) {  // selection of the `keep` largest eigenvalues
         bool used[kKMax];
         for (int i = 0; i < k; ++i) used[i] = false;
@@ -1379,6 +1413,7 @@ __global__ void __launch_bounds__(128) k_view_dots(const T *__restrict__ HV, lon
 }
 
 struct VpShared {
+    static constexpr int kLd = kVpMax + 1;
     double M[kVpMax * kLd];                    // (HV)^T HV + lambda (P Psi V)^T (P Psi V)
     double L[kVpMax * kLd];                    // its Cholesky factor
     double C[2 * kVpMax][2 * kVpMax + 2];      // capacitance | right-hand side
@@ -1402,6 +1437,7 @@ __global__ void __launch_bounds__(1024) k_varpro_direction(const double *__restr
 {
     extern __shared__ unsigned char smem_raw[];
     VpShared &S = *reinterpret_cast<VpShared *>(smem_raw);
+    constexpr int kLd = VpShared::kLd;
     const int tid = threadIdx.x, nt = blockDim.x, K = 2 * k;
     if (tid == 0) S.bad = 0;
     for (int idx = tid; idx < k * k; idx += nt) {
@@ -1411,7 +1447,7 @@ __global__ void __launch_bounds__(1024) k_varpro_direction(const double *__restr
         S.L[i * kLd + l] = v;
     }
     __syncthreads();
-    chol(S.L, k, &S.bad);
+    chol<VpShared::kLd>(S.L, k, &S.bad);
     __syncthreads();
     // Y[:, j] = -M^{-1} (G[:, j] + E[:, j]) by L z = -(G + E), L^T y = z; then
     // (J^T J)_jj = |H_j u|^2 + 2 E[:, j] . y + y^T M y, with y^T M y = |z|^2

@@ -100,7 +100,7 @@ def test_solver_argument_errors(ct):
     b = torch.zeros(8 * 23, device="cuda")
     th = torch.zeros(8, dtype=torch.float64, device="cuda")
     with pytest.raises(ct.CTError):
-        op.solve(b, th, noise_norm=1.0, k_max=80)       # basis above the FP64 small-algebra limit
+        op.solve(b, th, noise_norm=1.0, k_max=121)      # basis above the small-algebra limit
     with pytest.raises(ct.CTError):
         op.solve(b, th)                                 # no noise level and no fixed lambda
 
@@ -177,3 +177,39 @@ def test_plain_form_takes_the_same_iterates(ct, dtype):
     assert st1["lambda"] == st2["lambda"] and st1["enlarge_steps"] == st2["enlarge_steps"]
     with pytest.raises(ct.CTError):
         op.solve(dev(b, dtype), dev(th_nom), plain=2, **kw)
+
+
+def test_fp64_solver_with_a_basis_of_100_follows_the_oracle(ct):
+    """k_max = 100 (the memory-bounded basis of the large streaming workload):
+    above 64 columns the FP64 small algebra (LDL^T, the discrepancy search,
+    Compress's eigensolver) runs from a device work area instead of shared
+    memory.  One outer iteration of 95 Enlarge steps plus a second one, FP64,
+    against the oracle's iterates."""
+    g, th_nom, th_true, u_true, b, nn = problem(32, 40, seed=11)
+    kw = dict(k_min=5, k_max=100, outer_iters=2, tol1=0.0)
+    o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, **kw)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true, theta_true=th_true)
+    op = ct.CTOperator(g.N, g.B, g.V, max_batch=8, dtype=torch.float64)
+    x, th, st = op.solve(dev(b), dev(th_nom), x_true=dev(u_true), noise_norm=nn, stop_on_convergence=0, **kw)
+    assert st["enlarge_steps"] == h_o.enlarge_steps == [95, 95]
+    np.testing.assert_allclose(st["lambda"], h_o.lam, rtol=1e-7)
+    np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-7)
+    assert np.linalg.norm(x.cpu().numpy() - u_o) <= 1e-7 * np.linalg.norm(u_o)
+    assert np.max(np.abs(th.cpu().numpy() - th_o)) <= 1e-8
+
+
+def test_fp32_solver_with_a_basis_of_120_reaches_the_oracle_reconstruction_error(ct):
+    """FP32 operators with k_max = 120 (the largest basis): the weighted Gram of
+    Psi V runs in its pipelined form, then the register-blocked one, then the
+    512-thread register-blocked one (more than 88 columns) as the basis grows."""
+    g, th_nom, th_true, u_true, b, nn = problem(40, 48, seed=12)
+    kw = dict(k_min=5, k_max=120, outer_iters=2, tol1=0.0)
+    o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, armijo_eps=2.0 ** -24, **kw)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true, theta_true=th_true)
+    op = ct.CTOperator(g.N, g.B, g.V, max_batch=8, dtype=torch.float32)
+    x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
+                         stop_on_convergence=0, **kw)
+    assert st["enlarge_steps"] == h_o.enlarge_steps
+    assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
+    with pytest.raises(ct.CTError):
+        op.solve(dev(b, torch.float32), dev(th_nom), noise_norm=nn, k_min=5, k_max=121)
