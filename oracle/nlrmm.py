@@ -53,6 +53,14 @@ Readings where the paper is silent (also listed in the design notes):
     (r of that view), on the data residual of the reduced objective in the
     VarPro update.  Such a test compares two misfits that differ by less than
     their own rounding, so its outcome carries no information;
+  * shared angle offset (Options.shared_offset, the scalar parameter of the
+    paper's CT experiments, Sec. 6.2, and of its dynamic CT, where one offset
+    serves every frame): theta_v = theta_v^0 + p for all views; the
+    Gauss-Newton step on p uses g = sum_v g_v (the gradient along the
+    direction 1) and J^T J = sum_v |J_v|^2, damped by mu = mu_rel J^T J,
+    with the Armijo test and its noise floor on the total misfit (rho summed
+    over the views); no accepted step ends the update with the offset kept;
+    not combined with the VarPro update;
   * VarPro (Options.varpro): the basis is the compressed V^(k+1)_kmin of the
     primary solve, lambda_hat = lambda^(k), B_hat = P Psi V with P^2 the MM
     weights of u^(k+1); the Gauss-Newton matrix is damped by mu = 1e-8 times
@@ -166,6 +174,7 @@ class Options:
     fixed_weights: np.ndarray | None = None   # freeze P^2 (pins only)
     temporal: bool = False                    # ANISO-TV: add frame-to-frame differences to Psi
     varpro: bool = False                      # parameter update by Alg. "UPDATE-PARAM-VarPro"
+    shared_offset: bool = False               # one angle offset shared by every view (theta^0 + p)
 
 
 @dataclass
@@ -330,6 +339,31 @@ class NLRMMGKS:
             self.last_trials = trials
         return theta
 
+    def update_param_shared(self, theta, u):
+        """UPDATE-PARAM for one offset p shared by every view: theta + p 1."""
+        o = self.o
+        theta = theta.copy()
+        for _ in range(o.maxiter_p):
+            grad, jn2, f0, rho = self.view_terms(theta, u)
+            g, jj, f, r = float(grad.sum()), float(jn2.sum()), float(f0.sum()), float(rho.sum())
+            d = -g / (jj + o.mu_rel * max(jj, 1e-300))
+            alpha = o.alpha0
+            accepted = False
+            self.last_trials = 0
+            for _h in range(o.max_halvings + 1):
+                if alpha * abs(g * d) < o.armijo_eps * r:
+                    break  # noise floor: the first-order change of f is below its rounding
+                ft = float(self.view_f(theta + alpha * d, u).sum())
+                self.last_trials += 1
+                if ft <= f + o.c1 * alpha * g * d:
+                    accepted = True
+                    break
+                alpha *= o.beta
+            if not accepted:
+                break  # no acceptable step: the offset stays
+            theta = theta + alpha * d
+        return theta
+
     # -- Alg. "UPDATE-PARAM-VarPro" (Sec. 4.2) ----------------------------------
     def update_param_varpro(self, theta, V, lam, w):
         """maxiter_p Gauss-Newton steps on the reduced objective f(theta) on the
@@ -365,6 +399,10 @@ class NLRMMGKS:
     def param_update(self, theta, u, V, lam):
         """UPDATE-PARAM of the outer iteration: per-view AltMin, or VarPro on
         the compressed basis V with the MM weights of u."""
+        if self.o.shared_offset:
+            if self.o.varpro:
+                raise ValueError("the shared offset is updated by UPDATE-PARAM, not the VarPro update")
+            return self.update_param_shared(theta, u)
         if not self.o.varpro:
             return self.update_param(theta, u)
         o = self.o

@@ -675,3 +675,67 @@ def test_rounding_scale_bounds_the_float32_misfit_error():
     assert np.all(ratio <= 2.0 + 1e-6), ratio.max()
     assert ratio.max() > 1e-3          # and rho is not a vacuous bound
     assert np.all(rho >= 2 * f)
+
+
+def test_shared_offset_update_reaches_the_minimizer_over_the_offset():
+    # every view shifted by one offset p_true (the scalar parameter of the paper's
+    # CT experiments); noise-free data and the true image: the Gauss-Newton
+    # update on p (gradient sum_v g_v, matrix sum_v |J_v|^2) reaches the
+    # brute-force minimizer of F(p) = sum_v f_v(theta_nom + p), which is p_true
+    N, V = 24, 14
+    g = oracle.Geometry(N, synth.n_bins(N), V)
+    rng = np.random.default_rng(31)
+    u = synth.rasterize(N, synth.random_ellipses(N, 4, rng)).ravel()
+    th_nom = np.sort(rng.uniform(0, math.pi, V))
+    p_true = math.radians(0.7)
+    b = oracle.forward(g, th_nom + p_true, u)
+    s = nlrmm.NLRMMGKS(g, b, nlrmm.Options(maxiter_p=1, shared_offset=True))
+    th = th_nom.copy()
+    for _ in range(30):
+        th = s.update_param_shared(th, u)
+    shift = th - th_nom
+    assert np.ptp(shift) <= 1e-15                         # one offset for every view
+    F = lambda p: float(s.view_f(th_nom + p, u).sum())
+    lo, hi = p_true - math.radians(2), p_true + math.radians(2)
+    gr = (math.sqrt(5) - 1) / 2
+    a, c = hi - gr * (hi - lo), lo + gr * (hi - lo)
+    for _ in range(80):
+        if F(a) < F(c):
+            hi = c
+        else:
+            lo = a
+        a, c = hi - gr * (hi - lo), lo + gr * (hi - lo)
+    assert abs(shift[0] - 0.5 * (lo + hi)) <= 1e-7
+    assert abs(shift[0] - p_true) <= 1e-7
+    # the gradient it steps on is that of F: J 1 summed over the views
+    grad, _, _, _ = s.view_terms(th_nom, u)
+    h = 1e-6
+    assert abs(grad.sum() - (F(h) - F(-h)) / (2 * h)) <= 2e-3 * abs(grad.sum())
+
+
+@pytest.mark.slow
+def test_small_solve_with_a_shared_offset_keeps_one_offset():
+    # a common shift of every angle is equivalent to rotating the image, so the
+    # reconstruction absorbs most of it and the alternating solve recovers it
+    # slowly (with the true image one update recovers it, see above); what the
+    # solve must do: keep one offset for all views, move it towards p_true, and
+    # lower the image error
+    N, V = 32, 30
+    rng = np.random.default_rng(32)
+    g = oracle.Geometry(N, synth.n_bins(N), V)
+    th_nom = np.sort(rng.uniform(0, math.pi, V))
+    p_true = math.radians(0.8)
+    u_true = synth.rasterize(N, synth.random_ellipses(N, 3, rng)).ravel()
+    b_true = oracle.forward(g, th_nom + p_true, u_true)
+    e = rng.standard_normal(g.m)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    opts = nlrmm.Options(noise_norm=float(np.linalg.norm(e)), outer_iters=8, stop_on_convergence=False,
+                         shared_offset=True)
+    u, th, hist = nlrmm.NLRMMGKS(g, b_true + e, opts).solve(th_nom, u_true=u_true)
+    shift = th - th_nom
+    assert np.ptp(shift) <= 1e-14
+    assert 0.05 * p_true < shift[0] < p_true
+    assert hist.rre[-1] < hist.rre[0]
+    with pytest.raises(ValueError):
+        nlrmm.NLRMMGKS(g, b_true + e, nlrmm.Options(noise_norm=1.0, shared_offset=True, varpro=True)).param_update(
+            th_nom, u_true, None, 1.0)
