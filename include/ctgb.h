@@ -307,7 +307,12 @@ typedef struct {
     int32_t plain;          /* 1: the unpackaged form, for comparison: no CUDA graphs, every projection
                                of the basis one column per launch (no Krylov-block batching), the
                                Armijo flag read after every trial round; same iterates.  Default 0 */
-    int32_t reserved0;      /* must be 0 */
+    int32_t shared_offset;  /* 1: one angle offset p shared by every view and frame, theta_v = theta_v^0 + p
+                               (the scalar parameter of the paper's CT experiments, Sec. 6.2, shared by
+                               all frames in its dynamic CT, Sec. 7): Gauss-Newton on p with gradient
+                               sum_v g_v and J^T J = sum_v |J_v|^2 (damped by mu_rel J^T J), Armijo and
+                               its noise floor on the total misfit; no accepted step ends the update.
+                               Not with varpro, not in nlrmm_stream_solve.  Default 0: one angle per view */
 } nlrmm_opts;
 
 typedef struct {

@@ -505,6 +505,48 @@ template <typename T> struct Solver {
         return CT_OK;
     }
 
+    // ---- UPDATE-PARAM for one offset shared by every view ------------------------
+    // theta = theta_k + p 1: Gauss-Newton on p from the per-view terms summed in a
+    // fixed order (g = sum_v g_v, J^T J = sum_v |J_v|^2, f = sum_v f_v, rho = sum_v
+    // rho_v), Armijo on the total misfit with its noise floor; the step d fills the
+    // per-view direction array so that the trial angles are th_n + alpha d.
+    int update_param_shared(const T *uimg)
+    {
+        SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        for (int it = 0; it < o.maxiter_p; ++it) {
+            SV_CUDA(launch_pairs_img<T>(h, uimg, h.F, nullptr, th_n, delta));
+            SV_CUDA(launch_gn<T>(h, b, nullptr, g, j2, f0, h.tune.der_split, h.tune.der_vw, h.tune.der_stage,
+                                 nullptr, nullptr, 1, 1, rho));
+            k_view_sums<<<1, 1024, 0, h.stream>>>(g, j2, f0, rho, h.V, part_n);
+            double s4[4];
+            SV_TRY(read_doubles(part_n, 4, s4));
+            const double G = s4[0], JJ = s4[1], F = s4[2], R = s4[3];
+            const double dp = -G / (JJ + o.mu_rel * std::max(JJ, 1e-300));
+            k_fill<double><<<grid_for(h.V), kThreads, 0, h.stream>>>(d, h.V, dp);
+            bool accepted = false;
+            double alpha = o.alpha0;
+            for (int hv = 0; hv <= o.max_halvings; ++hv) {
+                if (alpha * std::fabs(G * dp) < armijo_u() * R) break;  // noise floor: no step
+                k_theta_step<<<grid_for(h.V), kThreads, 0, h.stream>>>(th_n, d, alpha, h.V, th_t);
+                SV_CUDA(launch_view_setup_wide(h, th_t, delta, ctl + kViewChanged, nullptr));
+                SV_CUDA(launch_gn<T>(h, b, nullptr, scratch_v, scratch_v, ft, h.tune.der_split, h.tune.der_vw,
+                                     h.tune.der_stage));
+                k_view_sums<<<1, 1024, 0, h.stream>>>(ft, nullptr, nullptr, nullptr, h.V, part_n);
+                double fsum[1];
+                SV_TRY(read_doubles(part_n, 1, fsum));
+                if (fsum[0] <= F + o.c1 * alpha * G * dp) {
+                    accepted = true;
+                    break;
+                }
+                alpha *= o.beta;
+            }
+            if (!accepted) break;  // the offset stays
+            SV_CUDA(cudaMemcpyAsync(th_n, th_t, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
+        }
+        SV_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
+
     // ---- VarPro Gauss-Newton update (Alg. "UPDATE-PARAM-VarPro", Sec. 4.2) --------
     int varpro_setup()
     {
@@ -627,6 +669,7 @@ template <typename T> struct Solver {
             SV_CUDA(cudaMemcpyAsync(th_n, th_k, sizeof(double) * h.V, cudaMemcpyDeviceToDevice, h.stream));
             return CT_OK;
         }
+        if (o.shared_offset) return update_param_shared(u);
         if (!o.varpro) return update_param(u);
         k_weights<T><<<grid_for(ne), kThreads, 0, h.stream>>>(u, w, h.N, h.F, o.temporal, o.eps, nullptr);
         double lam;
@@ -987,7 +1030,9 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !(o.noise_norm > 0.0)))
         return CT_ERR_ARG;
-    if ((o.plain != 0 && o.plain != 1) || o.reserved0 != 0) return CT_ERR_ARG;
+    if ((o.plain != 0 && o.plain != 1) || (o.shared_offset != 0 && o.shared_offset != 1) ||
+        (o.shared_offset && o.varpro))
+        return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
     h.fwd_ready = h.adj_ready = 0;
     // The solve runs on a private stream ordered after the work already queued
@@ -1026,7 +1071,9 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
         o.outer_iters < 1 || o.maxiter_p < 0 || o.max_halvings < 0 || o.lam_iters < 1 || !(o.eps > 0.0) ||
         !(o.tau > 0.0) || (o.lam_fix <= 0.0 && !noise_norms))
         return CT_ERR_ARG;
-    if ((o.plain != 0 && o.plain != 1) || o.reserved0 != 0) return CT_ERR_ARG;
+    if ((o.plain != 0 && o.plain != 1) || o.shared_offset != 0 ||
+        (o.shared_offset && o.varpro))
+        return CT_ERR_ARG;
     std::vector<const ctgb::Handle *> hs(nblocks);
     for (int j = 0; j < nblocks; ++j) {
         if (!blocks[j] || !b[j] || !theta_inout[j]) return CT_ERR_ARG;

@@ -1321,6 +1321,23 @@ __global__ void k_gn_direction(const double *__restrict__ g, const double *__res
     }
 }
 
+// Sums over the views, in a fixed order, of up to four per-view arrays (null
+// entries give 0): out[q] = sum_v a_q[v].  One block.
+__global__ void k_view_sums(const double *__restrict__ a0, const double *__restrict__ a1,
+                            const double *__restrict__ a2, const double *__restrict__ a3, int V,
+                            double *__restrict__ out)
+{
+    __shared__ double sh[40];
+    const double *a[4] = {a0, a1, a2, a3};
+    for (int q = 0; q < 4; ++q) {
+        double s = 0.0;
+        if (a[q])
+            for (int v = threadIdx.x; v < V; v += blockDim.x) s += a[q][v];
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) out[q] = s;
+    }
+}
+
 // Armijo test for the views still searching; shrinks alpha of the failures.
 // A failure whose next first-order change alpha |g_v d_v| falls below u rho_v
 // (the noise floor) ends its search with no step, as does a failure in the

@@ -65,7 +65,7 @@ class nlrmm_opts(ctypes.Structure):
         ("lam_hi", ctypes.c_double), ("c1", ctypes.c_double), ("beta", ctypes.c_double),
         ("alpha0", ctypes.c_double), ("mu_rel", ctypes.c_double), ("tol_u", ctypes.c_double),
         ("tol_p", ctypes.c_double), ("temporal", ctypes.c_int32), ("varpro", ctypes.c_int32),
-        ("armijo_eps", ctypes.c_double), ("plain", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("armijo_eps", ctypes.c_double), ("plain", ctypes.c_int32), ("shared_offset", ctypes.c_int32),
     ]
 
 

@@ -213,3 +213,66 @@ def test_fp32_solver_with_a_basis_of_120_reaches_the_oracle_reconstruction_error
     assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
     with pytest.raises(ct.CTError):
         op.solve(dev(b, torch.float32), dev(th_nom), noise_norm=nn, k_min=5, k_max=121)
+
+
+def _shifted_problem(N, V, seed, p_deg=0.8, vpf=None, moving=False):
+    """Data whose angles are the nominal ones plus one common offset p."""
+    rng = np.random.default_rng(seed)
+    vpf = vpf or [V]
+    F = len(vpf)
+    ells = synth.random_ellipses(N, 3, rng)
+    u_true = np.concatenate([synth.rasterize(N, ells, shift=(0.5 * f if moving else 0.0, 0.0)).ravel()
+                             for f in range(F)])
+    g = oracle.Geometry(N, synth.n_bins(N), sum(vpf), views_per_frame=vpf if F > 1 else None)
+    th_nom = np.sort(synth.random_angles(sum(vpf), rng))
+    b_true = oracle.forward(g, th_nom + math.radians(p_deg), u_true)
+    e = rng.standard_normal(g.m)
+    e *= 0.01 * np.linalg.norm(b_true) / np.linalg.norm(e)
+    return g, th_nom, u_true, b_true + e, float(np.linalg.norm(e))
+
+
+def test_fp64_shared_offset_follows_the_oracle_iterates(ct):
+    """One angle offset shared by every view (opts.shared_offset): FP64 against the
+    oracle's iterates; every view moves by the same offset."""
+    g, th_nom, u_true, b, nn = _shifted_problem(32, 40, seed=61)
+    kw = dict(k_min=5, k_max=15, outer_iters=4, tol1=0.0)
+    o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, shared_offset=True, **kw)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(g.N, g.B, g.V, max_batch=8, dtype=torch.float64)
+    x, th, st = op.solve(dev(b), dev(th_nom), x_true=dev(u_true), noise_norm=nn, stop_on_convergence=0,
+                         shared_offset=1, **kw)
+    shift = th.cpu().numpy() - th_nom
+    assert np.ptp(shift) <= 1e-13 and shift[0] > 0.0
+    assert st["enlarge_steps"] == h_o.enlarge_steps
+    np.testing.assert_allclose(st["lambda"], h_o.lam, rtol=1e-7)
+    np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-7)
+    assert np.linalg.norm(x.cpu().numpy() - u_o) <= 1e-7 * np.linalg.norm(u_o)
+    assert np.max(np.abs(th.cpu().numpy() - th_o)) <= 1e-9
+
+
+def test_fp32_dynamic_shared_offset_reaches_the_oracle_reconstruction_error(ct):
+    """The dynamic form (ANISO-TV over frames of uneven view counts) with one offset
+    for every frame, as in the paper's dynamic CT: FP32 against the oracle's RRE."""
+    vpf = [10, 13, 9, 12]
+    g, th_nom, u_true, b, nn = _shifted_problem(40, sum(vpf), seed=62, vpf=vpf, moving=True)
+    kw = dict(outer_iters=5, temporal=True)
+    o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, shared_offset=True, armijo_eps=2.0 ** -24, **kw)
+    u_o, th_o, h_o = nlrmm.NLRMMGKS(g, b, o).solve(th_nom, u_true=u_true)
+    op = ct.CTOperator(g.N, g.B, g.V, vpf, max_batch=8, dtype=torch.float32)
+    x, th, st = op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), noise_norm=nn,
+                         stop_on_convergence=0, shared_offset=1, outer_iters=5, temporal=1)
+    assert abs(st["rre"][-1] - h_o.rre[-1]) <= 1e-3 * h_o.rre[-1], (st["rre"][-1], h_o.rre[-1])
+    shift = th.cpu().numpy() - th_nom
+    assert np.ptp(shift) <= 1e-13
+
+
+def test_shared_offset_argument_errors(ct):
+    op = ct.CTOperator(16, 23, 8, max_batch=2, dtype=torch.float32)
+    b = torch.zeros(8 * 23, device="cuda")
+    th = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(ct.CTError):
+        op.solve(b, th, noise_norm=1.0, shared_offset=1, varpro=1)     # the VarPro update is per view
+    with pytest.raises(ct.CTError):
+        op.solve(b, th, noise_norm=1.0, shared_offset=2)
+    with pytest.raises(ct.CTError):
+        ct.stream_solve([op], [b], [th], [1.0], shared_offset=1)      # not in the streaming solver
