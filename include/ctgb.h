@@ -76,9 +76,9 @@ typedef struct {
                                          the centre, bin b centred at s_b = b - (B-1)/2 + delta_v on
                                          it; ray (v,b) joins the source and s_b (cos, sin)(theta_v).
                                          Must exceed 0.75 max(N, B) + 2.  Fan-beam handles run H, H^T,
-                                         J_theta, J_theta^T and the solvers; offsets delta are
-                                         accepted in H and H^T, their derivatives are not (ct_jac
-                                         with ddelta and ct_jacT with gdelta return CT_ERR_ARG). */
+                                         the angle and offset derivatives and the solvers (an offset
+                                         moves the bin centres along the detector line; the source
+                                         stays). */
 } ct_geom;
 
 typedef struct ct_handle ct_handle;
@@ -191,7 +191,6 @@ int ct_gn_terms(ct_handle *h, const double *theta, const double *delta,
  * ct_gn_terms_batch: the four ct_gn_terms outputs for each image, against
  *   data bdata [batch][n_views][B]: res [batch][n_views][B] (nullable),
  *   grad, jnorm2, fval (nullable) [batch][n_views].
- * Fan-beam handles: angle derivatives only (ddelta / gdelta give CT_ERR_ARG).
  * CT_ERR_ARG for batch out of range, null required pointers or unknown flags.
  */
 #define CT_BATCH_PER_IMAGE_DIRECTION 1

@@ -540,7 +540,6 @@ int ct_jac(ct_handle *H, const double *theta, const double *delta, const void *x
            const double *ddelta, void *dy)
 {
     if (!H || !theta || !x || !dtheta || !dy) return CT_ERR_ARG;
-    if (H->h.fan_D > 0.0 && ddelta) return CT_ERR_ARG;  // fan beam: angle derivatives only
     H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jac<double>(H->h, theta, delta, x, dtheta, ddelta, dy)
                           : do_jac<float>(H->h, theta, delta, x, dtheta, ddelta, dy);
@@ -550,7 +549,6 @@ int ct_jacT(ct_handle *H, const double *theta, const double *delta, const void *
             double *gdelta)
 {
     if (!H || !theta || !x || !r || !gtheta) return CT_ERR_ARG;
-    if (H->h.fan_D > 0.0 && gdelta) return CT_ERR_ARG;  // fan beam: angle derivatives only
     H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jacT<double>(H->h, theta, delta, x, r, gtheta, gdelta)
                           : do_jacT<float>(H->h, theta, delta, x, r, gtheta, gdelta);
@@ -571,7 +569,6 @@ int ct_jac_batch(ct_handle *H, const double *theta, const double *delta, const v
     if (!H || !theta || !X || !dtheta || !dY || batch < 1 || batch > H->h.max_batch ||
         (flags & ~CT_BATCH_PER_IMAGE_DIRECTION))
         return CT_ERR_ARG;
-    if (H->h.fan_D > 0.0 && ddelta) return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jac_batch<double>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags)
                           : do_jac_batch<float>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags);
@@ -583,7 +580,6 @@ int ct_jacT_batch(ct_handle *H, const double *theta, const double *delta, const 
     if (!H || !theta || !X || !R || !gtheta || batch < 1 || batch > H->h.max_batch ||
         (flags & ~(CT_BATCH_SHARED_R | CT_BATCH_SUM)))
         return CT_ERR_ARG;
-    if (H->h.fan_D > 0.0 && gdelta) return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
     return H->h.precision ? do_jacT_batch<double>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags)
                           : do_jacT_batch<float>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags);

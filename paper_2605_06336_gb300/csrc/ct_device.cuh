@@ -222,8 +222,10 @@ __device__ __forceinline__ void ray_epilogue(const RayArgs<T> &a, const ViewGeo 
 bool band_shape_ok(int mode, int kb, int vw, int rb);
 cudaError_t run_ray_band(const Handle &h, const RayArgs<float> &a, int mode, bool offs, int kb, int rb);
 // Fan-beam ray march (ct_fan.cu) for the same arguments: mode kFwd (kb
-// images), kJvp, kVjp or kGn (angle derivatives only); split warps share a ray.
-template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb, int split);
+// images), kJvp, kVjp (angle and, with offs, offset derivatives) or kGn
+// (angle derivatives); split warps share a ray.
+template <typename T>
+cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb, int split, bool offs);
 // Y[k][v][b] = w_v * (Y + P_1 + ... + P_{segs-1}), summed in segment order.
 cudaError_t launch_fwd_combine(const Handle &h, float *Y, const float *P, int segs, long long stride, int batch,
                                const int *skip);

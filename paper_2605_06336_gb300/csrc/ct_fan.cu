@@ -16,7 +16,9 @@
 // fixed point as the parallel-beam lines.  The geometry turns rigidly with
 // theta (dr/dtheta = (-r_y, r_x), dP_b/dtheta = s_b t), so
 // dq/dtheta = g0 + r gr with gr = -dC/dtheta, g0 = +-dA/dtheta + h dC/dtheta,
-// and dw/dtheta = C dC/dtheta / w.
+// and dw/dtheta = C dC/dtheta / w.  An offset delta_v moves every bin centre
+// along e (ds_b/ddelta = 1, the source stays): dq/ddelta = s0 + r sr with
+// sr = -dC/ds, s0 = +-dA/ds + h dC/ds, and dw/ddelta = C dC/ds / w.
 //
 //   k_fan_rays   per-ray table (fixed-point line, weight, derivative
 //                constants, march range) from the view table, for the views
@@ -52,6 +54,7 @@ template <typename T> struct __align__(16) FanRay {
     float rlo, rhi;    // march indices with -1 < q < N lie in [rlo, rhi] (two indices of margin)
     int mode;          // 0: rows of X, 1: rows of X^T (columns)
     int gen;           // generation of the view record the entry was built from (0: never)
+    T dws, s0, sr;     // d w / d delta, dq/ddelta = s0 + r sr
 };
 
 // Per view: FP32 constants of the transpose's candidate search and the bin
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
         const double c = g.c, sn = g.s, s = g.sb0d + (double)b;
         const double rx = s * c - D * sn, ry = s * sn + D * c;
         const double px = s * c, py = s * sn, dpx = -s * sn, dpy = s * c;
-        double C, A, dC, dA, qh, g0;
+        double C, A, dC, dA, qh, g0, dCs, s0;
         int mode;
         if (fabs(rx) <= fabs(ry)) {
             mode = 0;
@@ -87,6 +90,8 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
             dA = dpx - C * dpy - py * dC;
             qh = h + A;
             g0 = dA + h * dC;
+            dCs = (c * ry - sn * rx) / (ry * ry);  // d/ds of C and A: P_b and r move by e
+            s0 = (c - C * sn - py * dCs) + h * dCs;
         } else {
             mode = 1;
             C = ry / rx;
@@ -95,6 +100,8 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
             dA = dpy - C * dpx - px * dC;
             qh = h - A;
             g0 = -dA + h * dC;
+            dCs = (sn * rx - c * ry) / (rx * rx);
+            s0 = -(sn - C * c - px * dCs) + h * dCs;
         }
         const double qr = -C;
         const double w = sqrt(1.0 + C * C);
@@ -105,6 +112,9 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
         R.dw = (T)(C * dC / w);
         R.g0 = (T)g0;
         R.gr = (T)(-dC);
+        R.dws = (T)(C * dCs / w);
+        R.s0 = (T)s0;
+        R.sr = (T)(-dCs);
         R.mode = mode;
         R.gen = g.gen;
         if (fabs(qr) < 1e-12) {
@@ -162,11 +172,11 @@ __global__ void __launch_bounds__(256) k_fan_views(const ViewGeo *__restrict__ v
 // (and one batch group of KB images for the forward).  The warps march
 // consecutive segments of the warp-union row range; their sums are added in
 // segment order in shared memory and warp 0 writes the result.
-template <typename T, int MODE, int KB, int SPLIT>
+template <typename T, int MODE, int KB, int SPLIT, bool OFFS>
 __global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanRay<T> *__restrict__ rays)
 {
     using P2 = pair_t<T>;
-    constexpr int NACC = (MODE == kFwd) ? KB : 2;
+    constexpr int NACC = (MODE == kFwd) ? KB : (OFFS ? 3 : 2);
     __shared__ T red[SPLIT > 1 ? SPLIT : 1][NACC][32];
     const int lane = threadIdx.x & 31;
     const int seg = threadIdx.x >> 5;
@@ -228,8 +238,9 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanR
                 }
             }
         } else {
-            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta;
-            // rows in blocks of U whose loads are all issued first
+            // acc[0] = sum of interpolated values, acc[1] = sum slope * dq/dtheta,
+            // acc[2] (offsets) = sum slope * dq/ddelta; rows in blocks of U whose
+            // loads are all issued first
             for (; r + U - 1 <= r1; r += U) {
                 P2 p[U];
                 T f[U];
@@ -245,6 +256,7 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanR
                     const T d = p[u].y - p[u].x;
                     acc[0] += fma(f[u], d, p[u].x);
                     acc[1] = fma(d, fma((T)(r + u), R.gr, R.g0), acc[1]);
+                    if constexpr (OFFS) acc[NACC - 1] = fma(d, fma((T)(r + u), R.sr, R.s0), acc[NACC - 1]);
                 }
                 Q += (long long)U * dQ;
             }
@@ -255,6 +267,7 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanR
                 const T d = q.y - q.x;
                 acc[0] += fma(fr, d, q.x);
                 acc[1] = fma(d, fma((T)r, R.gr, R.g0), acc[1]);
+                if constexpr (OFFS) acc[NACC - 1] = fma(d, fma((T)r, R.sr, R.s0), acc[NACC - 1]);
             }
         }
         if constexpr (SPLIT > 1) {
@@ -282,15 +295,27 @@ __global__ void __launch_bounds__(32 * SPLIT) k_ray_fan(RayArgs<T> a, const FanR
                 // one image per lane in the derivative modes: image k0 of the batch
                 const size_t img = (size_t)k0, vb = (size_t)v * a.B + b;
                 const T jt = fma(R.dw, acc[0], R.w * acc[1]);
+                T jd = T(0);
+                if constexpr (OFFS) jd = fma(R.dws, acc[0], R.w * acc[NACC - 1]);
                 if constexpr (MODE == kJvp) {
-                    if (active) a.Y[img * a.sino_stride + vb] = (T)a.dtheta[img * a.dir_stride + v] * jt;
+                    if (active) {
+                        T out = (T)a.dtheta[img * a.dir_stride + v] * jt;
+                        if constexpr (OFFS) out = fma((T)a.ddelta[img * a.dir_stride + v], jd, out);
+                        a.Y[img * a.sino_stride + vb] = out;
+                    }
                 } else if constexpr (MODE == kVjp) {
-                    double pt = active ? (double)(a.R[img * a.r_stride + vb] * jt) : 0.0;
+                    double pt = 0.0, pd = 0.0;
+                    if (active) {
+                        const T rr = a.R[img * a.r_stride + vb];
+                        pt = (double)(rr * jt);
+                        if constexpr (OFFS) pd = (double)(rr * jd);
+                    }
                     pt = warp_sum(pt);
+                    if constexpr (OFFS) pd = warp_sum(pd);
                     if (lane == 0) {
                         double *p = a.partial + img * a.part_stride + ((size_t)v * a.nchunks + chunk) * 4;
                         p[0] = pt;
-                        p[1] = 0.0;
+                        p[1] = pd;
                     }
                 } else {  // kGn
                     double pg = 0.0, pj = 0.0, pf = 0.0, pr = 0.0;
@@ -464,21 +489,23 @@ __global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const Fan
     }
 }
 
-template <typename T, int MODE, int KB, int SPLIT> cudaError_t run_fan(const Handle &h, const RayArgs<T> &a)
+template <typename T, int MODE, int KB, int SPLIT, bool OFFS = false>
+cudaError_t run_fan(const Handle &h, const RayArgs<T> &a)
 {
-    auto kern = k_ray_fan<T, MODE, KB, SPLIT>;
+    auto kern = k_ray_fan<T, MODE, KB, SPLIT, OFFS>;
     const long long items = (long long)a.ngroups * a.V * a.nchunks;
     const int grid = persistent_grid(kern, 32 * SPLIT, 0, items, h.num_sms);
     kern<<<grid, 32 * SPLIT, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays);
     return cudaGetLastError();
 }
 
-template <typename T, int MODE, int KB> cudaError_t run_fan_split(const Handle &h, const RayArgs<T> &a, int split)
+template <typename T, int MODE, int KB, bool OFFS = false>
+cudaError_t run_fan_split(const Handle &h, const RayArgs<T> &a, int split)
 {
     switch (split) {
-    case 1: return run_fan<T, MODE, KB, 1>(h, a);
-    case 2: return run_fan<T, MODE, KB, 2>(h, a);
-    default: return run_fan<T, MODE, KB, 4>(h, a);
+    case 1: return run_fan<T, MODE, KB, 1, OFFS>(h, a);
+    case 2: return run_fan<T, MODE, KB, 2, OFFS>(h, a);
+    default: return run_fan<T, MODE, KB, 4, OFFS>(h, a);
     }
 }
 
@@ -523,8 +550,10 @@ cudaError_t launch_fan_rays(const Handle &h, const int *skip)
     return cudaGetLastError();
 }
 
-// split: warps per work item (row segments), 1, 2 or 4 (larger values take 4)
-template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb, int split)
+// split: warps per work item (row segments), 1, 2 or 4 (larger values take 4);
+// offs: the JVP / VJP also carry the offset derivatives
+template <typename T>
+cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> &a, int mode, int kb, int split, bool offs)
 {
     switch (mode) {
     case kFwd:
@@ -534,8 +563,8 @@ template <typename T> cudaError_t run_fan_ray(const Handle &h, const RayArgs<T> 
         case 4: return run_fan_split<T, kFwd, 4>(h, a, split);
         default: return run_fan_split<T, kFwd, 8>(h, a, split);
         }
-    case kJvp: return run_fan_split<T, kJvp, 1>(h, a, split);
-    case kVjp: return run_fan_split<T, kVjp, 1>(h, a, split);
+    case kJvp: return offs ? run_fan_split<T, kJvp, 1, true>(h, a, split) : run_fan_split<T, kJvp, 1>(h, a, split);
+    case kVjp: return offs ? run_fan_split<T, kVjp, 1, true>(h, a, split) : run_fan_split<T, kVjp, 1>(h, a, split);
     default: return run_fan_split<T, kGn, 1>(h, a, split);
     }
 }
@@ -587,8 +616,8 @@ template <typename T> cudaError_t launch_fan_sino(const Handle &h, const T *Y, i
 
 template cudaError_t launch_fan_sino<float>(const Handle &, const float *, int, const int *);
 template cudaError_t launch_fan_sino<double>(const Handle &, const double *, int, const int *);
-template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int, int);
-template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int, int);
+template cudaError_t run_fan_ray<float>(const Handle &, const RayArgs<float> &, int, int, int, bool);
+template cudaError_t run_fan_ray<double>(const Handle &, const RayArgs<double> &, int, int, int, bool);
 template cudaError_t launch_fan_adjoint<float>(const Handle &, float *, int, int, int, const int *);
 template cudaError_t launch_fan_adjoint<double>(const Handle &, double *, int, int, int, const int *);
 

@@ -561,7 +561,7 @@ cudaError_t run_ray_split(const Handle &h, const RayArgs<T> &a, int split)
 template <typename T, int MODE, bool OFFS, int KB>
 cudaError_t run_ray_any(const Handle &h, const RayArgs<T> &a, int split, int stage)
 {
-    if (h.fan_D > 0.0) return run_fan_ray<T>(h, a, MODE, KB, split);
+    if (h.fan_D > 0.0) return run_fan_ray<T>(h, a, MODE, KB, split, OFFS);
     if constexpr (std::is_same<T, float>::value) {
         if (stage > 0 && band_shape_ok(MODE, KB, a.VW, stage)) return run_ray_band(h, a, MODE, OFFS, KB, stage);
     }

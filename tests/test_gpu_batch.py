@@ -10,7 +10,7 @@ Sec. 3.2, whose sensitivities enter the VarPro Gauss-Newton system of Sec. 4.2).
 * every image's result is bit-identical to the single-image call on it at
   1, 2 and 4 images per lane: batching shares the line, cell and fraction of
   a ray between images and leaves each image's summation order unchanged;
-* the fan-beam handle batches its angle derivatives the same way.
+* the fan-beam handle batches its angle and offset derivatives the same way.
 """
 import numpy as np
 import pytest
@@ -147,8 +147,15 @@ def test_fan_beam_batched_angle_derivatives():
     for k in range(K):
         assert rel(dY[k], oracle.jac(g, theta, X[k], dth)) <= 1e-5
         assert rel(gt[k], oracle.jacT(g, theta, X[k], R[k])[0]) <= 1e-5
-    with pytest.raises(ct.CTError):
-        op.jac_batch(dev(X, torch.float32), th, dev(dth), dev(np.zeros(V)), dev(np.zeros(V)))
+    # with offsets: J_theta dtheta + J_delta ddelta and both gradients per image
+    delta = rng.normal(0, 0.5, V)
+    ddl = rng.standard_normal(V)
+    dY = host(op.jac_batch(dev(X, torch.float32), th, dev(dth), dev(delta), dev(ddl)))
+    gt, gd = op.jacT_batch(dev(X, torch.float32), th, dev(R, torch.float32), dev(delta), want_delta=True)
+    for k in range(K):
+        assert rel(dY[k], oracle.jac(g, theta, X[k], dth, delta, ddl)) <= 1e-5
+        a, b = oracle.jacT(g, theta, X[k], R[k], delta)
+        assert rel(host(gt[k]), a) <= 1e-5 and rel(host(gd[k]), b) <= 1e-5
 
 
 def test_batched_argument_errors():

@@ -6,8 +6,9 @@ H^T, J_theta, J_theta^T and the Gauss-Newton terms; float64 1e-12.  The cases
 mix views whose rays all march rows or all march columns with views whose fan
 straddles 45 degrees (rays of both kinds in one view), odd image sides, ragged
 batches, frames with an empty one, and fixed detector offsets in H and H^T.
-Also: the adjoint identity, the parallel-beam limit of a distant source,
-refusal of offset derivatives, and NL-RMM-GKS on fan-beam data following the
+Also: the offset derivatives (J_delta, J_delta^T: an offset moves the bin
+centres along the detector line), the adjoint identity, the parallel-beam
+limit of a distant source, and NL-RMM-GKS on fan-beam data following the
 oracle's iterates.
 """
 import math
@@ -151,14 +152,38 @@ def test_fan_adjoint_identity_and_parallel_limit():
     assert rel(yf, oracle.forward(oracle.Geometry(N, B, V, fan_D=1e7), theta, x)) <= 1e-12
 
 
-def test_fan_refuses_offset_derivatives():
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("N,vpf,D", [(16, [10], 20.0), (37, [11], 60.0), (24, [4, 1, 0, 6], 40.0),
+                                     (64, [90], 128.0)])
+def test_fan_offset_derivative_parity(N, vpf, D, dtype):
+    """J_theta dtheta + J_delta ddelta and J^T r (both gradients) with per-view
+    offsets, against the oracle's fan-beam derivatives (pinned by central
+    differences and by Gaussian-blob line integrals); per view as well as
+    normwise."""
     from paper_2605_06336_gb300 import ct
-    op = ct.CTOperator(16, 23, 6, max_batch=1, dtype=torch.float64, source_distance=32.0)
-    z = torch.zeros(6, dtype=torch.float64, device="cuda")
-    x = torch.zeros(256, dtype=torch.float64, device="cuda")
-    with pytest.raises(ct.CTError) as e:
-        op.jac(x, z, z, z, z)
-    assert e.value.code == ct.CT_ERR_ARG
+    B, V = synth.n_bins(N), sum(vpf)
+    theta, _, X, Y, rng = _inputs(N, vpf, 1, False, seed=5 * N + 1)
+    delta = rng.normal(0, 0.5, V)
+    g = oracle.Geometry(N, B, V, vpf, fan_D=D)
+    op = ct.CTOperator(N, B, V, vpf, max_batch=1, dtype=dtype, source_distance=D)
+    th, dl = dev(theta), dev(delta)
+    x, r = X[0], Y[0]
+    dth, ddl = rng.standard_normal(V), rng.standard_normal(V)
+    dy = host(op.jac(dev(x, dtype), th, dev(dth), dl, dev(ddl)))
+    dyo = oracle.jac(g, theta, x, dth, delta, ddl)
+    assert rel(dy, dyo) <= TOL[dtype]
+    dyv, dyov = dy.reshape(V, B), dyo.reshape(V, B)
+    if V:
+        sc = np.maximum(np.abs(dyov).max(1), 1e-300)
+        assert float((np.abs(dyv - dyov).max(1) / sc).max()) <= TOL[dtype]
+    gt, gd = op.jacT(dev(x, dtype), th, dev(r, dtype), dl, want_delta=True)
+    gto, gdo = oracle.jacT(g, theta, x, r, delta)
+    assert rel(host(gt), gto) <= TOL[dtype]
+    assert rel(host(gd), gdo) <= TOL[dtype]
+    dt, dd = oracle.dsample(g, theta, x, delta)
+    mag = (np.abs(r.reshape(V, B)) * np.abs(dd.reshape(V, B))).sum(1)
+    if V:
+        assert float((np.abs(host(gd) - gdo) / np.maximum(mag, 1e-300)).max()) <= TOL[dtype]
 
 
 def test_fp64_fan_solver_follows_the_oracle_iterates():
