@@ -589,7 +589,7 @@ def operator_line(name, w, K, dtype, dev, steps, flush, peaks, delta=None, tunin
     return out, s
 
 
-def jacobian_batch_line(w, K, dev, steps, flush, peaks):
+def jacobian_batch_line(w, K, dev, steps, flush, peaks, tuning=None):
     """J and J^T on a block of K images sharing the angles, one batched call each
     (ct_jac_batch, ct_jacT_batch), against K single-image calls; gathers per
     launch 8 B x K x interpolation steps, served from L2 (L1-gather kernels)."""
@@ -597,7 +597,10 @@ def jacobian_batch_line(w, K, dev, steps, flush, peaks):
     from paper_2605_06336_gb300 import ct
     rng = np.random.default_rng(8)
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=K, dtype=torch.float32)
-    op.autotune()
+    if tuning:
+        op.tuning = tuning
+    else:
+        op.autotune()
     th = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
     X = torch.tensor(np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(K - 1, w.N * w.N))]),
                      dtype=torch.float32, device=dev)
@@ -909,7 +912,7 @@ def main():
     if args.ops_only:
         w = synth.make_workload(WORKLOAD)
         if args.ops_only == "jac8":
-            out = jacobian_batch_line(w, KBLOCK, dev, args.steps, flush, (l2_gbs, smem_gbs))
+            out = jacobian_batch_line(w, KBLOCK, dev, args.steps, flush, (l2_gbs, smem_gbs), tun)
         else:
             wl = {"C2": w, "C2fp64": w, "C3": synth.make_workload("C3"), "C5chunk": c5_chunk_workload()}[args.ops_only]
             dt = torch.float64 if args.ops_only == "C2fp64" else torch.float32

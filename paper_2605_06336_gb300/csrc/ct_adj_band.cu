@@ -28,11 +28,6 @@ namespace {
 
 constexpr int kWin = 32;  // staged pairs per (view, sinogram)
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -54,8 +49,16 @@ struct AdjBandArgs {
 // Per (view, tile) constants of a staged block.
 struct __align__(16) AdjView {
     float c, s, w, frac;  // direction, weight, fractional part of the tile anchor
-    int lo, hi, off, pad; // slot of in-tile offset m: min(max(m, lo), hi) + off
+    float w1;             // 1 - w
+    int off;              // slot of in-tile offset m: min(max(m + off, 0), kWin - 1)
+    int pad0, pad1;
 };
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 
 template <int KB, int VB>
 __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
@@ -112,10 +115,9 @@ __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
                 av.s = s;
                 av.w = GeoT<float>::w(g);
                 av.frac = frac;
-                av.lo = -2 - ix;
-                av.hi = a.B - ix;
+                av.w1 = 1.0f - av.w;
                 av.off = ix + 2 - start;
-                av.pad = 0;
+                av.pad0 = av.pad1 = 0;
                 s_view[buf][q] = av;
             }
             float2 *dst = sbuf + (size_t)buf * BUF + (size_t)q * KB * kWin;
@@ -150,10 +152,12 @@ __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
                 float fr;
                 floor_split(t, mm, fr);
                 const float wv = av.w;
-                const float wa = wv * fmaxf(0.0f, fmaf(-fr, wv, 1.0f));      // bin floor(beta)
-                const float wb = wv * fmaxf(0.0f, fmaf(fr, wv, 1.0f - wv));  // bin floor(beta) + 1
-                // the window holds the pair; the outer clamp only guards the buffer bounds
-                const int slot = min(max(min(max(mm, av.lo), av.hi) + av.off, 0), kWin - 1);
+                const float wa = wv * fmaxf(0.0f, fmaf(-fr, wv, 1.0f));    // bin floor(beta)
+                const float wb = wv * fmaxf(0.0f, fmaf(fr, wv, av.w1));    // bin floor(beta) + 1
+                // Every cell the tile reads lies in the window unless the window
+                // was clamped to an end of the row; there the clamped slot is a
+                // zero padding pair, as is every pair beyond the detector.
+                const int slot = min(max(mm + av.off, 0), kWin - 1);
                 const float2 *sp = base + q * KB * kWin + slot;
 #pragma unroll
                 for (int k = 0; k < KB; ++k) {

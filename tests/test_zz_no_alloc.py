@@ -3,7 +3,8 @@
 Some callers cannot allocate device memory (a host application that owns all
 of it through its own pool, a service whose budget is fixed after start-up);
 ct_jacT_noalloc serves them with a static device workspace.  Its results must
-equal those of ct_jacT, the entry point it mirrors, on calls in a row: the
+equal those of ct_jacT, the entry point it mirrors, and the FP64 oracle's, on
+calls in a row: the
 second call keeps the first call's angles and offsets but changes the image
 size and the bin count, so a per-view table left over from the first call
 (its constants are cached by angle and offset) would give wrong gradients;
@@ -15,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2605_06336_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -54,6 +56,13 @@ def test_noalloc_matches_ct_jacT_on_calls_in_a_row():
         assert _rel(gt, gt_ref) <= 1e-5, (N, with_delta)
         if with_delta:
             assert _rel(gd, gd_ref) <= 1e-5, N
+        # and against the FP64 oracle directly, so a defect shared with ct_jacT would show
+        g = oracle.Geometry(N, B, V)
+        d_h = delta.cpu().numpy() if with_delta else None
+        gto, gdo = oracle.jacT(g, theta.cpu().numpy(), x.double().cpu().numpy(), r.double().cpu().numpy(), d_h)
+        assert np.linalg.norm(gt.cpu().numpy() - gto) <= 1e-5 * np.linalg.norm(gto), (N, with_delta)
+        if with_delta:
+            assert np.linalg.norm(gd.cpu().numpy() - gdo) <= 1e-5 * np.linalg.norm(gdo), N
         op.close()
 
 
