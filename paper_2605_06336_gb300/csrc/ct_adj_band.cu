@@ -6,10 +6,13 @@
 // batch.  For view v the tile's bin coordinates beta = beta0 + j*c - i*s
 // span at most 15 (|c| + |s|) <= 21.3 bins, so the pairs a tile reads lie in
 // a window of W = 32 pairs (one pair of margin below for the FP32 in-tile
-// offset, aligned down to an even slot for 16-byte copies).  While the
-// windows of one block of VB views are read, those of the next block stream
-// into the other buffer with cp.async.  A half-warp is one tile row, whose
-// 16 pixels read at most 16 consecutive pairs: one shared-memory wavefront.
+// offset, aligned down to an even slot for 16-byte copies).  The per-(view,
+// tile) constants of up to kViewCap views are computed first, one thread
+// per view (the tile anchor is an FP64 sum, and FP64 issues slowly on this
+// part).  While the windows of one block of VB views are read, those of the
+// next block stream into the other buffer with cp.async.  A half-warp is one
+// tile row, whose 16 pixels read at most 16 consecutive pairs: one
+// shared-memory wavefront.
 //
 // With `segs` CTAs per tile, CTA s takes the views s, s + segs, ... of the
 // frame and writes its partial image (segment 0 to X, the others to a
@@ -26,7 +29,8 @@
 namespace ctgb {
 namespace {
 
-constexpr int kWin = 32;  // staged pairs per (view, sinogram)
+constexpr int kWin = 32;       // staged pairs per (view, sinogram)
+constexpr int kViewCap = 128;  // views whose tile constants are staged at a time (a multiple of VB)
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -46,12 +50,13 @@ struct AdjBandArgs {
     const int *skip;
 };
 
-// Per (view, tile) constants of a staged block.
+// Per (view, tile) constants.
 struct __align__(16) AdjView {
     float c, s, w, frac;  // direction, weight, fractional part of the tile anchor
     float w1;             // 1 - w
     int off;              // slot of in-tile offset m: min(max(m + off, 0), kWin - 1)
-    int pad0, pad1;
+    int start;            // first staged pair of the view's window in its sinogram row
+    int pad;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -63,9 +68,10 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 template <int KB, int VB>
 __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
 {
+    static_assert(kViewCap % VB == 0, "view chunks hold whole blocks");
     extern __shared__ float4 adj_smem[];
     float2 *sbuf = reinterpret_cast<float2 *>(adj_smem);  // [2][VB][KB][kWin]
-    __shared__ AdjView s_view[2][VB];
+    __shared__ AdjView s_view[kViewCap];
     constexpr int BUF = VB * KB * kWin;
     const int tid = threadIdx.x;
     const int tx = tid & (kTile - 1), ty = tid / kTile;
@@ -87,29 +93,25 @@ __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
         const float2 *yp = a.YP + (size_t)k0 * a.ysino_stride;
         const int vs = a.fstart[f], vc = a.fcount[f];
         const int nv = vc > seg ? (vc - seg + segs - 1) / segs : 0;  // this CTA's views: vs + seg + q * segs
-        const int nblk = (nv + VB - 1) / VB;
 
-        // Block blk: thread t handles view q = t / (256 / VB) of the block; it
-        // computes the view's window (every thread of the view alike) and
-        // copies its share of the KB windows.
-        auto stage = [&](int blk, int buf) {
-            constexpr int TPV = 256 / VB;         // threads per view
-            constexpr int UNITS = KB * kWin / 2;  // 16-byte copies per view
-            const int q = tid / TPV, r = tid % TPV;
-            const int qq = blk * VB + q;
-            if (qq >= nv) return;
-            const int v = vs + seg + qq * segs;
-            const ViewGeo &g = a.vg[v];
-            const double bt = g.beta0 + (double)j0 * g.c - (double)i0 * g.s;
-            const double fl = floor(bt);
-            const int ix = (int)fl;
-            const float frac = (float)(bt - fl);
-            const float c = (float)g.c, s = (float)g.s;
-            // lowest in-tile offset floor, one pair of margin, even slot, inside the row
-            const float tmin = frac + fminf(0.0f, 15.0f * c) + fminf(0.0f, -15.0f * s);
-            int start = ix + 2 + (int)floorf(tmin) - 1;
-            start = min(max(start, 0), a.Pb - kWin) & ~1;
-            if (r == 0) {
+        float acc[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) acc[k] = 0.0f;
+        for (int cb = 0; cb < nv; cb += kViewCap) {
+            const int nc = min(kViewCap, nv - cb);
+            const int nblk = (nc + VB - 1) / VB;
+            __syncthreads();  // the previous chunk (or item) is done with s_view and both buffers
+            for (int q = tid; q < nc; q += blockDim.x) {
+                const ViewGeo &g = a.vg[vs + seg + (cb + q) * segs];
+                const double bt = g.beta0 + (double)j0 * g.c - (double)i0 * g.s;
+                const double fl = floor(bt);
+                const int ix = (int)fl;
+                const float frac = (float)(bt - fl);
+                const float c = (float)g.c, s = (float)g.s;
+                // lowest in-tile offset floor, one pair of margin, even slot, inside the row
+                const float tmin = frac + fminf(0.0f, 15.0f * c) + fminf(0.0f, -15.0f * s);
+                int start = ix + 2 + (int)floorf(tmin) - 1;
+                start = min(max(start, 0), a.Pb - kWin) & ~1;
                 AdjView av;
                 av.c = c;
                 av.s = s;
@@ -117,56 +119,65 @@ __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
                 av.frac = frac;
                 av.w1 = 1.0f - av.w;
                 av.off = ix + 2 - start;
-                av.pad0 = av.pad1 = 0;
-                s_view[buf][q] = av;
+                av.start = start;
+                av.pad = 0;
+                s_view[q] = av;
             }
-            float2 *dst = sbuf + (size_t)buf * BUF + (size_t)q * KB * kWin;
-            const float2 *src = yp + (size_t)v * a.Pb + start;
-            for (int u = r; u < UNITS; u += TPV) {
-                const int k = u / (kWin / 2), c2 = 2 * (u % (kWin / 2));
-                cp_async16(dst + k * kWin + c2, src + (size_t)k * a.ysino_stride + c2);
-            }
-        };
-
-        float acc[KB];
-#pragma unroll
-        for (int k = 0; k < KB; ++k) acc[k] = 0.0f;
-        __syncthreads();  // the previous item is done with both buffers
-        if (nblk > 0) stage(0, 0);
-        cp_async_commit();
-        for (int blk = 0; blk < nblk; ++blk) {
-            cp_async_wait0();
-            // block blk is visible to every thread, and every thread has finished
-            // block blk - 1, whose buffer the next copies overwrite
             __syncthreads();
-            if (blk + 1 < nblk) stage(blk + 1, (blk + 1) & 1);
+
+            // Block blk of the chunk: thread t copies its share of the KB windows
+            // of view q = t / (256 / VB) of the block.
+            auto stage = [&](int blk, int buf) {
+                constexpr int TPV = 256 / VB;         // threads per view
+                constexpr int UNITS = KB * kWin / 2;  // 16-byte copies per view
+                const int q = tid / TPV, r = tid % TPV;
+                const int qq = blk * VB + q;
+                if (qq >= nc) return;
+                const int v = vs + seg + (cb + qq) * segs;
+                float2 *dst = sbuf + (size_t)buf * BUF + (size_t)q * KB * kWin;
+                const float2 *src = yp + (size_t)v * a.Pb + s_view[qq].start;
+                for (int u = r; u < UNITS; u += TPV) {
+                    const int k = u / (kWin / 2), c2 = 2 * (u % (kWin / 2));
+                    cp_async16(dst + k * kWin + c2, src + (size_t)k * a.ysino_stride + c2);
+                }
+            };
+
+            stage(0, 0);
             cp_async_commit();
-            const int nq = min(VB, nv - blk * VB);
-            const float2 *base = sbuf + (size_t)(blk & 1) * BUF;
-            const AdjView *sv = s_view[blk & 1];
+            for (int blk = 0; blk < nblk; ++blk) {
+                cp_async_wait0();
+                // block blk is visible to every thread, and every thread has finished
+                // block blk - 1, whose buffer the next copies overwrite
+                __syncthreads();
+                if (blk + 1 < nblk) stage(blk + 1, (blk + 1) & 1);
+                cp_async_commit();
+                const int nq = min(VB, nc - blk * VB);
+                const float2 *base = sbuf + (size_t)(blk & 1) * BUF;
+                const AdjView *sv = s_view + blk * VB;
 #pragma unroll 4
-            for (int q = 0; q < nq; ++q) {
-                const AdjView av = sv[q];
-                const float t = fmaf(fx, av.c, fmaf(-fy, av.s, av.frac));
-                int mm;
-                float fr;
-                floor_split(t, mm, fr);
-                const float wv = av.w;
-                const float wa = wv * fmaxf(0.0f, fmaf(-fr, wv, 1.0f));    // bin floor(beta)
-                const float wb = wv * fmaxf(0.0f, fmaf(fr, wv, av.w1));    // bin floor(beta) + 1
-                // Every cell the tile reads lies in the window unless the window
-                // was clamped to an end of the row; there the clamped slot is a
-                // zero padding pair, as is every pair beyond the detector.
-                const int slot = min(max(mm + av.off, 0), kWin - 1);
-                const float2 *sp = base + q * KB * kWin + slot;
+                for (int q = 0; q < nq; ++q) {
+                    const AdjView av = sv[q];
+                    const float t = fmaf(fx, av.c, fmaf(-fy, av.s, av.frac));
+                    int mm;
+                    float fr;
+                    floor_split(t, mm, fr);
+                    const float wv = av.w;
+                    const float wa = wv * fmaxf(0.0f, fmaf(-fr, wv, 1.0f));    // bin floor(beta)
+                    const float wb = wv * fmaxf(0.0f, fmaf(fr, wv, av.w1));    // bin floor(beta) + 1
+                    // Every cell the tile reads lies in the window unless the window
+                    // was clamped to an end of the row; there the clamped slot is a
+                    // zero padding pair, as is every pair beyond the detector.
+                    const int slot = min(max(mm + av.off, 0), kWin - 1);
+                    const float2 *sp = base + q * KB * kWin + slot;
 #pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    const float2 p = sp[k * kWin];
-                    acc[k] = fmaf(wa, p.x, fmaf(wb, p.y, acc[k]));
+                    for (int k = 0; k < KB; ++k) {
+                        const float2 p = sp[k * kWin];
+                        acc[k] = fmaf(wa, p.x, fmaf(wb, p.y, acc[k]));
+                    }
                 }
             }
+            cp_async_wait0();  // the last group is empty
         }
-        cp_async_wait0();  // the last group is empty
         const int i = i0 + ty, j = j0 + tx;
         if (i < N && j < N) {
             float *dst = seg == 0 ? a.X : a.part + (size_t)(seg - 1) * a.part_stride;
