@@ -68,8 +68,9 @@ def launches_per_step(t):
     forward, J and J^T lay out their image and the transpose its sinograms
     (1 each; the same launch brings the view table up to date); the forward
     ray kernel(s) over the 8-image block, the transpose, the JVP, the VJP and
-    its per-view reduction; staged shapes with several CTAs per ray / tile
-    add a combining kernel."""
+    its per-view reduction; the staged forward with several CTAs per ray adds
+    a combining kernel (the staged transpose combines its CTAs per tile inside
+    their thread-block cluster)."""
     fkb, fsplit, _, akb, asplit, _, _, fstage, _, astage = t[:10]
     fwd = 0
     k = 0
@@ -84,7 +85,6 @@ def launches_per_step(t):
         if width <= akb and (KBLOCK - k) // width > 0:
             adj += 1
             k += (KBLOCK - k) // width * width
-    adj += 1 if (astage > 0 and asplit > 1) else 0
     return 3 + 1 + fwd + adj + 1 + 1 + 1
 
 

@@ -14,11 +14,15 @@
 // tile row, whose 16 pixels read at most 16 consecutive pairs: one
 // shared-memory wavefront.
 //
-// With `segs` CTAs per tile, CTA s takes the views s, s + segs, ... of the
-// frame and writes its partial image (segment 0 to X, the others to a
-// workspace); a second kernel adds them in segment order.  Every pixel sums
-// its views in the same order with the same fused multiply-adds as k_adjoint
-// with `segs` view groups, so the results are bit-identical to it.
+// With `segs` CTAs per tile, the CTAs of a tile form one thread-block
+// cluster and CTA s takes the views s, s + segs, ... of the frame.  At the
+// end of the tile each CTA leaves its partial sums in its shared memory and
+// CTA 0 adds the others' through distributed shared memory, in segment
+// order, before it writes the pixel: no partial images in global memory and
+// no second kernel.  Every pixel sums its views in the same order with the
+// same fused multiply-adds as k_adjoint with `segs` view groups, so the
+// results are bit-identical to it.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,9 +48,7 @@ struct AdjBandArgs {
     int kbase, ngroups;
     float *X;
     long long img_stride;     // F * N * N
-    int segs;                 // CTAs per tile (view subsets)
-    float *part;              // segments 1..segs-1
-    long long part_stride;    // elements per segment
+    int segs;                 // CTAs per tile (view subsets) = cluster size
     const int *skip;
 };
 
@@ -81,11 +83,14 @@ __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
     const int total = a.ngroups * a.F * tiles * segs;
     const int N = a.N;
     if (a.skip && *a.skip) return;
+    // The grid is a whole number of clusters and total a multiple of segs, so
+    // the CTAs of a cluster take the segments of one tile in every iteration
+    // and leave the loop together (the cluster barriers below are uniform).
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int tile = item % tiles;
-        int t2 = item / tiles;
-        const int seg = t2 % segs;
-        t2 /= segs;
+        const int seg = item % segs;  // = rank of the CTA in its cluster
+        int t2 = item / segs;
+        const int tile = t2 % tiles;
+        t2 /= tiles;
         const int f = t2 % a.F;
         const int grp = t2 / a.F;
         const int i0 = (tile / a.tps) * kTile, j0 = (tile % a.tps) * kTile;
@@ -178,30 +183,36 @@ __global__ void __launch_bounds__(256) k_adj_band(AdjBandArgs a)
             }
             cp_async_wait0();  // the last group is empty
         }
-        const int i = i0 + ty, j = j0 + tx;
-        if (i < N && j < N) {
-            float *dst = seg == 0 ? a.X : a.part + (size_t)(seg - 1) * a.part_stride;
+        if (segs > 1) {
+            // segment sums of the tile: CTA 0 adds those of CTAs 1..segs-1 in order
+            namespace cg = cooperative_groups;
+            cg::cluster_group cl = cg::this_cluster();
+            float *red = reinterpret_cast<float *>(adj_smem);  // [KB][256], inside the staging buffers
+            __syncthreads();  // every warp is done with the staging buffers
 #pragma unroll
-            for (int k = 0; k < KB; ++k) dst[(size_t)(k0 + k) * a.img_stride + (size_t)f * N * N + (size_t)i * N + j] = acc[k];
+            for (int k = 0; k < KB; ++k) red[k * 256 + tid] = acc[k];
+            cl.sync();
+            if (seg == 0) {
+                for (int q = 1; q < segs; ++q) {
+                    const float *rq = cl.map_shared_rank(red, q);
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) acc[k] += rq[k * 256 + tid];
+                }
+            }
+            cl.sync();  // the others keep their shared memory until CTA 0 has read it
         }
-    }
-}
-
-__global__ void k_adj_combine(float *__restrict__ X, const float *__restrict__ P, int segs, long long stride,
-                              long long total, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        float s = X[e];
-        for (int q = 1; q < segs; ++q) s += P[(q - 1) * stride + e];
-        X[e] = s;
+        const int i = i0 + ty, j = j0 + tx;
+        if (seg == 0 && i < N && j < N) {
+#pragma unroll
+            for (int k = 0; k < KB; ++k) a.X[(size_t)(k0 + k) * a.img_stride + (size_t)f * N * N + (size_t)i * N + j] = acc[k];
+        }
     }
 }
 
 template <int KB, int VB>
 cudaError_t launch_adj_band_kb(const Handle &h, const AdjBandArgs &a)
 {
+    static_assert(KB * 256 * sizeof(float) <= 2 * VB * KB * kWin * sizeof(float2), "segment sums fit the buffers");
     auto kern = k_adj_band<KB, VB>;
     const size_t smem = (size_t)2 * VB * KB * kWin * sizeof(float2);
     static bool attr_set = false;  // per instantiation; the attribute is idempotent, so a race is harmless
@@ -211,9 +222,21 @@ cudaError_t launch_adj_band_kb(const Handle &h, const AdjBandArgs &a)
         attr_set = true;
     }
     const long long items = (long long)a.ngroups * a.F * a.tps * a.tps * a.segs;
-    const int grid = persistent_grid(kern, 256, smem, items, h.num_sms);
-    kern<<<grid, 256, smem, h.stream>>>(a);
-    return cudaGetLastError();
+    int grid = persistent_grid(kern, 256, smem, items, h.num_sms);
+    grid -= grid % a.segs;  // whole clusters (items is a multiple of segs, so grid >= segs)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.segs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <int VB>
@@ -231,8 +254,7 @@ cudaError_t launch_adj_band_vb(const Handle &h, const AdjBandArgs &a, int kb)
 
 bool adj_band_ok(const Handle &h, int stage, int segs)
 {
-    return (stage == 8 || stage == 16) && (segs == 1 || segs == 2 || segs == 4) && h.Pb >= kWin &&
-           (h.Pb & 1) == 0 && (segs == 1 || h.d_segpart != nullptr);
+    return (stage == 8 || stage == 16) && (segs == 1 || segs == 2 || segs == 4) && h.Pb >= kWin && (h.Pb & 1) == 0;
 }
 
 cudaError_t launch_adjoint_band(const Handle &h, float *X, int batch, int kb, int segs, int stage, const int *skip)
@@ -252,8 +274,6 @@ cudaError_t launch_adjoint_band(const Handle &h, float *X, int batch, int kb, in
     a.X = X;
     a.img_stride = (long long)h.F * h.N * h.N;
     a.segs = segs;
-    a.part = (float *)h.d_segpart;
-    a.part_stride = (long long)h.max_batch * h.F * h.N * h.N;
     a.skip = skip;
     int k = 0;
     for (int width : {8, 4, 2, 1}) {
@@ -265,13 +285,6 @@ cudaError_t launch_adjoint_band(const Handle &h, float *X, int batch, int kb, in
         cudaError_t e = stage == 8 ? launch_adj_band_vb<8>(h, a, width) : launch_adj_band_vb<16>(h, a, width);
         if (e != cudaSuccess) return e;
         k += groups * width;
-    }
-    if (segs > 1) {
-        const long long total = (long long)batch * a.img_stride;
-        if (total > 0) {
-            const long long blocks = std::min<long long>((total + 255) / 256, (long long)h.num_sms * 8);
-            k_adj_combine<<<(int)blocks, 256, 0, h.stream>>>(X, a.part, segs, a.part_stride, total, skip);
-        }
     }
     return cudaGetLastError();
 }

@@ -136,8 +136,8 @@ int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void 
     return CT_OK;
 }
 
-// Workspace of the staged forward and transpose with several CTAs per ray or
-// pixel tile (segment partials), allocated the first time such a shape is set.
+// Workspace of the staged forward with several CTAs per ray (segment
+// partials), allocated the first time such a shape is set.
 int ensure_seg_partials(ctgb::Handle &h)
 {
     if (h.d_segpart || h.precision != 0) return CT_OK;
@@ -291,7 +291,7 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
             if (kb > K) continue;
             for (int st : {0, 8, 16}) {
                 for (int sp : {1, 2, 4}) {
-                    if (st > 0 && (!fp32 || (sp > 1 && ensure_seg_partials(h) != CT_OK) || !ctgb::adj_band_ok(h, st, sp)))
+                    if (st > 0 && (!fp32 || !ctgb::adj_band_ok(h, st, sp)))
                         continue;
                     const float ms = time_config(h.stream, [&] {
                         ctgb::launch_pairs_sino<T>(h, X, K);
@@ -629,7 +629,7 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
         (in[8] == 0 && in[5] * in[6] > 16) || !stage_ok(in[7], in[2]) || !stage_ok(in[8], in[6]) ||
         (in[7] > 0 && in[1] > 4) || (in[9] != 0 && in[9] != 8 && in[9] != 16) || !pow2(in[10], 4))
         return CT_ERR_ARG;
-    if ((in[7] > 0 && in[1] > 1) || (in[9] > 0 && in[4] > 1)) {
+    if (in[7] > 0 && in[1] > 1) {
         const int rc = ensure_seg_partials(H->h);
         if (rc != CT_OK) return rc;
     }

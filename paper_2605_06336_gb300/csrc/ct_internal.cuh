@@ -71,7 +71,8 @@ struct __align__(16) ViewGeo {
 // stage: 0 = gather through L1; 4 or 8 = rows per block of the band-staged
 // FP32 march (vw 4 or 8).  There the forward's split is the number of CTAs
 // that share one ray (row segments, combined by a second kernel); the
-// derivative kernels march whole rays.
+// derivative kernels march whole rays.  The staged transpose's split is the
+// number of CTAs per pixel tile, one thread-block cluster.
 struct Tuning {
     int fwd_kb = 8, fwd_split = 2, fwd_vw = 1;  // forward projection of a batch
     int adj_kb = 8, adj_split = 2;              // transpose of a batch
@@ -97,9 +98,9 @@ struct Handle {
     void *d_pt = nullptr;     // pair images, rows of X^T: (max_batch + 1) * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
     double *d_partial = nullptr;  // per (image, view, chunk) reduction partials, 4 per item, max_batch images
-    void *d_segpart = nullptr;    // segment partials of the staged forward (sinograms) and transpose
-                                  // (images): 3 * max_batch * max(V * B, F * N * N) floats, allocated
-                                  // when a shape with several CTAs per ray or tile is set
+    void *d_segpart = nullptr;    // segment partials of the staged forward (sinograms):
+                                  // 3 * max_batch * max(V * B, F * N * N) floats, allocated
+                                  // when a shape with several CTAs per ray is set
     int nchunks = 0;              // ceil(B / kChunk)
     double fan_D = 0.0;           // > 0: fan beam with the source at this distance (ct_fan.cu); 0: parallel
     void *d_rays = nullptr;       // fan beam: per-ray table, V * B entries
