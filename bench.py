@@ -65,8 +65,9 @@ TRAFFIC_PER_FOOTPRINT = {
 
 def launches_per_step(t):
     """Kernels of one bench step at launch shapes t (the ct_get_tuning values):
-    forward, J and J^T lay out their image and the transpose its sinograms
-    (1 each; the same launch brings the view table up to date); the forward
+    forward and J lay out their images and the transpose its sinograms (1
+    each; the same launch brings the view table up to date), J^T reuses the
+    layout of the J call and brings the view table up to date (1); the forward
     ray kernel(s) over the 8-image block, the transpose, the JVP, the VJP and
     its per-view reduction; the staged forward with several CTAs per ray adds
     a combining kernel (the staged transpose combines its CTAs per tile inside
@@ -467,7 +468,9 @@ def graph_step_timing(op, step, steps, flush):
 # ---------------------------------------------------------------------------
 class OperatorStep:
     """H on K images, H^T on K sinograms, J dtheta and J^T r on one image, through
-    the C ABI on op's handle, with the inputs resident on the device."""
+    the C ABI on op's handle, with the inputs resident on the device.  J^T is
+    taken at the image of the J call, whose pair layouts it uses again (x =
+    NULL), as a Gauss-Newton step does."""
 
     def __init__(self, w, K, dtype, dev, tuning=None, delta=None, seed=100):
         import torch
@@ -503,7 +506,8 @@ class OperatorStep:
         return [lambda: ct.ct_forward(op.h, th, dl, self.X, self.Y, K),
                 lambda: ct.ct_adjoint(op.h, th, dl, self.Ys, self.Xa, K),
                 lambda: ct.ct_jac(op.h, th, dl, self.X[0], self.dth, None, self.dy),
-                lambda: ct.ct_jacT(op.h, th, dl, self.X[0], self.Y[0], self.gt, None)]
+                # J^T at the image of the J call: its layouts are used again (x = NULL)
+                lambda: ct.ct_jacT(op.h, th, dl, None, self.Y[0], self.gt, None)]
 
     def step(self, ev=None, stream=None):
         for i, c in enumerate(self.calls()):
@@ -821,7 +825,7 @@ def batched_frames(dev, steps, flush):
         ct.ct_forward(op.h, th, None, X, Y, K)
         ct.ct_adjoint(op.h, th, None, Ys, Xa, K)
         ct.ct_jac(op.h, th, None, X[0], dth, None, dy)
-        ct.ct_jacT(op.h, th, None, X[0], Ys[0], gt, None)
+        ct.ct_jacT(op.h, th, None, None, Ys[0], gt, None)  # the image of the J call
 
     ms = graph_step_timing(op, step, steps, flush)
     samples = w.V * w.B * (K + K + 1 + 1)
@@ -858,7 +862,7 @@ def fan_beam_step(dev, steps, flush):
         ct.ct_forward(op.h, th, None, X, Y, K)
         ct.ct_adjoint(op.h, th, None, Ys, Xa, K)
         ct.ct_jac(op.h, th, None, X[0], dth, None, dy)
-        ct.ct_jacT(op.h, th, None, X[0], Ys[0], gt, None)
+        ct.ct_jacT(op.h, th, None, None, Ys[0], gt, None)  # the image of the J call
 
     ms = graph_step_timing(op, step, steps, flush)
     samples = w.V * w.B * (K + K + 1 + 1)
@@ -1015,7 +1019,7 @@ def main():
             ct.ct_forward(op.h, sl["theta"], None, sl["X"], sl["Y"], K)
             ct.ct_adjoint(op.h, sl["theta"], None, sl["Ys"], sl["Xa"], K)
             ct.ct_jac(op.h, sl["theta"], None, sl["X"][0], sl["dth"], None, sl["dy"])
-            ct.ct_jacT(op.h, sl["theta"], None, sl["X"][0], sl["Y"][0], sl["gt"], None)
+            ct.ct_jacT(op.h, sl["theta"], None, None, sl["Y"][0], sl["gt"], None)  # the image of the J call
             ev_done[j].record(stream)
             with torch.cuda.stream(s_down):
                 s_down.wait_event(ev_done[j])
@@ -1122,7 +1126,8 @@ def main():
                   "note": "the same step as individual launches (per-op times below)"},
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "C2: 256x256 random-ellipse phantom, 180 views (1 deg angle errors), 363 bins; "
-                               "step = H on 8 images + H^T on 8 sinograms + J dtheta + J^T r",
+                               "step = H on 8 images + H^T on 8 sinograms + J dtheta + J^T r at one image "
+                               "(J^T reuses the image layout of the J call)",
                    "krylov_block": K, "samples_per_step": samples_per_step,
                    "l2": "flushed between timed steps (512 MB write, outside the events)",
                    "launch": "step captured once in a CUDA graph and replayed (value); eager launches under 'eager'",

@@ -101,6 +101,18 @@ void ct_destroy(ct_handle *h);
  * "H u" in the residual of every MM-GKS step, Eq. (3.6), Alg. "Enlarge").
  *   theta  [n_views] radians; delta [n_views] bins or NULL (zero offsets)
  *   X      [batch][n_frames][N][N]      Y [batch][n_views][B]
+ *
+ * Image reuse (this call, ct_jac, ct_jacT, ct_gn_terms and the batched
+ * forms): every call that takes images lays them out in the handle (pairs
+ * of neighbouring pixels along rows and along columns).  Passing X (x) =
+ * NULL uses the layouts of the previous such call on the handle again,
+ * i.e. that call's first `batch` images, at this call's angles and offsets:
+ * the Jacobian and its transpose at one image (a Gauss-Newton step, an
+ * inner least-squares solve on J) then lay the image out once.  CT_ERR_ARG
+ * when no layouts are current (none yet, or an error, ct_autotune or a
+ * solver call on the handle since) or batch exceeds that call's.  Calls
+ * that take no image (ct_adjoint, the repeats) keep them.  No counterpart
+ * in the paper.
  */
 int ct_forward(ct_handle *h, const double *theta, const double *delta,
                const void *X, void *Y, int batch);
@@ -135,7 +147,8 @@ int ct_adjoint_repeat(ct_handle *h, void *X, int batch);
  * (the columns H_{p_i} u of Alg. "UPDATE-PARAM").  The derivative of the
  * linear interpolation uses the slope of the cell floor(u) (right derivative
  * at integer u).
- *   x [n_frames][N][N], dtheta [n_views] (device, double),
+ *   x [n_frames][N][N] or NULL (the image of the previous call, see
+ *   ct_forward), dtheta [n_views] (device, double),
  *   ddelta [n_views] or NULL, dy [n_views][B]
  */
 int ct_jac(ct_handle *h, const double *theta, const double *delta,
@@ -148,7 +161,8 @@ int ct_jac(ct_handle *h, const double *theta, const double *delta,
  * with respect to p, (H_{p_i} u)^T (H u - b), appendix lemma on the
  * Lipschitz gradient).  Per-view sums are reduced in a fixed order (no
  * atomics): results are bitwise reproducible.
- *   x [n_frames][N][N], r [n_views][B], gtheta [n_views] (device double),
+ *   x [n_frames][N][N] or NULL (the image of the previous call, see
+ *   ct_forward), r [n_views][B], gtheta [n_views] (device double),
  *   gdelta [n_views] or NULL
  */
 int ct_jacT(ct_handle *h, const double *theta, const double *delta,
@@ -162,7 +176,8 @@ int ct_jacT(ct_handle *h, const double *theta, const double *delta,
  *   fval[v]   = 1/2 sum_b res[v,b]^2
  * With per-view angles the Gauss-Newton matrix J^T J of Alg. "UPDATE-PARAM"
  * is diagonal, so these four arrays are all the parameter update needs.
- * grad, jnorm2, fval: [n_views] device double (fval may be NULL).
+ * grad, jnorm2, fval: [n_views] device double (fval may be NULL); x may be
+ * NULL (the image of the previous call, see ct_forward).
  */
 int ct_gn_terms(ct_handle *h, const double *theta, const double *delta,
                 const void *x, const void *bdata, void *res, double *grad,
@@ -191,6 +206,8 @@ int ct_gn_terms(ct_handle *h, const double *theta, const double *delta,
  * ct_gn_terms_batch: the four ct_gn_terms outputs for each image, against
  *   data bdata [batch][n_views][B]: res [batch][n_views][B] (nullable),
  *   grad, jnorm2, fval (nullable) [batch][n_views].
+ * X may be NULL: the first `batch` images of the previous call that took
+ * images (see ct_forward).
  * CT_ERR_ARG for batch out of range, null required pointers or unknown flags.
  */
 #define CT_BATCH_PER_IMAGE_DIRECTION 1

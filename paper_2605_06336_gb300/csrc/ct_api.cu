@@ -60,10 +60,20 @@ void free_all(ctgb::Handle &h)
     h.d_segpart = nullptr;
 }
 
+// The pair layouts of the call's images and the view table.  X == null: the
+// layouts left by the previous call that took images are current (the caller
+// checked h.img_ready); only the view table is brought up to date.
+template <typename T>
+cudaError_t prep_images(const ctgb::Handle &h, const T *X, int nimg, const double *theta, const double *delta)
+{
+    if (X) return ctgb::launch_pairs_img<T>(h, X, nimg, nullptr, theta, delta);
+    return ctgb::launch_view_setup(h, theta, delta);
+}
+
 template <typename T>
 int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
-    CT_CUDA(ctgb::launch_prep_forward<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)X, batch * h.F, theta, delta));
     CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
     return CT_OK;
 }
@@ -80,7 +90,7 @@ template <typename T>
 int do_jac(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const double *dtheta,
            const double *ddelta, void *dy)
 {
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)x, h.F, theta, delta));
     CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dy, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
     return CT_OK;
 }
@@ -89,7 +99,7 @@ template <typename T>
 int do_jacT(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *r, double *gtheta,
             double *gdelta)
 {
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)x, h.F, theta, delta));
     CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)r, gtheta, gdelta, h.tune.der_split, h.tune.der_vw, h.tune.der_stage));
     return CT_OK;
 }
@@ -99,7 +109,7 @@ int do_jac_batch(ctgb::Handle &h, const double *theta, const double *delta, cons
                  const double *ddelta, void *dY, int batch, int flags)
 {
     const long long dstride = (flags & CT_BATCH_PER_IMAGE_DIRECTION) ? h.V : 0;
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)X, batch * h.F, theta, delta));
     CT_CUDA(ctgb::launch_jvp<T>(h, dtheta, ddelta, (T *)dY, h.tune.der_split, h.tune.der_vw, h.tune.der_stage, batch,
                                 h.tune.der_kb, dstride));
     return CT_OK;
@@ -110,7 +120,7 @@ int do_jacT_batch(ctgb::Handle &h, const double *theta, const double *delta, con
                   double *gtheta, double *gdelta, int batch, int flags)
 {
     const long long rstride = (flags & CT_BATCH_SHARED_R) ? 0 : (long long)h.V * h.B;
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)X, batch * h.F, theta, delta));
     CT_CUDA(ctgb::launch_vjp<T>(h, (const T *)R, gtheta, gdelta, h.tune.der_split, h.tune.der_vw, h.tune.der_stage,
                                 batch, h.tune.der_kb, rstride, (flags & CT_BATCH_SUM) ? 1 : 0));
     return CT_OK;
@@ -120,7 +130,7 @@ template <typename T>
 int do_gn_batch(ctgb::Handle &h, const double *theta, const double *delta, const void *X, const void *bdata,
                 void *res, double *grad, double *jnorm2, double *fval, int batch)
 {
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)X, batch * h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)X, batch * h.F, theta, delta));
     CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw,
                                h.tune.der_stage, nullptr, nullptr, batch, h.tune.der_kb));
     return CT_OK;
@@ -130,7 +140,7 @@ template <typename T>
 int do_gn(ctgb::Handle &h, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
           double *grad, double *jnorm2, double *fval)
 {
-    CT_CUDA(ctgb::launch_pairs_img<T>(h, (const T *)x, h.F, nullptr, theta, delta));
+    CT_CUDA(prep_images<T>(h, (const T *)x, h.F, theta, delta));
     CT_CUDA(ctgb::launch_gn<T>(h, (const T *)bdata, (T *)res, grad, jnorm2, fval, h.tune.der_split, h.tune.der_vw,
                                   h.tune.der_stage));
     return CT_OK;
@@ -372,6 +382,16 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
 
 }  // namespace
 
+// After an operator call that took images (X) or reused the current layouts
+// (X == null): the handle's layouts now hold the call's `batch` images, or
+// (after an error) nothing usable.
+int images_laid_out(ctgb::Handle &h, const void *X, int batch, int rc)
+{
+    if (rc != CT_OK) h.img_ready = 0;
+    else if (X) h.img_ready = batch;
+    return rc;
+}
+
 extern "C" {
 
 int ct_init(const ct_geom *g, void *cuda_stream, ct_handle **out)
@@ -494,12 +514,13 @@ void ct_destroy(ct_handle *H)
 
 int ct_forward(ct_handle *H, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
-    if (!H || !theta || !X || !Y || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
+    if (!H || !theta || !Y || batch < 1 || batch > H->h.max_batch || (!X && batch > H->h.img_ready))
+        return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
     const int rc = H->h.precision ? do_forward<double>(H->h, theta, delta, X, Y, batch)
                                   : do_forward<float>(H->h, theta, delta, X, Y, batch);
     if (rc == CT_OK) H->h.fwd_ready = batch;
-    return rc;
+    return images_laid_out(H->h, X, batch, rc);
 }
 
 int ct_forward_repeat(ct_handle *H, void *Y, int batch)
@@ -539,59 +560,67 @@ int ct_adjoint(ct_handle *H, const double *theta, const double *delta, const voi
 int ct_jac(ct_handle *H, const double *theta, const double *delta, const void *x, const double *dtheta,
            const double *ddelta, void *dy)
 {
-    if (!H || !theta || !x || !dtheta || !dy) return CT_ERR_ARG;
+    if (!H || !theta || (!x && H->h.img_ready < 1) || !dtheta || !dy) return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
-    return H->h.precision ? do_jac<double>(H->h, theta, delta, x, dtheta, ddelta, dy)
-                          : do_jac<float>(H->h, theta, delta, x, dtheta, ddelta, dy);
+    return images_laid_out(H->h, x, 1,
+                           H->h.precision ? do_jac<double>(H->h, theta, delta, x, dtheta, ddelta, dy)
+                                          : do_jac<float>(H->h, theta, delta, x, dtheta, ddelta, dy));
 }
 
 int ct_jacT(ct_handle *H, const double *theta, const double *delta, const void *x, const void *r, double *gtheta,
             double *gdelta)
 {
-    if (!H || !theta || !x || !r || !gtheta) return CT_ERR_ARG;
+    if (!H || !theta || (!x && H->h.img_ready < 1) || !r || !gtheta) return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
-    return H->h.precision ? do_jacT<double>(H->h, theta, delta, x, r, gtheta, gdelta)
-                          : do_jacT<float>(H->h, theta, delta, x, r, gtheta, gdelta);
+    return images_laid_out(H->h, x, 1,
+                           H->h.precision ? do_jacT<double>(H->h, theta, delta, x, r, gtheta, gdelta)
+                                          : do_jacT<float>(H->h, theta, delta, x, r, gtheta, gdelta));
 }
 
 int ct_gn_terms(ct_handle *H, const double *theta, const double *delta, const void *x, const void *bdata, void *res,
                 double *grad, double *jnorm2, double *fval)
 {
-    if (!H || !theta || !x || !bdata || !grad || !jnorm2) return CT_ERR_ARG;
+    if (!H || !theta || (!x && H->h.img_ready < 1) || !bdata || !grad || !jnorm2) return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
-    return H->h.precision ? do_gn<double>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval)
-                          : do_gn<float>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval);
+    return images_laid_out(H->h, x, 1,
+                           H->h.precision ? do_gn<double>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval)
+                                          : do_gn<float>(H->h, theta, delta, x, bdata, res, grad, jnorm2, fval));
 }
 
 int ct_jac_batch(ct_handle *H, const double *theta, const double *delta, const void *X, const double *dtheta,
                  const double *ddelta, void *dY, int batch, int flags)
 {
-    if (!H || !theta || !X || !dtheta || !dY || batch < 1 || batch > H->h.max_batch ||
+    if (!H || !theta || !dtheta || !dY || batch < 1 || batch > H->h.max_batch || (!X && batch > H->h.img_ready) ||
         (flags & ~CT_BATCH_PER_IMAGE_DIRECTION))
         return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
-    return H->h.precision ? do_jac_batch<double>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags)
-                          : do_jac_batch<float>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags);
+    return images_laid_out(H->h, X, batch,
+                           H->h.precision ? do_jac_batch<double>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags)
+                                          : do_jac_batch<float>(H->h, theta, delta, X, dtheta, ddelta, dY, batch, flags));
 }
 
 int ct_jacT_batch(ct_handle *H, const double *theta, const double *delta, const void *X, const void *R,
                   double *gtheta, double *gdelta, int batch, int flags)
 {
-    if (!H || !theta || !X || !R || !gtheta || batch < 1 || batch > H->h.max_batch ||
+    if (!H || !theta || !R || !gtheta || batch < 1 || batch > H->h.max_batch || (!X && batch > H->h.img_ready) ||
         (flags & ~(CT_BATCH_SHARED_R | CT_BATCH_SUM)))
         return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
-    return H->h.precision ? do_jacT_batch<double>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags)
-                          : do_jacT_batch<float>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags);
+    return images_laid_out(H->h, X, batch,
+                           H->h.precision ? do_jacT_batch<double>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags)
+                                          : do_jacT_batch<float>(H->h, theta, delta, X, R, gtheta, gdelta, batch, flags));
 }
 
 int ct_gn_terms_batch(ct_handle *H, const double *theta, const double *delta, const void *X, const void *bdata,
                       void *res, double *grad, double *jnorm2, double *fval, int batch)
 {
-    if (!H || !theta || !X || !bdata || !grad || !jnorm2 || batch < 1 || batch > H->h.max_batch) return CT_ERR_ARG;
+    if (!H || !theta || !bdata || !grad || !jnorm2 || batch < 1 || batch > H->h.max_batch ||
+        (!X && batch > H->h.img_ready))
+        return CT_ERR_ARG;
     H->h.fwd_ready = H->h.adj_ready = 0;
-    return H->h.precision ? do_gn_batch<double>(H->h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch)
-                          : do_gn_batch<float>(H->h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch);
+    return images_laid_out(H->h, X, batch,
+                           H->h.precision ? do_gn_batch<double>(H->h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch)
+                                          : do_gn_batch<float>(H->h, theta, delta, X, bdata, res, grad, jnorm2, fval, batch));
 }
 
 int ct_set_stream(ct_handle *H, void *cuda_stream)
@@ -604,7 +633,7 @@ int ct_set_stream(ct_handle *H, void *cuda_stream)
 int ct_autotune(ct_handle *H)
 {
     if (!H) return CT_ERR_ARG;
-    H->h.fwd_ready = H->h.adj_ready = 0;
+    H->h.fwd_ready = H->h.adj_ready = H->h.img_ready = 0;
     return H->h.precision ? autotune_impl<double>(H->h) : autotune_impl<float>(H->h);
 }
 

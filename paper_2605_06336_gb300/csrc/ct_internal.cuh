@@ -111,6 +111,11 @@ struct Handle {
     // (ct_adjoint_repeat) may rerun the projection kernel alone.  Any other
     // call that may change the view table or the pair layouts clears them.
     int fwd_ready = 0, adj_ready = 0;
+    // Images (of F frames) whose pair layouts are current from the last
+    // operator call that took images: a later call may pass X = null to use
+    // them again (its batch at most this).  The solvers and the autotuner,
+    // which lay out images of their own, clear it.
+    int img_ready = 0;
     int num_sms = 0;
     Tuning tune;
 };

@@ -1034,7 +1034,7 @@ int nlrmm_gks_solve(ct_handle *H, const void *b, double *theta_inout, const doub
         (o.shared_offset && o.varpro))
         return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
-    h.fwd_ready = h.adj_ready = 0;
+    h.fwd_ready = h.adj_ready = h.img_ready = 0;
     // The solve runs on a private stream ordered after the work already queued
     // on the handle's stream; it synchronises before returning.
     cudaStream_t ps = nullptr;
@@ -1084,7 +1084,7 @@ int nlrmm_stream_solve(ct_handle *const *blocks, int nblocks, const void *const 
         if (o.lam_fix <= 0.0 && !(noise_norms[j] > 0.0)) return CT_ERR_ARG;
         hs[j] = &hj;
     }
-    for (int j = 0; j < nblocks; ++j) blocks[j]->h.fwd_ready = blocks[j]->h.adj_ready = 0;
+    for (int j = 0; j < nblocks; ++j) blocks[j]->h.fwd_ready = blocks[j]->h.adj_ready = blocks[j]->h.img_ready = 0;
     ctgb::Handle &h = blocks[0]->h;
     cudaStream_t ps = nullptr;
     cudaEvent_t e0 = nullptr;
@@ -1127,7 +1127,7 @@ int nlrmm_varpro(ct_handle *H, const void *b, const double *theta, const double 
         (u_w && !(eps > 0.0)))
         return CT_ERR_ARG;
     ctgb::Handle &h = H->h;
-    h.fwd_ready = h.adj_ready = 0;
+    h.fwd_ready = h.adj_ready = h.img_ready = 0;
     nlrmm_opts o;
     nlrmm_default_opts(&o);
     o.k_min = 2;
@@ -1182,7 +1182,7 @@ int nlrmm_varpro_update(ct_handle *H, const void *b, double *theta_inout, const 
         o.plain = opts->plain;
     }
     ctgb::Handle &h = H->h;
-    h.fwd_ready = h.adj_ready = 0;
+    h.fwd_ready = h.adj_ready = h.img_ready = 0;
     o.k_min = 2;
     o.k_max = std::max(k, 3);
     o.eps = u_w ? eps : 1e-3;

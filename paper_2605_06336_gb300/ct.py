@@ -447,10 +447,19 @@ class CTOperator:
             raise ValueError(f"{name}: expected contiguous float64 CUDA tensor of {self.V} views")
         return a
 
-    def forward(self, X, theta, delta=None, out=None):
-        self._chk(X, self.n, "X")
-        K = 1 if X.dim() == 1 else X.shape[0]
-        Y = out if out is not None else torch.empty(X.shape[:-1] + (self.m,), dtype=self.dtype, device=X.device)
+    def forward(self, X, theta, delta=None, out=None, batch=None):
+        """Y = H(theta, delta) X.  X = None: the images of the previous call on this
+        operator that took images (their layouts are reused), `batch` of them (1
+        by default)."""
+        if X is None:
+            K = int(batch or 1)
+            shape = (self.m,) if batch is None else (K, self.m)
+            dev = theta.device
+        else:
+            self._chk(X, self.n, "X")
+            K = 1 if X.dim() == 1 else X.shape[0]
+            shape, dev = X.shape[:-1] + (self.m,), X.device
+        Y = out if out is not None else torch.empty(shape, dtype=self.dtype, device=dev)
         ct_forward(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), X, Y, K)
         return Y
 
@@ -461,18 +470,24 @@ class CTOperator:
         ct_adjoint(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), Y, X, K)
         return X
 
+    def _img(self, x, name):
+        """x, checked; None (the image of the previous call that took one) passes."""
+        if x is not None:
+            self._chk(x, self.n, name)
+        return x
+
     def jac(self, x, theta, dtheta, delta=None, ddelta=None, out=None):
-        self._chk(x, self.n, "x")
-        dy = out if out is not None else torch.empty(self.m, dtype=self.dtype, device=x.device)
+        self._img(x, "x")
+        dy = out if out is not None else torch.empty(self.m, dtype=self.dtype, device=theta.device)
         ct_jac(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, self._ang(dtheta, "dtheta"),
                self._ang(ddelta, "ddelta"), dy)
         return dy
 
     def jacT(self, x, theta, r, delta=None, want_delta=False):
-        self._chk(x, self.n, "x")
+        self._img(x, "x")
         self._chk(r, self.m, "r")
-        gt = torch.empty(self.V, dtype=torch.float64, device=x.device)
-        gd = torch.empty(self.V, dtype=torch.float64, device=x.device) if want_delta else None
+        gt = torch.empty(self.V, dtype=torch.float64, device=r.device)
+        gd = torch.empty(self.V, dtype=torch.float64, device=r.device) if want_delta else None
         ct_jacT(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, r, gt, gd)
         return (gt, gd) if want_delta else gt
 
@@ -525,12 +540,12 @@ class CTOperator:
         return g, j2, f, res
 
     def gn_terms(self, x, theta, bdata, delta=None, want_residual=False):
-        self._chk(x, self.n, "x")
+        self._img(x, "x")
         self._chk(bdata, self.m, "bdata")
-        res = torch.empty(self.m, dtype=self.dtype, device=x.device) if want_residual else None
-        g = torch.empty(self.V, dtype=torch.float64, device=x.device)
-        j2 = torch.empty(self.V, dtype=torch.float64, device=x.device)
-        f = torch.empty(self.V, dtype=torch.float64, device=x.device)
+        res = torch.empty(self.m, dtype=self.dtype, device=bdata.device) if want_residual else None
+        g = torch.empty(self.V, dtype=torch.float64, device=bdata.device)
+        j2 = torch.empty(self.V, dtype=torch.float64, device=bdata.device)
+        f = torch.empty(self.V, dtype=torch.float64, device=bdata.device)
         ct_gn_terms(self.h, self._ang(theta, "theta"), self._ang(delta, "delta"), x, bdata, res, g, j2, f)
         return g, j2, f, res
 

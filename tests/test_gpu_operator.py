@@ -356,3 +356,57 @@ def test_repeat_reruns_the_projection_alone(ct):
     op.jac(X[0], th, dev(rng.standard_normal(V)))
     with pytest.raises(ct.CTError):
         ct.ct_adjoint_repeat(op.h, x1, 1)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_image_reuse_with_null_x(ct, dtype):
+    """x = NULL uses the pair layouts of the previous call that took images, at
+    the call's own angles: bit for bit what passing that image again gives; the
+    layouts survive calls that take no image and are refused when none is
+    current (a fresh handle, after ct_autotune, batch above the laid-out one)."""
+    N, B, vpf = 40, 57, [7, 5]
+    V = sum(vpf)
+    rng = np.random.default_rng(41)
+    op = ct.CTOperator(N, B, V, vpf, max_batch=4, dtype=dtype)
+    n = op.n
+    th1, th2 = dev(synth.random_angles(V, rng)), dev(synth.random_angles(V, rng))
+    dl = dev(rng.normal(0, 0.5, V))
+    X = dev(rng.uniform(size=(4, n)), dtype)
+    R = dev(rng.standard_normal((4, V * B)), dtype)
+    dth = dev(rng.standard_normal(V))
+    with pytest.raises(ct.CTError) as e:
+        op.jac(None, th1, dth)
+    assert e.value.code == ct.CT_ERR_ARG
+
+    y_ref = op.forward(X[:3], th2, dl).clone()
+    op.forward(X[:3], th1)
+    op.adjoint(R, th1)                       # takes no image: the layouts stay
+    assert torch.equal(op.forward(None, th2, dl, batch=3), y_ref)   # other angles, same images
+    with pytest.raises(ct.CTError):
+        op.forward(None, th1, batch=4)       # only 3 images are laid out
+    dy_ref = op.jac(X[0], th2, dth, dl).clone()
+    g_ref = op.jacT(X[1], th1, R[0], dl, want_delta=True)
+    gn_ref = op.gn_terms(X[1], th2, R[1], dl, want_residual=True)
+    op.jac(X[0], th1, dth)
+    assert torch.equal(op.jac(None, th2, dth, dl), dy_ref)
+    op.jacT(X[1], th2, R[3])
+    g = op.jacT(None, th1, R[0], dl, want_delta=True)
+    assert torch.equal(g[0], g_ref[0]) and torch.equal(g[1], g_ref[1])
+    gn = op.gn_terms(None, th2, R[1], dl, want_residual=True)
+    assert all(torch.equal(a, b) for a, b in zip(gn, gn_ref))
+    # batched forms: the first `batch` images of the last layout
+    op.forward(X, th1)
+    dY = torch.empty(2, V * B, dtype=dtype, device="cuda")
+    ct.ct_jac_batch(op.h, th2, None, None, dth, None, dY, 2)
+    assert torch.equal(dY, op.jac_batch(X[:2], th2, dth))
+    G = torch.empty(2, V, dtype=torch.float64, device="cuda")
+    ct.ct_jacT_batch(op.h, th1, None, None, R[:2], G, None, 2)
+    assert torch.equal(G, op.jacT_batch(X[:2], th1, R[:2]))
+    # and against the oracle, so a stale layout shared by both forms would show
+    g = oracle.Geometry(N, B, V, vpf)
+    yo = oracle.forward(g, host(th2), host(X[0]), host(dl))
+    assert rel(host(op.forward(None, th2, dl)), yo) <= TOL[dtype]
+    op.autotune()
+    with pytest.raises(ct.CTError):
+        op.jacT(None, th1, R[0])
+    op.close()
