@@ -195,10 +195,10 @@ template <typename T> struct Solver {
                                      (int)sizeof(SmallShared<kKSmem>)));
         if (KC > kKSmem) SV_TRY(alloc(small_work, kSmallWorkBytes / sizeof(double) + 1));
         if constexpr (sizeof(T) == 4) {
-            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gram_rb_smem(kKLimit, 3, 256)));
-            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_rb<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gram_rb_smem(kKLimit, 3, 512)));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_pipe8<2, kP8Threads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGramP8SmemMax));
+            SV_CUDA(cudaFuncSetAttribute(k_gram_psi_pipe8<1, kP8Threads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGramP8SmemMax));
             SV_CUDA(cudaFuncSetAttribute(k_gram_psi_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kGramPipeSmemMax));
         } else {
@@ -244,16 +244,16 @@ template <typename T> struct Solver {
     {
         const bool tm = o.temporal && h.F > 1;
         if constexpr (sizeof(T) == 4) {
-            const size_t pipe = gram_pipe_smem(k, tm ? 3 : 2);
-            const int nt = gram_rb_threads(k);
-            if (pipe <= kGramPipeSmemMax && nt == 256)  // both raw buffers fit next to the edge block
-                k_gram_psi_pipe<<<gram_blocks, kThreads, pipe, h.stream>>>(V, n, k, w, h.N, h.F, o.temporal,
-                                                                            part_gram, stop);
-            else if (nt == 256)
-                k_gram_psi_rb<256><<<gram_blocks, 256, gram_rb_smem(k, tm ? 3 : 2, 256), h.stream>>>(
+            const int epp = tm ? 3 : 2;
+            if (gram_pipe_smem(k, epp) <= kGramPipeSmemMax && gram_rb_threads(k) == 256)
+                // 4 x 4 blocks: both raw buffers fit next to the edge block, one thread per block pair
+                k_gram_psi_pipe<<<gram_blocks, kThreads, gram_pipe_smem(k, epp), h.stream>>>(
                     V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
-            else
-                k_gram_psi_rb<512><<<gram_blocks, 512, gram_rb_smem(k, tm ? 3 : 2, 512), h.stream>>>(
+            else if (gram_p8_rows(k, epp) == 2)  // larger bases: 2-row tiles, 8 x 8 blocks
+                k_gram_psi_pipe8<2, kP8Threads><<<gram_blocks, kP8Threads, gram_p8_smem(k, epp, 2), h.stream>>>(
+                    V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
+            else  // 1-row tiles (fits up to the largest basis)
+                k_gram_psi_pipe8<1, kP8Threads><<<gram_blocks, kP8Threads, gram_p8_smem(k, epp, 1), h.stream>>>(
                     V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
         } else {
             if (k <= kKSmem)

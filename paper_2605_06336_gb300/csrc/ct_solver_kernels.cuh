@@ -216,18 +216,17 @@ __global__ void __launch_bounds__(256) k_gram_psi(const T *__restrict__ V, long 
     }
 }
 
-// Register-blocked form for FP32 bases.  A tile is 4 x 32 pixels of one
-// frame; its edges (right, down, and with ANISO-TV the next frame) of all k
-// columns go to shared memory as rows E[e][0..KP) (KP = k rounded up to 32),
-// each 16-byte group of a row stored at group ^ (pixel & 7) so that the
-// float4 stores of 8 consecutive pixels fall in distinct bank groups.  The
-// k x k upper triangle is cut into 4 x 4 blocks; block pair (bi <= bj) and
-// edge phase ph go to one thread, which sums its edges e = ph, ph + phases, ...
-// with two float4 reads and 16 FMAs per edge.  Per tile the phases are added
-// in FP32 in shared memory and the sum goes to the owner's FP64 accumulators;
-// per-CTA FP64 partials as for k_gram_psi.
-// NT threads (256, or 512 for bases above 88 columns, whose 4 x 4 block pairs
-// outnumber 256 threads) each own one block pair.
+// 4 x 4 register blocks for FP32 bases (k_gram_psi_pipe below).  A tile is
+// 4 x 32 pixels of one frame; its edges (right, down, and with ANISO-TV the
+// next frame) of all k columns go to shared memory as rows E[e][0..KP) (KP = k
+// rounded up to 32), each 16-byte group of a row stored at group ^ (pixel & 7)
+// so that the float4 stores of 8 consecutive pixels fall in distinct bank
+// groups.  The k x k upper triangle is cut into 4 x 4 blocks; block pair
+// (bi <= bj) and edge phase ph go to one thread, which sums its edges e = ph,
+// ph + phases, ... with two float4 reads and 16 FMAs per edge.  Per tile the
+// phases are added in FP32 in shared memory and the sum goes to the owner's
+// FP64 accumulators; per-CTA FP64 partials as for k_gram_psi.  Up to 256
+// block pairs (k <= 88).
 constexpr int kRbRows = 4;                      // tile rows
 constexpr int kRbPix = kRbRows * 32;            // tile pixels
 inline size_t gram_rb_smem(int k, int epp, int nt = 256)
@@ -242,118 +241,10 @@ inline int gram_rb_threads(int k)
     return kb * (kb + 1) / 2 <= 256 ? 256 : 512;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_gram_psi_rb(const float *__restrict__ V, long long n, int k,
-                                                    const float *__restrict__ w, int N, int F, int temporal,
-                                                    double *__restrict__ part, const int *stop)
-{
-    if (stopped(stop)) return;
-    extern __shared__ float4 rb_smem[];
-    const int EPP = (temporal && F > 1) ? 3 : 2;
-    const int KP = 32 * ((k + 31) / 32);
-    const int NE = EPP * kRbPix;
-    float *E = reinterpret_cast<float *>(rb_smem);  // [NE][KP], swizzled 16-byte groups
-    float *red = E + (size_t)NE * KP;               // [NT][16]
-    const int kb = (k + 3) / 4;
-    const int P = kb * (kb + 1) / 2;
-    const int phases = max(1, min(8, NT / P));
-    const int t = threadIdx.x;
-    const bool busy = t < P * phases;
-    const int p = t % P, ph = t / P;
-    int bi = 0, rem = p;
-    while (rem >= kb - bi) {
-        rem -= kb - bi;
-        ++bi;
-    }
-    const int bj = bi + rem;
-    double acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-    const int tiles_x = (N + 31) / 32, tiles_y = (N + kRbRows - 1) / kRbRows;
-    const int ntiles = tiles_x * tiles_y * F;
-    const long long nx = (long long)F * N * (N - 1);
-    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-        const int tile = tt % (tiles_x * tiles_y);
-        const int f = tt / (tiles_x * tiles_y);
-        const int i0 = (tile / tiles_x) * kRbRows, j0 = (tile % tiles_x) * 32;
-        const float *wx = w + (long long)f * N * (N - 1);
-        const float *wy = w + nx + (long long)f * (N - 1) * N;
-        const float *wt = w + 2 * nx + (long long)f * N * N;
-        __syncthreads();  // the previous tile is done with E and red
-        // edges: thread = (column group of 4, pixel); consecutive threads take consecutive pixels
-        for (int idx = t; idx < kb * kRbPix; idx += NT) {
-            const int g = idx / kRbPix, pix = idx % kRbPix;
-            const int i = i0 + pix / 32, j = j0 + pix % 32;
-            float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, et[4] = {0.f, 0.f, 0.f, 0.f};
-            if (i < N && j < N) {
-                const float sx = j < N - 1 ? sqrtf(wx[i * (N - 1) + j]) : 0.f;
-                const float sy = i < N - 1 ? sqrtf(wy[i * N + j]) : 0.f;
-                const float st = (EPP == 3 && f < F - 1) ? sqrtf(wt[(size_t)i * N + j]) : 0.f;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int a = 4 * g + c;
-                    if (a < k) {
-                        const float *va = V + (long long)a * n + (long long)f * N * N;
-                        const float v0 = va[(size_t)i * N + j];
-                        if (j < N - 1) ex[c] = (va[(size_t)i * N + j + 1] - v0) * sx;
-                        if (i < N - 1) ey[c] = (va[(size_t)(i + 1) * N + j] - v0) * sy;
-                        if (EPP == 3 && f < F - 1) et[c] = (va[(size_t)N * N + (size_t)i * N + j] - v0) * st;
-                    }
-                }
-            }
-            const int col = (4 * g) ^ ((pix & 7) << 2);
-            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix) * KP + col) = make_float4(ex[0], ex[1], ex[2], ex[3]);
-            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 1) * KP + col) =
-                make_float4(ey[0], ey[1], ey[2], ey[3]);
-            if (EPP == 3)
-                *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 2) * KP + col) =
-                    make_float4(et[0], et[1], et[2], et[3]);
-        }
-        __syncthreads();
-        if (busy) {
-            float s[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) s[q] = 0.f;
-            for (int e = ph; e < NE; e += phases) {
-                const int sw = ((e / EPP) & 7) << 2;
-                const float4 A = *reinterpret_cast<const float4 *>(E + (size_t)e * KP + ((4 * bi) ^ sw));
-                const float4 Bv = *reinterpret_cast<const float4 *>(E + (size_t)e * KP + ((4 * bj) ^ sw));
-                const float av[4] = {A.x, A.y, A.z, A.w}, bv[4] = {Bv.x, Bv.y, Bv.z, Bv.w};
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) s[4 * r + c] = fmaf(av[r], bv[c], s[4 * r + c]);
-            }
-#pragma unroll
-            for (int q = 0; q < 16; q += 4)
-                *reinterpret_cast<float4 *>(red + (size_t)t * 16 + q) = make_float4(s[q], s[q + 1], s[q + 2], s[q + 3]);
-        }
-        __syncthreads();
-        if (t < P) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float v = 0.f;
-                for (int r = 0; r < phases; ++r) v += red[(size_t)(r * P + t) * 16 + q];
-                acc[q] += (double)v;
-            }
-        }
-    }
-    if (t < P) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int a = 4 * bi + q / 4, b = 4 * bj + q % 4;
-            if (a <= b && b < k) part[(long long)blockIdx.x * kGramPairs + a * k - a * (a - 1) / 2 + (b - a)] = acc[q];
-        }
-    }
-}
-
-// Pipelined form of k_gram_psi_rb: the raw values a tile needs (rows
-// i0 .. i0 + 4 and columns j0 .. j0 + 32 of every basis column, the next
-// frame's rows with ANISO-TV, and the tile's weights) are copied to shared
-// memory with cp.async, the next tile's while the current tile builds its
-// edges and runs its products, so the tile loads no longer stall the CTA.
-// Same edges, blocks, phases and summation order as k_gram_psi_rb: the
-// results are bit-identical.
+// The raw values a tile needs (rows i0 .. i0 + 4 and columns j0 .. j0 + 32
+// of every basis column, the next frame's rows with ANISO-TV, and the tile's
+// weights) are copied to shared memory with cp.async, the next tile's while
+// the current tile builds its edges and runs its products.
 constexpr int kRawRows = kRbRows + 1, kRawCols = 33;  // rows and columns of a tile's raw block
 constexpr size_t kGramPipeSmemMax = 200 * 1024;        // dynamic shared memory of the pipelined form
 inline int gram_raw_floats(int k, int epp)
@@ -526,6 +417,214 @@ __global__ void __launch_bounds__(256) k_gram_psi_pipe(const float *__restrict__
             const int a = 4 * bi + q / 4, b = 4 * bj + q % 4;
             if (a <= b && b < k) part[(long long)blockIdx.x * kGramPairs + a * k - a * (a - 1) / 2 + (b - a)] = acc[q];
         }
+    }
+}
+
+// Large bases (k above what the pipelined 4 x 4 form holds in shared memory):
+// the same cp.async pipeline over smaller tiles (TR = 2 or 1 rows of 32
+// pixels) with 8 x 8 register blocks.  Block pair (bi <= bj) and edge phase ph
+// go to one thread, which keeps its 64 sums in FP32 registers over kP8Flush
+// tiles (four float4 reads and 64 FMAs per edge, a quarter of the
+// shared-memory reads per FMA of the 4 x 4 blocks); every kP8Flush tiles and
+// after the CTA's last tile the threads leave their sums in shared memory and
+// the phases of each block pair are added in phase order, in FP64, to the
+// CTA's FP64 sums (also in shared memory).  Per-CTA FP64 partials as for
+// k_gram_psi; k_gram_reduce sums them in order.
+constexpr int kP8Flush = 16;     // tiles summed in FP32 between two FP64 flushes
+constexpr int kP8Threads = 384;  // threads of the large-basis form
+inline int gram_p8_pairs(int k)
+{
+    const int kb = (k + 7) / 8;
+    return kb * (kb + 1) / 2;
+}
+inline size_t gram_p8_smem(int k, int epp, int tr)
+{
+    const int kp = 32 * ((k + 31) / 32);
+    const size_t e = (size_t)epp * tr * 32 * kp * sizeof(float);
+    const size_t red = (size_t)kP8Threads * 32 * sizeof(float);
+    const size_t raw = (size_t)k * ((tr + 1) * kRawCols + (epp == 3 ? tr * 32 : 0)) + 3 * tr * 32;
+    return (e > red ? e : red) + 2 * raw * sizeof(float) + (size_t)gram_p8_pairs(k) * 64 * sizeof(double);
+}
+constexpr size_t kGramP8SmemMax = 226 * 1024;
+// tile rows of the large-basis form: 2, or 1 when two rows do not fit (0: neither fits)
+inline int gram_p8_rows(int k, int epp)
+{
+    return gram_p8_smem(k, epp, 2) <= kGramP8SmemMax ? 2 : (gram_p8_smem(k, epp, 1) <= kGramP8SmemMax ? 1 : 0);
+}
+
+template <int TR, int NT>
+__global__ void __launch_bounds__(NT, 1) k_gram_psi_pipe8(const float *__restrict__ V, long long n, int k,
+                                                          const float *__restrict__ w, int N, int F, int temporal,
+                                                          double *__restrict__ part, const int *stop)
+{
+    if (stopped(stop)) return;
+    extern __shared__ float4 p8_smem[];
+    constexpr int TPIX = TR * 32;
+    constexpr int RR = TR + 1;  // raw rows: the tile's and the one below
+    const int EPP = (temporal && F > 1) ? 3 : 2;
+    const int KP = 32 * ((k + 31) / 32);
+    const int NE = EPP * TPIX;
+    const size_t efl = max((size_t)NE * KP, (size_t)NT * 32);  // floats of E (and of the flush buffer)
+    float *E = reinterpret_cast<float *>(p8_smem);               // [NE][KP], swizzled 16-byte groups
+    const int RAWC = k * RR * kRawCols;                          // per buffer: [k][RR][33]
+    const int RAWT = EPP == 3 ? k * TPIX : 0;                    // then [k][TR][32] (next frame)
+    const int RAW = RAWC + RAWT + 3 * TPIX;                      // then the weights
+    float *raw0 = E + efl;
+    double *acc = reinterpret_cast<double *>(raw0 + 2 * (size_t)RAW);  // [P][64]
+    const int kb = (k + 7) / 8;
+    const int kg = (k + 3) / 4;  // column groups of 4 of the edge build
+    const int P = kb * (kb + 1) / 2;
+    const int phases = max(1, NT / P);
+    const int t = threadIdx.x;
+    const bool busy = t < P * phases;
+    const int p = t % P, ph = t / P;
+    int bi = 0, rem = p;
+    while (rem >= kb - bi) {
+        rem -= kb - bi;
+        ++bi;
+    }
+    const int bj = bi + rem;
+    for (int idx = t; idx < P * 64; idx += NT) acc[idx] = 0.0;
+    float s[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) s[q] = 0.f;
+    const int tiles_x = (N + 31) / 32, tiles_y = (N + TR - 1) / TR;
+    const int ntiles = tiles_x * tiles_y * F;
+    const long long nx = (long long)F * N * (N - 1);
+
+    // copies of tile tt into raw buffer dst
+    auto issue = [&](int tt, float *dst) {
+        const int tile = tt % (tiles_x * tiles_y);
+        const int f = tt / (tiles_x * tiles_y);
+        const int i0 = (tile / tiles_x) * TR, j0 = (tile % tiles_x) * 32;
+        for (int idx = t; idx < RAWC; idx += NT) {
+            const int a = idx / (RR * kRawCols), r = (idx / kRawCols) % RR, c = idx % kRawCols;
+            const int gi = i0 + r, gj = j0 + c;
+            const bool ok = gi < N && gj < N;
+            const float *col = V + (long long)a * n + (long long)f * N * N;
+            cp_async4_zfill(dst + idx, ok ? col + (size_t)gi * N + gj : col, ok);
+        }
+        for (int idx = t; idx < RAWT; idx += NT) {  // the next frame's pixels of the tile
+            const int a = idx / TPIX, r = (idx / 32) % TR, c = idx % 32;
+            const int gi = i0 + r, gj = j0 + c;
+            const bool ok = f < F - 1 && gi < N && gj < N;
+            const float *col = V + (long long)a * n + (long long)(f + 1 < F ? f + 1 : f) * N * N;
+            cp_async4_zfill(dst + RAWC + idx, ok ? col + (size_t)gi * N + gj : col, ok);
+        }
+        for (int idx = t; idx < 3 * TPIX; idx += NT) {  // weights of the right, down, next-frame edges
+            const int e = idx / TPIX, pix = idx % TPIX;
+            const int gi = i0 + pix / 32, gj = j0 + pix % 32;
+            bool ok;
+            long long off;
+            if (e == 0) {
+                ok = gi < N && gj < N - 1;
+                off = (long long)f * N * (N - 1) + (long long)gi * (N - 1) + gj;
+            } else if (e == 1) {
+                ok = gi < N - 1 && gj < N;
+                off = nx + (long long)f * (N - 1) * N + (long long)gi * N + gj;
+            } else {
+                ok = EPP == 3 && f < F - 1 && gi < N && gj < N;
+                off = 2 * nx + (long long)f * N * N + (long long)gi * N + gj;
+            }
+            cp_async4_zfill(dst + RAWC + RAWT + idx, ok ? w + off : w, ok);
+        }
+    };
+
+    int buf = 0, batch = 0;
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, raw0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const int nxt = tt + gridDim.x;
+        if (nxt < ntiles) issue(nxt, raw0 + (size_t)(buf ^ 1) * RAW);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // tile tt has landed
+        __syncthreads();  // ... for every thread; the previous tile (or flush) is done with E
+        const float *rw = raw0 + (size_t)buf * RAW;
+        const float *rwt = rw + RAWC, *rww = rw + RAWC + RAWT;
+        const int tile = tt % (tiles_x * tiles_y);
+        const int f = tt / (tiles_x * tiles_y);
+        const int i0 = (tile / tiles_x) * TR, j0 = (tile % tiles_x) * 32;
+        // (columns 4 kg .. KP of a row are not written: they meet only entries with b >= k, not kept)
+        for (int idx = t; idx < kg * TPIX; idx += NT) {
+            const int g = idx / TPIX, pix = idx % TPIX;
+            const int li = pix / 32, lj = pix % 32;
+            const int i = i0 + li, j = j0 + lj;
+            float ex[4] = {0.f, 0.f, 0.f, 0.f}, ey[4] = {0.f, 0.f, 0.f, 0.f}, et[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < N && j < N) {
+                const float sx = j < N - 1 ? sqrtf(rww[pix]) : 0.f;
+                const float sy = i < N - 1 ? sqrtf(rww[TPIX + pix]) : 0.f;
+                const float st = (EPP == 3 && f < F - 1) ? sqrtf(rww[2 * TPIX + pix]) : 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int a = 4 * g + c;
+                    if (a < k) {
+                        const float *ra = rw + (size_t)a * RR * kRawCols;
+                        const float v0 = ra[li * kRawCols + lj];
+                        if (j < N - 1) ex[c] = (ra[li * kRawCols + lj + 1] - v0) * sx;
+                        if (i < N - 1) ey[c] = (ra[(li + 1) * kRawCols + lj] - v0) * sy;
+                        if (EPP == 3 && f < F - 1) et[c] = (rwt[(size_t)a * TPIX + li * 32 + lj] - v0) * st;
+                    }
+                }
+            }
+            const int col = (4 * g) ^ ((pix & 7) << 2);
+            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix) * KP + col) = make_float4(ex[0], ex[1], ex[2], ex[3]);
+            *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 1) * KP + col) =
+                make_float4(ey[0], ey[1], ey[2], ey[3]);
+            if (EPP == 3)
+                *reinterpret_cast<float4 *>(E + (size_t)(EPP * pix + 2) * KP + col) =
+                    make_float4(et[0], et[1], et[2], et[3]);
+        }
+        __syncthreads();
+        if (busy) {
+#pragma unroll 2
+            for (int e = ph; e < NE; e += phases) {
+                const int sw = ((e / EPP) & 7) << 2;
+                const float *row = E + (size_t)e * KP;
+                const float4 A0 = *reinterpret_cast<const float4 *>(row + ((8 * bi) ^ sw));
+                const float4 A1 = *reinterpret_cast<const float4 *>(row + ((8 * bi + 4) ^ sw));
+                const float4 B0 = *reinterpret_cast<const float4 *>(row + ((8 * bj) ^ sw));
+                const float4 B1 = *reinterpret_cast<const float4 *>(row + ((8 * bj + 4) ^ sw));
+                const float av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+                const float bv[8] = {B0.x, B0.y, B0.z, B0.w, B1.x, B1.y, B1.z, B1.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) s[8 * r + c] = fmaf(av[r], bv[c], s[8 * r + c]);
+            }
+        }
+        if (++batch == kP8Flush || nxt >= ntiles) {  // uniform over the CTA
+            batch = 0;
+            float *red = E;  // [32][NT], one half of the 64 sums at a time
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                __syncthreads();  // every thread is done with E (or with the previous half)
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    red[q * NT + t] = busy ? s[32 * half + q] : 0.f;
+                    s[32 * half + q] = 0.f;
+                }
+                __syncthreads();
+                for (int idx = t; idx < P * 32; idx += NT) {
+                    const int pp = idx / 32, q = idx % 32;
+                    double v = 0.0;
+                    for (int r = 0; r < phases; ++r) v += (double)red[q * NT + r * P + pp];
+                    acc[pp * 64 + 32 * half + q] += v;
+                }
+            }
+        }
+        buf ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    for (int idx = t; idx < P * 64; idx += NT) {
+        const int pp = idx / 64, q = idx % 64;
+        int i = 0, rr = pp;
+        while (rr >= kb - i) {
+            rr -= kb - i;
+            ++i;
+        }
+        const int a = 8 * i + q / 8, b = 8 * (i + rr) + q % 8;
+        if (a <= b && b < k) part[(long long)blockIdx.x * kGramPairs + a * k - a * (a - 1) / 2 + (b - a)] = acc[idx];
     }
 }
 
