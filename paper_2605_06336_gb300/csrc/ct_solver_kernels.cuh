@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) k_gram_psi_pipe(const float *__restrict__
     const int KP = 32 * ((k + 31) / 32);
     const int NE = EPP * kRbPix;
     float *E = reinterpret_cast<float *>(rb_smem);  // [NE][KP], swizzled 16-byte groups
-    float *red = E + (size_t)NE * KP;               // [256][16]
+    float *red = E + (size_t)NE * KP;               // [16][256]
     float *raw0 = red + 256 * 16;                   // two raw buffers
     const int RAWC = k * kRawRows * kRawCols;        // per buffer: [k][5][33], then [k][4][32] (next frame), then weights
     const int RAWT = EPP == 3 ? k * kRbRows * 32 : 0;
@@ -395,16 +395,14 @@ __global__ void __launch_bounds__(256) k_gram_psi_pipe(const float *__restrict__
                     for (int c = 0; c < 4; ++c) sacc[4 * r + c] = fmaf(av[r], bv[c], sacc[4 * r + c]);
             }
 #pragma unroll
-            for (int q = 0; q < 16; q += 4)
-                *reinterpret_cast<float4 *>(red + (size_t)t * 16 + q) =
-                    make_float4(sacc[q], sacc[q + 1], sacc[q + 2], sacc[q + 3]);
+            for (int q = 0; q < 16; ++q) red[q * 256 + t] = sacc[q];  // conflict-free by thread
         }
         __syncthreads();
         if (t < P) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 float v = 0.f;
-                for (int r = 0; r < phases; ++r) v += red[(size_t)(r * P + t) * 16 + q];
+                for (int r = 0; r < phases; ++r) v += red[q * 256 + r * P + t];
                 acc[q] += (double)v;
             }
         }
@@ -470,7 +468,7 @@ __global__ void __launch_bounds__(NT, 1) k_gram_psi_pipe8(const float *__restric
     const int RAWT = EPP == 3 ? k * TPIX : 0;                    // then [k][TR][32] (next frame)
     const int RAW = RAWC + RAWT + 3 * TPIX;                      // then the weights
     float *raw0 = E + efl;
-    double *acc = reinterpret_cast<double *>(raw0 + 2 * (size_t)RAW);  // [P][64]
+    double *acc = reinterpret_cast<double *>(raw0 + 2 * (size_t)RAW);  // [64][P]
     const int kb = (k + 7) / 8;
     const int kg = (k + 3) / 4;  // column groups of 4 of the edge build
     const int P = kb * (kb + 1) / 2;
@@ -604,11 +602,11 @@ __global__ void __launch_bounds__(NT, 1) k_gram_psi_pipe8(const float *__restric
                     s[32 * half + q] = 0.f;
                 }
                 __syncthreads();
-                for (int idx = t; idx < P * 32; idx += NT) {
-                    const int pp = idx / 32, q = idx % 32;
+                for (int idx = t; idx < P * 32; idx += NT) {  // consecutive threads: consecutive block pairs
+                    const int q = idx / P, pp = idx % P;
                     double v = 0.0;
                     for (int r = 0; r < phases; ++r) v += (double)red[q * NT + r * P + pp];
-                    acc[pp * 64 + 32 * half + q] += v;
+                    acc[(32 * half + q) * P + pp] += v;
                 }
             }
         }
@@ -617,7 +615,7 @@ __global__ void __launch_bounds__(NT, 1) k_gram_psi_pipe8(const float *__restric
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     for (int idx = t; idx < P * 64; idx += NT) {
-        const int pp = idx / 64, q = idx % 64;
+        const int q = idx / P, pp = idx % P;
         int i = 0, rr = pp;
         while (rr >= kb - i) {
             rr -= kb - i;
