@@ -57,6 +57,18 @@ template <typename T> struct __align__(16) FanRay {
     T dws, s0, sr;     // d w / d delta, dq/ddelta = s0 + r sr
 };
 
+// The fields of a ray the transpose's candidate search reads, in a table of
+// their own after the FanRay table (24 bytes a ray instead of 64: the search
+// touches a few records per pixel and view, scattered over the whole table).
+template <typename T> struct FanLine {
+    long long Qc, Qh;
+    T w;
+};
+template <typename T> __host__ __device__ inline FanLine<T> *fan_lines(void *rays, long long nrays)
+{
+    return reinterpret_cast<FanLine<T> *>(reinterpret_cast<unsigned char *>(rays) + nrays * sizeof(FanRay<T>));
+}
+
 // Per view: FP32 constants of the transpose's candidate search and the bin
 // ranges of the two march axes (the ray direction turns monotonically with
 // s_b over a fan narrower than 90 degrees, so the axis changes at most once:
@@ -68,7 +80,8 @@ struct __align__(16) FanView {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg, int V, int B, int N, double D,
-                                                  FanRay<T> *__restrict__ out, const int *__restrict__ skip)
+                                                  FanRay<T> *__restrict__ out, FanLine<T> *__restrict__ lines,
+                                                  const int *__restrict__ skip)
 {
     if (skip && *skip) return;
     const double h = 0.5 * (N - 1);
@@ -127,6 +140,11 @@ __global__ void __launch_bounds__(256) k_fan_rays(const ViewGeo *__restrict__ vg
             R.rhi = (float)fmax(fmin(fmax(ra, rb) + 2.0, (double)(N - 1)), -1.0);
         }
         out[idx] = R;
+        FanLine<T> L;
+        L.Qc = R.Qc;
+        L.Qh = R.Qh;
+        L.w = R.w;
+        lines[idx] = L;
     }
 }
 
@@ -408,7 +426,7 @@ template <typename T, int KB> __device__ __forceinline__ void load_bin(const T *
 // SPLIT, ... of its frame in order; the groups' sums are added in group
 // order in shared memory.
 template <typename T, int KB, int SPLIT>
-__global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const FanRay<T> *__restrict__ rays,
+__global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const FanLine<T> *__restrict__ rays,
                                                          const FanView *__restrict__ views,
                                                          const T *__restrict__ YI, T *__restrict__ X)
 {
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(256 * SPLIT) k_adj_fan(AdjFanArgs a, const Fan
         const int vs = a.fstart[f], vc = a.fcount[f];
         for (int v = vs + grp_v; inside && v < vs + vc; v += SPLIT) {
             const FanView fv = views[v];
-            const FanRay<T> *rv = rays + (size_t)v * a.B;
+            const FanLine<T> *rv = rays + (size_t)v * a.B;
             // the KB sinograms of this group at bin b: KB consecutive values (KB divides 8, and a
             // group starts at a multiple of its width)
             const T *yv = YI + ((size_t)(k0 >> 3) * a.ysino_stride + (size_t)v * a.B) * 8 + (k0 & 7);
@@ -514,8 +532,8 @@ template <typename T, int KB, int SPLIT> cudaError_t run_adj_fan(const Handle &h
     auto kern = k_adj_fan<T, KB, SPLIT>;
     const long long items = (long long)a.ngroups * a.F * a.tps * a.tps;
     const int grid = persistent_grid(kern, 256 * SPLIT, 0, items, h.num_sms);
-    kern<<<grid, 256 * SPLIT, 0, h.stream>>>(a, (const FanRay<T> *)h.d_rays, (const FanView *)h.d_fanview,
-                                             (const T *)h.d_yi, X);
+    kern<<<grid, 256 * SPLIT, 0, h.stream>>>(a, fan_lines<T>(h.d_rays, (long long)h.V * h.B),
+                                             (const FanView *)h.d_fanview, (const T *)h.d_yi, X);
     return cudaGetLastError();
 }
 
@@ -527,7 +545,11 @@ template <typename T, int KB> cudaError_t run_adj_fan_split(const Handle &h, con
 
 }  // namespace
 
-size_t fan_ray_bytes(int precision) { return precision ? sizeof(FanRay<double>) : sizeof(FanRay<float>); }
+// bytes a ray takes in the handle's table: its FanRay and its FanLine
+size_t fan_ray_bytes(int precision)
+{
+    return precision ? sizeof(FanRay<double>) + sizeof(FanLine<double>) : sizeof(FanRay<float>) + sizeof(FanLine<float>);
+}
 size_t fan_view_bytes() { return sizeof(FanView); }
 
 cudaError_t launch_fan_rays(const Handle &h, const int *skip)
@@ -537,13 +559,14 @@ cudaError_t launch_fan_rays(const Handle &h, const int *skip)
     const int vgrid = (h.V + 7) / 8;
     if (h.precision) {
         k_fan_rays<double><<<grid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.N, h.fan_D,
-                                                       (FanRay<double> *)h.d_rays, skip);
+                                                       (FanRay<double> *)h.d_rays, fan_lines<double>(h.d_rays, n),
+                                                       skip);
         k_fan_views<double><<<vgrid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.fan_D,
                                                          (const FanRay<double> *)h.d_rays, (FanView *)h.d_fanview,
                                                          skip);
     } else {
         k_fan_rays<float><<<grid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.N, h.fan_D, (FanRay<float> *)h.d_rays,
-                                                      skip);
+                                                      fan_lines<float>(h.d_rays, n), skip);
         k_fan_views<float><<<vgrid, 256, 0, h.stream>>>(h.d_views, h.V, h.B, h.fan_D, (const FanRay<float> *)h.d_rays,
                                                         (FanView *)h.d_fanview, skip);
     }
