@@ -468,9 +468,13 @@ def graph_step_timing(op, step, steps, flush):
 # ---------------------------------------------------------------------------
 class OperatorStep:
     """H on K images, H^T on K sinograms, J dtheta and J^T r on one image, through
-    the C ABI on op's handle, with the inputs resident on the device.  J^T is
-    taken at the image of the J call, whose pair layouts it uses again (x =
-    NULL), as a Gauss-Newton step does."""
+    the C ABI, with the inputs resident on the device.  J^T is taken at the
+    image of the J call, whose pair layouts it uses again (x = NULL), as a
+    Gauss-Newton step does.  `step` runs the four calls in order on one handle;
+    `step_overlapped` runs H^T on a second handle of the same geometry and
+    launch shapes, on a stream of its own, while H, J and J^T run on the first
+    (the four calls are independent; a handle's workspace serves one stream),
+    so that the shared-memory-bound transpose overlaps the L2-bound forward."""
 
     def __init__(self, w, K, dtype, dev, tuning=None, delta=None, seed=100):
         import torch
@@ -488,6 +492,9 @@ class OperatorStep:
         else:
             self.op.autotune()
         self.tuning = self.op.tuning
+        self.opT = ct.CTOperator(N, B, V, max_batch=K, dtype=dtype)  # H^T's handle in step_overlapped
+        self.opT.tuning = self.tuning
+        self.sideT = torch.cuda.Stream(device=dev)
         self.theta = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
         self.delta = None if delta is None else torch.tensor(delta, dtype=torch.float64, device=dev)
         self.delta_h = delta
@@ -516,6 +523,27 @@ class OperatorStep:
             c()
         if ev:
             ev[4].record(stream)
+
+    def step_overlapped(self):
+        """The same four calls with H^T on opT and its own stream, forked from and
+        joined back into the current stream (two branches of one graph when captured)."""
+        import torch
+        ct, op, opT, K = self.ct, self.op, self.opT, self.K
+        th, dl = self.theta, self.delta
+        cur = torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        self.sideT.wait_event(fork)
+        op.set_stream(cur)
+        opT.set_stream(self.sideT)
+        ct.ct_forward(op.h, th, dl, self.X, self.Y, K)
+        with torch.cuda.stream(self.sideT):
+            ct.ct_adjoint(opT.h, th, dl, self.Ys, self.Xa, K)
+        ct.ct_jac(op.h, th, dl, self.X[0], self.dth, None, self.dy)
+        ct.ct_jacT(op.h, th, dl, None, self.Y[0], self.gt, None)
+        join = torch.cuda.Event()
+        join.record(self.sideT)
+        cur.wait_event(join)
 
     def kernels_alone(self, flush, reps=200):
         """Per-call device time (each call replayed from its own graph) and the
@@ -576,8 +604,9 @@ def operator_line(name, w, K, dtype, dev, steps, flush, peaks, delta=None, tunin
     torch.cuda.synchronize()
     if s.op.status() != s.ct.CT_OK:
         raise RuntimeError(f"{name}: device status not OK")
-    g = capture_step(s.op, s.step)
+    g = capture_step(s.op, s.step_overlapped)
     ms, clk = graph_replay_timing(g, steps, flush, clock)
+    seq_ms, _ = graph_replay_timing(capture_step(s.op, s.step), steps, flush)
     per_call, kms = s.kernels_alone(flush, reps=min(200, max(steps, 20)))
     steps_img = interp_steps_per_image(w, delta)
     rl = s.roofline(kms, peaks[0], peaks[1], steps_img)
@@ -585,6 +614,7 @@ def operator_line(name, w, K, dtype, dev, steps, flush, peaks, delta=None, tunin
     nnz_per_step = 2 * steps_img * (s.K + s.K + 1 + 1)
     out = {"workload": name, "value": s.samples_per_step / (ms * 1e-3) / 1e9, "unit": "GSamples/s",
            "ms_per_step": ms, "gnnz_per_s": nnz_per_step / (ms * 1e-3) / 1e9,
+           "sequential": {"value": s.samples_per_step / (seq_ms * 1e-3) / 1e9, "ms_per_step": seq_ms},
            "per_call_ms": dict(zip(["forward", "adjoint", "jac", "jacT"], per_call)), "kernel_ms": kms,
            "roofline": rl[dom] | {"kernel": dom}, "roofline_other": rl["adjoint" if dom == "forward" else "forward"],
            "tuning": dict(zip(s.ct.TUNING_FIELDS, s.tuning)), "interp_steps_per_image": steps_img}
@@ -868,7 +898,8 @@ def fan_beam_step(dev, steps, flush):
     samples = w.V * w.B * (K + K + 1 + 1)
     out = {"workload": f"fan beam, source at {D:.0f} px: {w.N}x{w.N}, {w.V} views, {w.B} bins, Krylov block {K}",
            "ms_per_step": ms, "value": samples / (ms * 1e-3) / 1e9, "unit": "GSamples/s",
-           "tuning": dict(zip(ct.TUNING_FIELDS, op.tuning)), "launch": "CUDA graph replay"}
+           "tuning": dict(zip(ct.TUNING_FIELDS, op.tuning)),
+           "launch": "CUDA graph replay, the four calls in order on one handle and stream"}
     op.close()
     return out
 
@@ -954,8 +985,9 @@ def main():
     samples_per_step = s.samples_per_step
     value_eager = job_rate(samples_per_step * args.steps, total_ms, world)
 
-    # ---- the headline: the same step replayed from a CUDA graph (what the solver and a serving loop run)
-    g = capture_step(op, s.step)
+    # ---- the headline: the same step replayed from a CUDA graph (what the solver and a serving loop
+    # run), H^T on a second handle and stream: a parallel branch of the graph
+    g = capture_step(op, s.step_overlapped)
     clock = ClockSampler(torch.cuda.current_device())
     if world > 1:
         dist.barrier()
@@ -964,6 +996,16 @@ def main():
         dist.barrier()
     graph_ms = max_over_ranks(graph_ms, world, dev)
     value = job_rate(samples_per_step, graph_ms, world)
+    # the four calls in order on one handle and stream, for comparison
+    seq_ms, _ = graph_replay_timing(capture_step(op, s.step), args.steps, flush)
+    seq_ms = max_over_ranks(seq_ms, world, dev)
+    # the overlapped step computes what the sequential one does, bit for bit
+    s.step()
+    torch.cuda.synchronize()
+    seq_out = [t.clone() for t in (s.Y, s.Xa, s.dy, s.gt)]
+    s.step_overlapped()
+    torch.cuda.synchronize()
+    overlap_same = all(torch.equal(a, b) for a, b in zip(seq_out, (s.Y, s.Xa, s.dy, s.gt)))
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region.
     # Every step uploads its inputs from pinned host memory and downloads all its results.  Serial:
@@ -1124,13 +1166,19 @@ def main():
         "warmup": max(args.warmup, 3), "ms_per_step": graph_ms, "higher_is_better": True,
         "eager": {"value": value_eager, "ms_per_step": total_ms / args.steps,
                   "note": "the same step as individual launches (per-op times below)"},
+        "sequential": {"value": job_rate(samples_per_step, seq_ms, world), "ms_per_step": seq_ms,
+                       "same_results_as_overlapped": overlap_same,
+                       "note": "the four calls in order on one handle and stream, graph-replayed"},
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "C2: 256x256 random-ellipse phantom, 180 views (1 deg angle errors), 363 bins; "
                                "step = H on 8 images + H^T on 8 sinograms + J dtheta + J^T r at one image "
                                "(J^T reuses the image layout of the J call)",
                    "krylov_block": K, "samples_per_step": samples_per_step,
                    "l2": "flushed between timed steps (512 MB write, outside the events)",
-                   "launch": "step captured once in a CUDA graph and replayed (value); eager launches under 'eager'",
+                   "launch": "step captured once in a CUDA graph and replayed (value): H, J and J^T on one handle "
+                             "and stream, H^T on a second handle of the same geometry on a second stream (a "
+                             "parallel branch of the graph); the four calls in order on one handle under "
+                             "'sequential'; eager launches under 'eager'",
                    "parallelism": f"replicas x{world}"},
         "gnnz_per_s": nnz_per_step / (graph_ms * 1e-3) / 1e9,
         "gnnz_note": "interpolation nonzeros (two per interpolation step) touched per step over the step time",
