@@ -1043,6 +1043,8 @@ def main():
     ev_down = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_pipelined(n, start):
+        op.set_stream(stream)
+        s.opT.set_stream(s.sideT)
         s_up.wait_event(start)
         for k in range(n):
             j = k % 2
@@ -1058,10 +1060,18 @@ def main():
             stream.wait_event(ev_up[j])
             if k >= 2:
                 stream.wait_event(ev_down[j])         # step k-2's results have left this slot
+            # as in the headline step: H^T on the second handle and stream, forked and joined
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            s.sideT.wait_event(fork)
             ct.ct_forward(op.h, sl["theta"], None, sl["X"], sl["Y"], K)
-            ct.ct_adjoint(op.h, sl["theta"], None, sl["Ys"], sl["Xa"], K)
+            with torch.cuda.stream(s.sideT):
+                ct.ct_adjoint(s.opT.h, sl["theta"], None, sl["Ys"], sl["Xa"], K)
             ct.ct_jac(op.h, sl["theta"], None, sl["X"][0], sl["dth"], None, sl["dy"])
             ct.ct_jacT(op.h, sl["theta"], None, None, sl["Y"][0], sl["gt"], None)  # the image of the J call
+            join = torch.cuda.Event()
+            join.record(s.sideT)
+            stream.wait_event(join)
             ev_done[j].record(stream)
             with torch.cuda.stream(s_down):
                 s_down.wait_event(ev_done[j])
@@ -1207,8 +1217,9 @@ def main():
                 "max_abs_diff_vs_serial": e2e_check,
                 "note": "C ABI calls on host data: every step uploads its inputs from pinned memory and downloads "
                         "all its results, inside the timed region; uploads and downloads run on two copy streams "
-                        "overlapping the neighbouring steps' kernels (two device slots); serial_value: the same "
-                        "with copies and calls on one stream"},
+                        "overlapping the neighbouring steps' kernels (two device slots), and H^T runs on the "
+                        "second handle and stream as in the headline step; serial_value: the same with copies "
+                        "and the four calls in order on one stream"},
         "gpu_launches": launches_per_step(tuning) * args.steps,
         "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
         "tuning": dict(zip(ct.TUNING_FIELDS, tuning)),
