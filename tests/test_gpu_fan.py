@@ -236,3 +236,27 @@ def test_fp64_fan_varpro_solver_follows_the_oracle_iterates():
     np.testing.assert_allclose(st["rre"], h_o.rre, rtol=1e-6)
     assert rel(host(x), u_o) <= 1e-6
     assert np.max(np.abs(host(th) - th_o)) <= 1e-7
+
+
+def test_fan_image_reuse_with_null_x():
+    """Fan beam, x = NULL: the J^T (and J, and H) of the image laid out by the
+    previous call, at other angles, bit for bit what passing the image gives."""
+    from paper_2605_06336_gb300 import ct
+    N, vpf, K, D = 37, [11], 3, 60.0
+    theta, delta, X, Y, rng = _inputs(N, vpf, K, True, seed=71)
+    V = sum(vpf)
+    op = ct.CTOperator(N, synth.n_bins(N), V, max_batch=K, dtype=torch.float32, source_distance=D)
+    th1, th2, dl = dev(theta), dev(_angles(V, rng)), dev(delta)
+    Xd, Yd = dev(X, torch.float32), dev(Y, torch.float32)
+    dth = dev(rng.standard_normal(V))
+    g_ref = op.jacT(Xd[1], th2, Yd[0], dl, want_delta=True)
+    dy_ref = op.jac(Xd[1], th1, dth, dl).clone()
+    y_ref = op.forward(Xd[:2], th2, dl).clone()
+    op.forward(Xd, th1)
+    op.jac(Xd[1], th2, dth)
+    g = op.jacT(None, th2, Yd[0], dl, want_delta=True)
+    assert torch.equal(g[0], g_ref[0]) and torch.equal(g[1], g_ref[1])
+    assert torch.equal(op.jac(None, th1, dth, dl), dy_ref)
+    op.forward(Xd, th1)
+    assert torch.equal(op.forward(None, th2, dl, batch=2), y_ref)
+    op.close()
