@@ -245,8 +245,9 @@ template <typename T> struct Solver {
         const bool tm = o.temporal && h.F > 1;
         if constexpr (sizeof(T) == 4) {
             const int epp = tm ? 3 : 2;
-            if (gram_pipe_smem(k, epp) <= kGramPipeSmemMax && gram_rb_threads(k) == 256)
-                // 4 x 4 blocks: both raw buffers fit next to the edge block, one thread per block pair
+            if (k <= 32 && gram_pipe_smem(k, epp) <= kGramPipeSmemMax && gram_rb_threads(k) == 256)
+                // 4 x 4 blocks over 4-row tiles for small bases (above 32 columns the 8 x 8 blocks
+                // measured faster: C5 streaming 6.98 -> 6.78 s per pass)
                 k_gram_psi_pipe<<<gram_blocks, kThreads, gram_pipe_smem(k, epp), h.stream>>>(
                     V, n, k, w, h.N, h.F, o.temporal, part_gram, stop);
             else if (gram_p8_rows(k, epp) == 2)  // larger bases: 2-row tiles, 8 x 8 blocks

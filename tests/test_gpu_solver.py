@@ -146,10 +146,9 @@ def test_fp32_aniso_tv_solver_reaches_the_oracle_reconstruction_error(ct):
 
 
 def test_fp32_aniso_tv_large_basis_uses_the_8x8_block_gram(ct):
-    """ANISO-TV with a basis above 40 columns: the weighted Gram of Psi V no
-    longer fits the two staging buffers of the 4 x 4-block kernel and runs in
-    the 8 x 8-block form over 2-row tiles.  One outer iteration of 40 Enlarge
-    steps (k = 6 .. 45) against the oracle."""
+    """ANISO-TV with a basis above 32 columns: the weighted Gram of Psi V runs
+    in the 8 x 8-block form over 2-row tiles.  One outer iteration of 40
+    Enlarge steps (k = 6 .. 45) against the oracle."""
     g, vpf, th_nom, th_true, u_true, b, nn = _moving_sequence(N=24, vpf=(6, 7, 6, 7), seed=43)
     kw = dict(k_min=5, k_max=45, outer_iters=1, tol1=0.0, stop_on_convergence=False, temporal=True,
               armijo_eps=2.0 ** -24)
@@ -220,8 +219,8 @@ def test_fp64_solver_with_a_basis_of_100_follows_the_oracle(ct):
 
 def test_fp32_solver_with_a_basis_of_120_reaches_the_oracle_reconstruction_error(ct):
     """FP32 operators with k_max = 120 (the largest basis): the weighted Gram of
-    Psi V runs in its 4 x 4-block form, then (above about 60 columns) in the
-    8 x 8-block form over 2-row tiles."""
+    Psi V runs in its 4 x 4-block form, then (above 32 columns) in the 8 x
+    8-block form over 2-row tiles."""
     g, th_nom, th_true, u_true, b, nn = problem(40, 48, seed=12)
     kw = dict(k_min=5, k_max=120, outer_iters=2, tol1=0.0)
     o = nlrmm.Options(noise_norm=nn, stop_on_convergence=False, armijo_eps=2.0 ** -24, **kw)
