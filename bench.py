@@ -527,23 +527,9 @@ class OperatorStep:
     def step_overlapped(self):
         """The same four calls with H^T on opT and its own stream, forked from and
         joined back into the current stream (two branches of one graph when captured)."""
-        import torch
-        ct, op, opT, K = self.ct, self.op, self.opT, self.K
-        th, dl = self.theta, self.delta
-        cur = torch.cuda.current_stream()
-        fork = torch.cuda.Event()
-        fork.record(cur)
-        self.sideT.wait_event(fork)
-        op.set_stream(cur)
-        opT.set_stream(self.sideT)
-        ct.ct_forward(op.h, th, dl, self.X, self.Y, K)
-        with torch.cuda.stream(self.sideT):
-            ct.ct_adjoint(opT.h, th, dl, self.Ys, self.Xa, K)
-        ct.ct_jac(op.h, th, dl, self.X[0], self.dth, None, self.dy)
-        ct.ct_jacT(op.h, th, dl, None, self.Y[0], self.gt, None)
-        join = torch.cuda.Event()
-        join.record(self.sideT)
-        cur.wait_event(join)
+        _, overlapped = four_call_steps(self.op, self.opT, self.sideT, self.theta, self.X, self.Y, self.Ys, self.Xa,
+                                        self.dth, self.dy, self.gt, self.K, dl=self.delta, r=self.Y[0])
+        overlapped()
 
     def kernels_alone(self, flush, reps=200):
         """Per-call device time (each call replayed from its own graph) and the
@@ -833,17 +819,20 @@ def streaming_c5(dev, passes, scale=1.0, k_max=None):
 STREAM_KMAX = 100  # the memory-bounded basis of the large streaming workload
 
 
-def four_call_steps(op, opT, side, th, X, Y, Ys, Xa, dth, dy, gt, K):
-    """The step's four calls in order on op (sequential), and with H^T on opT and
-    stream `side`, forked from and joined back into the current stream (overlapped)."""
+def four_call_steps(op, opT, side, th, X, Y, Ys, Xa, dth, dy, gt, K, dl=None, r=None):
+    """The step's four calls (H on X, H^T on Ys, J dth and J^T r at X[0]; r defaults
+    to Ys[0]) in order on op (sequential), and with H^T on opT and stream `side`,
+    forked from and joined back into the current stream (overlapped: two branches
+    of one graph when captured)."""
     import torch
     from paper_2605_06336_gb300 import ct
+    r = Ys[0] if r is None else r
 
     def sequential():
-        ct.ct_forward(op.h, th, None, X, Y, K)
-        ct.ct_adjoint(op.h, th, None, Ys, Xa, K)
-        ct.ct_jac(op.h, th, None, X[0], dth, None, dy)
-        ct.ct_jacT(op.h, th, None, None, Ys[0], gt, None)  # the image of the J call
+        ct.ct_forward(op.h, th, dl, X, Y, K)
+        ct.ct_adjoint(op.h, th, dl, Ys, Xa, K)
+        ct.ct_jac(op.h, th, dl, X[0], dth, None, dy)
+        ct.ct_jacT(op.h, th, dl, None, r, gt, None)  # the image of the J call
 
     def overlapped():
         cur = torch.cuda.current_stream()
@@ -852,11 +841,11 @@ def four_call_steps(op, opT, side, th, X, Y, Ys, Xa, dth, dy, gt, K):
         side.wait_event(fork)
         op.set_stream(cur)
         opT.set_stream(side)
-        ct.ct_forward(op.h, th, None, X, Y, K)
+        ct.ct_forward(op.h, th, dl, X, Y, K)
         with torch.cuda.stream(side):
-            ct.ct_adjoint(opT.h, th, None, Ys, Xa, K)
-        ct.ct_jac(op.h, th, None, X[0], dth, None, dy)
-        ct.ct_jacT(op.h, th, None, None, Ys[0], gt, None)
+            ct.ct_adjoint(opT.h, th, dl, Ys, Xa, K)
+        ct.ct_jac(op.h, th, dl, X[0], dth, None, dy)
+        ct.ct_jacT(op.h, th, dl, None, r, gt, None)
         join = torch.cuda.Event()
         join.record(side)
         cur.wait_event(join)
