@@ -121,7 +121,8 @@ def parse():
                     help="with --stream-only: shrink the streaming workload (image side, bins, views)")
     ap.add_argument("--stream-kmax", type=int, default=None, help="with --stream-only: basis size k_max")
     ap.add_argument("--tuning", default=None,
-                    help="fixed launch shapes (the 11 ct_set_tuning values, comma separated) instead of autotuning")
+                    help="fixed launch shapes (the 12 ct_set_tuning values, comma separated; 11 = forward on "
+                         "the pair images) instead of autotuning")
     return ap.parse_args()
 
 
@@ -561,16 +562,18 @@ class OperatorStep:
         for name in ("forward", "adjoint"):
             staged = (t[7] > 0) if name == "forward" else (t[9] > 0)
             staged = staged and esz == 4
+            # the forward on interleaved images reads one float per pixel and image, not a pair
+            inter = name == "forward" and len(t) > 11 and t[11] == 1 and esz == 4
             # the L1-gather forward misses L1 and hits L2; the staged kernels read shared
             # memory; the L1-gather transpose mostly hits L1, which shares shared memory's data path
             level = "smem" if staged else ("l2" if name == "forward" else "l1")
             pk = l2_gbs if level == "l2" else smem_gbs
             ach = gather_bytes / (kernel_ms[name] * 1e-3) / 1e9
             if name == "forward":
-                footprint = 2.0 * K * w.F * w.N * (w.N + 4) * 2 * esz
+                footprint = 2.0 * K * w.F * w.N * (w.N + 4) * (1 if inter else 2) * esz
             else:
                 footprint = float(K * w.V * ((w.B + 5) & ~1) * 2 * esz)
-            fam = name + ("_staged" if staged else "")
+            fam = name + ("_staged" if staged else ("_interleaved" if inter else ""))
             ratio = TRAFFIC_PER_FOOTPRINT.get(fam) if esz == 4 else None
             out[name] = {"level": level, "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
                          "launch_ms": kernel_ms[name], "gather_bytes": gather_bytes,
@@ -1146,8 +1149,8 @@ def main():
     d = rl[dom]
     roofline = {"bound": d["level"], "kernel": f"{dom}_K{K}", "achieved": d["achieved"], "peak": d["peak"],
                 "unit": "GB/s", "frac": d["frac"], "traffic": d["traffic"],
-                "traffic_basis": f"ncu DRAM read + write per byte of the launch's pair layout ({d['traffic_family']} "
-                                 f"family) x this launch's pair footprint",
+                "traffic_basis": f"ncu DRAM read + write per byte of the launch's image or sinogram layout "
+                                 f"({d['traffic_family']} family) x this launch's layout footprint",
                 "launch_ms": d["launch_ms"],
                 "basis": f"8 B of gathered FP32 operands per interpolation step x {K} images x {steps_img} steps per "
                          f"launch, over the kernel's CUDA-event time",

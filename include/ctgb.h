@@ -249,7 +249,14 @@ int ct_autotune(ct_handle *h);
  *   [4] transpose view groups per pixel tile, [5] Jacobian warps per ray,
  *   [6] Jacobian views per CTA, [7] forward staging, [8] Jacobian staging,
  *   [9] transpose staging, [10] images per lane of the batched Jacobian
- *   products (1, 2 or 4; the staged and fan-beam forms take 1).
+ *   products (1, 2 or 4; the staged and fan-beam forms take 1), [11] forward
+ *   image layout: 0 pair images (each pixel stored beside its neighbour), 1
+ *   images interleaved in groups of 4 (FP32 parallel-beam handles, forward
+ *   staging 0, [0] 4 or 8; the forward then reads both taps of 4 images with
+ *   two 16-byte loads; a later call that passes X = NULL to a Jacobian
+ *   product converts them to pair images first).  Layout 1 allocates two
+ *   buffers of max_batch x n_frames x N x (N + 4) floats the first time
+ *   (CT_ERR_OOM if that fails; CT_ERR_ARG on an FP64 or fan-beam handle).
  * [0]..[6] are powers of two, at most 8 (view groups at most 4), warps per
  * ray x views per CTA at most 16 (unstaged kernels).  Forward / Jacobian
  * staging is 0 (gathers through L1) or 4 / 8 (rows per shared-memory block of
@@ -263,7 +270,7 @@ int ct_autotune(ct_handle *h);
  * that fails).  The Jacobian kernels ignore [5] when staged.  CT_ERR_ARG for
  * any other value.
  */
-#define CT_TUNING_COUNT 11
+#define CT_TUNING_COUNT 12
 int ct_get_tuning(ct_handle *h, int32_t *out);
 int ct_set_tuning(ct_handle *h, const int32_t *in);
 

@@ -50,6 +50,9 @@ void free_all(ctgb::Handle &h)
     cudaFree(h.d_rays);
     cudaFree(h.d_fanview);
     cudaFree(h.d_yi);
+    cudaFree(h.d_qx);
+    cudaFree(h.d_qt);
+    h.d_qx = h.d_qt = nullptr;
     h.d_rays = nullptr;
     h.d_fanview = nullptr;
     h.d_yi = nullptr;
@@ -62,19 +65,45 @@ void free_all(ctgb::Handle &h)
 
 // The pair layouts of the call's images and the view table.  X == null: the
 // layouts left by the previous call that took images are current (the caller
-// checked h.img_ready); only the view table is brought up to date.
+// checked h.img_ready; interleaved ones, left by a forward, are turned into
+// pair layouts first); only the view table is brought up to date.
 template <typename T>
-cudaError_t prep_images(const ctgb::Handle &h, const T *X, int nimg, const double *theta, const double *delta)
+cudaError_t prep_images(ctgb::Handle &h, const T *X, int nimg, const double *theta, const double *delta)
 {
-    if (X) return ctgb::launch_pairs_img<T>(h, X, nimg, nullptr, theta, delta);
+    if (X) {
+        h.img_kind = 0;
+        return ctgb::launch_pairs_img<T>(h, X, nimg, nullptr, theta, delta);
+    }
+    if (h.img_kind == 1) {
+        const cudaError_t e = ctgb::launch_interleaved_to_pairs(h, h.img_ready);
+        if (e != cudaSuccess) return e;
+        h.img_kind = 0;
+    }
     return ctgb::launch_view_setup(h, theta, delta);
+}
+
+// Whether a forward that takes images lays them out interleaved (the tuning
+// asks for it and the handle can: FP32, parallel beam, workspace present).
+bool forward_interleaves(const ctgb::Handle &h)
+{
+    return h.tune.fwd_layout == 1 && h.precision == 0 && h.fan_D == 0.0 && h.d_qx;
 }
 
 template <typename T>
 int do_forward(ctgb::Handle &h, const double *theta, const double *delta, const void *X, void *Y, int batch)
 {
-    CT_CUDA(prep_images<T>(h, (const T *)X, batch * h.F, theta, delta));
-    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage));
+    // X == null reads whichever layout the previous call left
+    const bool inter = X ? forward_interleaves(h) : h.img_kind == 1;
+    if (inter && X) {
+        CT_CUDA(ctgb::launch_interleave_img(h, (const float *)X, batch, theta, delta));
+        h.img_kind = 1;
+    } else if (inter) {
+        CT_CUDA(ctgb::launch_view_setup(h, theta, delta));
+    } else {
+        CT_CUDA(prep_images<T>(h, (const T *)X, batch * h.F, theta, delta));
+    }
+    CT_CUDA(ctgb::launch_forward<T>(h, (T *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw, h.tune.fwd_stage,
+                                    nullptr, inter, X ? batch : h.img_ready));
     return CT_OK;
 }
 
@@ -156,6 +185,23 @@ int ensure_seg_partials(ctgb::Handle &h)
     if (cudaMalloc(&h.d_segpart, bytes) != cudaSuccess) {
         cudaGetLastError();
         h.d_segpart = nullptr;
+        return CT_ERR_OOM;
+    }
+    return CT_OK;
+}
+
+// Workspace of the interleaved forward images, allocated the first time that
+// layout is set (FP32 parallel-beam handles).
+int ensure_interleaved(ctgb::Handle &h)
+{
+    if (h.d_qx) return CT_OK;
+    if (h.precision != 0 || h.fan_D > 0.0) return CT_ERR_ARG;
+    const size_t bytes = sizeof(float) * (size_t)h.max_batch * h.F * h.N * h.Pp;
+    if (cudaMalloc(&h.d_qx, bytes) != cudaSuccess || cudaMalloc(&h.d_qt, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h.d_qx);
+        cudaFree(h.d_qt);
+        h.d_qx = h.d_qt = nullptr;
         return CT_ERR_OOM;
     }
     return CT_OK;
@@ -274,6 +320,27 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
                         t.fwd_split = sp;
                         t.fwd_vw = vw;
                         t.fwd_stage = 0;
+                        t.fwd_layout = 0;
+                    }
+                }
+            }
+            // the same shapes reading the interleaved images (FP32 parallel beam, 4 or 8 per lane)
+            if ((kb == 4 || kb == 8) && fp32 && h.fan_D == 0.0 && ensure_interleaved(h) == CT_OK) {
+                for (int sp : {1, 2, 4, 8}) {
+                    for (int vw : {1, 2, 4, 8}) {
+                        if (sp * vw > 16) continue;
+                        const float ms = time_config(h.stream, [&] {
+                            ctgb::launch_interleave_img(h, (const float *)X, K);
+                            ctgb::launch_forward<T>(h, (T *)d_out, K, kb, sp, vw, 0, nullptr, true, K);
+                        });
+                        if (ms < best) {
+                            best = ms;
+                            t.fwd_kb = kb;
+                            t.fwd_split = sp;
+                            t.fwd_vw = vw;
+                            t.fwd_stage = 0;
+                            t.fwd_layout = 1;
+                        }
                     }
                 }
             }
@@ -291,6 +358,7 @@ template <typename T> int autotune_impl(ctgb::Handle &h)
                             t.fwd_split = sp;
                             t.fwd_vw = vw;
                             t.fwd_stage = st;
+                            t.fwd_layout = 0;
                         }
                     }
                 }
@@ -532,7 +600,7 @@ int ct_forward_repeat(ct_handle *H, void *Y, int batch)
                                              h.tune.fwd_stage));
     else
         CT_CUDA(ctgb::launch_forward<float>(h, (float *)Y, batch, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
-                                            h.tune.fwd_stage));
+                                            h.tune.fwd_stage, nullptr, h.img_kind == 1, h.img_ready));
     return CT_OK;
 }
 
@@ -643,7 +711,7 @@ int ct_get_tuning(ct_handle *H, int32_t *out)
     const ctgb::Tuning &t = H->h.tune;
     const int32_t v[CT_TUNING_COUNT] = {t.fwd_kb,    t.fwd_split, t.fwd_vw,    t.adj_kb,
                                         t.adj_split, t.der_split, t.der_vw,    t.fwd_stage,
-                                        t.der_stage, t.adj_stage, t.der_kb};
+                                        t.der_stage, t.adj_stage, t.der_kb,    t.fwd_layout};
     for (int i = 0; i < CT_TUNING_COUNT; ++i) out[i] = v[i];
     return CT_OK;
 }
@@ -656,10 +724,15 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
     if (!pow2(in[0], 8) || !pow2(in[1], 8) || !pow2(in[2], 8) || !pow2(in[3], 8) || !pow2(in[4], 4) ||
         !pow2(in[5], 8) || !pow2(in[6], 8) || (in[7] == 0 && in[1] * in[2] > 16) ||
         (in[8] == 0 && in[5] * in[6] > 16) || !stage_ok(in[7], in[2]) || !stage_ok(in[8], in[6]) ||
-        (in[7] > 0 && in[1] > 4) || (in[9] != 0 && in[9] != 8 && in[9] != 16) || !pow2(in[10], 4))
+        (in[7] > 0 && in[1] > 4) || (in[9] != 0 && in[9] != 8 && in[9] != 16) || !pow2(in[10], 4) ||
+        (in[11] != 0 && in[11] != 1) || (in[11] == 1 && (in[7] != 0 || in[0] < 4)))
         return CT_ERR_ARG;
     if (in[7] > 0 && in[1] > 1) {
         const int rc = ensure_seg_partials(H->h);
+        if (rc != CT_OK) return rc;
+    }
+    if (in[11] == 1) {
+        const int rc = ensure_interleaved(H->h);
         if (rc != CT_OK) return rc;
     }
     ctgb::Tuning &t = H->h.tune;
@@ -674,6 +747,7 @@ int ct_set_tuning(ct_handle *H, const int32_t *in)
     t.der_stage = in[8];
     t.adj_stage = in[9];
     t.der_kb = in[10];
+    t.fwd_layout = in[11];
     return CT_OK;
 }
 

@@ -119,6 +119,10 @@ template <typename T> struct RayArgs {
     int segs;               // band-staged forward: row segments per ray, one CTA each (1: whole rays)
     T *fpart;               // segments 1..segs-1 of the band-staged forward (segment 0 goes to Y)
     long long fpart_stride; // elements per segment in fpart
+    const float *QX, *QT;   // interleaved images (FP32 forward)
+    long long qimg_stride;  // floats per image in the interleaved layout (F * N * Pp)
+    int kend;               // FWD: images k >= kend of a group are not written (a batch below the
+                            // interleaved layout's ends inside a group)
 };
 
 // Warp-uniform row range [rlo, rhi] covering every row where one of the
@@ -156,7 +160,7 @@ __device__ __forceinline__ void ray_epilogue(const RayArgs<T> &a, const ViewGeo 
         if (active) {
 #pragma unroll
             for (int k = 0; k < KB; ++k)
-                a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = wv * acc[k];
+                if (k0 + k < a.kend) a.Y[(size_t)(k0 + k) * a.sino_stride + (size_t)v * a.B + b] = wv * acc[k];
         }
     } else {
         // image k of the group: acc[3k] interpolated sum, acc[3k+1] slope x dq/dtheta, acc[3k+2] slopes

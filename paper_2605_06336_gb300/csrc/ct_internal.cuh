@@ -25,6 +25,16 @@
 // operator reads sinograms the same way: pair b of view v holds
 // (Y[v][b], Y[v][b+1]) for b = -2 .. B+1 (stored at b + 2, pitch Pb = B + 4
 // rounded up to even, so that rows start on 16-byte boundaries).
+//
+// Interleaved images (FP32 forward, fwd_layout 1).  The forward of a batch
+// may read its images from a second layout without the pair duplication:
+// the batch is cut into groups of 4 images (a remainder of 2 or 3 gives one
+// group of 2, an odd remainder one group of 1, in that order), and element
+// c + 2 of row r holds X_k[r][c] of the group's w images side by side, for
+// c = -2 .. N+1 (pitch Pp elements of w floats, zero outside the image).
+// Group (k0, w) starts k0 * F * N * Pp floats into the buffer.  One 16-byte
+// load at c and one at c + 1 then fetch both taps of 4 images, and a warp's
+// rays touch half the bytes they touch in the pair layouts.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -81,7 +91,25 @@ struct Tuning {
     int fwd_stage = 0, der_stage = 0;
     int adj_stage = 0;  // 0: gather through L1; 8 or 16: views per shared-memory block of the
                         // staged FP32 transpose, whose adj_split is then CTAs per tile
+    int fwd_layout = 0; // 1: the FP32 L1-gather forward (fwd_stage 0, fwd_kb 4 or 8, parallel
+                        // beam) reads the interleaved images; 0: the pair images
 };
+
+// Group of image k in the interleaved layout of a batch of K: first image k0, width w.
+__host__ __device__ inline void interleave_group(int k, int K, int &k0, int &w)
+{
+    const int n4 = K & ~3;
+    if (k < n4) {
+        k0 = k & ~3;
+        w = 4;
+    } else if (K - n4 >= 2 && k < n4 + 2) {
+        k0 = n4;
+        w = 2;
+    } else {
+        k0 = K - 1;
+        w = 1;
+    }
+}
 
 struct Handle {
     int N = 0, B = 0, V = 0, F = 1, max_batch = 1, precision = 0, device = 0;
@@ -97,6 +125,8 @@ struct Handle {
     void *d_px = nullptr;     // pair images, rows of X:   (max_batch + 1) * F * N * Pp pairs
     void *d_pt = nullptr;     // pair images, rows of X^T: (max_batch + 1) * F * N * Pp pairs
     void *d_yp = nullptr;     // pair sinograms: max_batch * V * Pb pairs
+    float *d_qx = nullptr;    // interleaved images, rows of X and of X^T: max_batch * F * N * Pp
+    float *d_qt = nullptr;    // floats each, allocated when fwd_layout 1 is set (FP32 handles)
     double *d_partial = nullptr;  // per (image, view, chunk) reduction partials, 4 per item, max_batch images
     void *d_segpart = nullptr;    // segment partials of the staged forward (sinograms):
                                   // 3 * max_batch * max(V * B, F * N * N) floats, allocated
@@ -116,6 +146,7 @@ struct Handle {
     // them again (its batch at most this).  The solvers and the autotuner,
     // which lay out images of their own, clear it.
     int img_ready = 0;
+    int img_kind = 0;  // the layout holding them: 0 pair images, 1 interleaved images
     int num_sms = 0;
     Tuning tune;
 };
@@ -145,12 +176,21 @@ cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int 
 template <typename T>
 cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int *skip = nullptr,
                                 const double *theta = nullptr, const double *delta = nullptr);
+// Interleaved images of X and X^T for a batch of `batch` images of F frames
+// (into d_qx / d_qt), with the view-table step as in launch_pairs_img.
+cudaError_t launch_interleave_img(const Handle &h, const float *X, int batch, const double *theta = nullptr,
+                                  const double *delta = nullptr);
+// The pair images of the first `batch` images from the interleaved ones.
+cudaError_t launch_interleaved_to_pairs(const Handle &h, int batch);
 
 // stage > 0 (FP32 only): rows per shared-memory block of the band-staged
-// march (ct_band.cu); 0: gathers through L1.
+// march (ct_band.cu); 0: gathers through L1.  interleaved (FP32, parallel
+// beam): the first `batch` images of the interleaved layout of a batch of
+// layout_batch (>= batch) are read from d_qx / d_qt, 8 per lane when kb is 8,
+// else 4 (stage is then ignored).
 template <typename T>
 cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, int stage,
-                           const int *skip = nullptr);
+                           const int *skip = nullptr, bool interleaved = false, int layout_batch = 0);
 template <typename T>
 cudaError_t launch_adjoint(const Handle &h, T *X, int batch, int kb, int split, int stage,
                            const int *skip = nullptr);

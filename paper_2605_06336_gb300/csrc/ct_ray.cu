@@ -273,6 +273,88 @@ __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair
     }
 }
 
+// X -> interleaved images of X and X^T (FP32): each CTA writes a 32 x 32
+// element tile of one orientation, of one frame of one group, with the
+// group's images staged together so that every element is written as one
+// vector of w floats.  With p.on the last column of CTAs carries the
+// view-table step, as in k_pairs_img.
+__global__ void __launch_bounds__(256) k_interleave_img(const float *__restrict__ X, float *__restrict__ QX,
+                                                        float *__restrict__ QT, int N, int Pp, int F, int K,
+                                                        ViewPrep p)
+{
+    extern __shared__ unsigned long long prep_key[];
+    if (p.on && blockIdx.x == gridDim.x - 1) {
+        if (blockIdx.y == 0 && blockIdx.z == 0) view_prep_block(p, prep_key);
+        return;
+    }
+    // rows of X:    t[j][i][e] = X_j[r0 + i][e0 - 2 + e]
+    // columns of X: t[j][e][i] = X_j[e0 - 2 + e][r0 + i]
+    __shared__ float t[4][32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int e0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int n4 = K & ~3, rem = K - n4;
+    const int ngroups = n4 / 4 + (rem >= 2 ? 1 : 0) + (rem & 1);
+    for (int z = blockIdx.z; z < 2 * F * ngroups; z += gridDim.z) {
+        const int trans = z & 1, gf = z >> 1;
+        const int gi = gf / F, f = gf - gi * F;
+        int k0, w;
+        interleave_group(gi < n4 / 4 ? 4 * gi : (gi == n4 / 4 && rem >= 2 ? n4 : K - 1), K, k0, w);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < w) {
+                const float *src = X + ((size_t)(k0 + j) * F + f) * N * N;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int i = ty + 8 * m;
+                    const int rr = trans ? e0 - 2 + i : r0 + i, cc = trans ? r0 + tx : e0 - 2 + tx;
+                    t[j][i][tx] = (rr >= 0 && rr < N && cc >= 0 && cc < N) ? src[(size_t)rr * N + cc] : 0.0f;
+                }
+            }
+        }
+        __syncthreads();
+        float *Q = (trans ? QT : QX) + (size_t)k0 * F * N * Pp;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int i = ty + 8 * m;
+            const int r = r0 + i, e = e0 + tx;
+            if (r >= N || e >= Pp) continue;
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = trans ? t[j][tx][i] : t[j][i][tx];
+            float *q = Q + (((size_t)f * N + r) * Pp + e) * w;
+            if (w == 4)
+                *reinterpret_cast<float4 *>(q) = make_float4(v[0], v[1], v[2], v[3]);
+            else if (w == 2)
+                *reinterpret_cast<float2 *>(q) = make_float2(v[0], v[1]);
+            else
+                *q = v[0];
+        }
+    }
+}
+
+// Pair images of the first nimg images of a batch of K from the interleaved
+// ones: pair e of a row is (element e, element e + 1), zero past the row end.
+__global__ void k_interleaved_to_pairs(const float *__restrict__ QX, const float *__restrict__ QT,
+                                       float2 *__restrict__ PX, float2 *__restrict__ PT, int N, int Pp, int F,
+                                       int K, int nimg)
+{
+    const long long per = (long long)F * N * Pp;  // elements per image
+    const long long total = (long long)nimg * per;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / per);
+        const long long el = idx - k * per;
+        const int e = (int)(el % Pp);
+        int k0, w;
+        interleave_group(k, K, k0, w);
+        const size_t o = (size_t)k0 * per + (size_t)el * w + (k - k0);
+        const bool last = e + 1 >= Pp;
+        PX[idx] = make_float2(QX[o], last ? 0.0f : QX[o + w]);
+        PT[idx] = make_float2(QT[o], last ? 0.0f : QT[o + w]);
+    }
+}
+
 // YP[row][bp] = (Y[row][bp - 2], Y[row][bp - 1]), zero outside [0, B).
 // With p.on, the last CTA runs the view-table step of the call instead.
 template <typename T>
@@ -308,7 +390,36 @@ __global__ void k_pairs_sino(const T *__restrict__ Y, pair_t<T> *__restrict__ YP
 // same image band row by row and share it in L1.  SPLIT warps march
 // consecutive row segments of the same rays and are combined in shared memory
 // in a fixed order.
-template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
+// Both taps of the KB images of an interleaved group at element e of a row
+// (q points at element e): one vector load at e and one at e + 1 for each
+// group of 4 images (gstride floats per image between the groups).
+template <int KB>
+__device__ __forceinline__ void taps_interleaved(const float *__restrict__ q, long long gstride, float2 (&p)[KB])
+{
+    if constexpr (KB >= 4) {
+#pragma unroll
+        for (int h = 0; h < KB / 4; ++h) {
+            const float4 *e = reinterpret_cast<const float4 *>(q + (size_t)h * 4 * gstride);
+            const float4 x = __ldg(e), y = __ldg(e + 1);
+            p[4 * h + 0] = make_float2(x.x, y.x);
+            p[4 * h + 1] = make_float2(x.y, y.y);
+            p[4 * h + 2] = make_float2(x.z, y.z);
+            p[4 * h + 3] = make_float2(x.w, y.w);
+        }
+    } else if constexpr (KB == 2) {
+        const float2 *e = reinterpret_cast<const float2 *>(q);
+        const float2 x = __ldg(e), y = __ldg(e + 1);
+        p[0] = make_float2(x.x, y.x);
+        p[1] = make_float2(x.y, y.y);
+    } else {
+        p[0] = make_float2(__ldg(q), __ldg(q + 1));
+    }
+}
+
+// QL (FP32 forward only): the images come from the interleaved layout; the
+// taps, the fractions and the order of the sums are those of the pair form,
+// so both give the same bits.
+template <typename T, int MODE, bool OFFS, int KB, int SPLIT, bool QL = false>
 __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
 {
     using P2 = pair_t<T>;
@@ -354,7 +465,40 @@ __global__ void __launch_bounds__(512) k_ray(RayArgs<T> a)
             // before any of them is used, so U*KB gathers are in flight per warp.
             constexpr int U = KB >= 4 ? 4 : 8;
             const int pp = a.Pp;
-            if constexpr (MODE == kFwd) {
+            if constexpr (MODE == kFwd && QL) {
+                constexpr int QW = KB >= 4 ? 4 : KB;  // floats per element of the group's layout
+                const float *q = (g.mode ? a.QT : a.QX) + (size_t)k0 * a.qimg_stride +
+                                 (((size_t)g.frame * N + r0) * pp + 2) * QW;
+                int r = r0;
+                for (; r + U - 1 <= r1; r += U) {
+                    P2 p[U][KB];
+                    T f[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const long long Qu = Q + (long long)u * dQ;
+                        const int cell = min(max(cell_of(Qu), -2), N);
+                        f[u] = frac_of(Qu, T());
+                        taps_interleaved<KB>(q + ((size_t)u * pp + cell) * QW, a.qimg_stride, p[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const T omf = T(1) - f[u];
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) acc[k] = fma(omf, p[u][k].x, fma(f[u], p[u][k].y, acc[k]));
+                    }
+                    q += (size_t)U * pp * QW;
+                    Q += (long long)U * dQ;
+                }
+                for (; r <= r1; ++r, q += (size_t)pp * QW, Q += dQ) {
+                    const int cell = min(max(cell_of(Q), -2), N);
+                    const T fr = frac_of(Q, T());
+                    const T omf = T(1) - fr;
+                    P2 p[KB];
+                    taps_interleaved<KB>(q + (size_t)cell * QW, a.qimg_stride, p);
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) acc[k] = fma(omf, p[k].x, fma(fr, p[k].y, acc[k]));
+                }
+            } else if constexpr (MODE == kFwd) {
                 int r = r0;
                 for (; r + U - 1 <= r1; r += U) {
                     P2 p[U][KB];
@@ -529,13 +673,14 @@ template <typename T> RayArgs<T> base_args(const Handle &h)
     a.order = h.d_order;
     a.VW = 1;
     a.segs = 1;
+    a.kend = 1 << 30;
     return a;
 }
 
-template <typename T, int MODE, bool OFFS, int KB, int SPLIT>
+template <typename T, int MODE, bool OFFS, int KB, int SPLIT, bool QL = false>
 cudaError_t run_ray(const Handle &h, const RayArgs<T> &a)
 {
-    auto kern = k_ray<T, MODE, OFFS, KB, SPLIT>;
+    auto kern = k_ray<T, MODE, OFFS, KB, SPLIT, QL>;
     constexpr int NACC = (MODE == kFwd) ? KB : 3 * KB;
     const int threads = 32 * SPLIT * a.VW;
     const size_t smem = SPLIT > 1 ? (size_t)a.VW * SPLIT * NACC * 32 * sizeof(T) : 0;
@@ -566,6 +711,18 @@ cudaError_t run_ray_any(const Handle &h, const RayArgs<T> &a, int split, int sta
         if (stage > 0 && band_shape_ok(MODE, KB, a.VW, stage)) return run_ray_band(h, a, MODE, OFFS, KB, stage);
     }
     return run_ray_split<T, MODE, OFFS, KB>(h, a, split);
+}
+
+// The FP32 forward on the interleaved images: kb 8 (two groups of 4), 4, 2 or 1.
+template <int KB>
+cudaError_t run_fwd_interleaved(const Handle &h, const RayArgs<float> &a, int split)
+{
+    switch (split) {
+    case 1: return run_ray<float, kFwd, false, KB, 1, true>(h, a);
+    case 2: return run_ray<float, kFwd, false, KB, 2, true>(h, a);
+    case 4: return run_ray<float, kFwd, false, KB, 4, true>(h, a);
+    default: return run_ray<float, kFwd, false, KB, 8, true>(h, a);
+    }
 }
 
 template <typename T>
@@ -663,6 +820,30 @@ cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int
     return launch_pairs_img<T>(h, X, nimg, skip, theta, delta);
 }
 
+cudaError_t launch_interleave_img(const Handle &h, const float *X, int batch, const double *theta,
+                                  const double *delta)
+{
+    if (!h.d_qx || h.fan_D > 0.0 || batch < 1 || batch > h.max_batch) return cudaErrorInvalidValue;
+    const ViewPrep p = view_prep_args(h, theta, delta);
+    cudaError_t e = allow_prep_smem(k_interleave_img);
+    if (e != cudaSuccess) return e;
+    const int n4 = batch & ~3, rem = batch - n4;
+    const int ngroups = n4 / 4 + (rem >= 2 ? 1 : 0) + (rem & 1);
+    dim3 grid((h.Pp + 31) / 32 + (p.on ? 1 : 0), (h.N + 31) / 32, std::max(1, std::min(2 * h.F * ngroups, 65535)));
+    k_interleave_img<<<grid, 256, prep_smem(p), h.stream>>>(X, h.d_qx, h.d_qt, h.N, h.Pp, h.F, batch, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interleaved_to_pairs(const Handle &h, int batch)
+{
+    if (!h.d_qx || h.precision != 0 || batch < 1 || batch > h.max_batch) return cudaErrorInvalidValue;
+    const long long total = (long long)batch * h.F * h.N * h.Pp;
+    const long long blocks = std::min<long long>((total + 255) / 256, (long long)h.num_sms * 16);
+    k_interleaved_to_pairs<<<(int)std::max<long long>(1, blocks), 256, 0, h.stream>>>(
+        h.d_qx, h.d_qt, (float2 *)h.d_px, (float2 *)h.d_pt, h.N, h.Pp, h.F, batch, batch);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int *skip, const double *theta,
                               const double *delta)
@@ -688,12 +869,45 @@ cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int 
 }
 
 template <typename T>
-cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, int stage, const int *skip)
+cudaError_t launch_forward(const Handle &h, T *Y, int batch, int kb, int split, int vw, int stage, const int *skip,
+                           bool interleaved, int layout_batch)
 {
     RayArgs<T> a = base_args<T>(h);
     a.Y = Y;
     a.skip = skip;
     a.VW = vw;
+    if (interleaved) {
+        // The groups of the layout (a batch of layout_batch images: groups of 8 = two
+        // interleaved groups of 4, or 4, then the remainder's 2 and 1) that hold one of
+        // the first `batch` images; images past `batch` in the last of them are read
+        // but not written.
+        if constexpr (std::is_same<T, float>::value) {
+            if (!h.d_qx || h.fan_D > 0.0 || layout_batch < batch || layout_batch > h.max_batch)
+                return cudaErrorInvalidValue;
+            a.QX = h.d_qx;
+            a.QT = h.d_qt;
+            a.qimg_stride = (long long)h.F * h.N * h.Pp;
+            a.kend = batch;
+            int k = 0;
+            for (int width : {8, 4, 2, 1}) {
+                if (width == 8 && kb < 8) continue;
+                if (k >= batch) break;
+                const int groups = std::min((layout_batch - k) / width, (batch - k + width - 1) / width);
+                if (groups == 0) continue;
+                a.kbase = k;
+                a.ngroups = groups;
+                cudaError_t e = width == 8   ? run_fwd_interleaved<8>(h, a, split)
+                                : width == 4 ? run_fwd_interleaved<4>(h, a, split)
+                                : width == 2 ? run_fwd_interleaved<2>(h, a, split)
+                                             : run_fwd_interleaved<1>(h, a, split);
+                if (e != cudaSuccess) return e;
+                k += groups * width;
+            }
+            return cudaSuccess;
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     // band-staged FP32 march with `split` CTAs per ray: segment partials go to Y and d_segpart
     const bool band = std::is_same<T, float>::value && stage > 0 && band_shape_ok(kFwd, 1, vw, stage) &&
                       !(h.fan_D > 0.0);
@@ -809,7 +1023,7 @@ cudaError_t launch_gn(const Handle &h, const T *bdata, T *res, double *grad, dou
                                               const double *);                                             \
     template cudaError_t launch_prep_forward<T>(const Handle &, const T *, int, const int *, const double *, \
                                                 const double *);                                           \
-    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, int, const int *);     \
+    template cudaError_t launch_forward<T>(const Handle &, T *, int, int, int, int, int, const int *, bool, int); \
     template cudaError_t launch_jvp<T>(const Handle &, const double *, const double *, T *, int, int, int, int, \
                                        int, long long);                                                   \
     template cudaError_t launch_vjp<T>(const Handle &, const T *, double *, double *, int, int, int, int, int, \

@@ -247,7 +247,7 @@ def ct_autotune(h):
 
 TUNING_FIELDS = ("fwd_images_per_lane", "fwd_warps_per_ray", "fwd_views_per_cta", "adj_images_per_thread",
                  "adj_view_groups", "jac_warps_per_ray", "jac_views_per_cta", "fwd_staging", "jac_staging",
-                 "adj_staging", "jac_images_per_lane")
+                 "adj_staging", "jac_images_per_lane", "fwd_interleaved")
 
 
 def ct_get_tuning(h):
@@ -257,6 +257,11 @@ def ct_get_tuning(h):
 
 
 def ct_set_tuning(h, values):
+    """The ct_set_tuning values in TUNING_FIELDS order; without the last one
+    (fwd_interleaved) the forward reads the pair images."""
+    values = list(values)
+    if len(values) == len(TUNING_FIELDS) - 1:
+        values.append(0)
     if len(values) != len(TUNING_FIELDS):
         raise ValueError(f"expected {len(TUNING_FIELDS)} launch-shape values, got {len(values)}")
     buf = (ctypes.c_int32 * len(TUNING_FIELDS))(*[int(v) for v in values])

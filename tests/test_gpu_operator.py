@@ -270,10 +270,11 @@ def test_large_image_sampled_views(ct):
     assert rel(host(op.adjoint(dev(y, torch.float32), th)), oracle.adjoint(g, theta, y)) <= 1e-5
 
 
-@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 1], [2, 4, 2, 2, 2, 2, 4, 0, 0, 8, 2],
-                                    [8, 8, 2, 8, 4, 8, 2, 0, 0, 16, 4], [4, 2, 8, 1, 4, 4, 4, 0, 4, 0, 1],
-                                    [8, 1, 8, 8, 2, 1, 8, 8, 8, 16, 2], [4, 1, 4, 2, 2, 1, 4, 4, 8, 8, 4],
-                                    [2, 2, 8, 4, 1, 2, 8, 8, 4, 16, 1], [8, 1, 4, 1, 1, 1, 8, 4, 0, 8, 4]])
+@pytest.mark.parametrize("tuning", [[1, 1, 1, 1, 1, 1, 1, 0, 0, 0, 1, 0], [2, 4, 2, 2, 2, 2, 4, 0, 0, 8, 2, 0],
+                                    [8, 8, 2, 8, 4, 8, 2, 0, 0, 16, 4, 0], [4, 2, 8, 1, 4, 4, 4, 0, 4, 0, 1, 0],
+                                    [8, 1, 8, 8, 2, 1, 8, 8, 8, 16, 2, 0], [4, 1, 4, 2, 2, 1, 4, 4, 8, 8, 4, 0],
+                                    [2, 2, 8, 4, 1, 2, 8, 8, 4, 16, 1, 0], [8, 1, 4, 1, 1, 1, 8, 4, 0, 8, 4, 0],
+                                    [4, 4, 1, 8, 2, 4, 1, 0, 0, 8, 2, 1], [8, 2, 8, 4, 4, 2, 2, 0, 0, 0, 4, 1]])
 def test_results_do_not_depend_on_launch_shapes(ct, tuning):
     N, B, vpf = 40, 59, [7, 13]
     V = sum(vpf)
@@ -306,8 +307,9 @@ def test_autotune_picks_valid_shapes(ct):
     w = synth.make_workload("C2")
     op = ct.CTOperator(w.N, w.B, w.V, max_batch=8, dtype=torch.float32)
     t = op.autotune()
-    assert len(t) == 11 and all(x in (1, 2, 4, 8) for x in t[:7]) and t[7] in (0, 4, 8) and t[8] in (0, 4, 8)
-    assert t[9] in (0, 8, 16) and t[10] in (1, 2, 4)
+    assert len(t) == 12 and all(x in (1, 2, 4, 8) for x in t[:7]) and t[7] in (0, 4, 8) and t[8] in (0, 4, 8)
+    assert t[9] in (0, 8, 16) and t[10] in (1, 2, 4) and t[11] in (0, 1)
+    assert t[11] == 0 or (t[0] in (4, 8) and t[7] == 0)
     th = dev(w.theta_true)
     x = w.images.reshape(1, -1)
     g = oracle.Geometry(w.N, w.B, w.V)
@@ -409,4 +411,79 @@ def test_image_reuse_with_null_x(ct, dtype):
     op.autotune()
     with pytest.raises(ct.CTError):
         op.jacT(None, th1, R[0])
+    op.close()
+
+
+@pytest.mark.parametrize("kb,split,vw", [(4, 4, 1), (8, 2, 2), (4, 1, 8), (8, 8, 1)])
+def test_interleaved_forward_matches_the_pair_form(ct, kb, split, vw):
+    """The forward on the interleaved images takes the same taps, fractions and
+    sums as on the pair images: the same bits for every batch size (groups of
+    8 / 4 and the remainder's 2 and 1), uneven frames with an empty one, and
+    offsets; within the FP32 bound of the oracle."""
+    N, B, vpf = 37, 55, [9, 0, 6, 4]
+    V = sum(vpf)
+    rng = np.random.default_rng(61)
+    theta = synth.random_angles(V, rng)
+    delta = rng.normal(0, 0.7, V)
+    F = len(vpf)
+    X = rng.uniform(size=(11, F * N * N))
+    pairs = ct.CTOperator(N, B, V, vpf, max_batch=11, dtype=torch.float32)
+    inter = ct.CTOperator(N, B, V, vpf, max_batch=11, dtype=torch.float32)
+    pairs.tuning = [kb, split, vw, 4, 2, 4, 1, 0, 0, 0, 1, 0]
+    inter.tuning = [kb, split, vw, 4, 2, 4, 1, 0, 0, 0, 1, 1]
+    th, dl = dev(theta), dev(delta)
+    Xg = dev(X, torch.float32)
+    g = oracle.Geometry(N, B, V, vpf)
+    for K in (1, 2, 3, 4, 5, 6, 7, 8, 11):
+        y0 = pairs.forward(Xg[:K], th, dl)
+        y1 = inter.forward(Xg[:K], th, dl)
+        assert torch.equal(y0, y1), K
+    yo = oracle.forward(g, theta, X, delta)
+    assert rel(host(y1), yo) <= 1e-5
+    assert rows_rel(host(y1), yo, B) <= 1e-5
+    pairs.close()
+    inter.close()
+
+
+def test_interleaved_layout_reuse(ct):
+    """After a forward on interleaved images, x = NULL still means that call's
+    images: the forward and its repeat read the interleaved layout again, and
+    the Jacobian products (which read pair images) get them converted, bit for
+    bit what passing the images gives."""
+    N, B, vpf = 33, 47, [6, 5]
+    V = sum(vpf)
+    rng = np.random.default_rng(62)
+    op = ct.CTOperator(N, B, V, vpf, max_batch=7, dtype=torch.float32)
+    op.tuning = [4, 2, 2, 4, 2, 4, 1, 0, 0, 0, 2, 1]
+    assert op.tuning[11] == 1
+    th1, th2 = dev(synth.random_angles(V, rng)), dev(synth.random_angles(V, rng))
+    dl = dev(rng.normal(0, 0.5, V))
+    X = dev(rng.uniform(size=(7, op.n)), torch.float32)
+    R = dev(rng.standard_normal((7, V * B)), torch.float32)
+    dth = dev(rng.standard_normal(V))
+    y_ref = op.forward(X, th2, dl).clone()
+    dY_ref = op.jac_batch(X[:6], th1, dth).clone()
+    g_ref = op.jacT(X[0], th2, R[0], dl, want_delta=True)
+    g_ref = (g_ref[0].clone(), g_ref[1].clone())
+    op.forward(X, th1)
+    assert torch.equal(op.forward(None, th2, dl, batch=7), y_ref)
+    y1 = torch.zeros_like(y_ref)
+    ct.ct_forward_repeat(op.h, y1, 7)
+    assert torch.equal(y1, y_ref)
+    # batches ending inside a group of the layout (4 + 2 + 1): the images past the
+    # batch are read but not written
+    for nb in (1, 3, 5, 6):
+        y1.zero_()
+        ct.ct_forward(op.h, th2, dl, None, y1, nb)
+        assert torch.equal(y1[:nb], y_ref[:nb]) and not y1[nb:].any(), nb
+        y1.zero_()
+        ct.ct_forward_repeat(op.h, y1, nb)
+        assert torch.equal(y1[:nb], y_ref[:nb]) and not y1[nb:].any(), nb
+    dY = torch.empty(6, V * B, device="cuda")
+    ct.ct_jac_batch(op.h, th1, None, None, dth, None, dY, 6)   # converts to pair images
+    assert torch.equal(dY, dY_ref)
+    g = op.jacT(None, th2, R[0], dl, want_delta=True)
+    assert torch.equal(g[0], g_ref[0]) and torch.equal(g[1], g_ref[1])
+    # the pair images are current now: the forward reads them and agrees
+    assert torch.equal(op.forward(None, th2, dl, batch=7), y_ref)
     op.close()
