@@ -48,8 +48,9 @@ LSU_BYTES_PER_CLK_SM = 128          # L1/shared data path per SM per clock
 NUM_SMS = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
 
-# DRAM traffic of the dominant kernels per byte of the pair layout they read
-# (the images' pairs for the forward, the sinograms' pairs for the transpose):
+# DRAM traffic of the dominant kernels per byte of the layout they read (the
+# images' pairs or the interleaved images for the forward, the sinograms' pairs
+# for the transpose):
 # ncu's dram__bytes_read.sum + dram__bytes_write.sum of one launch (cold
 # cache) divided by that launch's pair footprint.  The traffic reported for a
 # launch is this ratio times its own footprint (the ray kernels read each pair
@@ -58,6 +59,8 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 TRAFFIC_PER_FOOTPRINT = {
     "forward": 8.56e6 / (2 * 8 * 256 * 260 * 8),        # k_ray<float, kFwd>: 8.56 MB for 8.52 MB of X and X^T pairs
     "forward_staged": 8.58e6 / (2 * 8 * 256 * 260 * 8),  # k_ray_band
+    # k_ray<float, kFwd, ..., interleaved>: 4.30 MB for 4.26 MB of interleaved X and X^T
+    "forward_interleaved": 4.30e6 / (2 * 8 * 256 * 260 * 4),
     "adjoint": 3.95e6 / (8 * 180 * 368 * 8),            # k_adjoint: 3.95 MB for 4.24 MB of sinogram pairs
     "adjoint_staged": 4.04e6 / (8 * 180 * 368 * 8),      # k_adj_band
 }
@@ -471,11 +474,12 @@ class OperatorStep:
     """H on K images, H^T on K sinograms, J dtheta and J^T r on one image, through
     the C ABI, with the inputs resident on the device.  J^T is taken at the
     image of the J call, whose pair layouts it uses again (x = NULL), as a
-    Gauss-Newton step does.  `step` runs the four calls in order on one handle;
-    `step_overlapped` runs H^T on a second handle of the same geometry and
-    launch shapes, on a stream of its own, while H, J and J^T run on the first
-    (the four calls are independent; a handle's workspace serves one stream),
-    so that the shared-memory-bound transpose overlaps the L2-bound forward."""
+    Gauss-Newton step does, with r = H's first sinogram.  `step` runs the four
+    calls in order on one handle; `step_overlapped` runs them on three handles of
+    the same geometry and launch shapes, each on a stream of its own (a handle's
+    workspace serves one stream): H on the first, H^T on the second, J and then
+    J^T (after H) on the third, so that the shared-memory-bound transpose and the
+    latency-bound Jacobian products overlap the L2-bound forward."""
 
     def __init__(self, w, K, dtype, dev, tuning=None, delta=None, seed=100):
         import torch
@@ -496,6 +500,9 @@ class OperatorStep:
         self.opT = ct.CTOperator(N, B, V, max_batch=K, dtype=dtype)  # H^T's handle in step_overlapped
         self.opT.tuning = self.tuning
         self.sideT = torch.cuda.Stream(device=dev)
+        self.opJ = ct.CTOperator(N, B, V, max_batch=K, dtype=dtype)  # J's and J^T's
+        self.opJ.tuning = self.tuning
+        self.sideJ = torch.cuda.Stream(device=dev)
         self.theta = torch.tensor(w.theta_true, dtype=torch.float64, device=dev)
         self.delta = None if delta is None else torch.tensor(delta, dtype=torch.float64, device=dev)
         self.delta_h = delta
@@ -526,10 +533,14 @@ class OperatorStep:
             ev[4].record(stream)
 
     def step_overlapped(self):
-        """The same four calls with H^T on opT and its own stream, forked from and
-        joined back into the current stream (two branches of one graph when captured)."""
-        _, overlapped = four_call_steps(self.op, self.opT, self.sideT, self.theta, self.X, self.Y, self.Ys, self.Xa,
-                                        self.dth, self.dy, self.gt, self.K, dl=self.delta, r=self.Y[0])
+        """The same four calls as three branches forked from and joined back into the
+        current stream (of one graph when captured): H on op, H^T on opT, J and J^T on
+        opJ, J^T after H (its r is H's first sinogram)."""
+        self.overlapped_on(self.theta, self.X, self.Y, self.Ys, self.Xa, self.dth, self.dy, self.gt)
+
+    def overlapped_on(self, th, X, Y, Ys, Xa, dth, dy, gt):
+        _, overlapped = four_call_steps(self.op, self.opT, self.sideT, th, X, Y, Ys, Xa, dth, dy, gt, self.K,
+                                        dl=self.delta, r=Y[0], opJ=self.opJ, sideJ=self.sideJ, r_from_forward=True)
         overlapped()
 
     def kernels_alone(self, flush, reps=200):
@@ -822,11 +833,14 @@ def streaming_c5(dev, passes, scale=1.0, k_max=None):
 STREAM_KMAX = 100  # the memory-bounded basis of the large streaming workload
 
 
-def four_call_steps(op, opT, side, th, X, Y, Ys, Xa, dth, dy, gt, K, dl=None, r=None):
+def four_call_steps(op, opT, side, th, X, Y, Ys, Xa, dth, dy, gt, K, dl=None, r=None, opJ=None, sideJ=None,
+                    r_from_forward=False):
     """The step's four calls (H on X, H^T on Ys, J dth and J^T r at X[0]; r defaults
-    to Ys[0]) in order on op (sequential), and with H^T on opT and stream `side`,
-    forked from and joined back into the current stream (overlapped: two branches
-    of one graph when captured)."""
+    to Ys[0]) in order on op (sequential), and overlapped: forked from and joined
+    back into the current stream (branches of one graph when captured), H^T on
+    opT and stream `side`; with opJ, J and J^T on opJ and stream sideJ, a third
+    branch, whose J^T waits for the forward when r_from_forward (r is one of the
+    forward's sinograms); without it, J and J^T follow H on op."""
     import torch
     from paper_2605_06336_gb300 import ct
     r = Ys[0] if r is None else r
@@ -841,17 +855,32 @@ def four_call_steps(op, opT, side, th, X, Y, Ys, Xa, dth, dy, gt, K, dl=None, r=
         cur = torch.cuda.current_stream()
         fork = torch.cuda.Event()
         fork.record(cur)
-        side.wait_event(fork)
+        branches = [side] + ([sideJ] if opJ else [])
+        for b in branches:
+            b.wait_event(fork)
         op.set_stream(cur)
         opT.set_stream(side)
+        if opJ:
+            opJ.set_stream(sideJ)
+            with torch.cuda.stream(sideJ):
+                ct.ct_jac(opJ.h, th, dl, X[0], dth, None, dy)
         ct.ct_forward(op.h, th, dl, X, Y, K)
+        if opJ and r_from_forward:
+            done = torch.cuda.Event()
+            done.record(cur)
+            sideJ.wait_event(done)
         with torch.cuda.stream(side):
             ct.ct_adjoint(opT.h, th, dl, Ys, Xa, K)
-        ct.ct_jac(op.h, th, dl, X[0], dth, None, dy)
-        ct.ct_jacT(op.h, th, dl, None, r, gt, None)
-        join = torch.cuda.Event()
-        join.record(side)
-        cur.wait_event(join)
+        if opJ:
+            with torch.cuda.stream(sideJ):
+                ct.ct_jacT(opJ.h, th, dl, None, r, gt, None)
+        else:
+            ct.ct_jac(op.h, th, dl, X[0], dth, None, dy)
+            ct.ct_jacT(op.h, th, dl, None, r, gt, None)
+        for b in branches:
+            join = torch.cuda.Event()
+            join.record(b)
+            cur.wait_event(join)
 
     return sequential, overlapped
 
@@ -884,16 +913,21 @@ def batched_frames(dev, steps, flush):
     gt = torch.empty(w.V, dtype=torch.float64, device=dev)
     opT = ct.CTOperator(w.N, w.B, w.V, w.views_per_frame, max_batch=K, dtype=torch.float32)
     opT.tuning = tuning
-    seq, ovl = four_call_steps(op, opT, torch.cuda.Stream(device=dev), th, X, Y, Ys, Xa, dth, dy, gt, K)
+    opJ = ct.CTOperator(w.N, w.B, w.V, w.views_per_frame, max_batch=K, dtype=torch.float32)
+    opJ.tuning = tuning
+    seq, ovl = four_call_steps(op, opT, torch.cuda.Stream(device=dev), th, X, Y, Ys, Xa, dth, dy, gt, K,
+                               opJ=opJ, sideJ=torch.cuda.Stream(device=dev))
     samples = w.V * w.B * (K + K + 1 + 1)
     out = {"workload": f"C4: {w.F} frames of {w.N}x{w.N}, {w.V} views in total "
                        f"({min(w.views_per_frame)}-{max(w.views_per_frame)} per frame), {w.B} bins, Krylov block {K}",
            **overlap_lines(op, seq, ovl, steps, flush, samples),
            "tuning": dict(zip(ct.TUNING_FIELDS, tuning)),
-           "launch": "CUDA graph replay, H^T on a second handle and stream as in the headline step; the four "
-                     "calls in order on one handle under 'sequential'"}
+           "launch": "CUDA graph replay, three branches on three handles and streams as in the headline step "
+                     "(here J^T's r is an input sinogram, so its branch does not wait for H); the four calls in "
+                     "order on one handle under 'sequential'"}
     op.close()
     opT.close()
+    opJ.close()
     return out
 
 
@@ -919,15 +953,20 @@ def fan_beam_step(dev, steps, flush):
     gt = torch.empty(w.V, dtype=torch.float64, device=dev)
     opT = ct.CTOperator(w.N, w.B, w.V, max_batch=K, dtype=torch.float32, source_distance=D)
     opT.tuning = op.tuning
-    seq, ovl = four_call_steps(op, opT, torch.cuda.Stream(device=dev), th, X, Y, Ys, Xa, dth, dy, gt, K)
+    opJ = ct.CTOperator(w.N, w.B, w.V, max_batch=K, dtype=torch.float32, source_distance=D)
+    opJ.tuning = op.tuning
+    seq, ovl = four_call_steps(op, opT, torch.cuda.Stream(device=dev), th, X, Y, Ys, Xa, dth, dy, gt, K,
+                               opJ=opJ, sideJ=torch.cuda.Stream(device=dev))
     samples = w.V * w.B * (K + K + 1 + 1)
     out = {"workload": f"fan beam, source at {D:.0f} px: {w.N}x{w.N}, {w.V} views, {w.B} bins, Krylov block {K}",
            **overlap_lines(op, seq, ovl, steps, flush, samples),
            "tuning": dict(zip(ct.TUNING_FIELDS, op.tuning)),
-           "launch": "CUDA graph replay, H^T on a second handle and stream as in the headline step; the four "
-                     "calls in order on one handle under 'sequential'"}
+           "launch": "CUDA graph replay, three branches on three handles and streams as in the headline step "
+                     "(here J^T's r is an input sinogram, so its branch does not wait for H); the four calls in "
+                     "order on one handle under 'sequential'"}
     op.close()
     opT.close()
+    opJ.close()
     return out
 
 
@@ -1013,7 +1052,7 @@ def main():
     value_eager = job_rate(samples_per_step * args.steps, total_ms, world)
 
     # ---- the headline: the same step replayed from a CUDA graph (what the solver and a serving loop
-    # run), H^T on a second handle and stream: a parallel branch of the graph
+    # run), H^T and the Jacobian products on handles and streams of their own: parallel branches
     g = capture_step(op, s.step_overlapped)
     clock = ClockSampler(torch.cuda.current_device())
     if world > 1:
@@ -1070,8 +1109,6 @@ def main():
     ev_down = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_pipelined(n, start):
-        op.set_stream(stream)
-        s.opT.set_stream(s.sideT)
         s_up.wait_event(start)
         for k in range(n):
             j = k % 2
@@ -1087,18 +1124,8 @@ def main():
             stream.wait_event(ev_up[j])
             if k >= 2:
                 stream.wait_event(ev_down[j])         # step k-2's results have left this slot
-            # as in the headline step: H^T on the second handle and stream, forked and joined
-            fork = torch.cuda.Event()
-            fork.record(stream)
-            s.sideT.wait_event(fork)
-            ct.ct_forward(op.h, sl["theta"], None, sl["X"], sl["Y"], K)
-            with torch.cuda.stream(s.sideT):
-                ct.ct_adjoint(s.opT.h, sl["theta"], None, sl["Ys"], sl["Xa"], K)
-            ct.ct_jac(op.h, sl["theta"], None, sl["X"][0], sl["dth"], None, sl["dy"])
-            ct.ct_jacT(op.h, sl["theta"], None, None, sl["Y"][0], sl["gt"], None)  # the image of the J call
-            join = torch.cuda.Event()
-            join.record(s.sideT)
-            stream.wait_event(join)
+            # as in the headline step: three branches, forked and joined
+            s.overlapped_on(sl["theta"], sl["X"], sl["Y"], sl["Ys"], sl["Xa"], sl["dth"], sl["dy"], sl["gt"])
             ev_done[j].record(stream)
             with torch.cuda.stream(s_down):
                 s_down.wait_event(ev_done[j])
@@ -1212,10 +1239,10 @@ def main():
                                "(J^T reuses the image layout of the J call)",
                    "krylov_block": K, "samples_per_step": samples_per_step,
                    "l2": "flushed between timed steps (512 MB write, outside the events)",
-                   "launch": "step captured once in a CUDA graph and replayed (value): H, J and J^T on one handle "
-                             "and stream, H^T on a second handle of the same geometry on a second stream (a "
-                             "parallel branch of the graph); the four calls in order on one handle under "
-                             "'sequential'; eager launches under 'eager'",
+                   "launch": "step captured once in a CUDA graph and replayed (value): three parallel branches "
+                             "on three handles of the same geometry, each on its own stream: H; H^T; J, then J^T "
+                             "once H is done (its r is H's first sinogram); the four calls in order on one handle "
+                             "under 'sequential'; eager launches under 'eager'",
                    "parallelism": f"replicas x{world}"},
         "gnnz_per_s": nnz_per_step / (graph_ms * 1e-3) / 1e9,
         "gnnz_note": "interpolation nonzeros (two per interpolation step) touched per step over the step time",
@@ -1244,9 +1271,9 @@ def main():
                 "max_abs_diff_vs_serial": e2e_check,
                 "note": "C ABI calls on host data: every step uploads its inputs from pinned memory and downloads "
                         "all its results, inside the timed region; uploads and downloads run on two copy streams "
-                        "overlapping the neighbouring steps' kernels (two device slots), and H^T runs on the "
-                        "second handle and stream as in the headline step; serial_value: the same with copies "
-                        "and the four calls in order on one stream"},
+                        "overlapping the neighbouring steps' kernels (two device slots), and the calls run as "
+                        "the headline step's three branches; serial_value: the same with copies and the four "
+                        "calls in order on one stream"},
         "gpu_launches": launches_per_step(tuning) * args.steps,
         "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
         "tuning": dict(zip(ct.TUNING_FIELDS, tuning)),
