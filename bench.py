@@ -1108,7 +1108,11 @@ def main():
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_down = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_pipelined(n, start):
+    def compute_on(sl):
+        return lambda: s.overlapped_on(sl["theta"], sl["X"], sl["Y"], sl["Ys"], sl["Xa"], sl["dth"], sl["dy"],
+                                       sl["gt"])
+
+    def e2e_pipelined(n, start, graphs=None):
         s_up.wait_event(start)
         for k in range(n):
             j = k % 2
@@ -1124,8 +1128,12 @@ def main():
             stream.wait_event(ev_up[j])
             if k >= 2:
                 stream.wait_event(ev_down[j])         # step k-2's results have left this slot
-            # as in the headline step: three branches, forked and joined
-            s.overlapped_on(sl["theta"], sl["X"], sl["Y"], sl["Ys"], sl["Xa"], sl["dth"], sl["dy"], sl["gt"])
+            # as in the headline step: three branches, forked and joined; replayed from the
+            # slot's graph of those calls, or the calls issued one by one
+            if graphs:
+                graphs[j].replay()
+            else:
+                compute_on(sl)()
             ev_done[j].record(stream)
             with torch.cuda.stream(s_down):
                 s_down.wait_event(ev_done[j])
@@ -1155,10 +1163,23 @@ def main():
     w0.record(stream)
     e2e_pipelined(3, w0)
     torch.cuda.synchronize()
-    e2e_ms = timed(lambda e0: e2e_pipelined(args.steps, e0))
+    e2e_eager_ms = timed(lambda e0: e2e_pipelined(args.steps, e0))
     # the pipelined results must be those of the serial form (same inputs, deterministic kernels)
     e2e_check = max(float((a.double() - b.double()).abs().max()) for a, b in zip((Yp, Xap, dyp, gtp), ref_out))
+    # the same pipeline with each slot's calls captured once in a graph (as a serving loop would):
+    # per step the host issues the copies and one graph launch instead of every call's launches
+    slot_graphs = [capture_step(op, compute_on(sl)) for sl in slots]
+    w1 = torch.cuda.Event()
+    w1.record(stream)
+    e2e_pipelined(3, w1, slot_graphs)
+    torch.cuda.synchronize()
+    for t in (Yp, Xap, dyp, gtp):
+        t.zero_()
+    e2e_ms = timed(lambda e0: e2e_pipelined(args.steps, e0, slot_graphs))
+    e2e_check = max(e2e_check, max(float((a.double() - b.double()).abs().max())
+                                   for a, b in zip((Yp, Xap, dyp, gtp), ref_out)))
     e2e_val = job_rate(samples_per_step * args.steps, e2e_ms, world)
+    e2e_eager_val = job_rate(samples_per_step * args.steps, e2e_eager_ms, world)
     e2e_serial_val = job_rate(samples_per_step * args.steps, e2e_serial_ms, world)
 
     if rank != 0:
@@ -1267,13 +1288,16 @@ def main():
         "dynamic_solver": dynamic,
         "varpro_solver": varpro,
         "e2e": {"value": e2e_val, "unit": "GSamples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_ms / args.steps, "serial_value": e2e_serial_val,
+                "ms_per_step": e2e_ms / args.steps, "eager_value": e2e_eager_val,
+                "eager_ms_per_step": e2e_eager_ms / args.steps, "serial_value": e2e_serial_val,
                 "max_abs_diff_vs_serial": e2e_check,
                 "note": "C ABI calls on host data: every step uploads its inputs from pinned memory and downloads "
                         "all its results, inside the timed region; uploads and downloads run on two copy streams "
                         "overlapping the neighbouring steps' kernels (two device slots), and the calls run as "
-                        "the headline step's three branches; serial_value: the same with copies and the four "
-                        "calls in order on one stream"},
+                        "the headline step's three branches, captured once per slot in a CUDA graph and "
+                        "replayed every step; eager_value: the same with the calls issued one by one every "
+                        "step; serial_value: copies and the four calls in order on one stream, issued one by "
+                        "one"},
         "gpu_launches": launches_per_step(tuning) * args.steps,
         "gpu_launches_note": f"{launches_per_step(tuning)} kernels per step in the replayed graph",
         "tuning": dict(zip(ct.TUNING_FIELDS, tuning)),
