@@ -330,6 +330,22 @@ def test_argument_errors(ct):
     op.forward(X[0], bad)
     assert op.status() == ct.CT_ERR_NAN
     assert op.status() == ct.CT_OK  # the flag is cleared once reported
+    # the interleaved forward layout: FP32 parallel beam, 4 or 8 images per lane, no staging
+    good = [4, 2, 2, 4, 2, 4, 1, 0, 0, 0, 1, 1]
+    for bad_t in ([2, 2, 2, 4, 2, 4, 1, 0, 0, 0, 1, 1],   # 2 images per lane
+                  [4, 2, 4, 4, 2, 4, 1, 4, 0, 0, 1, 1],   # staged forward
+                  good[:11] + [2]):                       # no such layout
+        with pytest.raises(ct.CTError) as e:
+            op.tuning = bad_t
+        assert e.value.code == ct.CT_ERR_ARG
+    op.tuning = good
+    assert op.tuning == good
+    for other in (ct.CTOperator(16, 23, 4, max_batch=2, dtype=torch.float64),
+                  ct.CTOperator(16, 23, 4, max_batch=2, dtype=torch.float32, source_distance=40.0)):
+        with pytest.raises(ct.CTError) as e:
+            other.tuning = good
+        assert e.value.code == ct.CT_ERR_ARG
+        other.close()
 
 
 def test_repeat_reruns_the_projection_alone(ct):
