@@ -226,28 +226,52 @@ def test_adjoint_identity_on_gpu(ct, dtype):
         1e-5 if dtype == torch.float32 else 1e-12)
 
 
-@pytest.mark.parametrize("name", ["C2"])
-def test_full_size_workload_parity(ct, name):
-    """The 256^2 / 180-view / 363-bin workload, batch 8, as the benchmark runs it."""
-    w = synth.make_workload(name)
+@pytest.fixture(scope="module")
+def c2_oracle():
+    """The 256^2 / 180-view / 363-bin workload with a batch of 8 and the oracle's
+    H, H^T, J and J^T on it (computed once for the launch shapes below)."""
+    w = synth.make_workload("C2")
     N, B, V = w.N, w.B, w.V
     g = oracle.Geometry(N, B, V)
     rng = np.random.default_rng(9)
     X = np.concatenate([w.images.reshape(1, -1), rng.uniform(size=(w.batch - 1, N * N))])
-    op = ct.CTOperator(N, B, V, dtype=torch.float32, max_batch=w.batch)
-    th = dev(w.theta_true)
-    Yg = host(op.forward(dev(X, torch.float32), th))
     Yo = oracle.forward(g, w.theta_true, X)
-    assert rel(Yg, Yo) <= 1e-5
-    Xg = host(op.adjoint(dev(Yo, torch.float32), th))
-    Xo = oracle.adjoint(g, w.theta_true, Yo)
-    assert rel(Xg, Xo) <= 1e-5
+    R = rng.standard_normal(Yo.shape)
+    Xo = oracle.adjoint(g, w.theta_true, R)
     dth = rng.standard_normal(V)
-    dy = host(op.jac(dev(X[0], torch.float32), th, dev(dth)))
-    assert rel(dy, oracle.jac(g, w.theta_true, X[0], dth)) <= 1e-5
+    dyo = oracle.jac(g, w.theta_true, X[0], dth)
     r = Yo[0] - oracle.forward(g, w.theta_nominal, X[0])
-    gt = host(op.jacT(dev(X[0], torch.float32), th, dev(r, torch.float32)))
-    assert rel(gt, oracle.jacT(g, w.theta_true, X[0], r)[0]) <= 1e-5
+    gto = oracle.jacT(g, w.theta_true, X[0], r)[0]
+    dt, _ = oracle.dsample(g, w.theta_true, X[0])
+    return dict(w=w, X=X, Yo=Yo, R=R, Xo=Xo, dth=dth, dyo=dyo, r=r, gto=gto, dt=dt)
+
+
+# the default shapes; the ones the autotuner picks in the benchmark's runs (forward on
+# images interleaved in groups of 4, staged transpose in clusters of 4 CTAs); the ones
+# it picks here
+@pytest.mark.parametrize("shape", ["default", [4, 4, 1, 8, 4, 4, 1, 0, 0, 8, 2, 1], "autotune"])
+def test_full_size_workload_parity(ct, c2_oracle, shape):
+    """The 256^2 / 180-view / 363-bin workload, batch 8, as the benchmark runs it:
+    normwise and per view / per image row against the oracle."""
+    o = c2_oracle
+    w = o["w"]
+    N, B, V = w.N, w.B, w.V
+    op = ct.CTOperator(N, B, V, dtype=torch.float32, max_batch=w.batch)
+    if shape == "autotune":
+        op.autotune()
+    elif shape != "default":
+        op.tuning = shape
+    th = dev(w.theta_true)
+    Yg = host(op.forward(dev(o["X"], torch.float32), th))
+    assert rel(Yg, o["Yo"]) <= 1e-5 and rows_rel(Yg, o["Yo"], B) <= 1e-5
+    Xg = host(op.adjoint(dev(o["R"], torch.float32), th))
+    assert rel(Xg, o["Xo"]) <= 1e-5 and rows_rel(Xg, o["Xo"], N) <= 1e-5
+    dy = host(op.jac(dev(o["X"][0], torch.float32), th, dev(o["dth"])))
+    assert rel(dy, o["dyo"]) <= 1e-5 and rows_rel(dy, o["dyo"], B) <= 1e-5
+    gt = host(op.jacT(None, th, dev(o["r"], torch.float32)))  # the image of the J call
+    assert rel(gt, o["gto"]) <= 1e-5
+    assert view_sum_rel(gt, o["gto"], o["r"], o["dt"], V, B) <= 1e-5
+    op.close()
 
 
 def test_large_image_sampled_views(ct):
