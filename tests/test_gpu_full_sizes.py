@@ -157,3 +157,38 @@ def test_2048_image_one_120_view_chunk():
     op = ct.CTOperator(N, B, 120, max_batch=1, dtype=torch.float32)
     op.autotune()
     _check_all(op, oracle.Geometry(N, B, 120), theta, None, X, rng)
+
+
+@pytest.mark.parametrize("size", ["512", "2048"])
+def test_interleaved_forward_at_full_sizes(size):
+    """The forward on images interleaved in groups of 4 (the layout the benchmark's
+    autotuned runs pick at these sizes) at the 512^2 / 360-view workload with offsets
+    and on a 120-view chunk of the 2048^2 grid: the same bits as on the pair images
+    for a batch of 5 (one group of 4 and one single image), and the phantom's
+    sinogram within the FP32 bound of the oracle, per view."""
+    from paper_2605_06336_gb300 import ct
+    rng = np.random.default_rng(45)
+    if size == "512":
+        w = synth.make_workload("C3")
+        N, B, V, theta, delta = w.N, w.B, w.V, w.theta_true, w.delta_true
+        x0 = w.images.reshape(-1)
+    else:
+        N, V = 2048, 120
+        B = synth.n_bins(N)
+        theta = np.sort(rng.uniform(0.0, math.pi, V))
+        delta = None
+        x0 = rng.uniform(size=N * N)
+    X = np.stack([x0] + [rng.uniform(size=N * N) for _ in range(4)])
+    th = dev(theta)
+    dl = None if delta is None else dev(delta)
+    Xg = dev(X, torch.float32)
+    out = []
+    for layout in (0, 1):
+        op = ct.CTOperator(N, B, V, max_batch=5, dtype=torch.float32)
+        op.tuning = [4, 4, 1, 4, 2, 4, 1, 0, 0, 0, 1, layout]
+        out.append(op.forward(Xg, th, dl).clone())
+        op.close()
+    assert torch.equal(out[0], out[1])
+    y = host(out[1][0])
+    yo = oracle.forward(oracle.Geometry(N, B, V), theta, x0, delta)
+    assert rel(y, yo) <= 1e-5 and rows_rel(y, yo, B) <= 1e-5
