@@ -104,15 +104,19 @@ void ct_destroy(ct_handle *h);
  *
  * Image reuse (this call, ct_jac, ct_jacT, ct_gn_terms and the batched
  * forms): every call that takes images lays them out in the handle (pairs
- * of neighbouring pixels along rows and along columns).  Passing X (x) =
+ * of neighbouring pixels along rows and along columns; for this call, with
+ * tuning value [11] = 1 on an FP32 parallel-beam handle, the images
+ * interleaved in groups of 4 instead, see ct_set_tuning).  Passing X (x) =
  * NULL uses the layouts of the previous such call on the handle again,
  * i.e. that call's first `batch` images, at this call's angles and offsets:
  * the Jacobian and its transpose at one image (a Gauss-Newton step, an
- * inner least-squares solve on J) then lay the image out once.  CT_ERR_ARG
- * when no layouts are current (none yet, or an error, ct_autotune or a
- * solver call on the handle since) or batch exceeds that call's.  Calls
- * that take no image (ct_adjoint, the repeats) keep them.  No counterpart
- * in the paper.
+ * inner least-squares solve on J) then lay the image out once.  A Jacobian
+ * product after a forward on interleaved images first turns them into pair
+ * layouts (one more kernel launch); the results are the same either way.
+ * CT_ERR_ARG when no layouts are current (none yet, or an error,
+ * ct_autotune or a solver call on the handle since) or batch exceeds that
+ * call's.  Calls that take no image (ct_adjoint, the repeats) keep them.
+ * No counterpart in the paper.
  */
 int ct_forward(ct_handle *h, const double *theta, const double *delta,
                const void *X, void *Y, int batch);
