@@ -759,11 +759,11 @@ ViewPrep view_prep_args(const Handle &h, const double *theta, const double *delt
 size_t prep_smem(const ViewPrep &p) { return p.on ? sizeof(unsigned long long) * std::min(p.V, kOrderMaxV) : 0; }
 
 // The layout kernels may carry the view-table step in up to 32 KB of dynamic shared memory.
-template <typename K> cudaError_t allow_prep_smem(K kernel)
+template <auto Kernel> cudaError_t allow_prep_smem()
 {
-    static bool done = false;  // per kernel; the attribute is idempotent, so a race is harmless
+    static bool done = false;  // one flag per kernel; the attribute is idempotent, so a race is harmless
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(unsigned long long) * kOrderMaxV));
     if (e == cudaSuccess) done = true;
     return e;
@@ -800,7 +800,7 @@ cudaError_t launch_pairs_img(const Handle &h, const T *X, int nimg, const int *s
                              const double *delta)
 {
     const ViewPrep p = view_prep_args(h, theta, delta);
-    cudaError_t e = allow_prep_smem(k_pairs_img<T>);
+    cudaError_t e = allow_prep_smem<k_pairs_img<T>>();
     if (e != cudaSuccess) return e;
     dim3 grid((h.Pp + 31) / 32 + (p.on ? 1 : 0), (h.N + 31) / 32, std::max(1, std::min(nimg, 65535)));
     k_pairs_img<T><<<grid, 256, prep_smem(p), h.stream>>>(X, (pair_t<T> *)h.d_px, (pair_t<T> *)h.d_pt, h.N, h.Pp,
@@ -825,7 +825,7 @@ cudaError_t launch_interleave_img(const Handle &h, const float *X, int batch, co
 {
     if (!h.d_qx || h.fan_D > 0.0 || batch < 1 || batch > h.max_batch) return cudaErrorInvalidValue;
     const ViewPrep p = view_prep_args(h, theta, delta);
-    cudaError_t e = allow_prep_smem(k_interleave_img);
+    cudaError_t e = allow_prep_smem<k_interleave_img>();
     if (e != cudaSuccess) return e;
     const int n4 = batch & ~3, rem = batch - n4;
     const int ngroups = n4 / 4 + (rem >= 2 ? 1 : 0) + (rem & 1);
@@ -849,7 +849,7 @@ cudaError_t launch_pairs_sino(const Handle &h, const T *Y, int nsino, const int 
                               const double *delta)
 {
     const ViewPrep p = view_prep_args(h, theta, delta);
-    cudaError_t e = allow_prep_smem(k_pairs_sino<T>);
+    cudaError_t e = allow_prep_smem<k_pairs_sino<T>>();
     if (e != cudaSuccess) return e;
     const long long total = (long long)nsino * h.V * h.Pb;
     const int threads = 256;
