@@ -179,7 +179,7 @@ cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int
 // Interleaved images of X and X^T for a batch of `batch` images of F frames
 // (into d_qx / d_qt), with the view-table step as in launch_pairs_img.
 cudaError_t launch_interleave_img(const Handle &h, const float *X, int batch, const double *theta = nullptr,
-                                  const double *delta = nullptr);
+                                  const double *delta = nullptr, const int *skip = nullptr);
 // The pair images of the first `batch` images from the interleaved ones.
 cudaError_t launch_interleaved_to_pairs(const Handle &h, int batch);
 

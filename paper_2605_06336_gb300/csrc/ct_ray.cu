@@ -280,9 +280,10 @@ __global__ void __launch_bounds__(256) k_pairs_img(const T *__restrict__ X, pair
 // view-table step, as in k_pairs_img.
 __global__ void __launch_bounds__(256) k_interleave_img(const float *__restrict__ X, float *__restrict__ QX,
                                                         float *__restrict__ QT, int N, int Pp, int F, int K,
-                                                        ViewPrep p)
+                                                        ViewPrep p, const int *__restrict__ skip)
 {
     extern __shared__ unsigned long long prep_key[];
+    if (skip && *skip) return;
     if (p.on && blockIdx.x == gridDim.x - 1) {
         if (blockIdx.y == 0 && blockIdx.z == 0) view_prep_block(p, prep_key);
         return;
@@ -821,7 +822,7 @@ cudaError_t launch_prep_forward(const Handle &h, const T *X, int nimg, const int
 }
 
 cudaError_t launch_interleave_img(const Handle &h, const float *X, int batch, const double *theta,
-                                  const double *delta)
+                                  const double *delta, const int *skip)
 {
     if (!h.d_qx || h.fan_D > 0.0 || batch < 1 || batch > h.max_batch) return cudaErrorInvalidValue;
     const ViewPrep p = view_prep_args(h, theta, delta);
@@ -830,7 +831,7 @@ cudaError_t launch_interleave_img(const Handle &h, const float *X, int batch, co
     const int n4 = batch & ~3, rem = batch - n4;
     const int ngroups = n4 / 4 + (rem >= 2 ? 1 : 0) + (rem & 1);
     dim3 grid((h.Pp + 31) / 32 + (p.on ? 1 : 0), (h.N + 31) / 32, std::max(1, std::min(2 * h.F * ngroups, 65535)));
-    k_interleave_img<<<grid, 256, prep_smem(p), h.stream>>>(X, h.d_qx, h.d_qt, h.N, h.Pp, h.F, batch, p);
+    k_interleave_img<<<grid, 256, prep_smem(p), h.stream>>>(X, h.d_qx, h.d_qt, h.N, h.Pp, h.F, batch, p, skip);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ctgb.h"
@@ -311,14 +312,24 @@ template <typename T> struct Solver {
     // columns per projection launch: the Krylov block (max_batch), or one in the plain form
     int block() const { return o.plain ? 1 : h.max_batch; }
 
-    // HV[:, j0:j0+cnt) = H(theta) V[:, j0:j0+cnt), in chunks of block() columns
+    // HV[:, j0:j0+cnt) = H(theta) V[:, j0:j0+cnt), in chunks of block() columns; a chunk
+    // of two or more columns reads them interleaved when the handle's forward does
+    // (the same bits; one column reads the pair images, which are as fast there)
     int project(const double *theta, int j0, int cnt, const int *stop)
     {
         if (cnt <= 0) SV_CUDA(launch_view_setup(h, theta, delta, stop));
         for (int j = j0; j < j0 + cnt; j += block()) {
             const int nb = std::min(block(), j0 + cnt - j);
-            // the first layout launch also brings the view table up to date
-            SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop, j == j0 ? theta : nullptr, delta));
+            const double *th = j == j0 ? theta : nullptr;  // the first layout launch also updates the view table
+            if constexpr (std::is_same<T, float>::value) {
+                if (nb >= 2 && h.tune.fwd_layout == 1 && h.d_qx && h.fan_D == 0.0) {
+                    SV_CUDA(launch_interleave_img(h, col(V, n, j), nb, th, delta, stop));
+                    SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
+                                              0, stop, true, nb));
+                    continue;
+                }
+            }
+            SV_CUDA(launch_prep_forward<T>(h, col(V, n, j), nb * h.F, stop, th, delta));
             SV_CUDA(launch_forward<T>(h, col(HV, m, j), nb, h.tune.fwd_kb, h.tune.fwd_split, h.tune.fwd_vw,
                                       h.tune.fwd_stage, stop));
         }

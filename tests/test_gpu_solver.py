@@ -198,6 +198,27 @@ def test_plain_form_takes_the_same_iterates(ct, dtype):
         op.solve(dev(b, dtype), dev(th_nom), plain=2, **kw)
 
 
+@pytest.mark.parametrize("varpro", [0, 1])
+def test_interleaved_block_projections_take_the_same_iterates(ct, varpro):
+    """With the forward on interleaved images, the solver projects its basis in
+    blocks of two or more columns from that layout (the same taps and sums as on
+    the pair images), so a solve takes the same iterates bit for bit."""
+    g, th_nom, th_true, u_true, b, nn = problem(32, 40, seed=6)
+    kw = dict(noise_norm=nn, k_min=5, k_max=15, outer_iters=3, stop_on_convergence=0, varpro=varpro)
+    out = []
+    for layout in (0, 1):
+        op = ct.CTOperator(g.N, g.B, g.V, max_batch=8, dtype=torch.float32)
+        t = op.tuning
+        t[0], t[7], t[11] = max(t[0], 4), 0, layout
+        op.tuning = t
+        out.append(op.solve(dev(b, torch.float32), dev(th_nom), x_true=dev(u_true, torch.float32), **kw))
+        op.close()
+    (x1, th1, st1), (x2, th2, st2) = out
+    assert torch.equal(x1, x2) and torch.equal(th1, th2)
+    assert st1["lambda"] == st2["lambda"] and st1["rre"] == st2["rre"]
+    assert st1["enlarge_steps"] == st2["enlarge_steps"]
+
+
 def test_fp64_solver_with_a_basis_of_100_follows_the_oracle(ct):
     """k_max = 100 (the memory-bounded basis of the large streaming workload):
     above 64 columns the FP64 small algebra (LDL^T, the discrepancy search,
