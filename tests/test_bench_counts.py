@@ -29,3 +29,18 @@ def test_interpolation_step_count_matches_the_dense_matrix():
         nz = A[v] != 0.0                                   # [B][N][N]
         count += int((nz.any(axis=2) if rows else nz.any(axis=1)).sum())
     assert bench.interp_steps_per_image(w) == count
+
+
+def test_launches_per_step_follow_the_launch_shapes():
+    """Kernels per bench step: the forward block's, the sinograms' and J's layouts,
+    J^T's view-table step, the forward kernel(s), the transpose kernel(s), JVP, VJP
+    and the per-view sums; one forward launch per group width the batch of 8 needs,
+    and a combining kernel for a staged forward split over CTAs."""
+    base = [4, 4, 1, 8, 4, 4, 1, 0, 0, 8, 2, 1]
+    assert bench.launches_per_step(base) == 9
+    assert bench.launches_per_step(base[:11] + [0]) == 9      # pair images: the same launches
+    assert bench.launches_per_step([8, 2, 1] + base[3:]) == 9
+    assert bench.launches_per_step([1, 2, 1] + base[3:]) == 9  # 8 groups of 1, one launch
+    staged = [4, 2, 4, 8, 4, 4, 1, 4, 0, 8, 2, 0]
+    assert bench.launches_per_step(staged) == 10             # + the segment combine
+    assert bench.launches_per_step([4, 1, 4, 8, 4, 4, 1, 4, 0, 8, 2, 0]) == 9  # staged, one CTA per ray
